@@ -1,0 +1,229 @@
+/*
+ * hp.h -- fused image-pipeline library for GB300 (sm_103a), C ABI.
+ *
+ * The library runs multi-stage image pipelines (DAGs of pointwise, 2-D stencil,
+ * pyramid down/upsample and histogram stages over 2-D images) on one GPU.  It
+ * keeps the algorithm -- which stages compute what -- separate from the
+ * schedule -- how stages are grouped into kernels and tiled -- as the paper
+ * sets out (Sec. 1; the compute-location and tiling decisions of Sec. 2 and
+ * Sec. 4).  Any valid schedule gives bit-identical results: the per-stage float
+ * expression is part of the algorithm and every kernel evaluates it the same
+ * way.
+ *
+ * Conventions
+ *   - Images are planar [C][H][W], row-major; x is the column (fastest), y the row.
+ *   - hp_buffer strides are in bytes and must be multiples of 16; data pointers
+ *     must be 16-byte aligned.
+ *   - Every stencil, downsample and upsample reads its own producer with a
+ *     clamp-to-edge boundary on that producer's domain:
+ *     P(min(max(x,0),W-1), min(max(y,0),H-1)).
+ *   - Stage ids are dense, assigned in hp_add_stage order; a stage may only read
+ *     pipeline inputs and earlier stages, so id order is a topological order.
+ *   - All functions return an hp_status; on failure hp_last_error() returns a
+ *     message (thread-local, valid until the next call on that thread).  No
+ *     function aborts the process.
+ *
+ * Ownership
+ *   - hp_pipeline objects are created and owned by the library; free them with
+ *     hp_pipeline_destroy.
+ *   - hp_buffer memory is owned by the caller (device memory for hp_realize,
+ *     host memory for hp_realize_host) and must stay valid until the work
+ *     enqueued on the stream has completed.
+ *   - Intermediate images of materialised stages, histogram scratch and TMA
+ *     descriptors are owned by the pipeline; they are allocated on the first
+ *     hp_realize for a given input size and freed by hp_pipeline_destroy.
+ */
+#ifndef HP_H
+#define HP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hp_pipeline hp_pipeline;
+
+typedef enum {
+  HP_OK = 0,
+  HP_ERR_INVALID_ARG = 1,   /* null pointer, bad id, dtype/channel/size mismatch, misalignment */
+  HP_ERR_UNSUPPORTED = 2,   /* a stage or group the kernels cannot run */
+  HP_ERR_SCHEDULE = 3,      /* schedule violates a rule (group shape, shared-memory or thread limit) */
+  HP_ERR_OOM = 4,           /* device allocation of library-owned scratch failed */
+  HP_ERR_CUDA = 5,          /* a CUDA runtime call failed; the message names it */
+  HP_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up (serving loop) */
+  HP_ERR_STATE = 7          /* call out of order (e.g. realize before set_output) */
+} hp_status;
+
+typedef enum { HP_U8 = 0, HP_U16 = 1, HP_F16 = 2, HP_BF16 = 3, HP_F32 = 4, HP_U32 = 5 } hp_dtype;
+
+/* Stage kinds: the operations of the imaging apps of Sec. 6. */
+typedef enum {
+  HP_STENCIL = 0,      /* separable 2-D stencil, per channel:
+                          h(x,y') = sum_i wx[i] * in(clamp(x+i-rx), y'),
+                          out(x,y) = sum_j wy[j] * h(x, clamp(y+j-ry));
+                          rx, ry <= HP_MAX_RADIUS (Sec. 2, Fig. 1 stencil chain) */
+  HP_POINTWISE = 1,    /* hp_op on same-size inputs at the same (x, y) (inlined producers, Sec. 4) */
+  HP_DOWNSAMPLE2 = 2,  /* binomial [1,4,6,4,1]/16 per axis at (2x+i, 2y+j); size ceil(W/2) x ceil(H/2) */
+  HP_UPSAMPLE2 = 3,    /* zero-stuff + [1,4,6,4,1]/8 per axis, coarse index clamped; inputs[1] is a
+                          size reference whose domain the output takes (it is not read) */
+  HP_HISTOGRAM = 4,    /* 256-bin counts of a 1-channel u8 image; output 256 x 1 u32 */
+  HP_CDF_LUT = 5,      /* equalization LUT (256 x 1 u8) from a histogram stage */
+  HP_LUT_APPLY = 6     /* out = lut[in] for a 1-channel u8 image */
+} hp_kind;
+
+/* Point-wise operations (HP_POINTWISE).  The float expression of each is fixed
+ * and shared by every kernel that evaluates it. */
+typedef enum {
+  HP_OP_GRAY = 0,      /* 1 input, 3 ch -> 1 ch: 0.299 R + 0.587 G + 0.114 B, each channel first
+                          multiplied by params[0] (1 for float inputs, 1/65535 for u16) */
+  HP_OP_MUL = 1,       /* a * b, per channel */
+  HP_OP_ADD = 2,       /* a + b */
+  HP_OP_SUB = 3,       /* a - b */
+  HP_OP_HARRIS = 4,    /* (Sxx, Syy, Sxy) -> Sxx*Syy - Sxy^2 - params[0] * (Sxx + Syy)^2 */
+  HP_OP_UNSHARP = 5,   /* (in, blur) -> in + params[0] * (in - blur), per channel */
+  HP_OP_LL_REMAP = 6,  /* 1 ch gray -> K+1 ch: channel k < K is the remap r_k(gray) around
+                          g_k = k/(K-1); channel K is gray itself.
+                          params = {sigma_r, alpha, beta, K} */
+  HP_OP_LL_INTERP = 7, /* (G stack K+1 ch, L stack >= K ch) -> 1 ch: t = G[K]*(K-1),
+                          k0 = min(floor(t), K-2), f = t - k0, (1-f) L[k0] + f L[k0+1].
+                          params = {K} */
+  HP_OP_LL_COLOUR = 8, /* (in 3 ch, gray, out_gray) -> 3 ch: v = in*params[0];
+                          (gray > 0 ? v * out_gray / gray : out_gray) * params[1] */
+  HP_OP_SELECT = 9,    /* 1 input -> 1 ch: channel params[0] */
+  HP_OP_SCALE = 10     /* a * params[0] + params[1], per channel (also dtype conversion) */
+} hp_op;
+
+#define HP_MAX_RADIUS 4
+#define HP_MAX_INPUTS 4
+#define HP_MAX_PARAMS 8
+#define HP_INLINE (-1)
+
+typedef struct {
+  int kind;              /* hp_kind */
+  int op;                /* hp_op for HP_POINTWISE, else ignored */
+  int n_inputs;
+  const int* inputs;     /* stage id >= 0, or -1-k for pipeline input k */
+  int rx, ry;            /* stencil radii */
+  const float* wx;       /* 2*rx+1 taps along x (HP_STENCIL) */
+  const float* wy;       /* 2*ry+1 taps along y (HP_STENCIL) */
+  const float* params;   /* op parameters (see hp_op) */
+  int n_params;
+  int storage;           /* hp_dtype the stage's values are rounded to wherever they are kept */
+  int channels;          /* output channels; must agree with the op's rule */
+  int boundary;          /* 0 = clamp-to-edge (the only boundary supported) */
+} hp_stage_desc;
+
+/* Schedule: the compute location and tiling decisions of Sec. 4.  Every stage
+ * belongs to a fusion group (one kernel per group), or is inlined (HP_INLINE,
+ * point-wise stages only: recomputed inside each consumer group).  A group
+ * computes every member over the tile its output needs, keeping members in
+ * shared memory or registers; only the group's output stage (the one stage read
+ * outside the group, or the pipeline output) is written to memory.  Singleton
+ * groups everywhere is the stage-per-kernel schedule ("compute root", Sec. 2). */
+enum { HP_IMPL_AUTO = 0, HP_IMPL_GENERIC = 1 };
+
+typedef struct {
+  int n_stages;                /* must equal the pipeline's stage count */
+  const int* group_of_stage;   /* per stage: group id in [0, n_groups) or HP_INLINE */
+  int n_groups;
+  const int* tile_w;           /* per group: output tile width  (NULL: defaults) */
+  const int* tile_h;           /* per group: output tile height (NULL: defaults) */
+  const int* threads;          /* per group: threads per block  (NULL: defaults) */
+  const int* serial_y;         /* per group: rows per thread segment (NULL: defaults) */
+  const int* impl;             /* per group: HP_IMPL_AUTO or HP_IMPL_GENERIC (NULL: auto) */
+} hp_schedule;
+
+typedef struct {
+  void* data;                  /* device (hp_realize) or host (hp_realize_host) pointer */
+  int dtype;                   /* hp_dtype */
+  int channels, width, height;
+  long long row_stride_bytes;  /* multiple of 16 */
+  long long plane_stride_bytes;/* multiple of 16 */
+} hp_buffer;
+
+/* Per-group facts after lowering, for tests and the tuner. */
+typedef struct {
+  int kernel;                  /* hp_kernel_id below */
+  int output_stage;
+  int n_members;               /* stages computed in the group (inlined ones included) */
+  int tile_w, tile_h, threads;
+  int grid_x, grid_y, grid_z;
+  int smem_bytes;
+} hp_group_info;
+
+enum {
+  HP_KERNEL_STENCIL_CHAIN = 0, /* fused chain of 5x5 stencils (TMA tile + halo, register sweeps) */
+  HP_KERNEL_UNSHARP = 1,       /* 5x5 stencil + unsharp combine, fused */
+  HP_KERNEL_HARRIS = 2,        /* whole Harris DAG in one kernel */
+  HP_KERNEL_GENERIC = 3,       /* interpreter over any group of stencil/point-wise/pyramid stages */
+  HP_KERNEL_POINTWISE = 4,
+  HP_KERNEL_DOWNSAMPLE = 5,
+  HP_KERNEL_UPSAMPLE = 6,
+  HP_KERNEL_HISTOGRAM = 7,
+  HP_KERNEL_CDF_LUT = 8,
+  HP_KERNEL_LUT_APPLY = 9
+};
+
+/* Create an empty pipeline with n_inputs inputs of the given dtypes and channel
+ * counts.  *out receives the handle. */
+hp_status hp_pipeline_create(hp_pipeline** out, int n_inputs, const int* in_dtypes,
+                             const int* in_channels);
+
+/* Append a stage; *out_stage_id receives its id.  Validates kinds, ops, input
+ * ids, radii, channel rules and parameter counts. */
+hp_status hp_add_stage(hp_pipeline* p, const hp_stage_desc* desc, int* out_stage_id);
+
+/* Mark the pipeline's output stage (exactly one). */
+hp_status hp_set_output(hp_pipeline* p, int stage_id);
+
+/* Set the schedule (copied).  Host-only validation of group structure; shared
+ * memory and thread limits are checked again at realize once sizes are known.
+ * Without a call, every stage is its own group. */
+hp_status hp_schedule_set(hp_pipeline* p, const hp_schedule* s);
+
+/* Enqueue the pipeline on a CUDA stream (cudaStream_t passed as void*, NULL =
+ * legacy default stream).  Inputs and the output are device buffers.  Never
+ * synchronises, except that the first call for a new input size allocates the
+ * pipeline's scratch (cudaMalloc). */
+hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                     const hp_buffer* output, void* stream);
+
+/* Same as hp_realize with HOST buffers: copies the inputs to device staging
+ * owned by the pipeline, runs, copies the output back and synchronises the
+ * stream before returning.  Pinned host memory gives asynchronous copies. */
+hp_status hp_realize_host(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                          const hp_buffer* output, void* stream);
+
+/* Lowering facts of group g for inputs of the given sizes (width/height per
+ * input).  Host only: needs no GPU. */
+hp_status hp_group_info_get(hp_pipeline* p, const int* in_widths, const int* in_heights,
+                            int group, hp_group_info* info);
+
+/* Number of groups of the current schedule. */
+hp_status hp_group_count(hp_pipeline* p, int* n_groups);
+
+/* Bounds inference (host only, needs no GPU): for group g and an output tile
+ * [x0, x0+w) x [y0, y0+h) of the group's output, the rectangle of every stage
+ * the group computes, in that stage's own coordinates, clamped to its domain.
+ * rects receives 4 ints per stage id (x0, y0, x1, y1; x1 == x0 for stages the
+ * group does not compute). */
+hp_status hp_infer_bounds(hp_pipeline* p, const int* in_widths, const int* in_heights,
+                          int group, int x0, int y0, int w, int h, int* rects, int n_rects);
+
+/* Reads and clears the pipeline's device error word (synchronises the device).
+ * *code: 0 = no error; 1 = a bounded TMA/mbarrier wait gave up; 2 = a fused
+ * kernel's read fell outside the tile bounds inference gave it (the read was
+ * skipped).  A non-zero code means the last outputs are not valid. */
+hp_status hp_check_device_error(hp_pipeline* p, int* code);
+
+hp_status hp_pipeline_destroy(hp_pipeline* p);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* hp_last_error(void);
+
+/* Kernel launches this library has issued since the process started. */
+unsigned long long hp_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HP_H */

@@ -1,0 +1,191 @@
+// Internal structures shared by the host runtime (pipeline.cpp) and the CUDA
+// kernels.  Plain C++ structs only: they are passed by value as kernel
+// parameters.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/hp.h"
+
+#if defined(__CUDACC__)
+#define HPHD __host__ __device__ __forceinline__
+#else
+#define HPHD inline
+#endif
+
+namespace hp {
+
+// A planar [C][H][W] image in device memory.  Strides in bytes.
+struct ImgView {
+  void* data;
+  int dtype;
+  int c, w, h;
+  int pad_;
+  long long rs, ps;
+};
+
+struct Rect {
+  int x0, y0, x1, y1;  // half-open; empty when x1 <= x0 or y1 <= y0
+};
+
+HPHD int imin(int a, int b) { return a < b ? a : b; }
+HPHD int imax(int a, int b) { return a > b ? a : b; }
+HPHD int iclamp(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+HPHD int floordiv2(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+HPHD int ceildiv2(int v) { return -floordiv2(-v); }
+
+// ---------------------------------------------------------------------------
+// Group plan for the generic fused-group kernel (and the host bounds
+// inference, which runs the same rect propagation).
+// ---------------------------------------------------------------------------
+constexpr int kMaxGNodes = 48;
+constexpr int kMaxGExt = 8;
+constexpr int kMaxGWeights = 512;
+constexpr int kMaxGParams = 192;
+
+struct GNode {
+  int kind, op, channels, storage;
+  int n_in;
+  int in[HP_MAX_INPUTS];  // >= 0: node index inside the group; < 0: -1-e, external e
+  int rx, ry;
+  int w_off;              // wx (2rx+1) then wy (2ry+1) in GPlan::weights
+  int p_off, n_params;    // in GPlan::params
+  int dom_w, dom_h;
+  int smem_off;           // float offset of this node's tile (channels * pitch * rows)
+  int pitch, rows;        // allocation bounds of the tile
+};
+
+struct GPlan {
+  int n_nodes;            // the output node is n_nodes - 1
+  int n_ext;
+  int tile_w, tile_h, tiles_x, tiles_y;
+  int smem_floats;
+  int pad_;
+  int* err;               // device error word: set when a read falls outside its tile
+  GNode nodes[kMaxGNodes];
+  ImgView ext[kMaxGExt];
+  ImgView out;
+  float weights[kMaxGWeights];
+  float params[kMaxGParams];
+};
+
+// Footprint of consumer `kind` (reading input slot `slot`) over its rect,
+// expressed in the producer's coordinates, before clamping.
+HPHD Rect footprint(int kind, int slot, int rx, int ry, Rect r) {
+  Rect f = r;
+  if (kind == HP_STENCIL) {
+    f.x0 = r.x0 - rx; f.x1 = r.x1 + rx; f.y0 = r.y0 - ry; f.y1 = r.y1 + ry;
+  } else if (kind == HP_DOWNSAMPLE2) {
+    f.x0 = 2 * r.x0 - 2; f.x1 = 2 * r.x1 + 1; f.y0 = 2 * r.y0 - 2; f.y1 = 2 * r.y1 + 1;
+  } else if (kind == HP_UPSAMPLE2) {
+    if (slot == 1) { f.x0 = f.x1 = 0; f.y0 = f.y1 = 0; return f; }  // size reference: not read
+    f.x0 = ceildiv2(r.x0 - 2); f.x1 = floordiv2(r.x1 + 1) + 1;
+    f.y0 = ceildiv2(r.y0 - 2); f.y1 = floordiv2(r.y1 + 1) + 1;
+  }
+  return f;
+}
+
+HPHD bool rect_empty(Rect r) { return r.x1 <= r.x0 || r.y1 <= r.y0; }
+
+// Rect of every node for the output tile at (tx0, ty0): the output node gets
+// the tile clipped to its domain; each producer gets the union of its
+// consumers' footprints clipped to its own domain (reverse topological order).
+HPHD void infer_rects(const GPlan& g, int tx0, int ty0, Rect* rects) {
+  for (int n = 0; n < g.n_nodes; ++n) rects[n] = Rect{0, 0, 0, 0};
+  const GNode& o = g.nodes[g.n_nodes - 1];
+  rects[g.n_nodes - 1] = Rect{tx0, ty0, imin(tx0 + g.tile_w, o.dom_w), imin(ty0 + g.tile_h, o.dom_h)};
+  for (int n = g.n_nodes - 1; n >= 0; --n) {
+    Rect r = rects[n];
+    if (rect_empty(r)) continue;
+    const GNode& nd = g.nodes[n];
+    for (int s = 0; s < nd.n_in; ++s) {
+      int m = nd.in[s];
+      if (m < 0) continue;
+      Rect f = footprint(nd.kind, s, nd.rx, nd.ry, r);
+      if (rect_empty(f)) continue;
+      const GNode& p = g.nodes[m];
+      f.x0 = imax(f.x0, 0); f.y0 = imax(f.y0, 0);
+      f.x1 = imin(f.x1, p.dom_w); f.y1 = imin(f.y1, p.dom_h);
+      if (rect_empty(f)) continue;
+      Rect& q = rects[m];
+      if (rect_empty(q)) {
+        q = f;
+      } else {
+        q.x0 = imin(q.x0, f.x0); q.y0 = imin(q.y0, f.y0);
+        q.x1 = imax(q.x1, f.x1); q.y1 = imax(q.y1, f.y1);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parameters of the specialised kernels.
+// ---------------------------------------------------------------------------
+constexpr int kChainMax = 32;
+
+struct ChainArgs {
+  ImgView in, out;
+  int depth;
+  int tile_w, tile_h, tiles_x, tiles_y;
+  int threads, seg;
+  int storage[kChainMax];
+  float w[kChainMax][10];  // per stage: wx[5] then wy[5]
+  int epilogue;            // 0: none; 1: unsharp out = in + amount*(in - chain(in))
+  float amount;
+  int* err;                // device error word (bounded waits)
+};
+
+struct PointwiseArgs {
+  int op, n_in, channels, storage;
+  ImgView in[HP_MAX_INPUTS];
+  ImgView out;
+  float params[HP_MAX_PARAMS];
+};
+
+struct ResampleArgs {  // downsample / upsample, per channel
+  ImgView in, out;
+  int storage;
+};
+
+struct HarrisArgs {
+  ImgView in, out;          // in: 3 ch; out: 1 ch
+  float gray_scale, k;
+  int storage_gray, storage_grad, storage_prod, storage_sum, storage_out;
+  int tile_w, tile_h, tiles_x, tiles_y, threads;
+  int* err;
+};
+
+struct HistArgs {
+  ImgView in;               // 1 ch u8
+  unsigned int* hist;       // 256 counters
+  int blocks;
+};
+
+struct LutArgs {
+  const unsigned int* hist;
+  unsigned char* lut;       // 256 entries
+  ImgView lut_view;         // where the LUT stage is materialised (256x1 u8)
+};
+
+struct LutApplyArgs {
+  ImgView in, out;          // u8, 1 ch
+  const unsigned char* lut;
+};
+
+// Launchers (defined in the .cu files).  Return a cudaError_t as int.
+int launch_chain(const ChainArgs& a, int smem_bytes, void* stream);
+int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype);
+int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream);
+int launch_pointwise(const PointwiseArgs& a, void* stream);
+int launch_downsample(const ResampleArgs& a, void* stream);
+int launch_upsample(const ResampleArgs& a, void* stream);
+int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream);
+int harris_smem_bytes(int tile_w, int tile_h);
+int launch_hist(const HistArgs& a, void* stream);
+int launch_cdf_lut(const LutArgs& a, void* stream);
+int launch_lut_apply(const LutApplyArgs& a, void* stream);
+const char* cuda_error_string(int e);
+
+extern unsigned long long g_launches;
+
+}  // namespace hp

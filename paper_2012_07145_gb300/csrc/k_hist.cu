@@ -1,0 +1,179 @@
+// Histogram equalization kernels: a 256-bin histogram of a u8 image, the CDF
+// scan and equalization lookup table, and the table lookup.
+//
+// Histogram: the parallel reduction the paper's histogram-equalize discussion
+// calls for (atomics expose the data parallelism, Sec. 6.5 and Sec. 8).  Each
+// warp keeps a private sub-histogram in shared memory; within a warp, lanes
+// holding the same value are combined with __match_any_sync so one lane adds
+// the group's count; the CTA's sub-histograms are summed and added to the
+// global counters with one atomic per bin.  All counts are exact integers.
+#include <cuda_runtime.h>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+namespace {
+
+constexpr int kHistThreads = 512;
+constexpr int kHistWarps = kHistThreads / 32;
+
+__device__ __forceinline__ void count_byte(unsigned int* wh, unsigned int v, unsigned int active) {
+  unsigned int peers = __match_any_sync(active, v);
+  int leader = __ffs(peers) - 1;
+  if ((int)(threadIdx.x & 31) == leader) atomicAdd(&wh[v], (unsigned int)__popc(peers));
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigned int* __restrict__ hist) {
+  __shared__ unsigned int sh[kHistWarps][256];
+  for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  unsigned int* wh = sh[threadIdx.x >> 5];
+  const int chunks_per_row = (in.w + 15) >> 4;
+  const long long n_chunks = (long long)chunks_per_row * in.h;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // every lane of a warp runs the same number of iterations (warp-uniform
+  // bound), so the full-warp match below is always legal
+  const long long warp_base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  for (long long base = warp_base; base < n_chunks; base += stride) {
+    long long ch = base + (threadIdx.x & 31);
+    bool valid = ch < n_chunks;
+    int y = valid ? (int)(ch / chunks_per_row) : 0;
+    int x0 = valid ? (int)(ch - (long long)y * chunks_per_row) << 4 : 0;
+    const unsigned char* row = (const unsigned char*)in.data + (long long)y * in.rs;
+    unsigned int words[4] = {0, 0, 0, 0};
+    int nbytes = valid ? min(16, in.w - x0) : 0;
+    if (nbytes == 16) {
+      uint4 q = *reinterpret_cast<const uint4*>(row + x0);
+      words[0] = q.x; words[1] = q.y; words[2] = q.z; words[3] = q.w;
+    } else {
+      for (int b = 0; b < nbytes; ++b) words[b >> 2] |= (unsigned int)row[x0 + b] << (8 * (b & 3));
+    }
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      unsigned int active = __ballot_sync(0xffffffffu, b < nbytes);
+      if (b < nbytes) count_byte(wh, (words[b >> 2] >> (8 * (b & 3))) & 0xffu, active);
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+    unsigned int s = 0;
+    for (int w = 0; w < kHistWarps; ++w) s += sh[w][v];
+    if (s) atomicAdd(&hist[v], s);
+  }
+}
+
+// One CTA of 256 threads: inclusive scan of the counts, then the table
+//   N == cmin: LUT[v] = v;  cdf[v] < cmin: 0;
+//   else ((cdf[v]-cmin)*510 + (N-cmin)) / (2*(N-cmin)) in 64-bit integers.
+__global__ void __launch_bounds__(256) k_cdf_lut(const unsigned int* __restrict__ hist, unsigned char* __restrict__ lut) {
+  __shared__ unsigned int warp_tot[8];
+  __shared__ unsigned int s_cmin, s_first;
+  const int v = threadIdx.x;
+  const int lane = v & 31, w = v >> 5;
+  unsigned int h = hist[v];
+  unsigned int c = h;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int t = __shfl_up_sync(0xffffffffu, c, o);
+    if (lane >= o) c += t;
+  }
+  if (lane == 31) warp_tot[w] = c;
+  if (v == 0) s_first = 256;
+  __syncthreads();
+  unsigned int off = 0;
+  for (int i = 0; i < w; ++i) off += warp_tot[i];
+  c += off;
+  if (h > 0) atomicMin(&s_first, (unsigned int)v);
+  __syncthreads();
+  if (v == (int)s_first) s_cmin = c;
+  if (s_first == 256 && v == 0) s_cmin = 0;
+  __syncthreads();
+  unsigned long long n = 0;
+  for (int i = 0; i < 8; ++i) n += warp_tot[i];
+  unsigned long long cmin = s_cmin;
+  unsigned int out;
+  if (n == cmin) {
+    out = (unsigned int)v;
+  } else if (c < cmin) {
+    out = 0;
+  } else {
+    unsigned long long den = n - cmin;
+    out = (unsigned int)((((unsigned long long)c - cmin) * 510ull + den) / (2ull * den));
+  }
+  lut[v] = (unsigned char)out;
+}
+
+__global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out,
+                                                   const unsigned char* __restrict__ lut) {
+  __shared__ unsigned char t[256];
+  if (threadIdx.x < 256) t[threadIdx.x] = lut[threadIdx.x];
+  __syncthreads();
+  const int chunks_per_row = (in.w + 15) >> 4;
+  const long long n_chunks = (long long)chunks_per_row * in.h;
+  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks;
+       ch += (long long)gridDim.x * blockDim.x) {
+    int y = (int)(ch / chunks_per_row);
+    int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+    const unsigned char* src = (const unsigned char*)in.data + (long long)y * in.rs + x0;
+    unsigned char* dst = (unsigned char*)out.data + (long long)y * out.rs + x0;
+    int nb = min(16, in.w - x0);
+    if (nb == 16) {
+      uint4 q = *reinterpret_cast<const uint4*>(src);
+      unsigned int wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        unsigned int a = wv[i];
+        wv[i] = (unsigned int)t[a & 0xff] | ((unsigned int)t[(a >> 8) & 0xff] << 8) |
+                ((unsigned int)t[(a >> 16) & 0xff] << 16) | ((unsigned int)t[a >> 24] << 24);
+      }
+      *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    } else {
+      for (int b = 0; b < nb; ++b) dst[b] = t[src[b]];
+    }
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace
+
+int launch_hist(const HistArgs& a, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  int e = (int)cudaMemsetAsync(a.hist, 0, 256 * sizeof(unsigned int), s);
+  if (e) return e;
+  long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
+  long long want = (chunks + kHistThreads - 1) / kHistThreads;
+  int blocks = (int)(want < 2LL * sm_count() ? want : 2LL * sm_count());
+  if (blocks < 1) blocks = 1;
+  k_hist<<<blocks, kHistThreads, 0, s>>>(a.in, a.hist);
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
+int launch_cdf_lut(const LutArgs& a, void* stream) {
+  k_cdf_lut<<<1, 256, 0, (cudaStream_t)stream>>>(a.hist, a.lut);
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
+int launch_lut_apply(const LutApplyArgs& a, void* stream) {
+  long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
+  long long want = (chunks + 255) / 256;
+  int blocks = (int)(want < 8LL * sm_count() ? want : 8LL * sm_count());
+  if (blocks < 1) blocks = 1;
+  k_lut_apply<<<blocks, 256, 0, (cudaStream_t)stream>>>(a.in, a.out, a.lut);
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace hp

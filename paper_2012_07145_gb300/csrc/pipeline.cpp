@@ -1,0 +1,994 @@
+// Pipeline IR, schedule validation, halo bounds inference, lowering of fusion
+// groups onto kernels, scratch management and the C ABI of include/hp.h.
+//
+// The algorithm (stages and their footprints) is fixed independently of the
+// schedule (Sec. 1).  A schedule assigns every stage a compute location: its
+// own kernel ("root"), a fusion group computed per output tile in shared memory
+// and registers, or inline (Sec. 2 "Fusion Options", Sec. 4 decision 1), plus
+// the tile and thread shape of each group (Sec. 2 "Tiling", Sec. 4.1-4.3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+unsigned long long g_launches = 0;
+
+namespace {
+
+thread_local std::string t_err;
+
+hp_status fail(hp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+hp_status cuda_fail(int e, const char* what) {
+  return fail(HP_ERR_CUDA, "%s: %s", what, cuda_error_string(e));
+}
+
+int dtype_bytes(int d) {
+  switch (d) {
+    case HP_U8: return 1;
+    case HP_U16: case HP_F16: case HP_BF16: return 2;
+    default: return 4;
+  }
+}
+
+bool valid_dtype(int d) { return d >= HP_U8 && d <= HP_U32; }
+
+long long round16(long long v) { return (v + 15) / 16 * 16; }
+
+constexpr int kSmemLimit = 227 * 1024;
+
+struct Stage {
+  int kind = 0, op = 0, channels = 1, storage = HP_F32;
+  std::vector<int> inputs;
+  int rx = 0, ry = 0;
+  std::vector<float> wx, wy, params;
+};
+
+struct Dom {
+  int w = 0, h = 0;
+};
+
+// One fusion group after lowering for a given set of input sizes.
+struct GroupPlan {
+  int kernel = HP_KERNEL_GENERIC;
+  int output = -1;
+  std::vector<int> members;  // stage ids (inlined copies included), ascending
+  int tile_w = 0, tile_h = 0, threads = 0, seg = 0;
+  int grid_x = 1, grid_y = 1, grid_z = 1;
+  int smem = 0;
+  // kernel-specific
+  ChainArgs chain{};
+  HarrisArgs harris{};
+  std::unique_ptr<GPlan> gplan;
+  std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
+};
+
+struct Scratch {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Plan {
+  std::vector<Dom> dom;          // per stage
+  std::vector<Dom> in_dom;       // per input
+  std::vector<GroupPlan> groups; // in execution order
+  std::map<int, Scratch> bufs;   // exported stage -> device buffer
+  std::vector<Scratch> staging;  // hp_realize_host device copies (inputs..., output)
+  bool allocated = false;
+};
+
+}  // namespace
+}  // namespace hp
+
+struct hp_pipeline {
+  std::vector<int> in_dtypes, in_channels;
+  std::vector<hp::Stage> stages;
+  int output = -1;
+  bool has_schedule = false;
+  std::vector<int> group_of;              // per stage
+  int n_groups = 0;
+  std::vector<int> tile_w, tile_h, threads, serial_y, impl;
+  std::map<std::vector<int>, std::unique_ptr<hp::Plan>> plans;
+  int* d_err = nullptr;
+};
+
+namespace hp {
+namespace {
+
+int stage_channels_of_ref(const hp_pipeline* p, int ref) {
+  return ref < 0 ? p->in_channels[-1 - ref] : p->stages[ref].channels;
+}
+
+int stage_dtype_of_ref(const hp_pipeline* p, int ref) {
+  return ref < 0 ? p->in_dtypes[-1 - ref] : p->stages[ref].storage;
+}
+
+hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
+  int nst = (int)p->stages.size();
+  if (d->n_inputs < 1 || d->n_inputs > HP_MAX_INPUTS || !d->inputs)
+    return fail(HP_ERR_INVALID_ARG, "stage needs 1..%d inputs", HP_MAX_INPUTS);
+  for (int i = 0; i < d->n_inputs; ++i) {
+    int r = d->inputs[i];
+    if (r >= nst || (r < 0 && -1 - r >= (int)p->in_dtypes.size()))
+      return fail(HP_ERR_INVALID_ARG, "input %d refers to unknown stage/input %d", i, r);
+  }
+  if (!valid_dtype(d->storage)) return fail(HP_ERR_INVALID_ARG, "bad storage dtype %d", d->storage);
+  if (d->boundary != 0) return fail(HP_ERR_UNSUPPORTED, "only clamp-to-edge boundaries are supported");
+  if (d->n_params < 0 || d->n_params > HP_MAX_PARAMS || (d->n_params > 0 && !d->params))
+    return fail(HP_ERR_INVALID_ARG, "bad params");
+  int c0 = stage_channels_of_ref(p, d->inputs[0]);
+  auto need = [&](int n, int ch) -> hp_status {
+    if (d->n_inputs != n) return fail(HP_ERR_INVALID_ARG, "kind %d op %d takes %d inputs", d->kind, d->op, n);
+    if (d->channels != ch)
+      return fail(HP_ERR_INVALID_ARG, "kind %d op %d produces %d channels, desc says %d", d->kind, d->op, ch,
+                  d->channels);
+    return HP_OK;
+  };
+  hp_status s;
+  switch (d->kind) {
+    case HP_STENCIL:
+      if ((s = need(1, c0))) return s;
+      if (d->rx < 0 || d->ry < 0 || d->rx > HP_MAX_RADIUS || d->ry > HP_MAX_RADIUS || !d->wx || !d->wy)
+        return fail(HP_ERR_INVALID_ARG, "stencil radii must be in [0,%d] with taps", HP_MAX_RADIUS);
+      if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
+      return HP_OK;
+    case HP_DOWNSAMPLE2:
+      if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
+      return need(1, c0);
+    case HP_UPSAMPLE2:
+      if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
+      return need(2, c0);
+    case HP_HISTOGRAM:
+      if ((s = need(1, 1))) return s;
+      if (c0 != 1 || stage_dtype_of_ref(p, d->inputs[0]) != HP_U8)
+        return fail(HP_ERR_INVALID_ARG, "histogram input must be a 1-channel u8 image");
+      if (d->storage != HP_U32) return fail(HP_ERR_INVALID_ARG, "histogram storage must be u32");
+      return HP_OK;
+    case HP_CDF_LUT:
+      if ((s = need(1, 1))) return s;
+      if (d->inputs[0] < 0 || p->stages[d->inputs[0]].kind != HP_HISTOGRAM)
+        return fail(HP_ERR_INVALID_ARG, "cdf_lut input must be a histogram stage");
+      if (d->storage != HP_U8) return fail(HP_ERR_INVALID_ARG, "lut storage must be u8");
+      return HP_OK;
+    case HP_LUT_APPLY:
+      if ((s = need(2, 1))) return s;
+      if (c0 != 1 || stage_dtype_of_ref(p, d->inputs[0]) != HP_U8)
+        return fail(HP_ERR_INVALID_ARG, "lut_apply image must be a 1-channel u8 image");
+      if (d->inputs[1] < 0 || p->stages[d->inputs[1]].kind != HP_CDF_LUT)
+        return fail(HP_ERR_INVALID_ARG, "lut_apply second input must be a cdf_lut stage");
+      if (d->storage != HP_U8) return fail(HP_ERR_INVALID_ARG, "lut_apply storage must be u8");
+      return HP_OK;
+    case HP_POINTWISE:
+      break;
+    default:
+      return fail(HP_ERR_UNSUPPORTED, "unknown stage kind %d", d->kind);
+  }
+  if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
+  auto chan = [&](int i) { return stage_channels_of_ref(p, d->inputs[i]); };
+  auto nparams = [&](int n) -> hp_status {
+    if (d->n_params < n) return fail(HP_ERR_INVALID_ARG, "op %d needs %d params", d->op, n);
+    return HP_OK;
+  };
+  switch (d->op) {
+    case HP_OP_GRAY:
+      if ((s = need(1, 1)) || (s = nparams(1))) return s;
+      if (c0 != 3) return fail(HP_ERR_INVALID_ARG, "gray needs a 3-channel input");
+      return HP_OK;
+    case HP_OP_MUL: case HP_OP_ADD: case HP_OP_SUB:
+      if ((s = need(2, c0))) return s;
+      if (chan(1) != c0) return fail(HP_ERR_INVALID_ARG, "binary op inputs differ in channels");
+      return HP_OK;
+    case HP_OP_HARRIS:
+      if ((s = need(3, 1)) || (s = nparams(1))) return s;
+      if (chan(0) != 1 || chan(1) != 1 || chan(2) != 1) return fail(HP_ERR_INVALID_ARG, "harris inputs are 1-channel");
+      return HP_OK;
+    case HP_OP_UNSHARP:
+      if ((s = need(2, c0)) || (s = nparams(1))) return s;
+      if (chan(1) != c0) return fail(HP_ERR_INVALID_ARG, "unsharp inputs differ in channels");
+      return HP_OK;
+    case HP_OP_LL_REMAP: {
+      if ((s = nparams(4))) return s;
+      int K = (int)d->params[3];
+      if (K < 2 || K > 16 || (float)K != d->params[3]) return fail(HP_ERR_INVALID_ARG, "remap K must be 2..16");
+      if ((s = need(1, K + 1))) return s;
+      if (c0 != 1) return fail(HP_ERR_INVALID_ARG, "remap input is 1-channel");
+      if (!(d->params[0] > 0.0f)) return fail(HP_ERR_INVALID_ARG, "sigma_r must be > 0");
+      return HP_OK;
+    }
+    case HP_OP_LL_INTERP: {
+      if ((s = need(2, 1)) || (s = nparams(1))) return s;
+      int K = (int)d->params[0];
+      if (K < 2 || chan(0) < K + 1 || chan(1) < K)
+        return fail(HP_ERR_INVALID_ARG, "interp needs a K+1-channel G stack and a K-channel L stack");
+      return HP_OK;
+    }
+    case HP_OP_LL_COLOUR:
+      if ((s = need(3, 3)) || (s = nparams(2))) return s;
+      if (chan(0) != 3 || chan(1) != 1 || chan(2) != 1) return fail(HP_ERR_INVALID_ARG, "colour inputs: 3, 1, 1 ch");
+      return HP_OK;
+    case HP_OP_SELECT: {
+      if ((s = need(1, 1)) || (s = nparams(1))) return s;
+      int c = (int)d->params[0];
+      if (c < 0 || c >= c0) return fail(HP_ERR_INVALID_ARG, "select channel out of range");
+      return HP_OK;
+    }
+    case HP_OP_SCALE:
+      if ((s = need(1, c0)) || (s = nparams(2))) return s;
+      return HP_OK;
+    default:
+      return fail(HP_ERR_UNSUPPORTED, "unknown point-wise op %d", d->op);
+  }
+}
+
+// Domains of every stage for the given input sizes.
+hp_status infer_domains(const hp_pipeline* p, const std::vector<Dom>& in_dom, std::vector<Dom>& dom) {
+  dom.assign(p->stages.size(), Dom{});
+  auto of = [&](int ref) { return ref < 0 ? in_dom[-1 - ref] : dom[ref]; };
+  for (size_t s = 0; s < p->stages.size(); ++s) {
+    const Stage& st = p->stages[s];
+    Dom d0 = of(st.inputs[0]);
+    switch (st.kind) {
+      case HP_DOWNSAMPLE2: dom[s] = Dom{(d0.w + 1) / 2, (d0.h + 1) / 2}; break;
+      case HP_UPSAMPLE2: {
+        Dom r = of(st.inputs[1]);
+        if ((r.w + 1) / 2 != d0.w || (r.h + 1) / 2 != d0.h)
+          return fail(HP_ERR_INVALID_ARG, "stage %zu: upsample of %dx%d cannot produce %dx%d", s, d0.w, d0.h, r.w, r.h);
+        dom[s] = r;
+        break;
+      }
+      case HP_HISTOGRAM: case HP_CDF_LUT: dom[s] = Dom{256, 1}; break;
+      default: {
+        dom[s] = d0;
+        int first = st.kind == HP_LUT_APPLY ? 1 : (int)st.inputs.size();
+        for (int i = 1; i < first; ++i) {
+          Dom di = of(st.inputs[i]);
+          if (di.w != d0.w || di.h != d0.h)
+            return fail(HP_ERR_INVALID_ARG, "stage %zu: inputs differ in size (%dx%d vs %dx%d)", s, d0.w, d0.h, di.w, di.h);
+        }
+      }
+    }
+    if (dom[s].w < 1 || dom[s].h < 1) return fail(HP_ERR_INVALID_ARG, "stage %zu has an empty domain", s);
+  }
+  return HP_OK;
+}
+
+// Members of each group: assigned stages plus the inline closure.
+struct GroupShape {
+  std::vector<int> members;
+  int output = -1;
+};
+
+hp_status group_shapes(const hp_pipeline* p, std::vector<GroupShape>& shapes) {
+  int ns = (int)p->stages.size();
+  int ng = p->n_groups;
+  std::vector<std::vector<char>> in_group(ng, std::vector<char>(ns, 0));
+  for (int s = 0; s < ns; ++s)
+    if (p->group_of[s] >= 0) in_group[p->group_of[s]][s] = 1;
+  // inline closure: walk producers of members through inlined stages
+  for (int g = 0; g < ng; ++g) {
+    for (int s = ns - 1; s >= 0; --s) {
+      if (!in_group[g][s]) continue;
+      for (int r : p->stages[s].inputs)
+        if (r >= 0 && p->group_of[r] == HP_INLINE) in_group[g][r] = 1;
+    }
+  }
+  // exported: stages read by a stage outside the group (or the output)
+  shapes.assign(ng, GroupShape{});
+  for (int g = 0; g < ng; ++g) {
+    std::vector<int> exported;
+    for (int s = 0; s < ns; ++s) {
+      if (!in_group[g][s]) continue;
+      shapes[g].members.push_back(s);
+      if (p->group_of[s] != g) continue;  // inlined copies are never exported
+      bool exp = s == p->output;
+      for (int c = 0; c < ns && !exp; ++c) {
+        bool reads = false;
+        for (int r : p->stages[c].inputs) reads |= r == s;
+        if (!reads) continue;
+        if (p->group_of[c] >= 0 && p->group_of[c] != g) exp = true;
+        if (p->group_of[c] == HP_INLINE) {
+          for (int h = 0; h < ng; ++h)
+            if (h != g && in_group[h][c]) exp = true;
+        }
+      }
+      if (exp) exported.push_back(s);
+    }
+    if (shapes[g].members.empty()) return fail(HP_ERR_SCHEDULE, "group %d is empty", g);
+    if (exported.size() != 1)
+      return fail(HP_ERR_SCHEDULE, "group %d must have exactly one stage read outside it (has %zu)", g,
+                  exported.size());
+    int last_assigned = -1;
+    for (int s : shapes[g].members)
+      if (p->group_of[s] == g) last_assigned = s;
+    if (exported[0] != last_assigned)
+      return fail(HP_ERR_SCHEDULE, "group %d: its output stage %d must be its last member", g, exported[0]);
+    shapes[g].output = exported[0];
+    // inlined stages read after the output would be dead; nothing else to check
+  }
+  return HP_OK;
+}
+
+bool is_r2_stencil(const Stage& s) { return s.kind == HP_STENCIL && s.rx == 2 && s.ry == 2; }
+
+// Picks the kernel of a group from its shape.
+int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
+  const auto& m = gs.members;
+  if (m.size() == 1) {
+    const Stage& s = p->stages[m[0]];
+    switch (s.kind) {
+      case HP_STENCIL: return is_r2_stencil(s) && impl != HP_IMPL_GENERIC ? HP_KERNEL_STENCIL_CHAIN : HP_KERNEL_GENERIC;
+      case HP_POINTWISE: return HP_KERNEL_POINTWISE;
+      case HP_DOWNSAMPLE2: return HP_KERNEL_DOWNSAMPLE;
+      case HP_UPSAMPLE2: return HP_KERNEL_UPSAMPLE;
+      case HP_HISTOGRAM: return HP_KERNEL_HISTOGRAM;
+      case HP_CDF_LUT: return HP_KERNEL_CDF_LUT;
+      case HP_LUT_APPLY: return HP_KERNEL_LUT_APPLY;
+    }
+  }
+  for (int s : m) {
+    int k = p->stages[s].kind;
+    if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY) return -1;
+  }
+  if (impl == HP_IMPL_GENERIC) return HP_KERNEL_GENERIC;
+  // linear chain of 5x5 stencils
+  bool chain = (int)m.size() <= kChainMax;
+  for (size_t i = 0; i < m.size() && chain; ++i) {
+    const Stage& s = p->stages[m[i]];
+    chain = is_r2_stencil(s) && (i == 0 ? (s.inputs[0] < 0 || std::find(m.begin(), m.end(), s.inputs[0]) == m.end())
+                                       : s.inputs[0] == m[i - 1]);
+  }
+  if (chain) return HP_KERNEL_STENCIL_CHAIN;
+  // 5x5 stencil + unsharp combine with the stencil's own input
+  if (m.size() == 2) {
+    const Stage& a = p->stages[m[0]];
+    const Stage& b = p->stages[m[1]];
+    if (is_r2_stencil(a) && b.kind == HP_POINTWISE && b.op == HP_OP_UNSHARP && b.inputs[1] == m[0] &&
+        b.inputs[0] == a.inputs[0] && a.inputs[0] != m[0])
+      return HP_KERNEL_UNSHARP;
+  }
+  return HP_KERNEL_GENERIC;
+}
+
+ImgView view_of(const hp_buffer& b) {
+  ImgView v{};
+  v.data = b.data;
+  v.dtype = b.dtype;
+  v.c = b.channels;
+  v.w = b.width;
+  v.h = b.height;
+  v.rs = b.row_stride_bytes;
+  v.ps = b.plane_stride_bytes;
+  return v;
+}
+
+ImgView scratch_view(const Stage& s, Dom d, void* ptr) {
+  ImgView v{};
+  v.data = ptr;
+  v.dtype = s.storage;
+  v.c = s.channels;
+  v.w = d.w;
+  v.h = d.h;
+  v.rs = round16((long long)d.w * dtype_bytes(s.storage));
+  v.ps = round16(v.rs * d.h);
+  return v;
+}
+
+size_t scratch_bytes(const Stage& s, Dom d) {
+  ImgView v = scratch_view(s, d, nullptr);
+  return (size_t)(v.ps * v.c);
+}
+
+int pick(const std::vector<int>& v, int g, int dflt) {
+  return g < (int)v.size() && v[g] > 0 ? v[g] : dflt;
+}
+
+// Builds the generic plan (GPlan) of a group: nodes in member order, the
+// output node last, external inputs listed once.
+hp_status build_gplan(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  auto g = std::make_unique<GPlan>();
+  memset(g.get(), 0, sizeof(GPlan));
+  if ((int)gp.members.size() > kMaxGNodes) return fail(HP_ERR_SCHEDULE, "group has more than %d stages", kMaxGNodes);
+  std::map<int, int> node_of;
+  for (size_t i = 0; i < gp.members.size(); ++i) node_of[gp.members[i]] = (int)i;
+  g->n_nodes = (int)gp.members.size();
+  int wpos = 0, ppos = 0;
+  for (size_t i = 0; i < gp.members.size(); ++i) {
+    const Stage& s = p->stages[gp.members[i]];
+    GNode& n = g->nodes[i];
+    n.kind = s.kind; n.op = s.op; n.channels = s.channels; n.storage = s.storage;
+    n.n_in = (int)s.inputs.size();
+    for (int k = 0; k < n.n_in; ++k) {
+      int r = s.inputs[k];
+      auto it = node_of.find(r);
+      if (r >= 0 && it != node_of.end()) {
+        n.in[k] = it->second;
+      } else {
+        auto e = std::find(gp.ext_refs.begin(), gp.ext_refs.end(), r);
+        int ei = (int)(e - gp.ext_refs.begin());
+        if (e == gp.ext_refs.end()) {
+          if ((int)gp.ext_refs.size() >= kMaxGExt) return fail(HP_ERR_SCHEDULE, "group reads more than %d buffers", kMaxGExt);
+          gp.ext_refs.push_back(r);
+        }
+        n.in[k] = -1 - ei;
+      }
+    }
+    n.rx = s.rx; n.ry = s.ry;
+    n.w_off = wpos;
+    if (s.kind == HP_STENCIL) {
+      if (wpos + (int)s.wx.size() + (int)s.wy.size() > kMaxGWeights) return fail(HP_ERR_SCHEDULE, "too many taps");
+      for (float w : s.wx) g->weights[wpos++] = w;
+      for (float w : s.wy) g->weights[wpos++] = w;
+    }
+    n.p_off = ppos;
+    n.n_params = (int)s.params.size();
+    if (ppos + n.n_params > kMaxGParams) return fail(HP_ERR_SCHEDULE, "too many params");
+    for (float v : s.params) g->params[ppos++] = v;
+    n.dom_w = plan.dom[gp.members[i]].w;
+    n.dom_h = plan.dom[gp.members[i]].h;
+  }
+  g->n_ext = (int)gp.ext_refs.size();
+  g->tile_w = gp.tile_w;
+  g->tile_h = gp.tile_h;
+  Dom od = plan.dom[gp.output];
+  g->tiles_x = (od.w + gp.tile_w - 1) / gp.tile_w;
+  g->tiles_y = (od.h + gp.tile_h - 1) / gp.tile_h;
+  // shared-memory bounds: the largest rect of each node over all tiles
+  std::vector<int> maxw(g->n_nodes, 0), maxh(g->n_nodes, 0);
+  std::vector<Rect> rects(g->n_nodes);
+  for (int ty = 0; ty < g->tiles_y; ++ty)
+    for (int tx = 0; tx < g->tiles_x; ++tx) {
+      infer_rects(*g, tx * g->tile_w, ty * g->tile_h, rects.data());
+      for (int n = 0; n < g->n_nodes; ++n) {
+        if (rect_empty(rects[n])) continue;
+        maxw[n] = std::max(maxw[n], rects[n].x1 - rects[n].x0);
+        maxh[n] = std::max(maxh[n], rects[n].y1 - rects[n].y0);
+      }
+    }
+  int off = 0;
+  for (int n = 0; n + 1 < g->n_nodes; ++n) {
+    GNode& nd = g->nodes[n];
+    nd.pitch = maxw[n];
+    nd.rows = maxh[n];
+    nd.smem_off = off;
+    off += nd.channels * nd.pitch * nd.rows;
+  }
+  g->smem_floats = off;
+  gp.smem = off * 4;
+  if (gp.smem > kSmemLimit)
+    return fail(HP_ERR_SCHEDULE, "group needs %d bytes of shared memory (limit %d); use smaller tiles", gp.smem,
+                kSmemLimit);
+  gp.grid_x = g->tiles_x;
+  gp.grid_y = g->tiles_y;
+  gp.gplan = std::move(g);
+  return HP_OK;
+}
+
+hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, bool unsharp) {
+  ChainArgs& a = gp.chain;
+  memset(&a, 0, sizeof a);
+  std::vector<int> st = gp.members;
+  if (unsharp) st.resize(1);
+  a.depth = (int)st.size();
+  for (int i = 0; i < a.depth; ++i) {
+    const Stage& s = p->stages[st[i]];
+    a.storage[i] = s.storage;
+    for (int k = 0; k < 5; ++k) {
+      a.w[i][k] = s.wx[k];
+      a.w[i][5 + k] = s.wy[k];
+    }
+  }
+  a.epilogue = unsharp ? 1 : 0;
+  a.amount = unsharp ? p->stages[gp.members[1]].params[0] : 0.0f;
+  a.tile_w = gp.tile_w;
+  a.tile_h = gp.tile_h;
+  if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_h < 1)
+    return fail(HP_ERR_SCHEDULE, "stencil-chain tile width must be a positive multiple of 8");
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  a.threads = gp.threads;
+  a.seg = gp.seg;
+  if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 512)
+    return fail(HP_ERR_SCHEDULE, "stencil-chain threads per block must be a multiple of 32 in [32, 512]");
+  if (a.seg < 1) return fail(HP_ERR_SCHEDULE, "serial_y must be >= 1");
+  int in_ref = p->stages[st[0]].inputs[0];
+  int in_dtype = in_ref < 0 ? p->in_dtypes[-1 - in_ref] : p->stages[in_ref].storage;
+  gp.smem = chain_smem_bytes(a.depth, a.tile_w, a.tile_h, in_dtype);
+  if (gp.smem > kSmemLimit)
+    return fail(HP_ERR_SCHEDULE, "stencil chain of depth %d with tile %dx%d needs %d bytes of shared memory", a.depth,
+                a.tile_w, a.tile_h, gp.smem);
+  gp.grid_x = a.tiles_x;
+  gp.grid_y = a.tiles_y;
+  gp.grid_z = p->stages[st[0]].channels;
+  return HP_OK;
+}
+
+hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
+  plan.in_dom = in_dom;
+  hp_status s = infer_domains(p, in_dom, plan.dom);
+  if (s) return s;
+  std::vector<GroupShape> shapes;
+  if ((s = group_shapes(p, shapes))) return s;
+  std::vector<int> order(p->n_groups);
+  for (int g = 0; g < p->n_groups; ++g) order[g] = g;
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return shapes[a].output < shapes[b].output; });
+  plan.groups.clear();
+  plan.groups.resize(p->n_groups);
+  for (int oi = 0; oi < p->n_groups; ++oi) {
+    int g = order[oi];
+    GroupPlan& gp = plan.groups[oi];
+    gp.members = shapes[g].members;
+    gp.output = shapes[g].output;
+    int impl = g < (int)p->impl.size() ? p->impl[g] : HP_IMPL_AUTO;
+    gp.kernel = choose_kernel(p, shapes[g], impl);
+    if (gp.kernel < 0) return fail(HP_ERR_UNSUPPORTED, "group %d mixes reductions with other stages", g);
+    switch (gp.kernel) {
+      case HP_KERNEL_STENCIL_CHAIN:
+      case HP_KERNEL_UNSHARP:
+        gp.tile_w = pick(p->tile_w, g, 64);
+        gp.tile_h = pick(p->tile_h, g, 32);
+        gp.threads = pick(p->threads, g, 256);
+        gp.seg = pick(p->serial_y, g, 8);
+        s = build_chain(p, plan, gp, gp.kernel == HP_KERNEL_UNSHARP);
+        break;
+      case HP_KERNEL_HISTOGRAM: case HP_KERNEL_CDF_LUT: case HP_KERNEL_LUT_APPLY:
+        gp.threads = 256;
+        break;
+      default: {
+        bool single = gp.members.size() == 1;
+        gp.tile_w = pick(p->tile_w, g, single ? 64 : 32);
+        gp.tile_h = pick(p->tile_h, g, single ? 16 : 32);
+        gp.threads = pick(p->threads, g, 256);
+        if (gp.threads % 32 != 0 || gp.threads > 1024)
+          return fail(HP_ERR_SCHEDULE, "threads per block must be a multiple of 32 in [32, 1024]");
+        s = build_gplan(p, plan, gp);
+      }
+    }
+    if (s) return s;
+  }
+  return HP_OK;
+}
+
+hp_status ensure_scratch(hp_pipeline* p, Plan& plan) {
+  if (plan.allocated) return HP_OK;
+  for (const GroupPlan& gp : plan.groups) {
+    if (gp.output == p->output) continue;
+    const Stage& st = p->stages[gp.output];
+    Scratch sc;
+    sc.bytes = scratch_bytes(st, plan.dom[gp.output]);
+    int e = cudaMalloc(&sc.ptr, sc.bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HP_ERR_OOM, "cudaMalloc of %zu bytes for stage %d failed", sc.bytes, gp.output);
+    }
+    plan.bufs[gp.output] = sc;
+  }
+  plan.allocated = true;
+  return HP_OK;
+}
+
+ImgView ref_view(const hp_pipeline* p, const Plan& plan, int ref, const hp_buffer* inputs,
+                 const hp_buffer* output) {
+  if (ref < 0) return view_of(inputs[-1 - ref]);
+  if (ref == p->output) return view_of(*output);
+  auto it = plan.bufs.find(ref);
+  return scratch_view(p->stages[ref], plan.dom[ref], it->second.ptr);
+}
+
+hp_status check_buffer(const hp_buffer& b, int dtype, int channels, Dom d, const char* what, int idx) {
+  if (!b.data) return fail(HP_ERR_INVALID_ARG, "%s %d: null data", what, idx);
+  if (b.dtype != dtype) return fail(HP_ERR_INVALID_ARG, "%s %d: dtype %d, expected %d", what, idx, b.dtype, dtype);
+  if (b.channels != channels)
+    return fail(HP_ERR_INVALID_ARG, "%s %d: %d channels, expected %d", what, idx, b.channels, channels);
+  if (d.w > 0 && (b.width != d.w || b.height != d.h))
+    return fail(HP_ERR_INVALID_ARG, "%s %d: size %dx%d, expected %dx%d", what, idx, b.width, b.height, d.w, d.h);
+  if (b.width < 1 || b.height < 1) return fail(HP_ERR_INVALID_ARG, "%s %d: empty image", what, idx);
+  if (((uintptr_t)b.data & 15) != 0) return fail(HP_ERR_INVALID_ARG, "%s %d: data not 16-byte aligned", what, idx);
+  if (b.row_stride_bytes % 16 != 0 || b.plane_stride_bytes % 16 != 0)
+    return fail(HP_ERR_INVALID_ARG, "%s %d: strides must be multiples of 16 bytes", what, idx);
+  if (b.row_stride_bytes < (long long)b.width * dtype_bytes(dtype) ||
+      (b.channels > 1 && b.plane_stride_bytes < b.row_stride_bytes * b.height))
+    return fail(HP_ERR_INVALID_ARG, "%s %d: strides too small for the image", what, idx);
+  return HP_OK;
+}
+
+hp_status get_plan(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan** out) {
+  if (p->output < 0) return fail(HP_ERR_STATE, "no output stage set");
+  std::vector<int> key;
+  for (Dom d : in_dom) { key.push_back(d.w); key.push_back(d.h); }
+  auto it = p->plans.find(key);
+  if (it != p->plans.end()) { *out = it->second.get(); return HP_OK; }
+  auto plan = std::make_unique<Plan>();
+  hp_status s = lower(p, in_dom, *plan);
+  if (s) return s;
+  *out = plan.get();
+  p->plans[key] = std::move(plan);
+  return HP_OK;
+}
+
+void free_plan(Plan& plan) {
+  for (auto& kv : plan.bufs) cudaFree(kv.second.ptr);
+  for (auto& sc : plan.staging) cudaFree(sc.ptr);
+  plan.bufs.clear();
+  plan.staging.clear();
+}
+
+void drop_plans(hp_pipeline* p) {
+  for (auto& kv : p->plans) free_plan(*kv.second);
+  p->plans.clear();
+}
+
+void default_schedule(hp_pipeline* p) {
+  int ns = (int)p->stages.size();
+  p->group_of.resize(ns);
+  for (int s = 0; s < ns; ++s) p->group_of[s] = s;
+  p->n_groups = ns;
+  p->tile_w.clear(); p->tile_h.clear(); p->threads.clear(); p->serial_y.clear(); p->impl.clear();
+}
+
+hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const hp_buffer* output, void* stream) {
+  for (GroupPlan& gp : plan.groups) {
+    ImgView out = ref_view(p, plan, gp.output, inputs, output);
+    int e = 0;
+    switch (gp.kernel) {
+      case HP_KERNEL_STENCIL_CHAIN:
+      case HP_KERNEL_UNSHARP: {
+        ChainArgs a = gp.chain;
+        int first = gp.members[0];
+        a.in = ref_view(p, plan, p->stages[first].inputs[0], inputs, output);
+        a.out = out;
+        a.err = p->d_err;
+        e = launch_chain(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_HISTOGRAM: {
+        HistArgs a{};
+        a.in = ref_view(p, plan, p->stages[gp.output].inputs[0], inputs, output);
+        a.hist = (unsigned int*)out.data;
+        e = launch_hist(a, stream);
+        break;
+      }
+      case HP_KERNEL_CDF_LUT: {
+        LutArgs a{};
+        a.hist = (const unsigned int*)ref_view(p, plan, p->stages[gp.output].inputs[0], inputs, output).data;
+        a.lut = (unsigned char*)out.data;
+        a.lut_view = out;
+        e = launch_cdf_lut(a, stream);
+        break;
+      }
+      case HP_KERNEL_LUT_APPLY: {
+        LutApplyArgs a{};
+        a.in = ref_view(p, plan, p->stages[gp.output].inputs[0], inputs, output);
+        a.lut = (const unsigned char*)ref_view(p, plan, p->stages[gp.output].inputs[1], inputs, output).data;
+        a.out = out;
+        e = launch_lut_apply(a, stream);
+        break;
+      }
+      default: {
+        GPlan& g = *gp.gplan;
+        for (size_t i = 0; i < gp.ext_refs.size(); ++i) g.ext[i] = ref_view(p, plan, gp.ext_refs[i], inputs, output);
+        g.out = out;
+        g.err = p->d_err;
+        e = launch_generic(g, gp.threads, gp.smem, stream);
+      }
+    }
+    if (e) return cuda_fail(e, "kernel launch");
+  }
+  return HP_OK;
+}
+
+}  // namespace
+}  // namespace hp
+
+using namespace hp;
+
+extern "C" {
+
+hp_status hp_pipeline_create(hp_pipeline** out, int n_inputs, const int* in_dtypes, const int* in_channels) {
+  if (!out || n_inputs < 1 || n_inputs > 16 || !in_dtypes || !in_channels)
+    return fail(HP_ERR_INVALID_ARG, "hp_pipeline_create: bad arguments");
+  for (int i = 0; i < n_inputs; ++i) {
+    if (!valid_dtype(in_dtypes[i]) || in_dtypes[i] == HP_U32)
+      return fail(HP_ERR_INVALID_ARG, "input %d: bad dtype %d", i, in_dtypes[i]);
+    if (in_channels[i] < 1 || in_channels[i] > 64) return fail(HP_ERR_INVALID_ARG, "input %d: bad channel count", i);
+  }
+  auto* p = new hp_pipeline();
+  p->in_dtypes.assign(in_dtypes, in_dtypes + n_inputs);
+  p->in_channels.assign(in_channels, in_channels + n_inputs);
+  *out = p;
+  t_err.clear();
+  return HP_OK;
+}
+
+hp_status hp_add_stage(hp_pipeline* p, const hp_stage_desc* d, int* out_id) {
+  if (!p || !d) return fail(HP_ERR_INVALID_ARG, "hp_add_stage: null argument");
+  hp_status s = validate_stage(p, d);
+  if (s) return s;
+  Stage st;
+  st.kind = d->kind;
+  st.op = d->op;
+  st.channels = d->channels;
+  st.storage = d->storage;
+  st.inputs.assign(d->inputs, d->inputs + d->n_inputs);
+  st.rx = d->rx;
+  st.ry = d->ry;
+  if (d->kind == HP_STENCIL) {
+    st.wx.assign(d->wx, d->wx + 2 * d->rx + 1);
+    st.wy.assign(d->wy, d->wy + 2 * d->ry + 1);
+  }
+  if (d->n_params > 0) st.params.assign(d->params, d->params + d->n_params);
+  p->stages.push_back(st);
+  if (out_id) *out_id = (int)p->stages.size() - 1;
+  p->has_schedule = false;
+  drop_plans(p);
+  return HP_OK;
+}
+
+hp_status hp_set_output(hp_pipeline* p, int stage_id) {
+  if (!p || stage_id < 0 || stage_id >= (int)p->stages.size())
+    return fail(HP_ERR_INVALID_ARG, "hp_set_output: bad stage id %d", stage_id);
+  p->output = stage_id;
+  if (!p->has_schedule) default_schedule(p);
+  drop_plans(p);
+  return HP_OK;
+}
+
+hp_status hp_schedule_set(hp_pipeline* p, const hp_schedule* s) {
+  if (!p || !s) return fail(HP_ERR_INVALID_ARG, "hp_schedule_set: null argument");
+  if (p->output < 0) return fail(HP_ERR_STATE, "set the output stage before the schedule");
+  int ns = (int)p->stages.size();
+  if (s->n_stages != ns || !s->group_of_stage || s->n_groups < 1 || s->n_groups > ns)
+    return fail(HP_ERR_SCHEDULE, "schedule must cover all %d stages with 1..%d groups", ns, ns);
+  for (int i = 0; i < ns; ++i) {
+    int g = s->group_of_stage[i];
+    if (g == HP_INLINE) {
+      if (p->stages[i].kind != HP_POINTWISE) return fail(HP_ERR_SCHEDULE, "only point-wise stages can be inlined");
+      if (i == p->output) return fail(HP_ERR_SCHEDULE, "the output stage cannot be inlined");
+    } else if (g < 0 || g >= s->n_groups) {
+      return fail(HP_ERR_SCHEDULE, "stage %d: group %d out of range", i, g);
+    }
+  }
+  auto per_group = [&](const int* v, std::vector<int>& dst, int lo, int hi, const char* what) -> hp_status {
+    dst.clear();
+    if (!v) return HP_OK;
+    dst.assign(v, v + s->n_groups);
+    for (int x : dst)
+      if (x != 0 && (x < lo || x > hi)) return fail(HP_ERR_SCHEDULE, "%s %d out of range [%d, %d]", what, x, lo, hi);
+    return HP_OK;
+  };
+  // keep the old schedule until the new one validates
+  hp_pipeline tmp;
+  tmp.stages = p->stages;
+  tmp.output = p->output;
+  tmp.in_dtypes = p->in_dtypes;
+  tmp.in_channels = p->in_channels;
+  tmp.group_of.assign(s->group_of_stage, s->group_of_stage + ns);
+  tmp.n_groups = s->n_groups;
+  hp_status st;
+  if ((st = per_group(s->tile_w, tmp.tile_w, 1, 4096, "tile_w")) || (st = per_group(s->tile_h, tmp.tile_h, 1, 4096, "tile_h")) ||
+      (st = per_group(s->threads, tmp.threads, 32, 1024, "threads")) ||
+      (st = per_group(s->serial_y, tmp.serial_y, 1, 256, "serial_y")) ||
+      (st = per_group(s->impl, tmp.impl, 0, 1, "impl")))
+    return st;
+  std::vector<GroupShape> shapes;
+  if ((st = group_shapes(&tmp, shapes))) return st;
+  drop_plans(p);
+  p->group_of = tmp.group_of;
+  p->n_groups = tmp.n_groups;
+  p->tile_w = tmp.tile_w; p->tile_h = tmp.tile_h; p->threads = tmp.threads;
+  p->serial_y = tmp.serial_y; p->impl = tmp.impl;
+  p->has_schedule = true;
+  return HP_OK;
+}
+
+static hp_status collect_in_dom(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, std::vector<Dom>& in_dom) {
+  if (!p || !inputs || n_inputs != (int)p->in_dtypes.size())
+    return fail(HP_ERR_INVALID_ARG, "expected %d input buffers", p ? (int)p->in_dtypes.size() : 0);
+  in_dom.clear();
+  for (int i = 0; i < n_inputs; ++i) {
+    hp_status s = check_buffer(inputs[i], p->in_dtypes[i], p->in_channels[i], Dom{0, 0}, "input", i);
+    if (s) return s;
+    in_dom.push_back(Dom{inputs[i].width, inputs[i].height});
+  }
+  return HP_OK;
+}
+
+hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output, void* stream) {
+  std::vector<Dom> in_dom;
+  hp_status s = collect_in_dom(p, inputs, n_inputs, in_dom);
+  if (s) return s;
+  if (!output) return fail(HP_ERR_INVALID_ARG, "null output buffer");
+  Plan* plan = nullptr;
+  if ((s = get_plan(p, in_dom, &plan))) return s;
+  const Stage& os = p->stages[p->output];
+  if ((s = check_buffer(*output, os.storage, os.channels, plan->dom[p->output], "output", 0))) return s;
+  if (!p->d_err) {
+    int e = cudaMalloc(&p->d_err, 16);
+    if (e) return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
+    cudaMemset(p->d_err, 0, 16);
+  }
+  if ((s = ensure_scratch(p, *plan))) return s;
+  return run_groups(p, *plan, inputs, output, stream);
+}
+
+hp_status hp_realize_host(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output,
+                          void* stream) {
+  std::vector<Dom> in_dom;
+  if (!p || !inputs || n_inputs != (int)p->in_dtypes.size() || !output)
+    return fail(HP_ERR_INVALID_ARG, "hp_realize_host: bad arguments");
+  for (int i = 0; i < n_inputs; ++i) in_dom.push_back(Dom{inputs[i].width, inputs[i].height});
+  Plan* plan = nullptr;
+  hp_status s = get_plan(p, in_dom, &plan);
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<hp_buffer> dev_in(n_inputs);
+  if (plan->staging.empty()) {
+    plan->staging.resize(n_inputs + 1);
+    for (int i = 0; i <= n_inputs; ++i) {
+      const hp_buffer& b = i < n_inputs ? inputs[i] : *output;
+      size_t bytes = (size_t)round16((long long)b.width * dtype_bytes(b.dtype)) * b.height * b.channels;
+      if (cudaMalloc(&plan->staging[i].ptr, bytes)) {
+        cudaGetLastError();
+        plan->staging.clear();
+        return fail(HP_ERR_OOM, "cudaMalloc of %zu staging bytes failed", bytes);
+      }
+      plan->staging[i].bytes = bytes;
+    }
+  }
+  for (int i = 0; i <= n_inputs; ++i) {
+    const hp_buffer& b = i < n_inputs ? inputs[i] : *output;
+    if (!b.data) return fail(HP_ERR_INVALID_ARG, "null host buffer");
+    hp_buffer d = b;
+    d.data = plan->staging[i].ptr;
+    d.row_stride_bytes = round16((long long)b.width * dtype_bytes(b.dtype));
+    d.plane_stride_bytes = d.row_stride_bytes * b.height;
+    if (i < n_inputs) {
+      dev_in[i] = d;
+      for (int c = 0; c < b.channels; ++c) {
+        int e = cudaMemcpy2DAsync((char*)d.data + c * d.plane_stride_bytes, d.row_stride_bytes,
+                                  (const char*)b.data + c * b.plane_stride_bytes, b.row_stride_bytes,
+                                  (size_t)b.width * dtype_bytes(b.dtype), b.height, cudaMemcpyHostToDevice, st);
+        if (e) return cuda_fail(e, "host-to-device copy");
+      }
+    }
+  }
+  hp_buffer dev_out = *output;
+  dev_out.data = plan->staging[n_inputs].ptr;
+  dev_out.row_stride_bytes = round16((long long)output->width * dtype_bytes(output->dtype));
+  dev_out.plane_stride_bytes = dev_out.row_stride_bytes * output->height;
+  if ((s = hp_realize(p, dev_in.data(), n_inputs, &dev_out, stream))) return s;
+  for (int c = 0; c < output->channels; ++c) {
+    int e = cudaMemcpy2DAsync((char*)output->data + c * output->plane_stride_bytes, output->row_stride_bytes,
+                              (const char*)dev_out.data + c * dev_out.plane_stride_bytes, dev_out.row_stride_bytes,
+                              (size_t)output->width * dtype_bytes(output->dtype), output->height,
+                              cudaMemcpyDeviceToHost, st);
+    if (e) return cuda_fail(e, "device-to-host copy");
+  }
+  int e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(e, "stream synchronize");
+  return HP_OK;
+}
+
+hp_status hp_group_count(hp_pipeline* p, int* n) {
+  if (!p || !n) return fail(HP_ERR_INVALID_ARG, "null argument");
+  if (p->output < 0) return fail(HP_ERR_STATE, "no output stage set");
+  *n = p->n_groups;
+  return HP_OK;
+}
+
+static hp_status plan_for_sizes(hp_pipeline* p, const int* ws, const int* hs, Plan** plan) {
+  if (!p || !ws || !hs) return fail(HP_ERR_INVALID_ARG, "null argument");
+  std::vector<Dom> in_dom;
+  for (size_t i = 0; i < p->in_dtypes.size(); ++i) {
+    if (ws[i] < 1 || hs[i] < 1) return fail(HP_ERR_INVALID_ARG, "input %zu: empty size", i);
+    in_dom.push_back(Dom{ws[i], hs[i]});
+  }
+  return get_plan(p, in_dom, plan);
+}
+
+hp_status hp_group_info_get(hp_pipeline* p, const int* ws, const int* hs, int group, hp_group_info* info) {
+  Plan* plan = nullptr;
+  hp_status s = plan_for_sizes(p, ws, hs, &plan);
+  if (s) return s;
+  if (!info || group < 0 || group >= (int)plan->groups.size()) return fail(HP_ERR_INVALID_ARG, "bad group");
+  const GroupPlan& gp = plan->groups[group];
+  info->kernel = gp.kernel;
+  info->output_stage = gp.output;
+  info->n_members = (int)gp.members.size();
+  info->tile_w = gp.tile_w;
+  info->tile_h = gp.tile_h;
+  info->threads = gp.threads;
+  info->grid_x = gp.grid_x;
+  info->grid_y = gp.grid_y;
+  info->grid_z = gp.grid_z;
+  info->smem_bytes = gp.smem;
+  return HP_OK;
+}
+
+hp_status hp_infer_bounds(hp_pipeline* p, const int* ws, const int* hs, int group, int x0, int y0, int w, int h,
+                          int* rects, int n_rects) {
+  Plan* plan = nullptr;
+  hp_status s = plan_for_sizes(p, ws, hs, &plan);
+  if (s) return s;
+  if (group < 0 || group >= (int)plan->groups.size() || !rects || n_rects < (int)p->stages.size() || w < 1 || h < 1)
+    return fail(HP_ERR_INVALID_ARG, "bad group, tile or rects array");
+  const GroupPlan& gp = plan->groups[group];
+  // same propagation as the kernels, for this tile size
+  GPlan g;
+  memset(&g, 0, sizeof g);
+  std::map<int, int> node_of;
+  for (size_t i = 0; i < gp.members.size(); ++i) node_of[gp.members[i]] = (int)i;
+  g.n_nodes = (int)gp.members.size();
+  g.tile_w = w;
+  g.tile_h = h;
+  for (size_t i = 0; i < gp.members.size(); ++i) {
+    const Stage& st = p->stages[gp.members[i]];
+    GNode& n = g.nodes[i];
+    n.kind = st.kind;
+    n.n_in = (int)st.inputs.size();
+    for (int k = 0; k < n.n_in; ++k) {
+      auto it = node_of.find(st.inputs[k]);
+      n.in[k] = st.inputs[k] >= 0 && it != node_of.end() ? it->second : -1;
+    }
+    n.rx = st.rx;
+    n.ry = st.ry;
+    n.dom_w = plan->dom[gp.members[i]].w;
+    n.dom_h = plan->dom[gp.members[i]].h;
+  }
+  std::vector<Rect> r(g.n_nodes);
+  infer_rects(g, x0, y0, r.data());
+  for (size_t i = 0; i < p->stages.size(); ++i) {
+    rects[4 * i] = rects[4 * i + 1] = rects[4 * i + 2] = rects[4 * i + 3] = 0;
+  }
+  for (int n = 0; n < g.n_nodes; ++n) {
+    int sid = gp.members[n];
+    rects[4 * sid] = r[n].x0;
+    rects[4 * sid + 1] = r[n].y0;
+    rects[4 * sid + 2] = r[n].x1;
+    rects[4 * sid + 3] = r[n].y1;
+  }
+  return HP_OK;
+}
+
+hp_status hp_check_device_error(hp_pipeline* p, int* code) {
+  if (!p || !code) return fail(HP_ERR_INVALID_ARG, "null argument");
+  *code = 0;
+  if (!p->d_err) return HP_OK;
+  int e = cudaMemcpy(code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e) return cuda_fail(e, "reading the device error word");
+  e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e) return cuda_fail(e, "clearing the device error word");
+  return HP_OK;
+}
+
+hp_status hp_pipeline_destroy(hp_pipeline* p) {
+  if (!p) return fail(HP_ERR_INVALID_ARG, "null pipeline");
+  drop_plans(p);
+  if (p->d_err) cudaFree(p->d_err);
+  delete p;
+  return HP_OK;
+}
+
+const char* hp_last_error(void) { return t_err.c_str(); }
+
+unsigned long long hp_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+"""Builders of the imaging pipelines of the paper's evaluation (Sec. 6) as hp
+pipelines, with their stage-per-kernel and fused schedules.
+
+Each builder states the algorithm once (stages, footprints, storage types);
+schedules only regroup stages into kernels and retile them (Sec. 1, Sec. 4).
+"""
+
+from . import hp
+
+BINOMIAL16 = [0.0625, 0.25, 0.375, 0.25, 0.0625]   # [1,4,6,4,1]/16, per axis
+BOX5 = [0.2] * 5                                    # 1/5 per axis -> 1/25 in 2-D
+SOBEL_SMOOTH = [1.0, 2.0, 1.0]
+SOBEL_DIFF = [-1.0, 0.0, 1.0]
+BOX3_SUM = [1.0, 1.0, 1.0]
+
+
+def chain_kinds(n_stages: int, pattern: str):
+    if pattern == "binomial":
+        return ["binomial"] * n_stages
+    if pattern == "alternate":
+        return ["binomial" if k % 2 == 0 else "box" for k in range(n_stages)]
+    raise ValueError(pattern)
+
+
+def stencil_chain(n_stages: int = 32, pattern: str = "alternate", storage: int = hp.HP_F32) -> hp.Pipeline:
+    """Chain of 5x5 separable stencils on a 1-channel image (Sec. 2, Fig. 1; the
+    32-stage stencil chain of Sec. 6).  Input and every stage use `storage`."""
+    p = hp.Pipeline([storage], [1])
+    prev = p.input(0)
+    for kind in chain_kinds(n_stages, pattern):
+        w = BINOMIAL16 if kind == "binomial" else BOX5
+        prev = p.add_stage(hp.HP_STENCIL, [prev], 1, storage, rx=2, ry=2, wx=w, wy=w)
+    p.set_output(prev)
+    return p
+
+
+def chain_schedule(p: hp.Pipeline, depth: int, tile_w: int = 64, tile_h: int = 32, threads: int = 256,
+                   serial_y: int = 8):
+    """Fuse consecutive runs of `depth` stages into one kernel each."""
+    n = len(p.stages)
+    groups = [k // depth for k in range(n)]
+    ng = groups[-1] + 1
+    p.schedule(groups, tile_w=[tile_w] * ng, tile_h=[tile_h] * ng, threads=[threads] * ng,
+               serial_y=[serial_y] * ng)
+
+
+def root_schedule(p: hp.Pipeline, impl=None):
+    """Every stage in its own kernel (compute root, Sec. 2 "Separate Kernels")."""
+    n = len(p.stages)
+    p.schedule(list(range(n)), impl=impl)
+
+
+def harris(io_storage: int = hp.HP_F32, inner_storage: int = hp.HP_F32, k: float = 0.04) -> hp.Pipeline:
+    """Harris corner response of an RGB image: gray, Sobel gradients, products,
+    3x3 box sums, det - k tr^2 (every stencil clamped on its own producer)."""
+    p = hp.Pipeline([io_storage], [3])
+    s = inner_storage
+    g = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, s, op=hp.HP_OP_GRAY, params=[1.0])
+    ix = p.add_stage(hp.HP_STENCIL, [g], 1, s, rx=1, ry=1, wx=SOBEL_DIFF, wy=SOBEL_SMOOTH)
+    iy = p.add_stage(hp.HP_STENCIL, [g], 1, s, rx=1, ry=1, wx=SOBEL_SMOOTH, wy=SOBEL_DIFF)
+    ixx = p.add_stage(hp.HP_POINTWISE, [ix, ix], 1, s, op=hp.HP_OP_MUL)
+    iyy = p.add_stage(hp.HP_POINTWISE, [iy, iy], 1, s, op=hp.HP_OP_MUL)
+    ixy = p.add_stage(hp.HP_POINTWISE, [ix, iy], 1, s, op=hp.HP_OP_MUL)
+    sxx = p.add_stage(hp.HP_STENCIL, [ixx], 1, s, rx=1, ry=1, wx=BOX3_SUM, wy=BOX3_SUM)
+    syy = p.add_stage(hp.HP_STENCIL, [iyy], 1, s, rx=1, ry=1, wx=BOX3_SUM, wy=BOX3_SUM)
+    sxy = p.add_stage(hp.HP_STENCIL, [ixy], 1, s, rx=1, ry=1, wx=BOX3_SUM, wy=BOX3_SUM)
+    r = p.add_stage(hp.HP_POINTWISE, [sxx, syy, sxy], 1, io_storage, op=hp.HP_OP_HARRIS, params=[k])
+    p.set_output(r)
+    return p
+
+
+def fused_schedule(p: hp.Pipeline, tile_w: int = 32, tile_h: int = 32, threads: int = 256, impl=None,
+                   inline_pointwise: bool = False):
+    """All stages in one kernel (optionally with point-wise producers inlined)."""
+    n = len(p.stages)
+    groups = []
+    for i, st in enumerate(p.stages):
+        inl = inline_pointwise and st["kind"] == hp.HP_POINTWISE and i != n - 1
+        groups.append(hp.HP_INLINE if inl else 0)
+    p.schedule(groups, tile_w=[tile_w], tile_h=[tile_h], threads=[threads],
+               impl=[impl] if impl is not None else None)
+
+
+def unsharp(storage: int = hp.HP_F32, amount: float = 1.5, channels: int = 3) -> hp.Pipeline:
+    """Per channel: blur = 5x5 binomial (clamped); out = in + amount (in - blur)."""
+    p = hp.Pipeline([storage], [channels])
+    blur = p.add_stage(hp.HP_STENCIL, [p.input(0)], channels, storage, rx=2, ry=2, wx=BINOMIAL16, wy=BINOMIAL16)
+    out = p.add_stage(hp.HP_POINTWISE, [p.input(0), blur], channels, storage, op=hp.HP_OP_UNSHARP, params=[amount])
+    p.set_output(out)
+    return p
+
+
+def histeq() -> hp.Pipeline:
+    """256-bin histogram -> CDF lookup table -> table lookup, on a u8 image."""
+    p = hp.Pipeline([hp.HP_U8], [1])
+    h = p.add_stage(hp.HP_HISTOGRAM, [p.input(0)], 1, hp.HP_U32)
+    lut = p.add_stage(hp.HP_CDF_LUT, [h], 1, hp.HP_U8)
+    out = p.add_stage(hp.HP_LUT_APPLY, [p.input(0), lut], 1, hp.HP_U8)
+    p.set_output(out)
+    return p
+
+
+def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, alpha: float = 1.0,
+                    beta: float = 1.0):
+    """Local Laplacian filter (Paris et al.; K discrete intensity levels) of a
+    u16 RGB image.  Returns (pipeline, stage-id map)."""
+    J, K = levels, k_levels
+    p = hp.Pipeline([hp.HP_U16], [3])
+    ids = {}
+    F = hp.HP_F32
+    gray = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, F, op=hp.HP_OP_GRAY, params=[1.0 / 65535.0])
+    G = [p.add_stage(hp.HP_POINTWISE, [gray], K + 1, F, op=hp.HP_OP_LL_REMAP, params=[sigma_r, alpha, beta, K])]
+    for _ in range(1, J):
+        G.append(p.add_stage(hp.HP_DOWNSAMPLE2, [G[-1]], K + 1, F))
+    U, L, Lout = [], [], []
+    for l in range(J - 1):
+        U.append(p.add_stage(hp.HP_UPSAMPLE2, [G[l + 1], G[l]], K + 1, F))
+        L.append(p.add_stage(hp.HP_POINTWISE, [G[l], U[l]], K + 1, F, op=hp.HP_OP_SUB))
+        Lout.append(p.add_stage(hp.HP_POINTWISE, [G[l], L[l]], 1, F, op=hp.HP_OP_LL_INTERP, params=[K]))
+    R = [None] * J
+    UR = [None] * (J - 1)
+    R[J - 1] = p.add_stage(hp.HP_POINTWISE, [G[J - 1]], 1, F, op=hp.HP_OP_SELECT, params=[K])
+    for l in range(J - 2, -1, -1):
+        UR[l] = p.add_stage(hp.HP_UPSAMPLE2, [R[l + 1], Lout[l]], 1, F)
+        R[l] = p.add_stage(hp.HP_POINTWISE, [Lout[l], UR[l]], 1, F, op=hp.HP_OP_ADD)
+    out = p.add_stage(hp.HP_POINTWISE, [p.input(0), gray, R[0]], 3, hp.HP_U16, op=hp.HP_OP_LL_COLOUR,
+                      params=[1.0 / 65535.0, 65535.0])
+    p.set_output(out)
+    ids.update(gray=gray, G=G, U=U, L=L, Lout=Lout, R=R, UR=UR, out=out)
+    return p, ids
+
+
+def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256):
+    """Per-level fusion: level 1 of the remapped pyramid from the input in one
+    kernel (gray and remap inlined); one downsample kernel per coarser level;
+    one kernel per level for Laplacian + interpolation + collapse step; the
+    finest level fused with the colour reconstruction."""
+    J = len(ids["G"])
+    n = len(p.stages)
+    groups = [None] * n
+    gid = 0
+    groups[ids["gray"]] = hp.HP_INLINE
+    groups[ids["G"][0]] = hp.HP_INLINE
+    for l in range(1, J):
+        groups[ids["G"][l]] = gid
+        gid += 1
+    groups[ids["R"][J - 1]] = hp.HP_INLINE
+    for l in range(J - 2, -1, -1):
+        for key in ("U", "L", "Lout", "UR", "R"):
+            groups[ids[key][l]] = gid
+        if l == 0:
+            groups[ids["out"]] = gid
+        gid += 1
+    assert all(g is not None for g in groups)
+    p.schedule(groups, tile_w=[tile] * gid, tile_h=[tile] * gid, threads=[threads] * gid)

@@ -1,0 +1,118 @@
+"""C ABI checks that need no GPU: the library loads and exports every symbol
+include/hp.h declares; stage/schedule validation; bounds inference; lowering."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2012_07145_gb300 import hp, pipelines
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "hp.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:hp_status|const char\*|unsigned long long)\s+(hp_\w+)\(", text, re.M)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_functions()
+    assert len(names) >= 12
+    L = ctypes.CDLL(hp.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(hp.EXPORTS)
+
+
+def test_stage_validation_errors():
+    p = hp.Pipeline([hp.HP_F32], [1])
+    with pytest.raises(hp.HPError) as e:
+        p.add_stage(hp.HP_STENCIL, [p.input(3)], 1, rx=2, ry=2, wx=[0.2] * 5, wy=[0.2] * 5)
+    assert e.value.status == hp.HP_ERR_INVALID_ARG
+    with pytest.raises(hp.HPError):
+        p.add_stage(hp.HP_STENCIL, [p.input(0)], 1, rx=9, ry=2, wx=[0.1] * 19, wy=[0.2] * 5)
+    with pytest.raises(hp.HPError):  # gray needs 3 channels
+        p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, op=hp.HP_OP_GRAY, params=[1.0])
+    with pytest.raises(hp.HPError):  # histogram of a float image
+        p.add_stage(hp.HP_HISTOGRAM, [p.input(0)], 1, hp.HP_U32)
+    s = p.add_stage(hp.HP_STENCIL, [p.input(0)], 1, rx=2, ry=2, wx=[0.2] * 5, wy=[0.2] * 5)
+    assert s == 0
+
+
+def test_schedule_validation():
+    p = pipelines.stencil_chain(4, "binomial")
+    with pytest.raises(hp.HPError) as e:  # stencils cannot be inlined
+        p.schedule([0, hp.HP_INLINE, 1, 1])
+    assert e.value.status == hp.HP_ERR_SCHEDULE
+    with pytest.raises(hp.HPError):  # group 0 would export two stages
+        p.schedule([0, 1, 0, 1])
+    p.schedule([0, 0, 1, 1])
+    assert p.group_count() == 2
+    # a tile that needs more shared memory than a CTA has fails at lowering
+    p.schedule([0, 0, 0, 0], tile_w=[512], tile_h=[512])
+    with pytest.raises(hp.HPError) as e:
+        p.group_info([(512, 512)], 0)
+    assert e.value.status == hp.HP_ERR_SCHEDULE
+
+
+def test_lowering_picks_kernels():
+    p = pipelines.stencil_chain(32, "alternate")
+    assert p.group_count() == 32
+    info = p.group_info([(2560, 1536)], 0)
+    assert info.kernel == hp.HP_KERNEL_STENCIL_CHAIN and info.n_members == 1
+    pipelines.chain_schedule(p, depth=8, tile_w=64, tile_h=32)
+    info = p.group_info([(2560, 1536)], 0)
+    assert info.kernel == hp.HP_KERNEL_STENCIL_CHAIN and info.n_members == 8
+    assert (info.grid_x, info.grid_y, info.grid_z) == (40, 48, 1)
+    u = pipelines.unsharp()
+    pipelines.fused_schedule(u)
+    assert u.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_UNSHARP
+    h = pipelines.histeq()
+    kinds = [h.group_info([(100, 50)], g).kernel for g in range(3)]
+    assert kinds == [hp.HP_KERNEL_HISTOGRAM, hp.HP_KERNEL_CDF_LUT, hp.HP_KERNEL_LUT_APPLY]
+    hr = pipelines.harris()
+    pipelines.fused_schedule(hr, impl=hp.HP_IMPL_GENERIC)
+    assert hr.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_GENERIC
+
+
+def test_bounds_inference_stencil_chain():
+    # Fusing d 5x5 stages: stage k of the group needs the tile grown by 2(d-1-k) per side, clamped.
+    p = pipelines.stencil_chain(4, "binomial")
+    p.schedule([0, 0, 0, 0])
+    W, H = 100, 60
+    r = p.infer_bounds([(W, H)], 0, 32, 16, 16, 8)
+    assert r[3] == (32, 16, 48, 24)
+    assert r[2] == (30, 14, 50, 26)
+    assert r[1] == (28, 12, 52, 28)
+    assert r[0] == (26, 10, 54, 30)
+    r = p.infer_bounds([(W, H)], 0, 0, 0, 16, 8)     # corner tile: clamped to the image
+    assert r[0] == (0, 0, 22, 14)
+    r = p.infer_bounds([(W, H)], 0, 96, 56, 16, 8)   # ragged corner tile
+    assert r[3] == (96, 56, 100, 60)
+    assert r[0] == (90, 50, 100, 60)
+
+
+def test_bounds_inference_pyramid_and_harris():
+    pl, ids = pipelines.local_laplacian(levels=3, k_levels=4)
+    pipelines.local_laplacian_fused_schedule(pl, ids, tile=16)
+    # group 0 computes G1 (downsample) from the inlined remap of gray
+    r = pl.infer_bounds([(64, 40)], 0, 8, 4, 8, 4)
+    assert r[ids["G"][1]] == (8, 4, 16, 8)
+    assert r[ids["G"][0]] == (14, 6, 33, 17)      # [2*8-2, 2*16+1) x [2*4-2, 2*8+1)
+    assert r[ids["gray"]] == r[ids["G"][0]]
+    hr = pipelines.harris()
+    pipelines.fused_schedule(hr)
+    r = hr.infer_bounds([(50, 40)], 0, 16, 8, 16, 8)
+    assert r[9] == (16, 8, 32, 16)                 # response
+    assert r[6] == r[7] == r[8] == (16, 8, 32, 16)  # box sums
+    assert r[3] == (15, 7, 33, 17)                 # products: +1 for the box
+    assert r[1] == (15, 7, 33, 17)
+    assert r[0] == (14, 6, 34, 18)                 # gray: +1 more for Sobel

@@ -1,0 +1,132 @@
+"""GPU parity of Harris, unsharp mask, histogram equalize and the local
+Laplacian against the FP64 / exact oracle, plus schedule invariance."""
+
+import numpy as np
+import pytest
+import torch
+
+import __graft_entry__
+from oracle import harris as ohr
+from oracle import histeq as ohe
+from oracle import local_laplacian as oll
+from oracle import unsharp as ous
+from paper_2012_07145_gb300 import hp, pipelines, synth
+
+from gpu_util import bits, rel_err, run, to_device, to_numpy, u16_close
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    __graft_entry__.build()
+
+
+# ---------------------------------------------------------------- Harris ----
+@pytest.mark.parametrize("h,w", [(1536, 2560), (37, 53), (1, 1), (2, 5)])
+def test_harris_against_oracle_and_schedules(h, w):
+    img = synth.rgb_f32(h, w, seed=3)
+    ref = ohr.harris(img.astype(np.float64))
+    x = to_device(img, hp.HP_F32)
+    p = pipelines.harris()
+    plain = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+    if h * w > 4:
+        assert rel_err(to_numpy(plain)[0], ref) <= TOL
+    else:
+        assert np.abs(to_numpy(plain)[0] - ref).max() < 1e-4
+    for kw in [dict(), dict(inline_pointwise=True), dict(tile_w=16, tile_h=8, threads=128)]:
+        pipelines.fused_schedule(p, **kw)
+        fused = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+        assert torch.equal(bits(fused), bits(plain)), kw
+
+
+def test_harris_bf16_io_error_is_stated():
+    h, w = 96, 160
+    img = synth.rgb_f32(h, w, seed=4)
+    p = pipelines.harris(io_storage=hp.HP_BF16)
+    x = to_device(img, hp.HP_BF16)
+    plain = run(p, [x], [hp.HP_BF16], (1, h, w), hp.HP_BF16)
+    pipelines.fused_schedule(p)
+    fused = run(p, [x], [hp.HP_BF16], (1, h, w), hp.HP_BF16)
+    assert torch.equal(bits(fused), bits(plain))
+    e_rounded = rel_err(to_numpy(fused)[0], ohr.harris(to_numpy(x).astype(np.float64)))
+    e_orig = rel_err(to_numpy(fused)[0], ohr.harris(img.astype(np.float64)))
+    print(f"harris bf16 I/O: rel err vs oracle on rounded input {e_rounded:.3e}, original {e_orig:.3e}")
+    assert e_rounded < 0.05
+
+
+# ---------------------------------------------------------------- unsharp ---
+@pytest.mark.parametrize("h,w", [(480, 640), (3, 9), (1, 1)])
+def test_unsharp_against_oracle_and_schedules(h, w):
+    img = synth.rgb_f32(h, w, seed=5)
+    ref = ous.unsharp(img.astype(np.float64))
+    x = to_device(img, hp.HP_F32)
+    p = pipelines.unsharp()
+    plain = run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)
+    got = to_numpy(plain)
+    assert rel_err(got, ref) <= TOL if h * w > 1 else np.abs(got - ref).max() < 1e-6
+    pipelines.fused_schedule(p, tile_w=64, tile_h=32)
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_UNSHARP
+    fused = run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)
+    assert torch.equal(bits(fused), bits(plain))
+    pipelines.fused_schedule(p, impl=hp.HP_IMPL_GENERIC)
+    gen = run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)
+    assert torch.equal(bits(gen), bits(plain))
+
+
+# -------------------------------------------------------- histogram equalize -
+@pytest.mark.parametrize("h,w", [(256, 256), (480, 640), (1080, 1920), (3072, 4096), (33, 17), (1, 1), (5, 3)])
+def test_histeq_bit_exact(h, w):
+    img = synth.gray_u8_lowcontrast(h, w, seed=h + w)
+    hist, table, ref = ohe.equalize(img[0])
+    p = pipelines.histeq()
+    x = to_device(img, hp.HP_U8)
+    y = run(p, [x], [hp.HP_U8], (1, h, w), hp.HP_U8)
+    assert np.array_equal(to_numpy(y)[0], ref)
+
+
+def test_histeq_constant_and_two_value_images():
+    p = pipelines.histeq()
+    const = np.full((1, 40, 50), 77, dtype=np.uint8)
+    y = run(p, [to_device(const, hp.HP_U8)], [hp.HP_U8], (1, 40, 50), hp.HP_U8)
+    assert np.array_equal(to_numpy(y), const)
+    two = np.zeros((1, 16, 32), dtype=np.uint8)
+    two[0, :, 16:] = 200
+    y = run(p, [to_device(two, hp.HP_U8)], [hp.HP_U8], (1, 16, 32), hp.HP_U8)
+    assert np.array_equal(to_numpy(y)[0], ohe.equalize(two[0])[2])
+
+
+# ------------------------------------------------------- local Laplacian ----
+def _ll_run(p, img):
+    h, w = img.shape[1:]
+    x = to_device(img, hp.HP_U16)
+    return to_numpy(run(p, [x], [hp.HP_U16], (3, h, w), hp.HP_U16))
+
+
+def test_local_laplacian_identity_parameters_full_size():
+    h, w = 1536, 2560
+    img = synth.rgb_u16_gradient_noise(h, w, seed=0)
+    p, ids = pipelines.local_laplacian(levels=8, k_levels=8, alpha=1.0, beta=1.0)
+    plain = _ll_run(p, img)
+    pipelines.local_laplacian_fused_schedule(p, ids)
+    fused = _ll_run(p, img)
+    assert np.array_equal(fused, plain)
+    # the oracle returns the input exactly for alpha = beta = 1
+    ok, n_b = u16_close(fused, img.astype(np.float64) / 65535.0)
+    diff = np.abs(fused.astype(np.int64) - img.astype(np.int64))
+    print(f"LL identity: max |diff| {diff.max()} LSB, {int((diff > 0).sum())} pixels off by one")
+    assert diff.max() <= 1
+
+
+@pytest.mark.parametrize("h,w,levels", [(192, 320, 6), (37, 53, 4)])
+def test_local_laplacian_detail_enhance_against_oracle(h, w, levels):
+    img = synth.rgb_u16_gradient_noise(h, w, seed=1)
+    ref = oll.local_laplacian_float(img, levels=levels, k_levels=8, sigma_r=0.1, alpha=0.25, beta=1.0)
+    p, ids = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=0.25, beta=1.0)
+    plain = _ll_run(p, img)
+    ok, n_b = u16_close(plain, ref)
+    print(f"LL alpha=0.25 {w}x{h}: {n_b} boundary pixels differ by one LSB")
+    assert ok
+    pipelines.local_laplacian_fused_schedule(p, ids, tile=16)
+    assert np.array_equal(_ll_run(p, img), plain)
