@@ -185,6 +185,9 @@ int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);
 const char* cuda_error_string(int e);
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// minus the kernel's static shared memory.  Returns a cudaError_t as int.
+int allow_max_dynamic_smem(const void* func);
 
 extern unsigned long long g_launches;
 

@@ -306,11 +306,11 @@ int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype) {
 }
 
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
-  static int configured = 0;
-  if (smem_bytes > configured) {
-    int e = cudaFuncSetAttribute(k_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  static bool configured = false;
+  if (smem_bytes > 48 * 1024 && !configured) {
+    int e = allow_max_dynamic_smem((const void*)k_chain);
     if (e) return e;
-    configured = 227 * 1024;
+    configured = true;
   }
   ChainKParams kp;
   memset(&kp, 0, sizeof kp);

@@ -150,11 +150,11 @@ __global__ void __launch_bounds__(1024) k_generic(const __grid_constant__ GPlan 
 }  // namespace
 
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream) {
-  static int configured = 0;
-  if (smem_bytes > configured) {
-    int e = cudaFuncSetAttribute(k_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  static bool configured = false;
+  if (smem_bytes > 48 * 1024 && !configured) {
+    int e = allow_max_dynamic_smem((const void*)k_generic);
     if (e) return e;
-    configured = 227 * 1024;
+    configured = true;
   }
   dim3 grid(g.tiles_x, g.tiles_y, 1);
   k_generic<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(g);
@@ -163,5 +163,17 @@ int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream) {
 }
 
 const char* cuda_error_string(int e) { return cudaGetErrorString((cudaError_t)e); }
+
+int allow_max_dynamic_smem(const void* func) {
+  cudaFuncAttributes fa;
+  int e = (int)cudaFuncGetAttributes(&fa, func);
+  if (e) return e;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  e = (int)cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e) return e;
+  return (int)cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   optin - (int)fa.sharedSizeBytes);
+}
 
 }  // namespace hp

@@ -53,7 +53,7 @@ bool valid_dtype(int d) { return d >= HP_U8 && d <= HP_U32; }
 
 long long round16(long long v) { return (v + 15) / 16 * 16; }
 
-constexpr int kSmemLimit = 227 * 1024;
+constexpr int kSmemLimit = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 
 struct Stage {
   int kind = 0, op = 0, channels = 1, storage = HP_F32;

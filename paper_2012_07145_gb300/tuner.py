@@ -1,0 +1,146 @@
+"""Benchmark-driven autotuner for fusion depth, tile shape and thread mapping.
+
+The paper's autotuning mode compiles and benchmarks candidate schedules and
+keeps the fastest (Sec. 6, "Autotuning").  Here every candidate is a runtime
+schedule of the same compiled kernels, so a candidate costs one launch
+sequence, not a compile.  The candidate space follows Sec. 4.1-4.3:
+
+  - fusion depth d (how many consecutive stages share a kernel),
+  - tile width (innermost thread dimension 16/32/64 x 4 columns per thread),
+    tile height (powers of two),
+  - threads per block and serial rows per thread (1, 2, 4, 8 plus odd 3, 5, 7
+    and longer segments),
+
+pruned by the rules of Sec. 4.6: hardware limits (shared memory per block,
+threads), too few blocks to keep every SM busy (fewer than 2 x SMs, Sec. 4.3),
+and thread counts that leave most threads idle.  Every timed candidate's
+output is compared bit for bit with the stage-per-kernel result, so tuning
+also checks schedule invariance.  Results go to schedules.json, keyed by
+workload.
+"""
+
+import argparse
+import itertools
+import json
+import os
+import statistics
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+DB_PATH = os.path.join(PKG, "schedules.json")
+SMS = 152
+SMEM_LIMIT = 227 * 1024 - 1024
+
+
+def chain_smem_bytes(depth, tile_w, tile_h):
+    """Mirror of the kernel's shared-memory plan (two ping-pong buffers)."""
+    W0, H0 = tile_w + 4 * depth, tile_h + 4 * depth
+    P = ((W0 + 3) & ~3) + 4
+    BH = min(H0, 256)
+    R = (H0 + BH - 1) // BH * BH
+    return 256 + 2 * P * R * 4
+
+
+def chain_candidates(n_stages, W, H, quick=False):
+    depths = [d for d in (1, 2, 4, 8, 16, 32) if n_stages % d == 0]
+    tws = (32, 64, 128) if not quick else (64, 128)
+    ths = (16, 32, 64, 128) if not quick else (32, 64)
+    threads = (128, 256, 512) if not quick else (256,)
+    serials = (4, 8, 16, 32) if not quick else (8, 16)
+    out = []
+    for d, tw, th, t, s in itertools.product(depths, tws, ths, threads, serials):
+        if chain_smem_bytes(d, tw, th) > SMEM_LIMIT:
+            continue                                   # hardware limit
+        blocks = -(-W // tw) * -(-H // th)
+        if blocks < 2 * SMS and (tw > 32 or th > 16):
+            continue                                   # leaves SMs idle
+        items = (tw // 4) * -(-th // s)
+        if items < t // 2:
+            continue                                   # most threads idle in the last stage
+        out.append(dict(depth=d, tile_w=tw, tile_h=th, threads=t, serial_y=s))
+    return out
+
+
+def time_candidate(p, bi, bo, stream, flush, reps=15):
+    import torch
+    s = stream.cuda_stream
+    p.realize(bi, bo, s)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        p.realize(bi, bo, s)
+        b.record(stream)
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    return statistics.median(x.elapsed_time(y) for x, y in ts)
+
+
+def tune_chain(name, n_stages=32, pattern="alternate", W=2560, H=1536, quick=False, log=print):
+    import torch
+    from . import hp, pipelines, synth
+    img = synth.stencil_input(H, W, seed=0)
+    x = hp.padded_copy(torch.from_numpy(img), "cuda")
+    ref = hp.padded_empty(1, H, W, torch.float32, "cuda")
+    y = hp.padded_empty(1, H, W, torch.float32, "cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    bi = [hp.buffer_from_tensor(x, hp.HP_F32)]
+    p = pipelines.stencil_chain(n_stages, pattern)
+    p.realize(bi, hp.buffer_from_tensor(ref, hp.HP_F32), stream.cuda_stream)
+    plain_ms = time_candidate(p, bi, hp.buffer_from_tensor(y, hp.HP_F32), stream, flush)
+    log(f"plain stage-per-kernel: {plain_ms:.4f} ms")
+    best = None
+    results = []
+    for c in chain_candidates(n_stages, W, H, quick):
+        try:
+            pipelines.chain_schedule(p, **c)
+            ms = time_candidate(p, bi, hp.buffer_from_tensor(y, hp.HP_F32), stream, flush)
+        except hp.HPError as e:
+            log(f"skip {c}: {e}")
+            continue
+        same = torch.equal(y.view(torch.int32), ref.view(torch.int32))
+        if not same:
+            raise RuntimeError(f"schedule {c} changed the result: schedules must be bit-identical")
+        results.append((ms, c))
+        if best is None or ms < best[0]:
+            best = (ms, c)
+            log(f"best so far {ms:.4f} ms {c}")
+    results.sort(key=lambda r: r[0])
+    return dict(params=best[1], ms=best[0], plain_ms=plain_ms, candidates=len(results),
+                top5=[dict(ms=m, **c) for m, c in results[:5]], device=torch.cuda.get_device_name())
+
+
+def save(name, entry):
+    db = json.load(open(DB_PATH)) if os.path.exists(DB_PATH) else {}
+    db[name] = entry
+    with open(DB_PATH, "w") as f:
+        json.dump(db, f, indent=1, sort_keys=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="chain32")
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--out", default=None, help="also write the entry to this JSON file")
+    args = ap.parse_args()
+    sys.path.insert(0, os.path.dirname(PKG))
+    import __graft_entry__
+    __graft_entry__.build()
+    if args.config == "chain32":
+        e = tune_chain("chain32", 32, "alternate", 2560, 1536, args.quick)
+    elif args.config == "chain4":
+        e = tune_chain("chain4", 4, "binomial", 512, 512, args.quick)
+    else:
+        raise SystemExit(f"unknown config {args.config}")
+    save(args.config, e)
+    if args.out:
+        json.dump({args.config: e}, open(args.out, "w"), indent=1)
+    print(json.dumps({args.config: e}))
+
+
+if __name__ == "__main__":
+    main()
