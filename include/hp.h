@@ -209,6 +209,17 @@ hp_status hp_group_count(hp_pipeline* p, int* n_groups);
 hp_status hp_infer_bounds(hp_pipeline* p, const int* in_widths, const int* in_heights,
                           int group, int x0, int y0, int w, int h, int* rects, int n_rects);
 
+/* Pipeline options.
+ * HP_OPT_CUDA_GRAPH (0/1, default 0): replay each realize as a CUDA graph.  The
+ *   launch sequence is captured per set of buffer addresses (input and output
+ *   pointers and strides): the first realize with new addresses runs
+ *   uncaptured, the second captures and instantiates a graph, later ones launch
+ *   it with one cudaGraphLaunch on the caller's stream.  Up to 16 graphs are
+ *   kept per input size (least recently used evicted).  Capture happens on a
+ *   private stream, so the caller's stream may be the legacy default stream. */
+enum { HP_OPT_CUDA_GRAPH = 1 };
+hp_status hp_set_option(hp_pipeline* p, int option, long long value);
+
 /* Reads and clears the pipeline's device error word (synchronises the device).
  * *code: 0 = no error; 1 = a bounded TMA/mbarrier wait gave up; 2 = a fused
  * kernel's read fell outside the tile bounds inference gave it (the read was

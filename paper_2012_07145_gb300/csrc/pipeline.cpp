@@ -86,14 +86,26 @@ struct Scratch {
   size_t bytes = 0;
 };
 
+// A captured launch sequence for one set of buffer addresses.
+struct GraphEntry {
+  std::vector<long long> key;    // data pointers and strides of the inputs and the output
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;
+  unsigned long long last_use = 0;
+};
+
 struct Plan {
   std::vector<Dom> dom;          // per stage
   std::vector<Dom> in_dom;       // per input
   std::vector<GroupPlan> groups; // in execution order
   std::map<int, Scratch> bufs;   // exported stage -> device buffer
   std::vector<Scratch> staging;  // hp_realize_host device copies (inputs..., output)
+  std::vector<GraphEntry> graphs;
+  std::vector<std::vector<long long>> seen;  // keys realized once without a graph
   bool allocated = false;
 };
+
+constexpr size_t kMaxGraphs = 16;
 
 }  // namespace
 }  // namespace hp
@@ -108,6 +120,9 @@ struct hp_pipeline {
   std::vector<int> tile_w, tile_h, threads, serial_y, impl;
   std::map<std::vector<int>, std::unique_ptr<hp::Plan>> plans;
   int* d_err = nullptr;
+  bool use_graph = false;
+  cudaStream_t capture_stream = nullptr;
+  unsigned long long uses = 0;
 };
 
 namespace hp {
@@ -625,6 +640,9 @@ hp_status get_plan(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan** out) {
 }
 
 void free_plan(Plan& plan) {
+  for (auto& g : plan.graphs) cudaGraphExecDestroy(g.exec);
+  plan.graphs.clear();
+  plan.seen.clear();
   for (auto& kv : plan.bufs) cudaFree(kv.second.ptr);
   for (auto& sc : plan.staging) cudaFree(sc.ptr);
   plan.bufs.clear();
@@ -692,6 +710,73 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
     }
     if (e) return cuda_fail(e, "kernel launch");
   }
+  return HP_OK;
+}
+
+// Replays the launch sequence as a CUDA graph.  The first realize for a set of
+// buffer addresses runs uncaptured (it also sets kernel attributes); the second
+// captures the sequence on a private stream and every later one launches the
+// instantiated graph on the caller's stream.
+hp_status run_graph(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, int n_inputs, const hp_buffer* output,
+                    void* stream) {
+  std::vector<long long> key;
+  for (int i = 0; i <= n_inputs; ++i) {
+    const hp_buffer& b = i < n_inputs ? inputs[i] : *output;
+    key.push_back((long long)(uintptr_t)b.data);
+    key.push_back(b.row_stride_bytes);
+    key.push_back(b.plane_stride_bytes);
+  }
+  ++p->uses;
+  for (GraphEntry& g : plan.graphs) {
+    if (g.key != key) continue;
+    g.last_use = p->uses;
+    int e = cudaGraphLaunch(g.exec, (cudaStream_t)stream);
+    if (e) return cuda_fail(e, "cudaGraphLaunch");
+    __atomic_add_fetch(&g_launches, g.kernels, __ATOMIC_RELAXED);
+    return HP_OK;
+  }
+  if (std::find(plan.seen.begin(), plan.seen.end(), key) == plan.seen.end()) {
+    if (plan.seen.size() > 4 * kMaxGraphs) plan.seen.clear();
+    plan.seen.push_back(key);
+    return run_groups(p, plan, inputs, output, stream);
+  }
+  if (!p->capture_stream) {
+    int e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking);
+    if (e) return cuda_fail(e, "cudaStreamCreate");
+  }
+  // capture only records; the graph launch below orders after the caller's work
+  unsigned long long before = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+  int e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e) return cuda_fail(e, "cudaStreamBeginCapture");
+  hp_status st = run_groups(p, plan, inputs, output, p->capture_stream);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(p->capture_stream, &graph);
+  unsigned long long kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - before;
+  __atomic_sub_fetch(&g_launches, kernels, __ATOMIC_RELAXED);  // captured, not executed
+  if (st) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e) return cuda_fail(e, "cudaStreamEndCapture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e) return cuda_fail(e, "cudaGraphInstantiate");
+  if (plan.graphs.size() >= kMaxGraphs) {
+    auto lru = std::min_element(plan.graphs.begin(), plan.graphs.end(),
+                                [](const GraphEntry& a, const GraphEntry& b) { return a.last_use < b.last_use; });
+    cudaGraphExecDestroy(lru->exec);
+    plan.graphs.erase(lru);
+  }
+  GraphEntry g;
+  g.key = key;
+  g.exec = exec;
+  g.kernels = kernels;
+  g.last_use = p->uses;
+  plan.graphs.push_back(g);
+  e = cudaGraphLaunch(exec, (cudaStream_t)stream);
+  if (e) return cuda_fail(e, "cudaGraphLaunch");
+  __atomic_add_fetch(&g_launches, kernels, __ATOMIC_RELAXED);
   return HP_OK;
 }
 
@@ -826,7 +911,8 @@ hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, cons
     cudaMemset(p->d_err, 0, 16);
   }
   if ((s = ensure_scratch(p, *plan))) return s;
-  return run_groups(p, *plan, inputs, output, stream);
+  if (!p->use_graph) return run_groups(p, *plan, inputs, output, stream);
+  return run_graph(p, *plan, inputs, n_inputs, output, stream);
 }
 
 hp_status hp_realize_host(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output,
@@ -979,9 +1065,28 @@ hp_status hp_check_device_error(hp_pipeline* p, int* code) {
   return HP_OK;
 }
 
+hp_status hp_set_option(hp_pipeline* p, int option, long long value) {
+  if (!p) return fail(HP_ERR_INVALID_ARG, "null pipeline");
+  switch (option) {
+    case HP_OPT_CUDA_GRAPH:
+      if (p->use_graph != (value != 0)) {
+        for (auto& kv : p->plans) {
+          for (auto& g : kv.second->graphs) cudaGraphExecDestroy(g.exec);
+          kv.second->graphs.clear();
+          kv.second->seen.clear();
+        }
+      }
+      p->use_graph = value != 0;
+      return HP_OK;
+    default:
+      return fail(HP_ERR_INVALID_ARG, "unknown option %d", option);
+  }
+}
+
 hp_status hp_pipeline_destroy(hp_pipeline* p) {
   if (!p) return fail(HP_ERR_INVALID_ARG, "null pipeline");
   drop_plans(p);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   if (p->d_err) cudaFree(p->d_err);
   delete p;
   return HP_OK;

@@ -20,6 +20,7 @@ HP_STENCIL, HP_POINTWISE, HP_DOWNSAMPLE2, HP_UPSAMPLE2, HP_HISTOGRAM, HP_CDF_LUT
 (HP_OP_GRAY, HP_OP_MUL, HP_OP_ADD, HP_OP_SUB, HP_OP_HARRIS, HP_OP_UNSHARP, HP_OP_LL_REMAP, HP_OP_LL_INTERP,
  HP_OP_LL_COLOUR, HP_OP_SELECT, HP_OP_SCALE) = range(11)
 HP_INLINE = -1
+HP_OPT_CUDA_GRAPH = 1
 HP_IMPL_AUTO, HP_IMPL_GENERIC = 0, 1
 (HP_KERNEL_STENCIL_CHAIN, HP_KERNEL_UNSHARP, HP_KERNEL_HARRIS, HP_KERNEL_GENERIC, HP_KERNEL_POINTWISE,
  HP_KERNEL_DOWNSAMPLE, HP_KERNEL_UPSAMPLE, HP_KERNEL_HISTOGRAM, HP_KERNEL_CDF_LUT, HP_KERNEL_LUT_APPLY) = range(10)
@@ -57,7 +58,7 @@ class GroupInfo(ctypes.Structure):
 
 
 EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_set", "hp_realize",
-           "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_check_device_error",
+           "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count"]
 
 _lib = None
@@ -82,6 +83,7 @@ def lib():
         L.hp_infer_bounds.argtypes = [P, _IP, _IP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, _IP, ctypes.c_int]
         L.hp_check_device_error.argtypes = [P, _IP]
+        L.hp_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
         L.hp_pipeline_destroy.argtypes = [P]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
@@ -199,6 +201,12 @@ class Pipeline:
     def realize_host(self, inputs, output, stream=None):
         arr = (Buffer * len(inputs))(*inputs)
         check(lib().hp_realize_host(self.h, arr, len(inputs), ctypes.byref(output), ctypes.c_void_p(stream or 0)))
+
+    def set_option(self, option: int, value: int):
+        check(lib().hp_set_option(self.h, option, value))
+
+    def use_cuda_graph(self, on: bool = True):
+        self.set_option(HP_OPT_CUDA_GRAPH, 1 if on else 0)
 
     def device_error(self) -> int:
         """Reads and clears the device error word (0 = none); synchronises."""

@@ -101,9 +101,11 @@ def histeq() -> hp.Pipeline:
 
 
 def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, alpha: float = 1.0,
-                    beta: float = 1.0):
+                    beta: float = 1.0, out_storage: int = hp.HP_U16):
     """Local Laplacian filter (Paris et al.; K discrete intensity levels) of a
-    u16 RGB image.  Returns (pipeline, stage-id map)."""
+    u16 RGB image.  The output is u16 (rounded from out * 65535), or with
+    out_storage = HP_F32 the float result in [0, 1] units before quantisation.
+    Returns (pipeline, stage-id map)."""
     J, K = levels, k_levels
     p = hp.Pipeline([hp.HP_U16], [3])
     ids = {}
@@ -123,8 +125,9 @@ def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, al
     for l in range(J - 2, -1, -1):
         UR[l] = p.add_stage(hp.HP_UPSAMPLE2, [R[l + 1], Lout[l]], 1, F)
         R[l] = p.add_stage(hp.HP_POINTWISE, [Lout[l], UR[l]], 1, F, op=hp.HP_OP_ADD)
-    out = p.add_stage(hp.HP_POINTWISE, [p.input(0), gray, R[0]], 3, hp.HP_U16, op=hp.HP_OP_LL_COLOUR,
-                      params=[1.0 / 65535.0, 65535.0])
+    out_scale = 65535.0 if out_storage == hp.HP_U16 else 1.0
+    out = p.add_stage(hp.HP_POINTWISE, [p.input(0), gray, R[0]], 3, out_storage, op=hp.HP_OP_LL_COLOUR,
+                      params=[1.0 / 65535.0, out_scale])
     p.set_output(out)
     ids.update(gray=gray, G=G, U=U, L=L, Lout=Lout, R=R, UR=UR, out=out)
     return p, ids

@@ -64,7 +64,8 @@ def chain_candidates(n_stages, W, H, quick=False):
 def time_candidate(p, bi, bo, stream, flush, reps=15):
     import torch
     s = stream.cuda_stream
-    p.realize(bi, bo, s)
+    p.realize(bi, bo, s)   # uncaptured first run
+    p.realize(bi, bo, s)   # graph capture
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
@@ -90,6 +91,7 @@ def tune_chain(name, n_stages=32, pattern="alternate", W=2560, H=1536, quick=Fal
     stream = torch.cuda.current_stream()
     bi = [hp.buffer_from_tensor(x, hp.HP_F32)]
     p = pipelines.stencil_chain(n_stages, pattern)
+    p.use_cuda_graph(True)
     p.realize(bi, hp.buffer_from_tensor(ref, hp.HP_F32), stream.cuda_stream)
     plain_ms = time_candidate(p, bi, hp.buffer_from_tensor(y, hp.HP_F32), stream, flush)
     log(f"plain stage-per-kernel: {plain_ms:.4f} ms")

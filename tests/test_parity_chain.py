@@ -92,3 +92,19 @@ def test_low_precision_storage_is_schedule_invariant_and_error_is_stated(dtype, 
     print(f"storage {dtype}: rel err vs oracle on rounded input {e1:.3e}, on original input {e2:.3e}")
     # stated, not gated: only a sanity bound (the output range of a 32-stage chain is ~0.1)
     assert np.isfinite(e1) and e1 < (0.3 if dtype == hp.HP_BF16 else 0.05)
+
+
+def test_cuda_graph_replay_matches_and_counts_launches():
+    img = synth.stencil_input(300, 200, seed=9)
+    p = pipelines.stencil_chain(32, "alternate")
+    pipelines.chain_schedule(p, depth=8, tile_w=64, tile_h=32)
+    ref = chain_run(p, img)
+    p.use_cuda_graph(True)
+    x = to_device(img, hp.HP_F32)
+    y = torch.zeros_like(ref)
+    for i in range(4):   # uncaptured, capture, replay, replay
+        n0 = hp.launch_count()
+        run(p, [x], [hp.HP_F32], None, hp.HP_F32, out=y)
+        assert hp.launch_count() - n0 == 4
+        assert torch.equal(bits(y), bits(ref))
+        y.zero_()
