@@ -208,6 +208,13 @@ def run_ours(args, cfg_name):
     yout = hp.padded_empty(C, H, W, torch.float32, "cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    if args.only_fused:   # profiling runs: the fused pipeline alone, nothing else on the GPU
+        p = cfg["build"]()
+        cfg["fused"](p)
+        ms, launches, _ = time_steps(p, xin, yout, args.steps, args.warmup, flush, stream, cfg["dtype"])
+        if rank == 0:
+            print(json.dumps({"only_fused": cfg["workload"], "ms_per_step": ms, "launches": launches}))
+        return None
     # stage-per-kernel comparator
     p_plain = cfg["build"]()
     p_plain.use_cuda_graph(True)
@@ -369,6 +376,8 @@ def main():
     ap.add_argument("--config", default="chain32")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--only-fused", action="store_true",
+                    help="time the fused pipeline only (for profiler runs); prints no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
