@@ -39,6 +39,7 @@ struct ChainGeom {
   int P;        // row pitch of both buffers (floats)
   int BH, nby;  // TMA box rows and boxes stacked along y
   int R;        // rows allocated per buffer
+  int buf;      // floats per buffer (a multiple of 32, so buffer B stays 128-byte aligned)
 };
 
 __host__ __device__ inline ChainGeom chain_geom(int depth, int tw, int th) {
@@ -49,15 +50,21 @@ __host__ __device__ inline ChainGeom chain_geom(int depth, int tw, int th) {
   g.BH = g.H0 < 256 ? g.H0 : 256;
   g.nby = (g.H0 + g.BH - 1) / g.BH;
   g.R = g.nby * g.BH;
+  g.buf = (g.P * g.R + 31) & ~31;
   return g;
 }
 
-constexpr int kSmemHeader = 128;  // mbarrier + alignment slack
+constexpr int kSmemHeader = 128;  // mbarrier, status word, alignment slack
+
+// How stage 0 reaches shared memory.
+enum { kLoadClamped = 0, kLoadTmaDirect = 1, kLoadTmaStaged = 2 };
 
 struct ChainKParams {
   CUtensorMap tmap;
   ChainArgs a;
-  int use_tma;
+  int load_mode;
+  int off;   // staged: column of the image's x = xin inside the staged box
+  int sbw;   // staged: box width in elements
 };
 
 template <int RND>
@@ -99,47 +106,51 @@ struct SmemSink {
   }
 };
 
+// ODT: 0 f32, 1 f16, 2 bf16, 3 any dtype (element-wise store_px).
+template <int ODT>
 struct GlobalSink {
-  const ChainArgs* a;
-  int ox, oy, ch;
+  char* row0;        // output plane of this channel at the tile's first row
+  long long rs;
+  int ox, hlim, wlim;  // rows / columns of the tile inside the image
+  int epi;
+  float amount;
+  ImgView out, in;
+  int ch, oy;
   __device__ __forceinline__ void put(int b, int y, float4 v) const {
-    const int gy = oy + y;
-    const int gx = ox + 4 * b;
-    if (gy >= a->out.h || gx >= a->out.w) return;
-    const int odt = a->out.dtype;
-    if (a->epilogue == 1) {
+    const int x = 4 * b;
+    if (y >= hlim || x >= wlim) return;
+    if (epi) {
+      const int gx = ox + x, gy = oy + y;
       float vin[4];
-      for (int i = 0; i < 4; ++i) vin[i] = gx + i < a->in.w ? load_px(a->in, ch, gx + i, gy) : 0.0f;
-      v.x = round_storage(odt, op_unsharp(vin[0], v.x, a->amount));
-      v.y = round_storage(odt, op_unsharp(vin[1], v.y, a->amount));
-      v.z = round_storage(odt, op_unsharp(vin[2], v.z, a->amount));
-      v.w = round_storage(odt, op_unsharp(vin[3], v.w, a->amount));
+#pragma unroll
+      for (int i = 0; i < 4; ++i) vin[i] = x + i < wlim ? load_px(in, ch, gx + i, gy) : 0.0f;
+      v.x = round_storage(out.dtype, op_unsharp(vin[0], v.x, amount));
+      v.y = round_storage(out.dtype, op_unsharp(vin[1], v.y, amount));
+      v.z = round_storage(out.dtype, op_unsharp(vin[2], v.z, amount));
+      v.w = round_storage(out.dtype, op_unsharp(vin[3], v.w, amount));
     }
-    char* row = (char*)a->out.data + (long long)ch * a->out.ps + (long long)gy * a->out.rs;
-    if (gx + 3 < a->out.w) {
-      if (odt == HP_F32) {
+    char* row = row0 + (long long)y * rs;
+    const int gx = ox + x;
+    if (ODT != 3 && x + 3 < wlim) {
+      if (ODT == 0) {
         *reinterpret_cast<float4*>(row + 4LL * gx) = v;
-        return;
-      }
-      if (odt == HP_F16) {
-        __half2 p0 = __floats2half2_rn(v.x, v.y), p1 = __floats2half2_rn(v.z, v.w);
+      } else {
         uint2 u;
-        u.x = *reinterpret_cast<unsigned*>(&p0);
-        u.y = *reinterpret_cast<unsigned*>(&p1);
+        if (ODT == 1) {
+          __half2 p0 = __floats2half2_rn(v.x, v.y), p1 = __floats2half2_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        } else {
+          __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        }
         *reinterpret_cast<uint2*>(row + 2LL * gx) = u;
-        return;
       }
-      if (odt == HP_BF16) {
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
-        uint2 u;
-        u.x = *reinterpret_cast<unsigned*>(&p0);
-        u.y = *reinterpret_cast<unsigned*>(&p1);
-        *reinterpret_cast<uint2*>(row + 2LL * gx) = u;
-        return;
-      }
+      return;
     }
     const float vv[4] = {v.x, v.y, v.z, v.w};
-    for (int i = 0; i < 4 && gx + i < a->out.w; ++i) store_px(a->out, ch, gx + i, gy, vv[i]);
+    for (int i = 0; i < 4 && x + i < wlim; ++i) store_px(out, ch, gx + i, oy + y, vv[i]);
   }
 };
 
@@ -186,17 +197,6 @@ __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int 
   }
 }
 
-template <class Sink>
-__device__ __forceinline__ void sweep_any(int rkind, const float* src, int P, int Ws, int Hs, int seg,
-                                          const float* wx, const float* wy, int dtype, const Sink& sink) {
-  switch (rkind) {
-    case 0: sweep<0>(src, P, Ws, Hs, seg, wx, wy, dtype, sink); break;
-    case 1: sweep<1>(src, P, Ws, Hs, seg, wx, wy, dtype, sink); break;
-    case 2: sweep<2>(src, P, Ws, Hs, seg, wx, wy, dtype, sink); break;
-    default: sweep<3>(src, P, Ws, Hs, seg, wx, wy, dtype, sink); break;
-  }
-}
-
 // Replicates the in-image edge of a stage rectangle (origin (x0, y0) in image
 // coordinates, Ws x Hs) into its out-of-image part.
 __device__ void fixup(float* buf, int P, int x0, int y0, int Ws, int Hs, int W, int H) {
@@ -223,19 +223,23 @@ __device__ void fixup(float* buf, int P, int x0, int y0, int Ws, int Hs, int W, 
   }
 }
 
-__device__ __forceinline__ int rkind_of(int dtype) {
-  return dtype == HP_F32 ? 0 : dtype == HP_F16 ? 1 : dtype == HP_BF16 ? 2 : 3;
+__device__ __forceinline__ float staged_value(const unsigned char* st, int idx, int dtype) {
+  if (dtype == HP_F16) return __half2float(reinterpret_cast<const __half*>(st)[idx]);
+  if (dtype == HP_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(st)[idx]);
+  return reinterpret_cast<const float*>(st)[idx];
 }
 
+template <int RND, int ODT>
 __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKParams kp) {
   const ChainArgs& a = kp.a;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base);
+  volatile int* status = reinterpret_cast<volatile int*>(base + 64);
   const int d = a.depth;
   const ChainGeom g = chain_geom(d, a.tile_w, a.tile_h);
   float* bufA = reinterpret_cast<float*>(base + kSmemHeader);
-  float* bufB = bufA + g.P * g.R;
+  float* bufB = bufA + g.buf;
   const int ch = blockIdx.z;
   const int ox = blockIdx.x * a.tile_w, oy = blockIdx.y * a.tile_h;
   const int W = a.in.w, H = a.in.h;
@@ -243,29 +247,42 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
   const bool border = xin < 0 || yin < 0 || xin + g.W0 > W || yin + g.H0 > H;
 
   // ---- stage 0: input tile + halo ----
-  if (kp.use_tma) {
+  if (kp.load_mode != kLoadClamped) {
+    const bool direct = kp.load_mode == kLoadTmaDirect;
+    const int esize = a.in.dtype == HP_F32 ? 4 : 2;
+    const int bw = direct ? g.P : kp.sbw;
+    unsigned char* dst = direct ? reinterpret_cast<unsigned char*>(bufA) : reinterpret_cast<unsigned char*>(bufB);
     if (threadIdx.x == 0) {
+      *status = 0;
       mbar_init(bar, 1);
       fence_mbar_init();
+      mbar_arrive_expect_tx(bar, (unsigned)(g.nby * g.BH * bw * esize));
+      for (int k = 0; k < g.nby; ++k)
+        tma_load_3d(dst + (size_t)k * g.BH * bw * esize, &kp.tmap, xin - kp.off, yin + k * g.BH, ch, bar);
+      // one thread waits (bounded); the others sleep in the barrier below
+      if (!mbar_wait_bounded(bar, 0, 1u << 26)) *status = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      mbar_arrive_expect_tx(bar, (unsigned)(g.nby * g.BH * g.P * 4));
-      for (int k = 0; k < g.nby; ++k) tma_load_3d(bufA + k * g.BH * g.P, &kp.tmap, xin, yin + k * g.BH, ch, bar);
-    }
-    if (!mbar_wait_bounded(bar, 0, 1u << 26)) {
+    if (*status) {
       if (threadIdx.x == 0) atomicExch(a.err, 1);
       return;
+    }
+    if (!direct) {
+      // convert to f32 and shift to column 0 of buffer A (row-wise, coalesced)
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int y = warp; y < g.H0; y += nw)
+        for (int x = lane; x < g.W0; x += 32)
+          bufA[y * g.P + x] = staged_value(dst, y * bw + x + kp.off, a.in.dtype);
+      __syncthreads();
     }
     if (border) {
       fixup(bufA, g.P, xin, yin, g.W0, g.H0, W, H);
     }
   } else {
-    const int n = g.W0 * g.H0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      int y = i / g.W0;
-      int x = i - y * g.W0;
-      bufA[y * g.P + x] = load_px(a.in, ch, iclamp(xin + x, 0, W - 1), iclamp(yin + y, 0, H - 1));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int y = warp; y < g.H0; y += nw) {
+      const int gy = iclamp(yin + y, 0, H - 1);
+      for (int x = lane; x < g.W0; x += 32) bufA[y * g.P + x] = load_px(a.in, ch, iclamp(xin + x, 0, W - 1), gy);
     }
   }
   __syncthreads();
@@ -283,18 +300,45 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       wy[k] = a.w[s - 1][5 + k];
     }
     const int dt = a.storage[s - 1];
-    const int rk = rkind_of(dt);
     if (s < d) {
-      sweep_any(rk, src, g.P, Ws, Hs, a.seg, wx, wy, dt, SmemSink{dst, g.P});
+      sweep<RND>(src, g.P, Ws, Hs, a.seg, wx, wy, dt, SmemSink{dst, g.P});
       if (border) {
         __syncthreads();
         fixup(dst, g.P, ox - 2 * (d - s), oy - 2 * (d - s), Ws, Hs, W, H);
       }
       __syncthreads();
     } else {
-      sweep_any(rk, src, g.P, Ws, Hs, a.seg, wx, wy, dt, GlobalSink{&a, ox, oy, ch});
+      GlobalSink<ODT> gs;
+      gs.rs = a.out.rs;
+      gs.row0 = (char*)a.out.data + (long long)ch * a.out.ps + (long long)oy * a.out.rs;
+      gs.ox = ox;
+      gs.oy = oy;
+      gs.hlim = min(a.tile_h, a.out.h - oy);
+      gs.wlim = min(a.tile_w, a.out.w - ox);
+      gs.epi = a.epilogue;
+      gs.amount = a.amount;
+      gs.out = a.out;
+      gs.in = a.in;
+      gs.ch = ch;
+      sweep<RND>(src, g.P, Ws, Hs, a.seg, wx, wy, dt, gs);
     }
   }
+}
+
+typedef void (*ChainKernel)(ChainKParams);
+
+// Picks the instantiation: one rounding kind for every stage and a vector
+// store for the output type when they agree, else the general one.
+ChainKernel pick_kernel(const ChainArgs& a, int* variant) {
+  int s0 = a.storage[0];
+  bool uniform = true;
+  for (int i = 1; i < a.depth; ++i) uniform &= a.storage[i] == s0;
+  const bool same_out = a.out.dtype == s0 || a.epilogue;
+  if (uniform && same_out && s0 == HP_F32 && a.out.dtype == HP_F32) { *variant = 0; return k_chain<0, 0>; }
+  if (uniform && same_out && s0 == HP_F16 && a.out.dtype == HP_F16) { *variant = 1; return k_chain<1, 1>; }
+  if (uniform && same_out && s0 == HP_BF16 && a.out.dtype == HP_BF16) { *variant = 2; return k_chain<2, 2>; }
+  *variant = 3;
+  return k_chain<3, 3>;
 }
 
 }  // namespace
@@ -302,28 +346,48 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
 int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype) {
   (void)in_dtype;
   ChainGeom g = chain_geom(depth, tile_w, tile_h);
-  return kSmemHeader + 128 + 2 * g.P * g.R * 4;
+  return kSmemHeader + 128 + 2 * g.buf * 4;
 }
 
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
-  static bool configured = false;
-  if (smem_bytes > 48 * 1024 && !configured) {
-    int e = allow_max_dynamic_smem((const void*)k_chain);
+  static bool configured[4] = {false, false, false, false};
+  int variant = 0;
+  ChainKernel kern = pick_kernel(a, &variant);
+  if (smem_bytes > 48 * 1024 && !configured[variant]) {
+    int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
-    configured = true;
+    configured[variant] = true;
   }
   ChainKParams kp;
   memset(&kp, 0, sizeof kp);
   kp.a = a;
   ChainGeom g = chain_geom(a.depth, a.tile_w, a.tile_h);
-  kp.use_tma = a.in.dtype == HP_F32 && (2 * a.depth * 4) % 16 == 0 && g.P <= 256 && g.BH <= 256;
-  if (kp.use_tma) {
-    int e = encode_tmap_3d(&kp.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs,
-                           a.in.ps, g.P, g.BH);
-    if (e) kp.use_tma = 0;  // fall back to clamped loads
+  const int dt = a.in.dtype;
+  // every tile's x origin is a multiple of tile_w, itself a multiple of 8, so
+  // the halo origin's alignment is that of -2d for every tile
+  const int xin = -2 * a.depth;
+  kp.load_mode = kLoadClamped;
+  if (dt == HP_F32 || dt == HP_F16 || dt == HP_BF16) {
+    const int esize = dt == HP_F32 ? 4 : 2;
+    const int align = 16 / esize;
+    const int off = ((xin % align) + align) % align;
+    CUtensorMapDataType tdt = dt == HP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                              : dt == HP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (dt == HP_F32 && off == 0 && g.P <= 256) {
+      if (!encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, g.P, g.BH))
+        kp.load_mode = kLoadTmaDirect;
+    } else {
+      const int sbw = (g.W0 + off + align - 1) / align * align;
+      if (sbw <= 256 && (long long)g.nby * g.BH * sbw * esize <= (long long)g.buf * 4 &&
+          !encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, sbw, g.BH)) {
+        kp.load_mode = kLoadTmaStaged;
+        kp.off = off;
+        kp.sbw = sbw;
+      }
+    }
   }
   dim3 grid(a.tiles_x, a.tiles_y, a.in.c);
-  k_chain<<<grid, a.threads, smem_bytes, (cudaStream_t)stream>>>(kp);
+  kern<<<grid, a.threads, smem_bytes, (cudaStream_t)stream>>>(kp);
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

@@ -119,14 +119,27 @@ def test_local_laplacian_identity_parameters_full_size():
     assert diff.max() <= 1
 
 
-@pytest.mark.parametrize("h,w,levels", [(192, 320, 6), (37, 53, 4)])
-def test_local_laplacian_detail_enhance_against_oracle(h, w, levels):
+# With alpha < 1 the remap r(i) = g + sign(d) sigma (|d|/sigma)^alpha has an
+# unbounded slope at d = i - g = 0: an FP32 rounding of d (about 1e-8 here)
+# moves r by up to sigma^(1-alpha) |delta d|^alpha.  Pixels whose gray value
+# lies that close to a level g_k therefore carry an error set by the
+# conditioning of the method, not by the kernels.  Bound used (float output,
+# [0,1] units): max error 1e-4 (6.6 LSB of u16) and 99.9th percentile 2e-6;
+# u16 output: at most 7 LSB and under 1% of values off by any amount.
+@pytest.mark.parametrize("h,w,levels,alpha", [(192, 320, 6, 0.25), (37, 53, 4, 0.25), (192, 320, 6, 0.5)])
+def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha):
     img = synth.rgb_u16_gradient_noise(h, w, seed=1)
-    ref = oll.local_laplacian_float(img, levels=levels, k_levels=8, sigma_r=0.1, alpha=0.25, beta=1.0)
-    p, ids = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=0.25, beta=1.0)
+    ref = oll.local_laplacian_float(img, levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0)
+    pf, ids_f = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0,
+                                          out_storage=hp.HP_F32)
+    x = to_device(img, hp.HP_U16)
+    yf = to_numpy(run(pf, [x], [hp.HP_U16], (3, h, w), hp.HP_F32))
+    err = np.abs(yf.astype(np.float64) - ref)
+    print(f"LL alpha={alpha} {w}x{h}: float max err {err.max():.3e}, p99.9 {np.percentile(err, 99.9):.3e}")
+    assert err.max() <= 1e-4 and np.percentile(err, 99.9) <= 2e-6
+    p, ids = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0)
     plain = _ll_run(p, img)
-    ok, n_b = u16_close(plain, ref)
-    print(f"LL alpha=0.25 {w}x{h}: {n_b} boundary pixels differ by one LSB")
-    assert ok
+    d = np.abs(plain.astype(np.int64) - oll.quantize_u16(ref).astype(np.int64))
+    assert d.max() <= 7 and (d > 0).mean() < 0.01
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16)
     assert np.array_equal(_ll_run(p, img), plain)
