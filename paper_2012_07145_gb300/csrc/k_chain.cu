@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       for (int k = 0; k < g.nby; ++k)
         tma_load_3d(dst + (size_t)k * g.BH * bw * esize, &kp.tmap, xin - kp.off, yin + k * g.BH, ch, bar);
       // one thread waits (bounded); the others sleep in the barrier below
-      if (!mbar_wait_bounded(bar, 0, 1u << 26)) *status = 1;
+      if (!mbar_wait_bounded(bar, 0, 2000000000ull)) *status = 1;  // gives up after 2 s
     }
     __syncthreads();
     if (*status) {

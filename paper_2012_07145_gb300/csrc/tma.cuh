@@ -38,11 +38,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned phase) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` polls and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase, unsigned limit) {
-  for (unsigned i = 0; i < limit; ++i)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
+// try_wait with a suspend-time hint: the thread sleeps (issuing nothing) until
+// the phase completes or about `hint_ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, unsigned phase, unsigned hint_ns) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: suspended polls until the phase completes or `limit_ns` of
+// wall time pass, then gives up and returns false (the caller reports it).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    if (mbar_try_wait_sleep(bar, phase, 100000u)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
 }
 
 // 3-D tiled load of one box into shared memory; completion is signalled on bar.
