@@ -35,25 +35,124 @@ FP32_LANES_PER_SM = 128
 
 
 # ------------------------------------------------------------------ configs --
+def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
+    from paper_2012_07145_gb300 import hp, pipelines, synth
+    st = {"f32": hp.HP_F32, "f16": hp.HP_F16, "bf16": hp.HP_BF16}[storage_name]
+    esize = 4 if storage_name == "f32" else 2
+    tuned_name = name if storage_name == "f32" else None
+
+    def fused(p):
+        pipelines.chain_schedule(p, **(tuned(tuned_name) if tuned_name else tuned("chain32")))
+
+    def oracle_sample(rows):
+        from oracle import stencil as ost
+        img = synth.stencil_input(rows, W, seed=0)[0].astype(np.float64)
+        return lambda: ost.stencil_chain(img, ost.chain_kinds(n, pattern))
+
+    def parity(out, inputs):
+        from oracle import stencil as ost
+        img = inputs[0][0][0].astype(np.float64)
+        pts = [(0, 0), (W - 1, H - 1), (W // 3, H // 2)]
+        ref = [ost.stencil_chain_point(img, ost.chain_kinds(n, pattern), x, y) for x, y in pts]
+        return max(abs(float(out[0][y, x]) - r) for (x, y), r in zip(pts, ref))
+
+    return dict(workload=f"stencil_chain_{n}_{pattern}_{W}x{H}_{storage_name}", h=H, w=W,
+                inputs=lambda seed: [(synth.stencil_input(H, W, seed=seed), st)], out=(1, H, W, st),
+                build=lambda: pipelines.stencil_chain(n, pattern, storage=st), fused=fused,
+                flops_px=n * 18, bytes_px=2 * esize, bound="alu", kernel="k_chain", dtype=storage_name,
+                oracle_sample=oracle_sample, parity=parity, sample_rows=64)
+
+
 def config_table():
-    from paper_2012_07145_gb300 import hp, pipelines
-    return {
+    from paper_2012_07145_gb300 import hp, pipelines, synth
+    cfgs = {
         # the headline: 32-stage chain, binomial/box alternating, fused + tuned
-        "chain32": dict(workload="stencil_chain_32_alternate_2560x1536_f32", h=1536, w=2560, c=1,
-                        build=lambda: pipelines.stencil_chain(32, "alternate"), dtype=hp.HP_F32,
-                        fused=lambda p: pipelines.chain_schedule(p, **tuned("chain32")),
-                        flops_px=32 * 18, bytes_px=8),
-        "chain4": dict(workload="stencil_chain_4_binomial_512x512_f32", h=512, w=512, c=1,
-                       build=lambda: pipelines.stencil_chain(4, "binomial"), dtype=hp.HP_F32,
-                       fused=lambda p: pipelines.chain_schedule(p, depth=4, tile_w=64, tile_h=32),
-                       flops_px=4 * 18, bytes_px=8),
+        "chain32": _chain_cfg("chain32", 32, "alternate", 1536, 2560),
+        "chain32_f16": _chain_cfg("chain32", 32, "alternate", 1536, 2560, "f16"),
+        "chain32_bf16": _chain_cfg("chain32", 32, "alternate", 1536, 2560, "bf16"),
+        "chain4": _chain_cfg("chain4", 4, "binomial", 512, 512),
     }
+    H, W = 1536, 2560
+
+    def harris_parity(out, inputs):
+        from oracle import harris as ohr
+        rgb = inputs[0][0][:, :64, :64].astype(np.float64)
+        ref = ohr.harris(rgb)[:62, :62]          # rows/cols away from the band's cut edge
+        return float(np.abs(out[0][:62, :62] - ref).max() / (ref.max() - ref.min()))
+
+    def harris_sample(rows):
+        from oracle import harris as ohr
+        rgb = synth.rgb_f32(rows, W, seed=0).astype(np.float64)
+        return lambda: ohr.harris(rgb)
+
+    cfgs["harris"] = dict(workload=f"harris_rgb_{W}x{H}_f32", h=H, w=W,
+                          inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_F32)], out=(1, H, W, hp.HP_F32),
+                          build=lambda: pipelines.harris(), fused=lambda p: pipelines.fused_schedule(p),
+                          flops_px=68, bytes_px=16, bound="hbm", kernel="k_", dtype="f32",
+                          oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
+    UH, UW = 3072, 4096
+
+    def unsharp_sample(rows):
+        from oracle import unsharp as ous
+        img = synth.rgb_f32(rows, UW, seed=0).astype(np.float64)
+        return lambda: ous.unsharp(img)
+
+    def unsharp_parity(out, inputs):
+        from oracle import unsharp as ous
+        img = inputs[0][0][:, :64, :64].astype(np.float64)
+        ref = ous.unsharp(img)[:, :60, :60]
+        return float(np.abs(out[:, :60, :60] - ref).max() / (ref.max() - ref.min()))
+
+    cfgs["unsharp"] = dict(workload=f"unsharp_rgb_{UW}x{UH}_f32", h=UH, w=UW,
+                           inputs=lambda seed: [(synth.rgb_f32(UH, UW, seed=seed), hp.HP_F32)],
+                           out=(3, UH, UW, hp.HP_F32), build=lambda: pipelines.unsharp(),
+                           fused=lambda p: pipelines.fused_schedule(p, tile_w=64, tile_h=32),
+                           flops_px=63, bytes_px=24, bound="hbm", kernel="k_chain", dtype="f32",
+                           oracle_sample=unsharp_sample, parity=unsharp_parity, sample_rows=96)
+
+    def histeq_sample(rows):
+        from oracle import histeq as ohe
+        img = synth.gray_u8_lowcontrast(rows, UW, seed=0)[0]
+        return lambda: ohe.equalize(img)
+
+    def histeq_parity(out, inputs):
+        from oracle import histeq as ohe
+        ref = ohe.equalize(inputs[0][0][0])[2]
+        return int((out[0] != ref).sum())
+
+    cfgs["histeq"] = dict(workload=f"histeq_u8_{UW}x{UH}", h=UH, w=UW,
+                          inputs=lambda seed: [(synth.gray_u8_lowcontrast(UH, UW, seed=seed), hp.HP_U8)],
+                          out=(1, UH, UW, hp.HP_U8), build=lambda: pipelines.histeq(), fused=lambda p: None,
+                          flops_px=0, bytes_px=3, bound="hbm", kernel="k_hist", dtype="u8",
+                          oracle_sample=histeq_sample, parity=histeq_parity, sample_rows=256)
+
+    def ll_build():
+        return pipelines.local_laplacian(levels=8, k_levels=8)[0]
+
+    def ll_fused(p):
+        pl, ids = pipelines.local_laplacian(levels=8, k_levels=8)
+        pipelines.local_laplacian_fused_schedule(p, ids)
+
+    def ll_sample(rows):
+        from oracle import local_laplacian as oll
+        img = synth.rgb_u16_gradient_noise(rows, W, seed=0)
+        return lambda: oll.local_laplacian(img, levels=8, k_levels=8)
+
+    def ll_parity(out, inputs):
+        return int(np.abs(out.astype(np.int64) - inputs[0][0].astype(np.int64)).max())   # identity parameters
+
+    cfgs["ll"] = dict(workload=f"local_laplacian_rgb_u16_{W}x{H}_J8_K8", h=H, w=W,
+                      inputs=lambda seed: [(synth.rgb_u16_gradient_noise(H, W, seed=seed), hp.HP_U16)],
+                      out=(3, H, W, hp.HP_U16), build=ll_build, fused=ll_fused,
+                      flops_px=0, bytes_px=12, bound="hbm", kernel="k_generic", dtype="u16",
+                      oracle_sample=ll_sample, parity=ll_parity, sample_rows=128)
+    return cfgs
 
 
 def tuned(name):
     """Schedule parameters chosen by the autotuner (schedules.json), else defaults."""
     path = os.path.join(ROOT, "paper_2012_07145_gb300", "schedules.json")
-    if os.path.exists(path):
+    if name and os.path.exists(path):
         db = json.load(open(path))
         if name in db:
             return db[name]["params"]
@@ -156,11 +255,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ our arm --
-def time_steps(p, xin, yout, steps, warmup, flush, stream, dtype, sampler=None):
+def time_steps(p, bi, bo, steps, warmup, flush, stream, sampler=None):
     import torch
     from paper_2012_07145_gb300 import hp
-    bi = [hp.buffer_from_tensor(xin, dtype)]
-    bo = hp.buffer_from_tensor(yout, dtype)
     s = stream.cuda_stream
     for _ in range(warmup):
         p.realize(bi, bo, s)
@@ -183,10 +280,39 @@ def time_steps(p, xin, yout, steps, warmup, flush, stream, dtype, sampler=None):
     return statistics.mean(ms), launches, ms
 
 
+def _torch_dtype(dt):
+    import torch
+    from paper_2012_07145_gb300 import hp
+    return {hp.HP_F32: torch.float32, hp.HP_F16: torch.float16, hp.HP_BF16: torch.bfloat16,
+            hp.HP_U8: torch.uint8, hp.HP_U16: torch.int16}[dt]
+
+
+def _host_tensor(arr, dt):
+    """Pinned host tensor of a numpy image in the hp dtype's element type."""
+    import torch
+    from paper_2012_07145_gb300 import hp
+    if dt in (hp.HP_F16, hp.HP_BF16):
+        t = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.float32)).to(_torch_dtype(dt))
+    elif dt == hp.HP_U16:
+        t = torch.from_numpy(np.ascontiguousarray(arr, dtype=np.uint16).view(np.int16))
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(arr))
+    return t.pin_memory()
+
+
+def _to_numpy(t, dt):
+    from paper_2012_07145_gb300 import hp
+    if dt in (hp.HP_F16, hp.HP_BF16):
+        return t.float().cpu().numpy()
+    if dt == hp.HP_U16:
+        return t.cpu().numpy().view(np.uint16)
+    return t.cpu().numpy()
+
+
 def run_ours(args, cfg_name):
     import torch
     import torch.distributed as dist
-    from paper_2012_07145_gb300 import hp, synth, pipelines
+    from paper_2012_07145_gb300 import hp
     import __graft_entry__
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -195,31 +321,34 @@ def run_ours(args, cfg_name):
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    if rank == 0 or world == 1:
+    if rank == 0:
         __graft_entry__.build()
     if world > 1:
         dist.barrier()
         __graft_entry__.build()
     cfg = config_table()[cfg_name]
-    H, W, C = cfg["h"], cfg["w"], cfg["c"]
-    img = synth.stencil_input(H, W, seed=rank)
+    H, W = cfg["h"], cfg["w"]
+    C, OH, OW, odt = cfg["out"]
+    inputs = cfg["inputs"](rank)
     stream = torch.cuda.current_stream()
-    xin = hp.padded_copy(torch.from_numpy(img), "cuda")
-    yout = hp.padded_empty(C, H, W, torch.float32, "cuda")
+    dev_in = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in inputs]
+    yout = hp.padded_empty(C, OH, OW, _torch_dtype(odt), "cuda")
+    bi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dev_in, inputs)]
+    bo = hp.buffer_from_tensor(yout, odt)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     if args.only_fused:   # profiling runs: the fused pipeline alone, nothing else on the GPU
         p = cfg["build"]()
         cfg["fused"](p)
-        ms, launches, _ = time_steps(p, xin, yout, args.steps, args.warmup, flush, stream, cfg["dtype"])
+        ms, launches, _ = time_steps(p, bi, bo, args.steps, args.warmup, flush, stream)
         if rank == 0:
             print(json.dumps({"only_fused": cfg["workload"], "ms_per_step": ms, "launches": launches}))
         return None
     # stage-per-kernel comparator
     p_plain = cfg["build"]()
     p_plain.use_cuda_graph(True)
-    plain_ms, plain_launches, _ = time_steps(p_plain, xin, yout, max(args.steps // 4, 3), args.warmup, flush,
-                                             stream, cfg["dtype"])
+    plain_steps = max(args.steps // 4, 3)
+    plain_ms, plain_launches, _ = time_steps(p_plain, bi, bo, plain_steps, args.warmup, flush, stream)
     # fused, tuned schedule (the headline)
     p = cfg["build"]()
     cfg["fused"](p)
@@ -229,10 +358,10 @@ def run_ours(args, cfg_name):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ms, launches, ms_all = time_steps(p, xin, yout, args.steps, args.warmup, flush, stream, cfg["dtype"],
-                                      sampler)
+    ms, launches, ms_all = time_steps(p, bi, bo, args.steps, args.warmup, flush, stream, sampler)
     clocks = sampler.stop()
     torch.cuda.synchronize()
+    assert p.device_error() == 0, "a kernel reported a device-side error"
     if world > 1:
         dist.barrier()
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
@@ -240,37 +369,45 @@ def run_ours(args, cfg_name):
         ms = float(t.item())
 
     # end to end through the C ABI with pinned host buffers
-    hin = torch.from_numpy(img).pin_memory()
-    hout = torch.empty((C, H, W), dtype=torch.float32).pin_memory()
-    bi = [hp.buffer_from_tensor(hin, cfg["dtype"])]
-    bo = hp.buffer_from_tensor(hout, cfg["dtype"])
+    hin = [_host_tensor(a, dt) for a, dt in inputs]
+    hout = torch.empty((C, OH, OW), dtype=_torch_dtype(odt)).pin_memory()
+    hbi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(hin, inputs)]
+    hbo = hp.buffer_from_tensor(hout, odt)
     for _ in range(3):
-        p.realize_host(bi, bo, stream.cuda_stream)
+        p.realize_host(hbi, hbo, stream.cuda_stream)
     e2e_steps = max(10, min(args.steps, 200))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        p.realize_host(bi, bo, stream.cuda_stream)
+        p.realize_host(hbi, hbo, stream.cuda_stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    out_check = hout.numpy()[0]
-
-    # parity spot check of this run's output against the oracle (a few points)
-    from oracle import stencil as ost
-    kinds = ost.chain_kinds(len(p.stages), "alternate" if cfg_name == "chain32" else "binomial")
-    pts = [(0, 0), (W - 1, H - 1), (W // 3, H // 2)]
-    err = max(abs(float(out_check[y, x]) - ost.stencil_chain_point(img[0].astype(np.float64), kinds, x, y))
-              for x, y in pts)
+    err = cfg["parity"](_to_numpy(hout, odt), inputs)
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return None
-    npx = H * W
+    npx = OH * OW
     peaks, peak_kind = measured_peaks()
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
     launches_per_step = launches / args.steps
     kernel_ms = ms / launches_per_step
-    flops_launch = cfg["flops_px"] * npx / launches_per_step
-    achieved = flops_launch / (kernel_ms * 1e-3) / 1e12
+    if cfg["bound"] == "alu":
+        achieved = cfg["flops_px"] * npx / launches_per_step / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4),
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops (FMA) x {clock_mhz} MHz max SM clock",
+                "algorithmic": f"{cfg['flops_px']} FP32 flops per output pixel (18 per 5x5 stage: 2 passes x (1 mul + 4 fma))"}
+    else:
+        achieved = cfg["bytes_px"] * npx / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "algorithmic": f"{cfg['bytes_px']} bytes per output pixel (input + output once), over the whole step"}
+    roof.update({"traffic": recorded_traffic(cfg["kernel"], cfg["workload"]), "kernel": cfg["kernel"],
+                 "kernel_ms": round(kernel_ms, 5), "launches_per_step": launches_per_step})
+    in_bytes = int(sum(a.nbytes for a, _ in inputs))
+    out_bytes = int(C * OH * OW * hp.DTYPE_BYTES[odt])
     line = {
         "metric": METRIC,
         "value": round(world * npx / (ms * 1e-3) / 1e6, 2),
@@ -282,57 +419,48 @@ def run_ours(args, cfg_name):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded uniform [0,1) image; no dataset)",
-        "config": {"workload": cfg["workload"], "schedule": tuned(cfg_name) if cfg_name == "chain32" else "fused",
+        "dtype": cfg["dtype"],
+        "data": "synthetic (seeded images with the workload's shape and value distribution; no dataset)",
+        "config": {"workload": cfg["workload"],
+                   "schedule": tuned(cfg_name) if cfg_name == "chain32" else "fused (see pipelines.py)",
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
-                   "launch": "CUDA graph replay of the fused launches"},
+                   "launch": "CUDA graph replay"},
         "plain": {"value": round(npx / (plain_ms * 1e-3) / 1e6, 2), "unit": "MPix/s", "ms_per_step": round(plain_ms, 5),
-                  "launches_per_step": plain_launches / max(args.steps // 4, 3),
+                  "launches_per_step": plain_launches / plain_steps,
                   "schedule": "stage-per-kernel (one launch per stage), CUDA graph replay"},
         "speedup_vs_plain": round(plain_ms / ms, 3),
         "e2e": {"value": round(npx / e2e_s / 1e6, 2), "unit": "MPix/s",
-                "h2d_bytes_per_step": int(img.nbytes), "d2h_bytes_per_step": int(img.nbytes)},
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2),
-                     "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
-                     "traffic": recorded_traffic("k_chain", cfg["workload"]),
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} clock)",
-                     "kernel": "k_chain", "kernel_ms": round(kernel_ms, 5),
-                     "hbm_achieved_gbs": round(cfg["bytes_px"] * npx / launches_per_step / (kernel_ms * 1e-3) / 1e9, 1),
-                     "hbm_peak_gbs": peaks.get("hbm_gbs")},
+        "roofline": roof,
         "clocks": clocks,
-        "parity_spot_max_abs_err": err,
+        "parity_spot": err,
         "step_ms_p50": round(statistics.median(ms_all), 5),
         "step_ms_p99": round(float(np.percentile(ms_all, 99)), 5),
     }
     if args.cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cfg_name, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(cfg, seconds=args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return line
 
 
 # ------------------------------------------------------------- oracle (CPU) --
-def cpu_baseline(cfg_name, seconds=15.0, rows=None):
-    """The FP64 oracle, as it stands, on a bounded band of the same workload."""
-    from oracle import stencil as ost
-    from paper_2012_07145_gb300 import synth
-    cfg = config_table()[cfg_name]
-    W = cfg["w"]
-    rows = rows or min(cfg["h"], 256)
-    img = synth.stencil_input(rows, W, seed=0)[0].astype(np.float64)
-    kinds = ost.chain_kinds(32 if cfg_name == "chain32" else 4, "alternate" if cfg_name == "chain32" else "binomial")
+def cpu_baseline(cfg, seconds=15.0):
+    """The oracle, as it stands, on a bounded band of the same workload."""
+    rows = cfg["sample_rows"]
+    fn = cfg["oracle_sample"](rows)
     t0 = time.perf_counter()
     n = 0
     while True:
-        ost.stencil_chain(img, kinds)
+        fn()
         n += 1
         if time.perf_counter() - t0 >= seconds * 0.5:
             break
     dt = (time.perf_counter() - t0) / n
-    return {"value": round(rows * W / dt / 1e6, 4), "unit": "MPix/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} run(s) of the FP64 oracle on a {W}x{rows} band (same per-pixel work), numpy, 1 thread"}
+    return {"value": round(rows * cfg["w"] / dt / 1e6, 4), "unit": "MPix/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} run(s) of the oracle on a {cfg['w']}x{rows} band of the workload (same per-pixel "
+                      f"work), numpy, 1 thread"}
 
 
 def run_reference(args, cfg_name):
@@ -340,30 +468,27 @@ def run_reference(args, cfg_name):
     if rank != 0:
         return None
     cfg = config_table()[cfg_name]
-    from oracle import stencil as ost
-    from paper_2012_07145_gb300 import synth
-    W = cfg["w"]
-    kinds = ost.chain_kinds(32 if cfg_name == "chain32" else 4, "alternate" if cfg_name == "chain32" else "binomial")
     # size each step's band so that all steps together take about two minutes
-    probe = synth.stencil_input(8, W, seed=0)[0].astype(np.float64)
+    probe_rows = 8
+    fn = cfg["oracle_sample"](probe_rows)
     t0 = time.perf_counter()
-    ost.stencil_chain(probe, kinds)
-    per_row = (time.perf_counter() - t0) / 8
-    rows = int(max(1, min(cfg["h"], 120.0 / max(args.steps, 1) / per_row)))
-    img = synth.stencil_input(rows, W, seed=0)[0].astype(np.float64)
+    fn()
+    per_row = (time.perf_counter() - t0) / probe_rows
+    rows = int(max(4, min(cfg["h"], 120.0 / max(args.steps, 1) / per_row)))
+    fn = cfg["oracle_sample"](rows)
     for _ in range(min(args.warmup, 1)):
-        ost.stencil_chain(img, kinds)
+        fn()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        ost.stencil_chain(img, kinds)
+        fn()
     dt = (time.perf_counter() - t0) / args.steps
-    v = round(rows * W / dt / 1e6, 4)
+    v = round(rows * cfg["w"] / dt / 1e6, 4)
     return {"metric": METRIC, "value": v, "unit": "MPix/s", "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": cfg["workload"], "sample": f"{W}x{rows} band per step"},
+            "config": {"workload": cfg["workload"], "sample": f"{cfg['w']}x{rows} band per step"},
             "cpu_baseline": {"value": v, "unit": "MPix/s", "cores": 1, "kind": "oracle",
-                             "sample": f"FP64 oracle on a {W}x{rows} band per step, numpy, 1 thread"},
+                             "sample": f"FP64 oracle on a {cfg['w']}x{rows} band per step, numpy, 1 thread"},
             "e2e": {"value": v, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -373,7 +498,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="chain32")
+    ap.add_argument("--config", default="chain32", help="workload name, or 'all' (one line per workload)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--only-fused", action="store_true",
@@ -381,9 +506,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    line = run_reference(args, args.config) if args.impl == "reference" else run_ours(args, args.config)
-    if line is not None:
-        print(json.dumps(line), flush=True)
+    names = list(config_table().keys()) if args.config == "all" else [args.config]
+    for name in names:
+        line = run_reference(args, name) if args.impl == "reference" else run_ours(args, name)
+        if line is not None:
+            print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
