@@ -87,8 +87,9 @@ def config_table():
 
     cfgs["harris"] = dict(workload=f"harris_rgb_{W}x{H}_f32", h=H, w=W,
                           inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_F32)], out=(1, H, W, hp.HP_F32),
-                          build=lambda: pipelines.harris(), fused=lambda p: pipelines.fused_schedule(p),
-                          flops_px=68, bytes_px=16, bound="hbm", kernel="k_", dtype="f32",
+                          build=lambda: pipelines.harris(),
+                          fused=lambda p: pipelines.fused_schedule(p, tile_w=64, tile_h=32),
+                          flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris", dtype="f32",
                           oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
     UH, UW = 3072, 4096
 

@@ -147,11 +147,16 @@ struct ResampleArgs {  // downsample / upsample, per channel
   int storage;
 };
 
+// Harris group: gray -> (Ix, Iy) 3x3 separable stencils -> products
+// (Ixx, Iyy, Ixy) -> 3x3 separable sums (Sxx, Syy, Sxy) -> response.
 struct HarrisArgs {
   ImgView in, out;          // in: 3 ch; out: 1 ch
   float gray_scale, k;
-  int storage_gray, storage_grad, storage_prod, storage_sum, storage_out;
-  int tile_w, tile_h, tiles_x, tiles_y, threads;
+  // storage of: gray, Ix, Iy, Ixx, Iyy, Ixy, Sxx, Syy, Sxy (the response uses out.dtype)
+  int st[9];
+  // 3 x-taps then 3 y-taps of: Ix, Iy, Sxx, Syy, Sxy
+  float w[5][6];
+  int tile_w, tile_h, tiles_x, tiles_y, threads, seg;
   int* err;
 };
 
@@ -180,7 +185,7 @@ int launch_pointwise(const PointwiseArgs& a, void* stream);
 int launch_downsample(const ResampleArgs& a, void* stream);
 int launch_upsample(const ResampleArgs& a, void* stream);
 int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream);
-int harris_smem_bytes(int tile_w, int tile_h);
+int harris_smem_bytes(int tile_w, int tile_h, int in_dtype);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

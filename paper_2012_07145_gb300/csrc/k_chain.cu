@@ -232,8 +232,10 @@ __device__ __forceinline__ float staged_value(const unsigned char* st, int idx, 
 template <int RND, int ODT>
 __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKParams kp) {
   const ChainArgs& a = kp.a;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // align to 128 bytes by offsetting the shared array itself (not through an
+  // integer cast), so every derived pointer stays a 32-bit shared address
+  unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   uint64_t* bar = reinterpret_cast<uint64_t*>(base);
   volatile int* status = reinterpret_cast<volatile int*>(base + 64);
   const int d = a.depth;

@@ -342,6 +342,51 @@ hp_status group_shapes(const hp_pipeline* p, std::vector<GroupShape>& shapes) {
 }
 
 bool is_r2_stencil(const Stage& s) { return s.kind == HP_STENCIL && s.rx == 2 && s.ry == 2; }
+bool is_r1_stencil(const Stage& s) { return s.kind == HP_STENCIL && s.rx == 1 && s.ry == 1; }
+
+// Roles of a Harris-shaped group: gray, Ix, Iy, Pxx, Pyy, Pxy, Sxx, Syy, Sxy,
+// response (stage ids), if the 10 members have exactly that structure.
+bool match_harris(const hp_pipeline* p, const std::vector<int>& m, int roles[10]) {
+  if (m.size() != 10) return false;
+  auto st = [&](int i) -> const Stage& { return p->stages[m[i]]; };
+  auto in_group = [&](int id) { return std::find(m.begin(), m.end(), id) != m.end(); };
+  const Stage& g = st(0);
+  if (!(g.kind == HP_POINTWISE && g.op == HP_OP_GRAY && !in_group(g.inputs[0]))) return false;
+  roles[0] = m[0];
+  int grads[2], ng = 0, prods[3], np = 0, sums[3], ns = 0, resp = -1;
+  for (int i = 1; i < 10; ++i) {
+    const Stage& s = st(i);
+    if (is_r1_stencil(s) && s.inputs[0] == m[0] && ng < 2) grads[ng++] = m[i];
+    else if (s.kind == HP_POINTWISE && s.op == HP_OP_MUL && np < 3) prods[np++] = m[i];
+    else if (is_r1_stencil(s) && ns < 3) sums[ns++] = m[i];
+    else if (s.kind == HP_POINTWISE && s.op == HP_OP_HARRIS) resp = m[i];
+    else return false;
+  }
+  if (ng != 2 || np != 3 || ns != 3 || resp != m[9]) return false;
+  roles[1] = grads[0];
+  roles[2] = grads[1];
+  auto is_prod = [&](int id, int a, int b) {
+    const Stage& s = p->stages[id];
+    return (s.inputs[0] == a && s.inputs[1] == b) || (s.inputs[0] == b && s.inputs[1] == a);
+  };
+  roles[3] = roles[4] = roles[5] = -1;
+  for (int q : prods) {
+    if (is_prod(q, grads[0], grads[0])) roles[3] = q;
+    else if (is_prod(q, grads[1], grads[1])) roles[4] = q;
+    else if (is_prod(q, grads[0], grads[1])) roles[5] = q;
+  }
+  if (roles[3] < 0 || roles[4] < 0 || roles[5] < 0) return false;
+  for (int k = 0; k < 3; ++k) {
+    roles[6 + k] = -1;
+    for (int q : sums)
+      if (p->stages[q].inputs[0] == roles[3 + k]) roles[6 + k] = q;
+    if (roles[6 + k] < 0) return false;
+  }
+  const Stage& r = p->stages[resp];
+  if (r.inputs[0] != roles[6] || r.inputs[1] != roles[7] || r.inputs[2] != roles[8]) return false;
+  roles[9] = resp;
+  return true;
+}
 
 // Picks the kernel of a group from its shape.
 int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
@@ -371,6 +416,11 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
                                        : s.inputs[0] == m[i - 1]);
   }
   if (chain) return HP_KERNEL_STENCIL_CHAIN;
+  int roles[10];
+  if (match_harris(p, m, roles)) {
+    int dt = stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]);
+    if (dt == HP_F32 || dt == HP_F16 || dt == HP_BF16) return HP_KERNEL_HARRIS;
+  }
   // 5x5 stencil + unsharp combine with the stencil's own input
   if (m.size() == 2) {
     const Stage& a = p->stages[m[0]];
@@ -536,6 +586,40 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   return HP_OK;
 }
 
+hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  int roles[10];
+  match_harris(p, gp.members, roles);
+  HarrisArgs& a = gp.harris;
+  memset(&a, 0, sizeof a);
+  a.gray_scale = p->stages[roles[0]].params[0];
+  a.k = p->stages[roles[9]].params[0];
+  for (int i = 0; i < 9; ++i) a.st[i] = p->stages[roles[i]].storage;
+  const int wst[5] = {roles[1], roles[2], roles[6], roles[7], roles[8]};
+  for (int q = 0; q < 5; ++q)
+    for (int k = 0; k < 3; ++k) {
+      a.w[q][k] = p->stages[wst[q]].wx[k];
+      a.w[q][3 + k] = p->stages[wst[q]].wy[k];
+    }
+  a.tile_w = gp.tile_w;
+  a.tile_h = gp.tile_h;
+  a.threads = gp.threads;
+  a.seg = gp.seg;
+  if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_w > 232 || a.tile_h < 1 || a.tile_h > 252)
+    return fail(HP_ERR_SCHEDULE, "Harris tile width must be a multiple of 8 in [8, 232], height in [1, 252]");
+  if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 512)
+    return fail(HP_ERR_SCHEDULE, "Harris threads per block must be a multiple of 32 in [32, 512]");
+  if (a.seg < 1) return fail(HP_ERR_SCHEDULE, "serial_y must be >= 1");
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  gp.smem = harris_smem_bytes(a.tile_w, a.tile_h, stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]));
+  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "Harris tile needs %d bytes of shared memory", gp.smem);
+  gp.grid_x = a.tiles_x;
+  gp.grid_y = a.tiles_y;
+  gp.ext_refs.assign(1, p->stages[roles[0]].inputs[0]);
+  return HP_OK;
+}
+
 hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
   plan.in_dom = in_dom;
   hp_status s = infer_domains(p, in_dom, plan.dom);
@@ -563,6 +647,13 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
         s = build_chain(p, plan, gp, gp.kernel == HP_KERNEL_UNSHARP);
+        break;
+      case HP_KERNEL_HARRIS:
+        gp.tile_w = pick(p->tile_w, g, 64);
+        gp.tile_h = pick(p->tile_h, g, 32);
+        gp.threads = pick(p->threads, g, 256);
+        gp.seg = pick(p->serial_y, g, 8);
+        s = build_harris(p, plan, gp);
         break;
       case HP_KERNEL_HISTOGRAM: case HP_KERNEL_CDF_LUT: case HP_KERNEL_LUT_APPLY:
         gp.threads = 256;
@@ -675,6 +766,14 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.out = out;
         a.err = p->d_err;
         e = launch_chain(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_HARRIS: {
+        HarrisArgs a = gp.harris;
+        a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        a.err = p->d_err;
+        e = launch_harris(a, gp.smem, stream);
         break;
       }
       case HP_KERNEL_HISTOGRAM: {

@@ -77,9 +77,9 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Host: encodes a 3-D (W, H, C) tiled tensor map with a (bw, bh, 1) box.
+// Host: encodes a 3-D (W, H, C) tiled tensor map with a (bw, bh, bz) box.
 // Returns 0 on success.
 int encode_tmap_3d(CUtensorMap* map, CUtensorMapDataType dt, int esize, const void* base, int w, int h, int c,
-                   long long row_stride, long long plane_stride, int bw, int bh);
+                   long long row_stride, long long plane_stride, int bw, int bh, int bz = 1);
 
 }  // namespace hp

@@ -81,6 +81,11 @@ def test_lowering_picks_kernels():
     hr = pipelines.harris()
     pipelines.fused_schedule(hr, impl=hp.HP_IMPL_GENERIC)
     assert hr.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_GENERIC
+    pipelines.fused_schedule(hr)
+    assert hr.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_HARRIS
+    pipelines.fused_schedule(hr, inline_pointwise=True)
+    info = hr.group_info([(64, 48)], 0)
+    assert info.kernel == hp.HP_KERNEL_HARRIS and info.n_members == 10
 
 
 def test_bounds_inference_stencil_chain():

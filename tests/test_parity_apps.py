@@ -35,8 +35,11 @@ def test_harris_against_oracle_and_schedules(h, w):
         assert rel_err(to_numpy(plain)[0], ref) <= TOL
     else:
         assert np.abs(to_numpy(plain)[0] - ref).max() < 1e-4
-    for kw in [dict(), dict(inline_pointwise=True), dict(tile_w=16, tile_h=8, threads=128)]:
+    for kw in [dict(), dict(inline_pointwise=True), dict(tile_w=16, tile_h=8, threads=128),
+               dict(tile_w=64, tile_h=32, threads=256), dict(impl=hp.HP_IMPL_GENERIC)]:
         pipelines.fused_schedule(p, **kw)
+        expect = hp.HP_KERNEL_GENERIC if kw.get("impl") == hp.HP_IMPL_GENERIC else hp.HP_KERNEL_HARRIS
+        assert p.group_info([(w, h)], 0).kernel == expect
         fused = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
         assert torch.equal(bits(fused), bits(plain)), kw
 
@@ -48,8 +51,11 @@ def test_harris_bf16_io_error_is_stated():
     x = to_device(img, hp.HP_BF16)
     plain = run(p, [x], [hp.HP_BF16], (1, h, w), hp.HP_BF16)
     pipelines.fused_schedule(p)
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_HARRIS
     fused = run(p, [x], [hp.HP_BF16], (1, h, w), hp.HP_BF16)
     assert torch.equal(bits(fused), bits(plain))
+    pipelines.fused_schedule(p, impl=hp.HP_IMPL_GENERIC)
+    assert torch.equal(bits(run(p, [x], [hp.HP_BF16], (1, h, w), hp.HP_BF16)), bits(plain))
     e_rounded = rel_err(to_numpy(fused)[0], ohr.harris(to_numpy(x).astype(np.float64)))
     e_orig = rel_err(to_numpy(fused)[0], ohr.harris(img.astype(np.float64)))
     print(f"harris bf16 I/O: rel err vs oracle on rounded input {e_rounded:.3e}, original {e_orig:.3e}")
