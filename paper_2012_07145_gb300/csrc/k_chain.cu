@@ -49,7 +49,10 @@ __host__ __device__ inline ChainGeom chain_geom(int depth, int tw, int th) {
   g.P = ((g.W0 + 3) & ~3) + 4;
   g.BH = g.H0 < 256 ? g.H0 : 256;
   g.nby = (g.H0 + g.BH - 1) / g.BH;
-  g.R = g.nby * g.BH;
+  // rows: the stacked TMA boxes, and the overshoot of a last row segment
+  // (segments of up to 16 rows read 4 rows further)
+  const int r_seg = ((g.H0 + 15) & ~15) + 4;
+  g.R = g.nby * g.BH > r_seg ? g.nby * g.BH : r_seg;
   g.buf = (g.P * g.R + 31) & ~31;
   return g;
 }
@@ -155,44 +158,28 @@ struct GlobalSink {
 };
 
 // One stage over a Ws x Hs rectangle: work items are (4-column block, row
-// segment); the producer rectangle starts 2 columns and 2 rows further out, so
-// output (x, y) reads producer rows y..y+4 and columns x..x+4 (rect-relative).
-template <int RND, class Sink>
-__device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int Ws, int Hs, int seg,
+// segment of SEG rows); the producer rectangle starts 2 columns and 2 rows
+// further out, so output (x, y) reads producer rows y..y+4 and columns x..x+4
+// (rect-relative).  The segment is unrolled completely: SEG + 4 producer rows
+// each get one x pass, kept in a 5-row register window for the y passes.  The
+// last segment may run past Hs; those rows are computed from rows that exist
+// in the buffer (it is allocated for that) and are never read by valid outputs.
+template <int SEG, int RND, class Sink>
+__device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int Ws, int Hs,
                                       const float* wx, const float* wy, int dtype, const Sink& sink) {
   const int nb = Ws >> 2;
-  const int nseg = (Hs + seg - 1) / seg;
+  const int nseg = (Hs + SEG - 1) / SEG;
   const int items = nb * nseg;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int sg = it / nb;
     const int b = it - sg * nb;
-    const int r0 = sg * seg;
-    const int r1 = min(Hs, r0 + seg);
+    const int r0 = sg * SEG;
     const float* p = src + r0 * P + 4 * b;
-    float4 h0 = xpass(p, wx);
-    float4 h1 = xpass(p + P, wx);
-    float4 h2 = xpass(p + 2 * P, wx);
-    float4 h3 = xpass(p + 3 * P, wx);
-    float4 h4;
-    p += 4 * P;
-    int y = r0;
-    // Five steps per iteration so the 5-row window rotates without moves.
-    while (true) {
-      h4 = xpass(p, wx); p += P;
-      sink.put(b, y, ypass<RND>(wy, h0, h1, h2, h3, h4, dtype));
-      if (++y >= r1) break;
-      h0 = xpass(p, wx); p += P;
-      sink.put(b, y, ypass<RND>(wy, h1, h2, h3, h4, h0, dtype));
-      if (++y >= r1) break;
-      h1 = xpass(p, wx); p += P;
-      sink.put(b, y, ypass<RND>(wy, h2, h3, h4, h0, h1, dtype));
-      if (++y >= r1) break;
-      h2 = xpass(p, wx); p += P;
-      sink.put(b, y, ypass<RND>(wy, h3, h4, h0, h1, h2, dtype));
-      if (++y >= r1) break;
-      h3 = xpass(p, wx); p += P;
-      sink.put(b, y, ypass<RND>(wy, h4, h0, h1, h2, h3, dtype));
-      if (++y >= r1) break;
+    float4 h[SEG + 4];
+#pragma unroll
+    for (int k = 0; k < SEG + 4; ++k) {
+      h[k] = xpass(p + k * P, wx);
+      if (k >= 4) sink.put(b, r0 + k - 4, ypass<RND>(wy, h[k - 4], h[k - 3], h[k - 2], h[k - 1], h[k], dtype));
     }
   }
 }
@@ -229,7 +216,7 @@ __device__ __forceinline__ float staged_value(const unsigned char* st, int idx, 
   return reinterpret_cast<const float*>(st)[idx];
 }
 
-template <int RND, int ODT>
+template <int RND, int ODT, int SEG>
 __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKParams kp) {
   const ChainArgs& a = kp.a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -303,7 +290,7 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
     }
     const int dt = a.storage[s - 1];
     if (s < d) {
-      sweep<RND>(src, g.P, Ws, Hs, a.seg, wx, wy, dt, SmemSink{dst, g.P});
+      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, SmemSink{dst, g.P});
       if (border) {
         __syncthreads();
         fixup(dst, g.P, ox - 2 * (d - s), oy - 2 * (d - s), Ws, Hs, W, H);
@@ -322,25 +309,32 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       gs.out = a.out;
       gs.in = a.in;
       gs.ch = ch;
-      sweep<RND>(src, g.P, Ws, Hs, a.seg, wx, wy, dt, gs);
+      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, gs);
     }
   }
 }
 
 typedef void (*ChainKernel)(ChainKParams);
 
+template <int RND, int ODT>
+ChainKernel by_seg(int seg) {
+  return seg == 4 ? k_chain<RND, ODT, 4> : seg == 16 ? k_chain<RND, ODT, 16> : k_chain<RND, ODT, 8>;
+}
+
 // Picks the instantiation: one rounding kind for every stage and a vector
-// store for the output type when they agree, else the general one.
+// store for the output type when they agree, else the general one; and the
+// unrolled segment length.
 ChainKernel pick_kernel(const ChainArgs& a, int* variant) {
   int s0 = a.storage[0];
   bool uniform = true;
   for (int i = 1; i < a.depth; ++i) uniform &= a.storage[i] == s0;
-  const bool same_out = a.out.dtype == s0 || a.epilogue;
-  if (uniform && same_out && s0 == HP_F32 && a.out.dtype == HP_F32) { *variant = 0; return k_chain<0, 0>; }
-  if (uniform && same_out && s0 == HP_F16 && a.out.dtype == HP_F16) { *variant = 1; return k_chain<1, 1>; }
-  if (uniform && same_out && s0 == HP_BF16 && a.out.dtype == HP_BF16) { *variant = 2; return k_chain<2, 2>; }
-  *variant = 3;
-  return k_chain<3, 3>;
+  const int si = a.seg == 4 ? 0 : a.seg == 16 ? 2 : 1;
+  const bool same = uniform && a.out.dtype == s0;
+  if (same && s0 == HP_F32) { *variant = 0 * 3 + si; return by_seg<0, 0>(a.seg); }
+  if (same && s0 == HP_F16) { *variant = 1 * 3 + si; return by_seg<1, 1>(a.seg); }
+  if (same && s0 == HP_BF16) { *variant = 2 * 3 + si; return by_seg<2, 2>(a.seg); }
+  *variant = 3 * 3 + si;
+  return by_seg<3, 3>(a.seg);
 }
 
 }  // namespace
@@ -352,7 +346,7 @@ int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype) {
 }
 
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
-  static bool configured[4] = {false, false, false, false};
+  static bool configured[12] = {};
   int variant = 0;
   ChainKernel kern = pick_kernel(a, &variant);
   if (smem_bytes > 48 * 1024 && !configured[variant]) {

@@ -573,7 +573,8 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   a.seg = gp.seg;
   if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 512)
     return fail(HP_ERR_SCHEDULE, "stencil-chain threads per block must be a multiple of 32 in [32, 512]");
-  if (a.seg < 1) return fail(HP_ERR_SCHEDULE, "serial_y must be >= 1");
+  if (a.seg != 4 && a.seg != 8 && a.seg != 16)
+    return fail(HP_ERR_SCHEDULE, "stencil-chain serial_y (rows per thread) must be 4, 8 or 16");
   int in_ref = p->stages[st[0]].inputs[0];
   int in_dtype = in_ref < 0 ? p->in_dtypes[-1 - in_ref] : p->stages[in_ref].storage;
   gp.smem = chain_smem_bytes(a.depth, a.tile_w, a.tile_h, in_dtype);

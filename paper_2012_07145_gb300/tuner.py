@@ -37,8 +37,9 @@ def chain_smem_bytes(depth, tile_w, tile_h):
     W0, H0 = tile_w + 4 * depth, tile_h + 4 * depth
     P = ((W0 + 3) & ~3) + 4
     BH = min(H0, 256)
-    R = (H0 + BH - 1) // BH * BH
-    return 256 + 2 * P * R * 4
+    R = max((H0 + BH - 1) // BH * BH, ((H0 + 15) & ~15) + 4)
+    buf = (P * R + 31) & ~31
+    return 256 + 2 * buf * 4
 
 
 def chain_candidates(n_stages, W, H, quick=False):
@@ -46,7 +47,7 @@ def chain_candidates(n_stages, W, H, quick=False):
     tws = (32, 64, 128) if not quick else (64, 128)
     ths = (16, 32, 64, 128) if not quick else (32, 64)
     threads = (128, 256, 512) if not quick else (256,)
-    serials = (4, 8, 16, 32) if not quick else (8, 16)
+    serials = (4, 8, 16) if not quick else (8, 16)
     out = []
     for d, tw, th, t, s in itertools.product(depths, tws, ths, threads, serials):
         if chain_smem_bytes(d, tw, th) > SMEM_LIMIT:
