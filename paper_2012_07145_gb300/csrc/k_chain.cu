@@ -100,60 +100,12 @@ __device__ __forceinline__ float4 ypass(const float* wy, const float4& a, const 
   return v;
 }
 
-// Output sink of a sweep: a shared buffer, or the global output (last stage).
+// Output sink of a sweep: the stage's shared buffer.
 struct SmemSink {
   float* dst;
   int P;
   __device__ __forceinline__ void put(int b, int y, const float4& v) const {
     *reinterpret_cast<float4*>(dst + y * P + 4 * b) = v;
-  }
-};
-
-// ODT: 0 f32, 1 f16, 2 bf16, 3 any dtype (element-wise store_px).
-template <int ODT>
-struct GlobalSink {
-  char* row0;        // output plane of this channel at the tile's first row
-  long long rs;
-  int ox, hlim, wlim;  // rows / columns of the tile inside the image
-  int epi;
-  float amount;
-  ImgView out, in;
-  int ch, oy;
-  __device__ __forceinline__ void put(int b, int y, float4 v) const {
-    const int x = 4 * b;
-    if (y >= hlim || x >= wlim) return;
-    if (epi) {
-      const int gx = ox + x, gy = oy + y;
-      float vin[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) vin[i] = x + i < wlim ? load_px(in, ch, gx + i, gy) : 0.0f;
-      v.x = round_storage(out.dtype, op_unsharp(vin[0], v.x, amount));
-      v.y = round_storage(out.dtype, op_unsharp(vin[1], v.y, amount));
-      v.z = round_storage(out.dtype, op_unsharp(vin[2], v.z, amount));
-      v.w = round_storage(out.dtype, op_unsharp(vin[3], v.w, amount));
-    }
-    char* row = row0 + (long long)y * rs;
-    const int gx = ox + x;
-    if (ODT != 3 && x + 3 < wlim) {
-      if (ODT == 0) {
-        *reinterpret_cast<float4*>(row + 4LL * gx) = v;
-      } else {
-        uint2 u;
-        if (ODT == 1) {
-          __half2 p0 = __floats2half2_rn(v.x, v.y), p1 = __floats2half2_rn(v.z, v.w);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
-        } else {
-          __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
-        }
-        *reinterpret_cast<uint2*>(row + 2LL * gx) = u;
-      }
-      return;
-    }
-    const float vv[4] = {v.x, v.y, v.z, v.w};
-    for (int i = 0; i < 4 && x + i < wlim; ++i) store_px(out, ch, gx + i, oy + y, vv[i]);
   }
 };
 
@@ -289,27 +241,61 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       wy[k] = a.w[s - 1][5 + k];
     }
     const int dt = a.storage[s - 1];
-    if (s < d) {
-      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, SmemSink{dst, g.P});
-      if (border) {
-        __syncthreads();
-        fixup(dst, g.P, ox - 2 * (d - s), oy - 2 * (d - s), Ws, Hs, W, H);
-      }
+    sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, SmemSink{dst, g.P});
+    if (s < d && border) {
       __syncthreads();
+      fixup(dst, g.P, ox - 2 * (d - s), oy - 2 * (d - s), Ws, Hs, W, H);
+    }
+    __syncthreads();
+  }
+
+  // ---- copy the last stage out with coalesced 128-bit (f32) / 64-bit stores ----
+  const float* last = (d & 1) ? bufB : bufA;
+  const int hlim = min(a.tile_h, a.out.h - oy), wlim = min(a.tile_w, a.out.w - ox);
+  const int nb4 = a.tile_w >> 2;
+  char* plane = (char*)a.out.data + (long long)ch * a.out.ps;
+  const int odt = a.out.dtype;
+  for (int i = threadIdx.x; i < hlim * nb4; i += blockDim.x) {
+    const int y = i / nb4;
+    const int x = 4 * (i - y * nb4);
+    if (x >= wlim) continue;
+    float4 v = *reinterpret_cast<const float4*>(last + y * g.P + x);
+    if (a.epilogue == 1) {
+      // unsharp: combine with the chain's input at the same pixel (stage 0 is
+      // still in buffer A when the chain has one stage)
+      float vin[4];
+      if (d == 1) {
+        const float* s0 = bufA + (y + 2) * g.P + x + 2;
+        vin[0] = s0[0]; vin[1] = s0[1]; vin[2] = s0[2]; vin[3] = s0[3];
+      } else {
+        for (int k = 0; k < 4; ++k) vin[k] = x + k < wlim ? load_px(a.in, ch, ox + x + k, oy + y) : 0.0f;
+      }
+      v.x = round_storage(odt, op_unsharp(vin[0], v.x, a.amount));
+      v.y = round_storage(odt, op_unsharp(vin[1], v.y, a.amount));
+      v.z = round_storage(odt, op_unsharp(vin[2], v.z, a.amount));
+      v.w = round_storage(odt, op_unsharp(vin[3], v.w, a.amount));
+    }
+    char* row = plane + (long long)(oy + y) * a.out.rs;
+    const int gx = ox + x;
+    if (ODT != 3 && x + 3 < wlim) {
+      if (ODT == 0) {
+        *reinterpret_cast<float4*>(row + 4LL * gx) = v;
+      } else {
+        uint2 u;
+        if (ODT == 1) {
+          __half2 p0 = __floats2half2_rn(v.x, v.y), p1 = __floats2half2_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        } else {
+          __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        }
+        *reinterpret_cast<uint2*>(row + 2LL * gx) = u;
+      }
     } else {
-      GlobalSink<ODT> gs;
-      gs.rs = a.out.rs;
-      gs.row0 = (char*)a.out.data + (long long)ch * a.out.ps + (long long)oy * a.out.rs;
-      gs.ox = ox;
-      gs.oy = oy;
-      gs.hlim = min(a.tile_h, a.out.h - oy);
-      gs.wlim = min(a.tile_w, a.out.w - ox);
-      gs.epi = a.epilogue;
-      gs.amount = a.amount;
-      gs.out = a.out;
-      gs.in = a.in;
-      gs.ch = ch;
-      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, gs);
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+      for (int k = 0; k < 4 && x + k < wlim; ++k) store_px(a.out, ch, gx + k, oy + y, vv[k]);
     }
   }
 }
