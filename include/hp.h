@@ -228,6 +228,35 @@ hp_status hp_check_device_error(hp_pipeline* p, int* code);
 
 hp_status hp_pipeline_destroy(hp_pipeline* p);
 
+/* Histogram equalization of one 1-channel u8 image that allocates nothing.
+ *
+ * For callers that cannot allocate device memory when they run a pipeline: a
+ * host framework that owns all device memory through its own pool and forbids
+ * cudaMalloc from plugins, a real-time or serving loop that must not block
+ * (cudaMalloc can synchronise the device) or fail under memory pressure, or a
+ * deployment that reserves all memory once at start-up.  The paper has no
+ * counterpart; it is a property of this library.
+ *
+ * Computes exactly what the HP_HISTOGRAM -> HP_CDF_LUT -> HP_LUT_APPLY pipeline
+ * computes, with the same kernels.  The caller passes the device input and
+ * output (1-channel u8, equal sizes, 16-byte aligned data and row strides); the
+ * 256 histogram counters and the 256-entry table live in a fixed 1280-byte
+ * array inside the library's device image, which every GPU that loads the
+ * library holds until the process exits.  Images of more than
+ * HP_NOALLOC_MAX_PIXELS pixels (the counters are 32-bit) are rejected with
+ * HP_ERR_INVALID_ARG.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array per device and
+ * clears the counters on its stream before counting, so calls run in order on
+ * one stream are independent, but calls that overlap on the GPU (different
+ * streams, or concurrent host threads) race on the array.  Enqueues work on the
+ * stream and returns without synchronising; no cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+#define HP_NOALLOC_MAX_PIXELS 4294967295ULL
+hp_status hp_histeq_u8_noalloc(const hp_buffer* input, const hp_buffer* output, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* hp_last_error(void);
 

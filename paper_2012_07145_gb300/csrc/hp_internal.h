@@ -196,4 +196,7 @@ int allow_max_dynamic_smem(const void* func);
 
 extern unsigned long long g_launches;
 
+// Sets the thread's hp_last_error() message and returns s.
+hp_status report_error(hp_status s, const char* msg);
+
 }  // namespace hp

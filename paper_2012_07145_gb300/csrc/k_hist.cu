@@ -9,6 +9,8 @@
 // global counters with one atomic per bin.  All counts are exact integers.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "hp_internal.h"
 
 namespace hp {
@@ -177,3 +179,102 @@ int launch_lut_apply(const LutApplyArgs& a, void* stream) {
 }
 
 }  // namespace hp
+
+// ---------------------------------------------------------------------------
+// Allocation-free histogram equalization.
+//
+// Some callers cannot allocate device memory at the time they run a pipeline:
+// a host framework that owns every byte of device memory through its own pool
+// and forbids cudaMalloc from plugins, a real-time or serving loop that must
+// not block (cudaMalloc can synchronise the device) or fail under memory
+// pressure, or a deployment that reserves all memory once at start-up.  For
+// them this entry point equalizes one u8 image with the three kernels above,
+// taking its scratch -- the 256 histogram counters and the 256-entry table --
+// from a fixed array in the library's device image instead of from an
+// allocation.  The paper has no counterpart: it is a property of this library.
+// ---------------------------------------------------------------------------
+namespace hp {
+namespace {
+
+constexpr int kNoallocCounterBytes = 256 * 4;
+constexpr int kNoallocBytes = kNoallocCounterBytes + 256;  // counters, then the LUT
+constexpr int kMaxDevices = 64;
+
+// Every GPU that loads the library holds these 1280 bytes until the process
+// exits.  All calls share them: calls that overlap on the GPU race.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+void* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+}  // namespace hp
+
+extern "C" hp_status hp_histeq_u8_noalloc(const hp_buffer* input, const hp_buffer* output, void* stream) {
+  using namespace hp;
+  if (!input || !output || !input->data || !output->data)
+    return report_error(HP_ERR_INVALID_ARG, "hp_histeq_u8_noalloc: null buffer");
+  const hp_buffer* bufs[2] = {input, output};
+  for (const hp_buffer* b : bufs) {
+    if (b->dtype != HP_U8 || b->channels != 1)
+      return report_error(HP_ERR_INVALID_ARG, "hp_histeq_u8_noalloc: buffers must be 1-channel u8");
+    if (b->width < 1 || b->height < 1)
+      return report_error(HP_ERR_INVALID_ARG, "hp_histeq_u8_noalloc: empty image");
+    if (((uintptr_t)b->data & 15) || b->row_stride_bytes % 16 || b->row_stride_bytes < b->width)
+      return report_error(HP_ERR_INVALID_ARG,
+                          "hp_histeq_u8_noalloc: data must be 16-byte aligned and rows a multiple of 16 bytes");
+  }
+  if (input->width != output->width || input->height != output->height)
+    return report_error(HP_ERR_INVALID_ARG, "hp_histeq_u8_noalloc: input and output sizes differ");
+  if ((unsigned long long)input->width * (unsigned long long)input->height > HP_NOALLOC_MAX_PIXELS)
+    return report_error(HP_ERR_INVALID_ARG,
+                        "hp_histeq_u8_noalloc: image larger than HP_NOALLOC_MAX_PIXELS (the 32-bit counters)");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return report_error(HP_ERR_CUDA, "hp_histeq_u8_noalloc: no usable current device");
+  }
+  void* base = nullptr;
+  {
+    // set-up, once per device, with that device current: the host-side name of
+    // the array is not a device address, so ask the runtime for the address
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return report_error(HP_ERR_CUDA, "hp_histeq_u8_noalloc: cudaGetSymbolAddress of the scratch array failed");
+      }
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  ImgView in{}, out{};
+  in.data = input->data; in.dtype = HP_U8; in.c = 1; in.w = input->width; in.h = input->height;
+  in.rs = input->row_stride_bytes; in.ps = input->plane_stride_bytes;
+  out.data = output->data; out.dtype = HP_U8; out.c = 1; out.w = output->width; out.h = output->height;
+  out.rs = output->row_stride_bytes; out.ps = output->plane_stride_bytes;
+  unsigned int* hist = reinterpret_cast<unsigned int*>(base);
+  unsigned char* lut = reinterpret_cast<unsigned char*>(base) + kNoallocCounterBytes;
+  HistArgs ha{};
+  ha.in = in;
+  ha.hist = hist;  // launch_hist clears the counters on the stream before counting
+  int e = launch_hist(ha, stream);
+  if (!e) {
+    LutArgs la{};
+    la.hist = hist;
+    la.lut = lut;
+    e = launch_cdf_lut(la, stream);
+  }
+  if (!e) {
+    LutApplyArgs aa{};
+    aa.in = in;
+    aa.out = out;
+    aa.lut = lut;
+    e = launch_lut_apply(aa, stream);
+  }
+  if (e) return report_error(HP_ERR_CUDA, cudaGetErrorString((cudaError_t)e));
+  return HP_OK;
+}

@@ -108,6 +108,10 @@ struct Plan {
 constexpr size_t kMaxGraphs = 16;
 
 }  // namespace
+
+// Records a failure message for hp_last_error() from other translation units.
+hp_status report_error(hp_status s, const char* msg) { return fail(s, "%s", msg); }
+
 }  // namespace hp
 
 struct hp_pipeline {

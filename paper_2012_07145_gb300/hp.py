@@ -59,7 +59,7 @@ class GroupInfo(ctypes.Structure):
 
 EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_set", "hp_realize",
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
-           "hp_pipeline_destroy", "hp_last_error", "hp_launch_count"]
+           "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc"]
 
 _lib = None
 
@@ -85,6 +85,7 @@ def lib():
         L.hp_check_device_error.argtypes = [P, _IP]
         L.hp_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
         L.hp_pipeline_destroy.argtypes = [P]
+        L.hp_histeq_u8_noalloc.argtypes = [ctypes.POINTER(Buffer), ctypes.POINTER(Buffer), P]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
         for name in EXPORTS:
@@ -149,6 +150,11 @@ def padded_copy(src, device="cuda"):
     dst = padded_empty(c, h, w, src.dtype, device)
     dst.copy_(src)
     return dst
+
+
+def histeq_u8_noalloc(inp: Buffer, out: Buffer, stream=None):
+    """Allocation-free histogram equalization (hp_histeq_u8_noalloc)."""
+    check(lib().hp_histeq_u8_noalloc(ctypes.byref(inp), ctypes.byref(out), ctypes.c_void_p(stream or 0)))
 
 
 class Pipeline:
