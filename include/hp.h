@@ -156,11 +156,12 @@ enum {
   HP_KERNEL_HARRIS = 2,        /* whole Harris DAG in one kernel */
   HP_KERNEL_GENERIC = 3,       /* interpreter over any group of stencil/point-wise/pyramid stages */
   HP_KERNEL_POINTWISE = 4,
-  HP_KERNEL_DOWNSAMPLE = 5,
+  HP_KERNEL_DOWNSAMPLE = 5,    /* every channel of a level; also from an inlined LL remap of gray */
   HP_KERNEL_UPSAMPLE = 6,
   HP_KERNEL_HISTOGRAM = 7,
   HP_KERNEL_CDF_LUT = 8,
-  HP_KERNEL_LUT_APPLY = 9
+  HP_KERNEL_LUT_APPLY = 9,
+  HP_KERNEL_LL_LEVEL = 10      /* local-Laplacian level: two-level blend + collapse step (+ colour) */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -160,6 +160,31 @@ struct HarrisArgs {
   int* err;
 };
 
+// Downsample of every channel of a source level (binomial per axis at 2x, 2y);
+// with remap = 1 the source is the local-Laplacian remap stack of the gray of
+// an RGB input, computed on the fly.
+struct LLDownArgs {
+  ImgView src, out;
+  int C;                       // channels produced
+  int remap;
+  float gray_scale, sigma, alpha, beta;
+  int K;
+  int st_gray, st_remap, st_out;
+  int tile_w, tile_h, tiles_x, tiles_y;
+};
+
+// One level of the local-Laplacian output pyramid and its collapse step
+// (see k_ll.cu).
+struct LLLevelArgs {
+  ImgView G, Gn, Rn, out, in;
+  int rn_ch, rn_st;            // channel of Rn read by the upsample; storage it is rounded to
+  int level0;
+  float gray_scale, sigma, alpha, beta, s_in, s_out;
+  int K;
+  int st_gray, st_G, st_U, st_L, st_Lout, st_UR, st_R;
+  int W, H;
+};
+
 struct HistArgs {
   ImgView in;               // 1 ch u8
   unsigned int* hist;       // 256 counters
@@ -186,6 +211,9 @@ int launch_downsample(const ResampleArgs& a, void* stream);
 int launch_upsample(const ResampleArgs& a, void* stream);
 int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream);
 int harris_smem_bytes(int tile_w, int tile_h, int in_dtype);
+int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
+int ll_down_smem_bytes(int tile_w, int tile_h);
+int launch_ll_level(const LLLevelArgs& a, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

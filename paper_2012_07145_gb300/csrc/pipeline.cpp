@@ -66,6 +66,13 @@ struct Dom {
   int w = 0, h = 0;
 };
 
+// Roles of a local-Laplacian level group (see k_ll.cu).
+struct LLRoles {
+  int U, L, Lout, UR, R, colour;   // stage ids (colour -1 above level 0)
+  int Gl, Gn, Rn;                  // refs: the level stack, the next coarser stack, the coarser result
+  int gray, remap, select;         // inlined producers (-1 if absent)
+};
+
 // One fusion group after lowering for a given set of input sizes.
 struct GroupPlan {
   int kernel = HP_KERNEL_GENERIC;
@@ -77,6 +84,9 @@ struct GroupPlan {
   // kernel-specific
   ChainArgs chain{};
   HarrisArgs harris{};
+  LLDownArgs lldown{};
+  LLLevelArgs lllevel{};
+  LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
 };
@@ -392,6 +402,92 @@ bool match_harris(const hp_pipeline* p, const std::vector<int>& m, int roles[10]
   return true;
 }
 
+// Downsample group: a single HP_DOWNSAMPLE (source read from memory), or the
+// first local-Laplacian level, gray -> LL remap -> downsample, with gray and
+// the remap in the group (inlined) and the RGB input outside it.
+bool match_down(const hp_pipeline* p, const std::vector<int>& m, int* remap, int* gray, int* rm) {
+  const Stage& last = p->stages[m.back()];
+  if (last.kind != HP_DOWNSAMPLE2) return false;
+  if (m.size() == 1) {
+    *remap = 0;
+    return true;
+  }
+  if (m.size() != 3) return false;
+  const Stage& g = p->stages[m[0]];
+  const Stage& r = p->stages[m[1]];
+  if (!(g.kind == HP_POINTWISE && g.op == HP_OP_GRAY && g.inputs[0] < 0)) return false;
+  if (!(r.kind == HP_POINTWISE && r.op == HP_OP_LL_REMAP && r.inputs[0] == m[0])) return false;
+  if (last.inputs[0] != m[1]) return false;
+  *remap = 1;
+  *gray = m[0];
+  *rm = m[1];
+  return true;
+}
+
+bool match_ll_level(const hp_pipeline* p, const std::vector<int>& m, LLRoles& r) {
+  auto in_m = [&](int id) { return id >= 0 && std::find(m.begin(), m.end(), id) != m.end(); };
+  r = LLRoles{-1, -1, -1, -1, -1, -1, 0, 0, 0, -1, -1, -1};
+  for (int id : m) {
+    const Stage& s = p->stages[id];
+    if (s.kind == HP_POINTWISE && s.op == HP_OP_LL_INTERP) {
+      if (r.Lout >= 0) return false;
+      r.Lout = id;
+    }
+  }
+  if (r.Lout < 0) return false;
+  const Stage& lo = p->stages[r.Lout];
+  r.Gl = lo.inputs[0];
+  r.L = lo.inputs[1];
+  if (!in_m(r.L)) return false;
+  const Stage& L = p->stages[r.L];
+  if (!(L.kind == HP_POINTWISE && L.op == HP_OP_SUB && L.inputs[0] == r.Gl && in_m(L.inputs[1]))) return false;
+  r.U = L.inputs[1];
+  const Stage& U = p->stages[r.U];
+  if (!(U.kind == HP_UPSAMPLE2 && U.inputs[1] == r.Gl && !in_m(U.inputs[0]))) return false;
+  r.Gn = U.inputs[0];
+  for (int id : m) {
+    const Stage& s = p->stages[id];
+    if (s.kind == HP_POINTWISE && s.op == HP_OP_ADD && s.inputs[0] == r.Lout) r.R = id;
+  }
+  if (r.R < 0) return false;
+  r.UR = p->stages[r.R].inputs[1];
+  if (!in_m(r.UR)) return false;
+  const Stage& UR = p->stages[r.UR];
+  if (!(UR.kind == HP_UPSAMPLE2 && UR.inputs[1] == r.Lout)) return false;
+  r.Rn = UR.inputs[0];
+  size_t expect = 5;
+  if (in_m(r.Rn)) {
+    const Stage& se = p->stages[r.Rn];
+    if (!(se.kind == HP_POINTWISE && se.op == HP_OP_SELECT && !in_m(se.inputs[0]))) return false;
+    r.select = r.Rn;
+    ++expect;
+  }
+  if (in_m(r.Gl)) {  // level 0: the stack is the inlined remap of an inlined gray
+    const Stage& rm = p->stages[r.Gl];
+    if (!(rm.kind == HP_POINTWISE && rm.op == HP_OP_LL_REMAP && in_m(rm.inputs[0]))) return false;
+    const Stage& g = p->stages[rm.inputs[0]];
+    if (!(g.kind == HP_POINTWISE && g.op == HP_OP_GRAY && g.inputs[0] < 0)) return false;
+    r.remap = r.Gl;
+    r.gray = rm.inputs[0];
+    for (int id : m) {
+      const Stage& s = p->stages[id];
+      if (s.kind == HP_POINTWISE && s.op == HP_OP_LL_COLOUR && s.inputs[1] == r.gray && s.inputs[2] == r.R &&
+          s.inputs[0] == g.inputs[0])
+        r.colour = id;
+    }
+    if (r.colour < 0) return false;
+    expect += 3;
+  } else if (in_m(r.Gn)) {
+    return false;
+  }
+  if (m.size() != expect) return false;
+  const int K = (int)lo.params[0];
+  if (r.remap >= 0 && (int)p->stages[r.remap].params[3] != K) return false;
+  if (r.select >= 0 && (int)p->stages[r.select].params[0] >= stage_channels_of_ref(p, p->stages[r.select].inputs[0]))
+    return false;
+  return m.back() == (r.colour >= 0 ? r.colour : r.R);
+}
+
 // Picks the kernel of a group from its shape.
 int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
   const auto& m = gs.members;
@@ -400,7 +496,7 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     switch (s.kind) {
       case HP_STENCIL: return is_r2_stencil(s) && impl != HP_IMPL_GENERIC ? HP_KERNEL_STENCIL_CHAIN : HP_KERNEL_GENERIC;
       case HP_POINTWISE: return HP_KERNEL_POINTWISE;
-      case HP_DOWNSAMPLE2: return HP_KERNEL_DOWNSAMPLE;
+      case HP_DOWNSAMPLE2: return impl == HP_IMPL_GENERIC ? HP_KERNEL_GENERIC : HP_KERNEL_DOWNSAMPLE;
       case HP_UPSAMPLE2: return HP_KERNEL_UPSAMPLE;
       case HP_HISTOGRAM: return HP_KERNEL_HISTOGRAM;
       case HP_CDF_LUT: return HP_KERNEL_CDF_LUT;
@@ -420,6 +516,12 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
                                        : s.inputs[0] == m[i - 1]);
   }
   if (chain) return HP_KERNEL_STENCIL_CHAIN;
+  {
+    int remap, gray, rm;
+    if (match_down(p, m, &remap, &gray, &rm)) return HP_KERNEL_DOWNSAMPLE;
+    LLRoles llr;
+    if (match_ll_level(p, m, llr)) return HP_KERNEL_LL_LEVEL;
+  }
   int roles[10];
   if (match_harris(p, m, roles)) {
     int dt = stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]);
@@ -625,6 +727,87 @@ hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   return HP_OK;
 }
 
+hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  int remap = 0, gray = -1, rm = -1;
+  match_down(p, gp.members, &remap, &gray, &rm);
+  LLDownArgs& a = gp.lldown;
+  memset(&a, 0, sizeof a);
+  const Stage& d = p->stages[gp.output];
+  a.remap = remap;
+  a.C = d.channels;
+  a.st_out = d.storage;
+  if (remap) {
+    const Stage& g = p->stages[gray];
+    const Stage& r = p->stages[rm];
+    a.gray_scale = g.params[0];
+    a.st_gray = g.storage;
+    a.sigma = r.params[0];
+    a.alpha = r.params[1];
+    a.beta = r.params[2];
+    a.K = (int)r.params[3];
+    a.st_remap = r.storage;
+    gp.ext_refs.assign(1, g.inputs[0]);
+  } else {
+    gp.ext_refs.assign(1, d.inputs[0]);
+  }
+  a.tile_w = gp.tile_w;
+  a.tile_h = gp.tile_h;
+  if (a.tile_w < 1 || a.tile_h < 1 || a.tile_w > 64 || a.tile_h > 64)
+    return fail(HP_ERR_SCHEDULE, "downsample tiles must be at most 64x64");
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  gp.threads = 256;
+  gp.smem = ll_down_smem_bytes(a.tile_w, a.tile_h);
+  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "downsample tile too large");
+  gp.grid_x = a.tiles_x;
+  gp.grid_y = a.tiles_y;
+  return HP_OK;
+}
+
+hp_status build_ll_level(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  LLRoles& r = gp.llroles;
+  match_ll_level(p, gp.members, r);
+  LLLevelArgs& a = gp.lllevel;
+  memset(&a, 0, sizeof a);
+  a.K = (int)p->stages[r.Lout].params[0];
+  a.level0 = r.remap >= 0;
+  a.st_U = p->stages[r.U].storage;
+  a.st_L = p->stages[r.L].storage;
+  a.st_Lout = p->stages[r.Lout].storage;
+  a.st_UR = p->stages[r.UR].storage;
+  a.st_R = p->stages[r.R].storage;
+  a.rn_ch = 0;
+  a.rn_st = HP_F32;
+  if (r.select >= 0) {
+    a.rn_ch = (int)p->stages[r.select].params[0];
+    a.rn_st = p->stages[r.select].storage;
+  }
+  if (a.level0) {
+    const Stage& g = p->stages[r.gray];
+    const Stage& rm = p->stages[r.remap];
+    const Stage& c = p->stages[r.colour];
+    a.gray_scale = g.params[0];
+    a.st_gray = g.storage;
+    a.sigma = rm.params[0];
+    a.alpha = rm.params[1];
+    a.beta = rm.params[2];
+    a.st_G = rm.storage;
+    a.s_in = c.params[0];
+    a.s_out = c.params[1];
+  } else {
+    a.st_G = stage_dtype_of_ref(p, r.Gl);
+  }
+  Dom d = plan.dom[r.Lout];
+  a.W = d.w;
+  a.H = d.h;
+  gp.threads = 256;
+  gp.grid_x = (d.w + 31) / 32;
+  gp.grid_y = (d.h + 7) / 8;
+  gp.smem = 0;
+  return HP_OK;
+}
+
 hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
   plan.in_dom = in_dom;
   hp_status s = infer_domains(p, in_dom, plan.dom);
@@ -652,6 +835,14 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
         s = build_chain(p, plan, gp, gp.kernel == HP_KERNEL_UNSHARP);
+        break;
+      case HP_KERNEL_DOWNSAMPLE:
+        gp.tile_w = std::min(pick(p->tile_w, g, 32), 64);
+        gp.tile_h = std::min(pick(p->tile_h, g, 16), 64);
+        s = build_down(p, plan, gp);
+        break;
+      case HP_KERNEL_LL_LEVEL:
+        s = build_ll_level(p, plan, gp);
         break;
       case HP_KERNEL_HARRIS:
         gp.tile_w = pick(p->tile_w, g, 64);
@@ -771,6 +962,27 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.out = out;
         a.err = p->d_err;
         e = launch_chain(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_DOWNSAMPLE: {
+        LLDownArgs a = gp.lldown;
+        a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_LL_LEVEL: {
+        LLLevelArgs a = gp.lllevel;
+        const LLRoles& r = gp.llroles;
+        if (a.level0) {
+          a.in = ref_view(p, plan, p->stages[r.gray].inputs[0], inputs, output);
+        } else {
+          a.G = ref_view(p, plan, r.Gl, inputs, output);
+        }
+        a.Gn = ref_view(p, plan, r.Gn, inputs, output);
+        a.Rn = ref_view(p, plan, r.select >= 0 ? p->stages[r.select].inputs[0] : r.Rn, inputs, output);
+        a.out = out;
+        e = launch_ll_level(a, stream);
         break;
       }
       case HP_KERNEL_HARRIS: {

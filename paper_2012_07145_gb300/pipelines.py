@@ -133,7 +133,7 @@ def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, al
     return p, ids
 
 
-def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256):
+def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None):
     """Per-level fusion: level 1 of the remapped pyramid from the input in one
     kernel (gray and remap inlined); one downsample kernel per coarser level;
     one kernel per level for Laplacian + interpolation + collapse step; the
@@ -155,4 +155,5 @@ def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, th
             groups[ids["out"]] = gid
         gid += 1
     assert all(g is not None for g in groups)
-    p.schedule(groups, tile_w=[tile] * gid, tile_h=[tile] * gid, threads=[threads] * gid)
+    p.schedule(groups, tile_w=[tile] * gid, tile_h=[tile] * gid, threads=[threads] * gid,
+               impl=[impl] * gid if impl is not None else None)

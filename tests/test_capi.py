@@ -121,3 +121,17 @@ def test_bounds_inference_pyramid_and_harris():
     assert r[3] == (15, 7, 33, 17)                 # products: +1 for the box
     assert r[1] == (15, 7, 33, 17)
     assert r[0] == (14, 6, 34, 18)                 # gray: +1 more for Sobel
+
+
+def test_local_laplacian_lowering():
+    J = 5
+    pl, ids = pipelines.local_laplacian(levels=J, k_levels=8)
+    pipelines.local_laplacian_fused_schedule(pl, ids, tile=16)
+    n = pl.group_count()
+    assert n == 2 * J - 2
+    kinds = [pl.group_info([(160, 96)], g).kernel for g in range(n)]
+    assert kinds == [hp.HP_KERNEL_DOWNSAMPLE] * (J - 1) + [hp.HP_KERNEL_LL_LEVEL] * (J - 1)
+    assert pl.group_info([(160, 96)], 0).n_members == 3          # gray and remap inlined
+    assert pl.group_info([(160, 96)], n - 1).n_members == 8      # level 0: + colour, gray, remap
+    pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
+    assert all(pl.group_info([(160, 96)], g).kernel == hp.HP_KERNEL_GENERIC for g in range(n))

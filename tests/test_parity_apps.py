@@ -149,3 +149,5 @@ def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha):
     assert d.max() <= 7 and (d > 0).mean() < 0.01
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16)
     assert np.array_equal(_ll_run(p, img), plain)
+    pipelines.local_laplacian_fused_schedule(p, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
+    assert np.array_equal(_ll_run(p, img), plain)
