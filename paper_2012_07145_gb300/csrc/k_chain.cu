@@ -335,7 +335,7 @@ int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
   static bool configured[12] = {};
   int variant = 0;
   ChainKernel kern = pick_kernel(a, &variant);
-  if (smem_bytes > 48 * 1024 && !configured[variant]) {
+  if (!configured[variant]) {  // opt in once: static shared memory also counts against the default 48 KB
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
     configured[variant] = true;

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(1024) k_generic(const __grid_constant__ GPlan 
 
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream) {
   static bool configured = false;
-  if (smem_bytes > 48 * 1024 && !configured) {
+  if (!configured) {  // opt in once: static shared memory also counts against the default 48 KB
     int e = allow_max_dynamic_smem((const void*)k_generic);
     if (e) return e;
     configured = true;

@@ -313,7 +313,7 @@ int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream) {
   else if (inner_f32 && a.out.dtype == HP_BF16) { variant = 1; kern = k_harris<0, 2>; }
   else { variant = 2; kern = k_harris<3, 3>; }
   static bool configured[3] = {false, false, false};
-  if (smem_bytes > 48 * 1024 && !configured[variant]) {
+  if (!configured[variant]) {  // opt in once: static shared memory also counts against the default 48 KB
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
     configured[variant] = true;

@@ -3,10 +3,13 @@
 //
 // Histogram: the parallel reduction the paper's histogram-equalize discussion
 // calls for (atomics expose the data parallelism, Sec. 6.5 and Sec. 8).  Each
-// warp keeps a private sub-histogram in shared memory; within a warp, lanes
-// holding the same value are combined with __match_any_sync so one lane adds
-// the group's count; the CTA's sub-histograms are summed and added to the
-// global counters with one atomic per bin.  All counts are exact integers.
+// warp keeps a private sub-histogram in shared memory and adds each byte with
+// a shared-memory atomic; when every active lane of the warp holds the same
+// value (flat regions, constant images: the worst case for contention) the
+// warp aggregates and one lane adds the whole count.  The CTA's sub-histograms
+// are summed and added to the global counters with one atomic per bin.  Each
+// thread loads 4 x 16 bytes before counting so enough reads are in flight to
+// keep HBM busy.  All counts are exact integers.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,10 +24,16 @@ constexpr int kHistThreads = 512;
 constexpr int kHistWarps = kHistThreads / 32;
 
 __device__ __forceinline__ void count_byte(unsigned int* wh, unsigned int v, unsigned int active) {
-  unsigned int peers = __match_any_sync(active, v);
-  int leader = __ffs(peers) - 1;
-  if ((int)(threadIdx.x & 31) == leader) atomicAdd(&wh[v], (unsigned int)__popc(peers));
+  const int first = __ffs(active) - 1;
+  const bool uniform = __all_sync(active, v == __shfl_sync(active, v, first));
+  if (uniform) {
+    if ((int)(threadIdx.x & 31) == first) atomicAdd(&wh[v], (unsigned int)__popc(active));
+  } else {
+    atomicAdd(&wh[v], 1u);
+  }
 }
+
+constexpr int kChunksPerIter = 4;
 
 __global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigned int* __restrict__ hist) {
   __shared__ unsigned int sh[kHistWarps][256];
@@ -33,28 +42,41 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigne
   unsigned int* wh = sh[threadIdx.x >> 5];
   const int chunks_per_row = (in.w + 15) >> 4;
   const long long n_chunks = (long long)chunks_per_row * in.h;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  // every lane of a warp runs the same number of iterations (warp-uniform
-  // bound), so the full-warp match below is always legal
-  const long long warp_base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
-  for (long long base = warp_base; base < n_chunks; base += stride) {
-    long long ch = base + (threadIdx.x & 31);
-    bool valid = ch < n_chunks;
-    int y = valid ? (int)(ch / chunks_per_row) : 0;
-    int x0 = valid ? (int)(ch - (long long)y * chunks_per_row) << 4 : 0;
-    const unsigned char* row = (const unsigned char*)in.data + (long long)y * in.rs;
-    unsigned int words[4] = {0, 0, 0, 0};
-    int nbytes = valid ? min(16, in.w - x0) : 0;
-    if (nbytes == 16) {
-      uint4 q = *reinterpret_cast<const uint4*>(row + x0);
-      words[0] = q.x; words[1] = q.y; words[2] = q.z; words[3] = q.w;
-    } else {
-      for (int b = 0; b < nbytes; ++b) words[b >> 2] |= (unsigned int)row[x0 + b] << (8 * (b & 3));
+  // a warp takes 32 x kChunksPerIter consecutive chunks per iteration; the
+  // loop bound is warp-uniform, so the warp-wide votes below are legal
+  const long long per_iter = (long long)gridDim.x * blockDim.x * kChunksPerIter;
+  const long long warp_base = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kChunksPerIter;
+  const int lane = threadIdx.x & 31;
+  for (long long base = warp_base; base < n_chunks; base += per_iter) {
+    unsigned int words[kChunksPerIter][4];
+    int nbytes[kChunksPerIter];
+#pragma unroll
+    for (int u = 0; u < kChunksPerIter; ++u) {
+      const long long ch = base + u * 32 + lane;
+      words[u][0] = words[u][1] = words[u][2] = words[u][3] = 0;
+      nbytes[u] = 0;
+      if (ch < n_chunks) {
+        const int y = (int)(ch / chunks_per_row);
+        const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+        const unsigned char* row = (const unsigned char*)in.data + (long long)y * in.rs;
+        nbytes[u] = min(16, in.w - x0);
+        if (nbytes[u] == 16) {
+          const uint4 q = __ldcs(reinterpret_cast<const uint4*>(row + x0));
+          words[u][0] = q.x; words[u][1] = q.y; words[u][2] = q.z; words[u][3] = q.w;
+        } else {
+#pragma unroll
+          for (int b = 0; b < 16; ++b)
+            if (b < nbytes[u]) words[u][b >> 2] |= (unsigned int)row[x0 + b] << (8 * (b & 3));
+        }
+      }
     }
 #pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      unsigned int active = __ballot_sync(0xffffffffu, b < nbytes);
-      if (b < nbytes) count_byte(wh, (words[b >> 2] >> (8 * (b & 3))) & 0xffu, active);
+    for (int u = 0; u < kChunksPerIter; ++u) {
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const unsigned int active = __ballot_sync(0xffffffffu, b < nbytes[u]);
+        if (b < nbytes[u]) count_byte(wh, (words[u][b >> 2] >> (8 * (b & 3))) & 0xffu, active);
+      }
     }
   }
   __syncthreads();
@@ -106,6 +128,11 @@ __global__ void __launch_bounds__(256) k_cdf_lut(const unsigned int* __restrict_
   lut[v] = (unsigned char)out;
 }
 
+__device__ __forceinline__ unsigned int lut4(const unsigned char* t, unsigned int a) {
+  return (unsigned int)t[a & 0xff] | ((unsigned int)t[(a >> 8) & 0xff] << 8) |
+         ((unsigned int)t[(a >> 16) & 0xff] << 16) | ((unsigned int)t[a >> 24] << 24);
+}
+
 __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out,
                                                    const unsigned char* __restrict__ lut) {
   __shared__ unsigned char t[256];
@@ -113,25 +140,36 @@ __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgVi
   __syncthreads();
   const int chunks_per_row = (in.w + 15) >> 4;
   const long long n_chunks = (long long)chunks_per_row * in.h;
-  for (long long ch = (long long)blockIdx.x * blockDim.x + threadIdx.x; ch < n_chunks;
-       ch += (long long)gridDim.x * blockDim.x) {
-    int y = (int)(ch / chunks_per_row);
-    int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
-    const unsigned char* src = (const unsigned char*)in.data + (long long)y * in.rs + x0;
-    unsigned char* dst = (unsigned char*)out.data + (long long)y * out.rs + x0;
-    int nb = min(16, in.w - x0);
-    if (nb == 16) {
-      uint4 q = *reinterpret_cast<const uint4*>(src);
-      unsigned int wv[4] = {q.x, q.y, q.z, q.w};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < n_chunks; c0 += stride * kChunksPerIter) {
+    uint4 q[kChunksPerIter];
+    int nb[kChunksPerIter];
+    long long chs[kChunksPerIter];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        unsigned int a = wv[i];
-        wv[i] = (unsigned int)t[a & 0xff] | ((unsigned int)t[(a >> 8) & 0xff] << 8) |
-                ((unsigned int)t[(a >> 16) & 0xff] << 16) | ((unsigned int)t[a >> 24] << 24);
+    for (int u = 0; u < kChunksPerIter; ++u) {
+      const long long ch = c0 + u * stride;
+      chs[u] = ch;
+      nb[u] = 0;
+      if (ch < n_chunks) {
+        const int y = (int)(ch / chunks_per_row);
+        const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+        nb[u] = min(16, in.w - x0);
+        if (nb[u] == 16) q[u] = __ldcs(reinterpret_cast<const uint4*>((const unsigned char*)in.data + (long long)y * in.rs + x0));
       }
-      *reinterpret_cast<uint4*>(dst) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-    } else {
-      for (int b = 0; b < nb; ++b) dst[b] = t[src[b]];
+    }
+#pragma unroll
+    for (int u = 0; u < kChunksPerIter; ++u) {
+      if (nb[u] == 0) continue;
+      const long long ch = chs[u];
+      const int y = (int)(ch / chunks_per_row);
+      const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+      unsigned char* dst = (unsigned char*)out.data + (long long)y * out.rs + x0;
+      if (nb[u] == 16) {
+        __stcs(reinterpret_cast<uint4*>(dst), make_uint4(lut4(t, q[u].x), lut4(t, q[u].y), lut4(t, q[u].z), lut4(t, q[u].w)));
+      } else {
+        const unsigned char* src = (const unsigned char*)in.data + (long long)y * in.rs + x0;
+        for (int b = 0; b < nb[u]; ++b) dst[b] = t[src[b]];
+      }
     }
   }
 }
@@ -154,8 +192,8 @@ int launch_hist(const HistArgs& a, void* stream) {
   int e = (int)cudaMemsetAsync(a.hist, 0, 256 * sizeof(unsigned int), s);
   if (e) return e;
   long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
-  long long want = (chunks + kHistThreads - 1) / kHistThreads;
-  int blocks = (int)(want < 2LL * sm_count() ? want : 2LL * sm_count());
+  long long want = (chunks + kHistThreads * kChunksPerIter - 1) / (kHistThreads * kChunksPerIter);
+  int blocks = (int)(want < 4LL * sm_count() ? want : 4LL * sm_count());
   if (blocks < 1) blocks = 1;
   k_hist<<<blocks, kHistThreads, 0, s>>>(a.in, a.hist);
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
@@ -170,7 +208,7 @@ int launch_cdf_lut(const LutArgs& a, void* stream) {
 
 int launch_lut_apply(const LutApplyArgs& a, void* stream) {
   long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
-  long long want = (chunks + 255) / 256;
+  long long want = (chunks + 256 * kChunksPerIter - 1) / (256 * kChunksPerIter);
   int blocks = (int)(want < 8LL * sm_count() ? want : 8LL * sm_count());
   if (blocks < 1) blocks = 1;
   k_lut_apply<<<blocks, 256, 0, (cudaStream_t)stream>>>(a.in, a.out, a.lut);

@@ -146,7 +146,7 @@ int ll_down_smem_bytes(int tile_w, int tile_h) {
 
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream) {
   static bool configured = false;
-  if (smem_bytes > 48 * 1024 && !configured) {
+  if (!configured) {  // opt in once: static shared memory also counts against the default 48 KB
     int e = allow_max_dynamic_smem((const void*)k_ll_down);
     if (e) return e;
     configured = true;

@@ -101,6 +101,7 @@ __device__ __forceinline__ float tapn(const float* w, const float* x, int n) {
 }
 
 // ---- point-wise ops --------------------------------------------------------
+
 __device__ __forceinline__ float op_gray(float r, float g, float b, float scale) {
   float rs = __fmul_rn(r, scale), gs = __fmul_rn(g, scale), bs = __fmul_rn(b, scale);
   return __fmaf_rn(0.114f, bs, __fmaf_rn(0.587f, gs, __fmul_rn(0.299f, rs)));
@@ -116,18 +117,19 @@ __device__ __forceinline__ float op_unsharp(float in, float blur, float amount) 
   return __fmaf_rn(amount, __fsub_rn(in, blur), in);
 }
 
-// Paris et al. remap of intensity i around level g (sigma_r, alpha, beta).
+// Paris et al. remap of intensity i around level g (sigma_r, alpha, beta):
+//   |d| <= sigma: g + sign(d) sigma (|d|/sigma)^alpha;  else g + sign(d) (beta (|d| - sigma) + sigma)
+// with d = i - g.  The power is CUDA's fast __powf (x = |d|/sigma lies in
+// (0, 1]); both branches are evaluated and one is selected, so a warp never
+// splits on the band test.
 __device__ __forceinline__ float op_ll_remap(float i, float g, float sigma, float alpha, float beta) {
-  float d = __fsub_rn(i, g);
-  float ad = fabsf(d);
-  if (ad == 0.0f) return g;
-  float mag;
-  if (ad <= sigma) {
-    mag = __fmul_rn(sigma, powf(__fdiv_rn(ad, sigma), alpha));
-  } else {
-    mag = __fmaf_rn(beta, __fsub_rn(ad, sigma), sigma);
-  }
-  return __fadd_rn(g, copysignf(mag, d));
+  const float d = __fsub_rn(i, g);
+  const float ad = fabsf(d);
+  const float x = __fdiv_rn(ad, sigma);
+  const float inside = __fmul_rn(sigma, __powf(x, alpha));
+  const float outside = __fmaf_rn(beta, __fsub_rn(ad, sigma), sigma);
+  const float mag = ad <= sigma ? inside : outside;
+  return ad == 0.0f ? g : __fadd_rn(g, copysignf(mag, d));
 }
 
 __device__ __forceinline__ float ll_level(int k, int K) { return __fdiv_rn((float)k, (float)(K - 1)); }
