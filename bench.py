@@ -493,6 +493,89 @@ def run_reference(args, cfg_name):
             "e2e": {"value": v, "unit": "MPix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ------------------------------------------------------------------ serving --
+SERVING_SIZES = [(256, 256), (480, 640), (1080, 1920), (1536, 2560), (3072, 4096)]
+
+
+def run_serving(args):
+    """Poisson streams of requests drawn uniformly from {unsharp, Harris,
+    histogram equalize} x five image sizes, through the continuous-batching
+    server; p50/p99 latency and MPix/s per arrival rate."""
+    import torch
+    from paper_2012_07145_gb300 import hp, pipelines, synth
+    import __graft_entry__
+    __graft_entry__.build()
+    un = pipelines.unsharp()
+    pipelines.fused_schedule(un, tile_w=64, tile_h=32)
+    hr = pipelines.harris()
+    pipelines.fused_schedule(hr, tile_w=64, tile_h=32)
+    he = pipelines.histeq()
+    kinds = [("unsharp", un, 3, hp.HP_F32, 3, torch.float32), ("harris", hr, 3, hp.HP_F32, 1, torch.float32),
+             ("histeq", he, 1, hp.HP_U8, 1, torch.uint8)]
+    ring = 3
+    bufs = {}
+    for name, p, ic, idt, oc, tdt in kinds:
+        for (h, w) in SERVING_SIZES:
+            arr = synth.rgb_f32(h, w, seed=7) if idt == hp.HP_F32 else synth.gray_u8_lowcontrast(h, w, seed=7)
+            hin = torch.from_numpy(arr).pin_memory()
+            outs = [torch.empty((oc, h, w), dtype=tdt).pin_memory() for _ in range(ring)]
+            bufs[(name, h, w)] = (p, hp.buffer_from_tensor(hin, idt), [hp.buffer_from_tensor(o, 0 if idt == hp.HP_U8 else hp.HP_F32) for o in outs], hin, outs)
+    rates = [float(r) for r in args.rates.split(",")]
+    rng = np.random.default_rng(0)
+    per_rate = []
+    for lam in rates:
+        n = args.requests
+        picks = [(kinds[rng.integers(3)][0],) + SERVING_SIZES[rng.integers(len(SERVING_SIZES))] for _ in range(n)]
+        gaps = rng.exponential(1.0 / lam, n)
+        srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
+        # warm the slots' pipeline copies (scratch, kernel attributes) outside the measured stream
+        warm = [srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][0]) for k in bufs for _ in range(2)]
+        for t in warm:
+            srv.wait(t, 120000)
+        srv.close()
+        srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
+        for k in bufs:
+            srv.wait(srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][0]), 120000)
+        base = srv.stats()
+        t0 = time.perf_counter()
+        due = t0
+        tickets = []
+        for i, (name, h, w) in enumerate(picks):
+            due += gaps[i]
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                if due - now > 2e-4:
+                    time.sleep((due - now) - 1e-4)
+            p, bi, bos, _, _ = bufs[(name, h, w)]
+            tickets.append(srv.submit(p, [bi], bos[i % ring]))
+        lats = []
+        for t in tickets:
+            st, lat = srv.wait(t, 300000)
+            if st == hp.HP_OK:
+                lats.append(lat)
+        t1 = time.perf_counter()
+        stats = srv.stats()
+        srv.close()
+        mpix = sum(h * w for _, h, w in picks) / 1e6
+        per_rate.append({"rate_per_s": lam, "requests": n, "completed": len(lats),
+                         "p50_ms": round(float(np.percentile(lats, 50)) / 1e3, 3),
+                         "p99_ms": round(float(np.percentile(lats, 99)) / 1e3, 3),
+                         "mpix_per_s": round(mpix / (t1 - t0), 1),
+                         "batched_launches": int(stats.batched_launches - base.batched_launches),
+                         "peak_hbm_bytes": int(stats.peak_bytes)})
+    top = per_rate[-1]
+    return {"metric": METRIC, "value": top["mpix_per_s"], "unit": "MPix/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed (f32 RGB, u8)", "data": "synthetic",
+            "config": {"workload": "serving_mix_unsharp_harris_histeq_poisson",
+                       "sizes": ["%dx%d" % (w, h) for h, w in SERVING_SIZES], "slots": 8, "max_batch": 8,
+                       "hbm_budget_bytes": 8 << 30,
+                       "latency": "host submit to completion observed by the server (includes host copies)"},
+            "serving": per_rate}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,11 +585,18 @@ def main():
     ap.add_argument("--config", default="chain32", help="workload name, or 'all' (one line per workload)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--rates", default="200,500,1000,2000", help="serving: Poisson arrival rates per second")
+    ap.add_argument("--requests", type=int, default=300, help="serving: requests per arrival rate")
     ap.add_argument("--only-fused", action="store_true",
                     help="time the fused pipeline only (for profiler runs); prints no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.config == "serving":
+        line = run_serving(args) if args.impl == "ours" else {"impl": "reference", "unavailable":
+                                                              "the serving loop has no CPU counterpart"}
+        print(json.dumps(line), flush=True)
+        return
     names = list(config_table().keys()) if args.config == "all" else [args.config]
     for name in names:
         line = run_reference(args, name) if args.impl == "reference" else run_ours(args, name)

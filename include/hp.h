@@ -221,6 +221,40 @@ hp_status hp_infer_bounds(hp_pipeline* p, const int* in_widths, const int* in_he
 enum { HP_OPT_CUDA_GRAPH = 1 };
 hp_status hp_set_option(hp_pipeline* p, int option, long long value);
 
+/* ---- Serving loop ---------------------------------------------------------
+ * Continuous batching of pipeline requests on one GPU.  Requests (a pipeline,
+ * HOST input buffers, a HOST output buffer) are admitted in arrival order as
+ * soon as one of `slots` CUDA streams and enough of an HBM arena reserved at
+ * creation (`hbm_budget_bytes`) are free; admitted requests run concurrently
+ * (copy in, realize, copy out).  Up to `max_batch` queued requests for the same
+ * pipeline and image size are served by one realize when every stage acts on
+ * each channel separately (stencils, resampling, per-channel point-wise ops):
+ * their planes are stacked, so each kernel launches once for the batch and
+ * every result equals the request's solo result.  Host buffers must stay
+ * valid until the request completes; pinned memory gives asynchronous copies.
+ * The pipeline must outlive the server.  Latency = submit to the completion the
+ * server's worker thread observes. */
+typedef struct hp_server hp_server;
+typedef struct {
+  unsigned long long submitted, completed, failed;
+  unsigned long long batched_launches;  /* realizes that served more than one request */
+  unsigned long long peak_bytes;        /* peak arena bytes admitted */
+  double p50_us, p99_us, mean_us, max_us;
+  double mpix;                          /* output megapixels completed */
+  double busy_s;                        /* first submit to last completion */
+} hp_server_stats;
+
+hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slots, int max_batch);
+/* Enqueues a request; *ticket identifies it.  Never blocks on the GPU. */
+hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                           const hp_buffer* output, unsigned long long* ticket);
+/* Waits up to timeout_ms for a request; HP_ERR_TIMEOUT if it is not complete
+ * by then (it stays queued or running), else the request's status. */
+hp_status hp_server_wait(hp_server* s, unsigned long long ticket, int timeout_ms, double* latency_us);
+hp_status hp_server_stats_get(hp_server* s, hp_server_stats* stats);
+/* Finishes queued and running requests, then frees the server. */
+hp_status hp_server_destroy(hp_server* s);
+
 /* Reads and clears the pipeline's device error word (synchronises the device).
  * *code: 0 = no error; 1 = a bounded TMA/mbarrier wait gave up; 2 = a fused
  * kernel's read fell outside the tile bounds inference gave it (the read was

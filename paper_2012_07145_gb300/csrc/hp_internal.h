@@ -212,7 +212,7 @@ int launch_upsample(const ResampleArgs& a, void* stream);
 int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream);
 int harris_smem_bytes(int tile_w, int tile_h, int in_dtype);
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
-int ll_down_smem_bytes(int tile_w, int tile_h);
+int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);

@@ -27,60 +27,82 @@ namespace hp {
 
 namespace {
 
+// Source value at clamped fine coordinates: a plane of the level (f32 fast
+// path or any dtype) or, for the remap source, computed from the gray tile.
+template <bool F32>
+__device__ __forceinline__ float level_px(const ImgView& v, int c, int x, int y) {
+  if (F32) return __ldg(reinterpret_cast<const float*>((const char*)v.data + (long long)c * v.ps + (long long)y * v.rs) + x);
+  return load_px(v, c, x, y);
+}
+
+template <bool REMAP, bool F32>
 __global__ void __launch_bounds__(256) k_ll_down(const LLDownArgs a) {
   extern __shared__ __align__(16) float sm[];
   const int FW = 2 * a.tile_w + 3, FH = 2 * a.tile_h + 3;
-  float* GR = sm;                 // gray tile (remap source only)
-  float* S = GR + FW * FH;        // source channel tile
-  float* HX = S + FW * FH;        // x-pass results, FH x tile_w
+  const int plane = FW * FH;
+  float* GR = sm;                           // gray tile (remap source only)
+  float* S = GR + (REMAP ? plane : 0);      // C source planes
+  float* HX = S + a.C * plane;              // C x-pass planes, FH x tile_w
   const int x0 = blockIdx.x * a.tile_w, y0 = blockIdx.y * a.tile_h;
   const int fx0 = 2 * x0 - 2, fy0 = 2 * y0 - 2;
   const int Wf = a.src.w, Hf = a.src.h;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (a.remap) {
-    for (int r = warp; r < FH; r += nw) {
-      const int fy = iclamp(fy0 + r, 0, Hf - 1);
-      for (int q = lane; q < FW; q += 32) {
-        const int fx = iclamp(fx0 + q, 0, Wf - 1);
-        GR[r * FW + q] = round_storage(a.st_gray, op_gray(load_px(a.src, 0, fx, fy), load_px(a.src, 1, fx, fy),
-                                                          load_px(a.src, 2, fx, fy), a.gray_scale));
-      }
+  const int nt = blockDim.x;
+  if (REMAP) {
+    for (int i = threadIdx.x; i < plane; i += nt) {
+      const int r = i / FW, q = i - r * FW;
+      const int fy = iclamp(fy0 + r, 0, Hf - 1), fx = iclamp(fx0 + q, 0, Wf - 1);
+      GR[i] = round_storage(a.st_gray, op_gray(load_px(a.src, 0, fx, fy), load_px(a.src, 1, fx, fy),
+                                               load_px(a.src, 2, fx, fy), a.gray_scale));
     }
     __syncthreads();
-  }
-  for (int c = 0; c < a.C; ++c) {
-    if (a.remap) {
-      const float gk = c < a.K ? ll_level(c, a.K) : 0.0f;
-      for (int r = warp; r < FH; r += nw)
-        for (int q = lane; q < FW; q += 32) {
-          const float g = GR[r * FW + q];
-          S[r * FW + q] = round_storage(a.st_remap, c < a.K ? op_ll_remap(g, gk, a.sigma, a.alpha, a.beta) : g);
+    for (int i = threadIdx.x; i < a.C * plane; i += nt) {
+      const int c = i / plane, j = i - c * plane;
+      const float g = GR[j];
+      S[i] = round_storage(a.st_remap, c < a.K ? op_ll_remap(g, ll_level(c, a.K), a.sigma, a.alpha, a.beta) : g);
+    }
+  } else {
+    // four loads in flight per thread before any store
+    const int total = a.C * plane;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * nt) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * nt;
+        v[u] = 0.0f;
+        if (i < total) {
+          const int c = i / plane, j = i - c * plane;
+          const int r = j / FW, q = j - r * FW;
+          v[u] = level_px<F32>(a.src, c, iclamp(fx0 + q, 0, Wf - 1), iclamp(fy0 + r, 0, Hf - 1));
         }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u * nt < total) S[i0 + u * nt] = v[u];
+    }
+  }
+  __syncthreads();
+  const int hxp = FH * a.tile_w;
+  for (int i = threadIdx.x; i < a.C * hxp; i += nt) {
+    const int c = i / hxp, j = i - c * hxp;
+    const int r = j / a.tile_w, x = j - r * a.tile_w;
+    const float* s = S + c * plane + r * FW + 2 * x;
+    HX[i] = tap5_binomial16(s[0], s[1], s[2], s[3], s[4]);
+  }
+  __syncthreads();
+  const int op = a.tile_h * a.tile_w;
+  const int tw = a.tile_w;
+  for (int i = threadIdx.x; i < a.C * op; i += nt) {
+    const int c = i / op, j = i - c * op;
+    const int y = j / tw, x = j - y * tw;
+    const int ox = x0 + x, oy = y0 + y;
+    if (ox >= a.out.w || oy >= a.out.h) continue;
+    const float* h = HX + c * hxp + 2 * y * tw + x;
+    const float v = round_storage(a.st_out, tap5_binomial16(h[0], h[tw], h[2 * tw], h[3 * tw], h[4 * tw]));
+    if (F32) {
+      reinterpret_cast<float*>((char*)a.out.data + (long long)c * a.out.ps + (long long)oy * a.out.rs)[ox] = v;
     } else {
-      for (int r = warp; r < FH; r += nw) {
-        const int fy = iclamp(fy0 + r, 0, Hf - 1);
-        for (int q = lane; q < FW; q += 32) S[r * FW + q] = load_px(a.src, c, iclamp(fx0 + q, 0, Wf - 1), fy);
-      }
+      store_px(a.out, c, ox, oy, v);
     }
-    __syncthreads();
-    for (int r = warp; r < FH; r += nw)
-      for (int x = lane; x < a.tile_w; x += 32) {
-        const float* s = S + r * FW + 2 * x;
-        HX[r * a.tile_w + x] = tap5_binomial16(s[0], s[1], s[2], s[3], s[4]);
-      }
-    __syncthreads();
-    for (int y = warp; y < a.tile_h; y += nw) {
-      const int oy = y0 + y;
-      for (int x = lane; x < a.tile_w; x += 32) {
-        const int ox = x0 + x;
-        if (ox >= a.out.w || oy >= a.out.h) continue;
-        const float* h = HX + 2 * y * a.tile_w + x;
-        const int tw = a.tile_w;
-        store_px(a.out, c, ox, oy,
-                 round_storage(a.st_out, tap5_binomial16(h[0], h[tw], h[2 * tw], h[3 * tw], h[4 * tw])));
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -88,48 +110,56 @@ __global__ void __launch_bounds__(256) k_ll_down(const LLDownArgs a) {
 // parity, coarse indices clamped; x pass over each needed coarse row, then y.
 // Each coarse value is first rounded to `st` (the storage of the stage it
 // stands for; a no-op when the buffer already holds that stage).
-__device__ __forceinline__ float upsample_at(const ImgView& v, int c, int X, int Y, int st = HP_F32) {
+template <bool F32>
+__device__ __forceinline__ float upsample_at(const ImgView& v, int c, int X, int Y, int st) {
   float wx[3], wy[3], xs[3], hs[3];
   int mx0, my0;
   const int nx = up_taps(X, &mx0, wx);
   const int ny = up_taps(Y, &my0, wy);
   for (int t = 0; t < ny; ++t) {
     const int yy = iclamp(my0 + t, 0, v.h - 1);
-    for (int i = 0; i < nx; ++i) xs[i] = round_storage(st, load_px(v, c, iclamp(mx0 + i, 0, v.w - 1), yy));
+    for (int i = 0; i < nx; ++i) {
+      const float raw = level_px<F32>(v, c, iclamp(mx0 + i, 0, v.w - 1), yy);
+      xs[i] = F32 ? raw : round_storage(st, raw);
+    }
     hs[t] = tapn(wx, xs, nx);
   }
   return tapn(wy, hs, ny);
 }
 
+// F32: every level buffer and every stage stored as f32 (no rounding steps).
+template <bool LEVEL0, bool F32>
 __global__ void __launch_bounds__(256) k_ll_level(const LLLevelArgs a) {
   const int X = blockIdx.x * 32 + (threadIdx.x & 31);
   const int Y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (X >= a.W || Y >= a.H) return;
+  auto rs = [](int st, float v) { return F32 ? v : round_storage(st, v); };
   const int K = a.K;
   float gray = 0.0f, rgb[3];
   float gK;
-  if (a.level0) {
+  if (LEVEL0) {
     for (int c = 0; c < 3; ++c) rgb[c] = load_px(a.in, c, X, Y);
-    gray = round_storage(a.st_gray, op_gray(rgb[0], rgb[1], rgb[2], a.gray_scale));
-    gK = round_storage(a.st_G, gray);
+    gray = rs(a.st_gray, op_gray(rgb[0], rgb[1], rgb[2], a.gray_scale));
+    gK = rs(a.st_G, gray);
   } else {
-    gK = load_px(a.G, K, X, Y);
+    gK = level_px<F32>(a.G, K, X, Y);
   }
   int k0;
   float f;
   ll_interp_index(gK, K, &k0, &f);
   float Lk[2];
+#pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int k = k0 + j;
-    const float g = a.level0 ? round_storage(a.st_G, op_ll_remap(gray, ll_level(k, K), a.sigma, a.alpha, a.beta))
-                             : load_px(a.G, k, X, Y);
-    const float u = round_storage(a.st_U, upsample_at(a.Gn, k, X, Y));
-    Lk[j] = round_storage(a.st_L, op_binary(HP_OP_SUB, g, u));
+    const float g = LEVEL0 ? rs(a.st_G, op_ll_remap(gray, ll_level(k, K), a.sigma, a.alpha, a.beta))
+                           : level_px<F32>(a.G, k, X, Y);
+    const float u = rs(a.st_U, upsample_at<F32>(a.Gn, k, X, Y, HP_F32));
+    Lk[j] = rs(a.st_L, op_binary(HP_OP_SUB, g, u));
   }
-  const float lout = round_storage(a.st_Lout, op_ll_blend(Lk[0], Lk[1], f));
-  const float ur = round_storage(a.st_UR, upsample_at(a.Rn, a.rn_ch, X, Y, a.rn_st));
-  const float r = round_storage(a.st_R, op_binary(HP_OP_ADD, lout, ur));
-  if (a.level0) {
+  const float lout = rs(a.st_Lout, op_ll_blend(Lk[0], Lk[1], f));
+  const float ur = rs(a.st_UR, upsample_at<F32>(a.Rn, a.rn_ch, X, Y, a.rn_st));
+  const float r = rs(a.st_R, op_binary(HP_OP_ADD, lout, ur));
+  if (LEVEL0) {
     for (int c = 0; c < 3; ++c)
       store_px(a.out, c, X, Y, round_storage(a.out.dtype, op_ll_colour(rgb[c], gray, r, a.s_in, a.s_out)));
   } else {
@@ -139,27 +169,42 @@ __global__ void __launch_bounds__(256) k_ll_level(const LLLevelArgs a) {
 
 }  // namespace
 
-int ll_down_smem_bytes(int tile_w, int tile_h) {
+int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap) {
   const int FW = 2 * tile_w + 3, FH = 2 * tile_h + 3;
-  return (2 * FW * FH + FH * tile_w) * 4;
+  return ((remap ? FW * FH : 0) + channels * FW * FH + channels * FH * tile_w) * 4;
 }
 
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream) {
-  static bool configured = false;
-  if (!configured) {  // opt in once: static shared memory also counts against the default 48 KB
-    int e = allow_max_dynamic_smem((const void*)k_ll_down);
+  typedef void (*K)(LLDownArgs);
+  const bool f32 = a.src.dtype == HP_F32 && a.out.dtype == HP_F32 && a.st_out == HP_F32;
+  const int variant = (a.remap ? 2 : 0) + (f32 ? 1 : 0);
+  const K kernels[4] = {k_ll_down<false, false>, k_ll_down<false, true>, k_ll_down<true, false>,
+                        k_ll_down<true, true>};
+  static bool configured[4] = {};
+  if (!configured[variant]) {  // opt in once: static shared memory also counts against the default 48 KB
+    int e = allow_max_dynamic_smem((const void*)kernels[variant]);
     if (e) return e;
-    configured = true;
+    configured[variant] = true;
   }
   dim3 grid(a.tiles_x, a.tiles_y, 1);
-  k_ll_down<<<grid, 256, smem_bytes, (cudaStream_t)stream>>>(a);
+  kernels[variant]<<<grid, 256, smem_bytes, (cudaStream_t)stream>>>(a);
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
 
 int launch_ll_level(const LLLevelArgs& a, void* stream) {
   dim3 grid((a.W + 31) / 32, (a.H + 7) / 8, 1);
-  k_ll_level<<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  bool f32 = a.Gn.dtype == HP_F32 && a.Rn.dtype == HP_F32 && a.rn_st == HP_F32 && a.st_G == HP_F32 &&
+             a.st_U == HP_F32 && a.st_L == HP_F32 && a.st_Lout == HP_F32 && a.st_UR == HP_F32 && a.st_R == HP_F32;
+  if (a.level0) {
+    f32 = f32 && a.st_gray == HP_F32;
+    if (f32) k_ll_level<true, true><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else k_ll_level<true, false><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  } else {
+    f32 = f32 && a.G.dtype == HP_F32;
+    if (f32) k_ll_level<false, true><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    else k_ll_level<false, false><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

@@ -758,8 +758,10 @@ hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
   gp.threads = 256;
-  gp.smem = ll_down_smem_bytes(a.tile_w, a.tile_h);
-  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "downsample tile too large");
+  gp.smem = ll_down_smem_bytes(a.tile_w, a.tile_h, a.C, a.remap);
+  if (gp.smem > kSmemLimit)
+    return fail(HP_ERR_SCHEDULE, "downsample of %d channels with tile %dx%d needs %d bytes of shared memory", a.C,
+                a.tile_w, a.tile_h, gp.smem);
   gp.grid_x = a.tiles_x;
   gp.grid_y = a.tiles_y;
   return HP_OK;
@@ -836,9 +838,20 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.seg = pick(p->serial_y, g, 8);
         s = build_chain(p, plan, gp, gp.kernel == HP_KERNEL_UNSHARP);
         break;
-      case HP_KERNEL_DOWNSAMPLE:
-        gp.tile_w = std::min(pick(p->tile_w, g, 32), 64);
-        gp.tile_h = std::min(pick(p->tile_h, g, 16), 64);
+      case HP_KERNEL_DOWNSAMPLE: {
+        // default: 16x16 coarse tiles, halved (down to 4x4) for small levels so
+        // that the grid still covers the SMs
+        Dom od = plan.dom[gp.output];
+        int t = 16;
+        while (t > 4 && ((od.w + t - 1) / t) * ((od.h + t - 1) / t) < 256) t /= 2;
+        gp.tile_w = std::min(pick(p->tile_w, g, t), 64);
+        gp.tile_h = std::min(pick(p->tile_h, g, t), 64);
+        const int c = p->stages[gp.output].channels;
+        while (ll_down_smem_bytes(gp.tile_w, gp.tile_h, c, 1) > kSmemLimit && gp.tile_w > 4) {
+          gp.tile_w /= 2;
+          gp.tile_h = std::max(4, gp.tile_h / 2);
+        }
+      }
         s = build_down(p, plan, gp);
         break;
       case HP_KERNEL_LL_LEVEL:
@@ -1369,6 +1382,49 @@ hp_status hp_infer_bounds(hp_pipeline* p, const int* ws, const int* hs, int grou
   }
   return HP_OK;
 }
+
+}  // extern "C"
+
+namespace hp {
+
+// True when every stage acts on each channel separately, so B images can be
+// stacked plane-wise into one image of B times the channels.
+bool pipeline_stackable(const hp_pipeline* p) {
+  for (const Stage& s : p->stages) {
+    if (s.kind == HP_STENCIL || s.kind == HP_DOWNSAMPLE2 || s.kind == HP_UPSAMPLE2) continue;
+    if (s.kind == HP_POINTWISE && (s.op == HP_OP_MUL || s.op == HP_OP_ADD || s.op == HP_OP_SUB ||
+                                   s.op == HP_OP_UNSHARP || s.op == HP_OP_SCALE))
+      continue;
+    return false;
+  }
+  return true;
+}
+
+// A copy of the pipeline's algorithm and schedule (no plans, no scratch); with
+// batch > 1 every channel count is multiplied by batch (stackable pipelines).
+hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch) {
+  if (batch > 1 && !pipeline_stackable(p)) return nullptr;
+  auto* c = new hp_pipeline();
+  c->in_dtypes = p->in_dtypes;
+  c->in_channels = p->in_channels;
+  for (int& ch : c->in_channels) ch *= batch;
+  c->stages = p->stages;
+  for (Stage& s : c->stages) s.channels *= batch;
+  c->output = p->output;
+  c->has_schedule = p->has_schedule;
+  c->group_of = p->group_of;
+  c->n_groups = p->n_groups;
+  c->tile_w = p->tile_w;
+  c->tile_h = p->tile_h;
+  c->threads = p->threads;
+  c->serial_y = p->serial_y;
+  c->impl = p->impl;
+  return c;
+}
+
+}  // namespace hp
+
+extern "C" {
 
 hp_status hp_check_device_error(hp_pipeline* p, int* code) {
   if (!p || !code) return fail(HP_ERR_INVALID_ARG, "null argument");

@@ -58,9 +58,17 @@ class GroupInfo(ctypes.Structure):
                 ("smem_bytes", ctypes.c_int)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong),
+                ("batched_launches", ctypes.c_ulonglong), ("peak_bytes", ctypes.c_ulonglong),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
+                ("max_us", ctypes.c_double), ("mpix", ctypes.c_double), ("busy_s", ctypes.c_double)]
+
+
 EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_set", "hp_realize",
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
-           "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc"]
+           "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
+           "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy"]
 
 _lib = None
 
@@ -87,6 +95,12 @@ def lib():
         L.hp_set_option.argtypes = [P, ctypes.c_int, ctypes.c_longlong]
         L.hp_pipeline_destroy.argtypes = [P]
         L.hp_histeq_u8_noalloc.argtypes = [ctypes.POINTER(Buffer), ctypes.POINTER(Buffer), P]
+        L.hp_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
+        L.hp_server_submit.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer),
+                                       ctypes.POINTER(ctypes.c_ulonglong)]
+        L.hp_server_wait.argtypes = [P, ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+        L.hp_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.hp_server_destroy.argtypes = [P]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
         for name in EXPORTS:
@@ -240,3 +254,41 @@ class Pipeline:
         out = (ctypes.c_int * (4 * n))()
         check(lib().hp_infer_bounds(self.h, ws, hs, g, x0, y0, w, h, out, n))
         return [tuple(out[4 * i:4 * i + 4]) for i in range(n)]
+
+
+class Server:
+    """Continuous-batching serving loop (hp_server_*): submit host-buffer
+    requests for any pipeline; they run as slots and HBM budget allow."""
+
+    def __init__(self, hbm_budget_bytes: int, slots: int = 4, max_batch: int = 8):
+        self.h = ctypes.c_void_p()
+        check(lib().hp_server_create(ctypes.byref(self.h), hbm_budget_bytes, slots, max_batch))
+        self._keep = {}
+
+    def submit(self, pipeline: "Pipeline", inputs, output) -> int:
+        arr = (Buffer * len(inputs))(*inputs)
+        t = ctypes.c_ulonglong()
+        check(lib().hp_server_submit(self.h, pipeline.h, arr, len(inputs), ctypes.byref(output), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        """(status, latency_us); status HP_ERR_TIMEOUT if not done in time."""
+        lat = ctypes.c_double()
+        st = lib().hp_server_wait(self.h, ticket, timeout_ms, ctypes.byref(lat))
+        return st, lat.value
+
+    def stats(self) -> ServerStats:
+        s = ServerStats()
+        check(lib().hp_server_stats_get(self.h, ctypes.byref(s)))
+        return s
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            check(lib().hp_server_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
