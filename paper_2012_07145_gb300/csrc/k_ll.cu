@@ -35,75 +35,86 @@ __device__ __forceinline__ float level_px(const ImgView& v, int c, int x, int y)
   return load_px(v, c, x, y);
 }
 
+// Tile widths are powers of two (checked on the host): lg_tw = log2(tile_w).
 template <bool REMAP, bool F32>
 __global__ void __launch_bounds__(256) k_ll_down(const LLDownArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const int FW = 2 * a.tile_w + 3, FH = 2 * a.tile_h + 3;
+  __shared__ float gk_level[HP_MAX_PARAMS * 2 + 1];
+  const int tw = a.tile_w, lg_tw = 31 - __clz(tw);
+  const int FW = 2 * tw + 3, FH = 2 * a.tile_h + 3;
   const int plane = FW * FH;
   float* GR = sm;                           // gray tile (remap source only)
   float* S = GR + (REMAP ? plane : 0);      // C source planes
   float* HX = S + a.C * plane;              // C x-pass planes, FH x tile_w
-  const int x0 = blockIdx.x * a.tile_w, y0 = blockIdx.y * a.tile_h;
+  const int x0 = blockIdx.x * tw, y0 = blockIdx.y * a.tile_h;
   const int fx0 = 2 * x0 - 2, fy0 = 2 * y0 - 2;
   const int Wf = a.src.w, Hf = a.src.h;
   const int nt = blockDim.x;
   if (REMAP) {
-    for (int i = threadIdx.x; i < plane; i += nt) {
-      const int r = i / FW, q = i - r * FW;
-      const int fy = iclamp(fy0 + r, 0, Hf - 1), fx = iclamp(fx0 + q, 0, Wf - 1);
-      GR[i] = round_storage(a.st_gray, op_gray(load_px(a.src, 0, fx, fy), load_px(a.src, 1, fx, fy),
-                                               load_px(a.src, 2, fx, fy), a.gray_scale));
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < a.C * plane; i += nt) {
-      const int c = i / plane, j = i - c * plane;
-      const float g = GR[j];
-      S[i] = round_storage(a.st_remap, c < a.K ? op_ll_remap(g, ll_level(c, a.K), a.sigma, a.alpha, a.beta) : g);
-    }
-  } else {
-    // four loads in flight per thread before any store
-    const int total = a.C * plane;
-    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * nt) {
-      float v[4];
+    if (threadIdx.x < a.K) gk_level[threadIdx.x] = ll_level(threadIdx.x, a.K);
+    // gray of the clamped fine tile, four pixels (12 loads) in flight per thread
+    for (int i0 = threadIdx.x; i0 < plane; i0 += 4 * nt) {
+      float rgb[4][3];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u * nt;
-        v[u] = 0.0f;
-        if (i < total) {
-          const int c = i / plane, j = i - c * plane;
-          const int r = j / FW, q = j - r * FW;
-          v[u] = level_px<F32>(a.src, c, iclamp(fx0 + q, 0, Wf - 1), iclamp(fy0 + r, 0, Hf - 1));
-        }
+        const int r = i / FW, q = i - r * FW;
+        const int fy = iclamp(fy0 + r, 0, Hf - 1), fx = iclamp(fx0 + q, 0, Wf - 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rgb[u][c] = i < plane ? load_px(a.src, c, fx, fy) : 0.0f;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (i0 + u * nt < total) S[i0 + u * nt] = v[u];
+        if (i0 + u * nt < plane)
+          GR[i0 + u * nt] = round_storage(a.st_gray, op_gray(rgb[u][0], rgb[u][1], rgb[u][2], a.gray_scale));
+    }
+    __syncthreads();
+    // every channel of the remap stack of one fine pixel per thread
+    for (int i = threadIdx.x; i < plane; i += nt) {
+      const float g = GR[i];
+      for (int c = 0; c < a.C; ++c)
+        S[c * plane + i] = round_storage(a.st_remap, c < a.K ? op_ll_remap(g, gk_level[c], a.sigma, a.alpha, a.beta) : g);
+    }
+  } else {
+    // four loads in flight per thread before any store
+    for (int c = 0; c < a.C; ++c) {
+      for (int i0 = threadIdx.x; i0 < plane; i0 += 4 * nt) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * nt;
+          const int r = i / FW, q = i - r * FW;
+          v[u] = i < plane ? level_px<F32>(a.src, c, iclamp(fx0 + q, 0, Wf - 1), iclamp(fy0 + r, 0, Hf - 1)) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u * nt < plane) S[c * plane + i0 + u * nt] = v[u];
+      }
     }
   }
   __syncthreads();
-  const int hxp = FH * a.tile_w;
-  for (int i = threadIdx.x; i < a.C * hxp; i += nt) {
-    const int c = i / hxp, j = i - c * hxp;
-    const int r = j / a.tile_w, x = j - r * a.tile_w;
-    const float* s = S + c * plane + r * FW + 2 * x;
-    HX[i] = tap5_binomial16(s[0], s[1], s[2], s[3], s[4]);
-  }
-  __syncthreads();
-  const int op = a.tile_h * a.tile_w;
-  const int tw = a.tile_w;
-  for (int i = threadIdx.x; i < a.C * op; i += nt) {
-    const int c = i / op, j = i - c * op;
-    const int y = j / tw, x = j - y * tw;
-    const int ox = x0 + x, oy = y0 + y;
-    if (ox >= a.out.w || oy >= a.out.h) continue;
-    const float* h = HX + c * hxp + 2 * y * tw + x;
-    const float v = round_storage(a.st_out, tap5_binomial16(h[0], h[tw], h[2 * tw], h[3 * tw], h[4 * tw]));
-    if (F32) {
-      reinterpret_cast<float*>((char*)a.out.data + (long long)c * a.out.ps + (long long)oy * a.out.rs)[ox] = v;
-    } else {
-      store_px(a.out, c, ox, oy, v);
+  const int hxp = FH << lg_tw;
+  for (int c = 0; c < a.C; ++c)
+    for (int j = threadIdx.x; j < hxp; j += nt) {
+      const int r = j >> lg_tw, x = j & (tw - 1);
+      const float* s = S + c * plane + r * FW + 2 * x;
+      HX[c * hxp + j] = tap5_binomial16(s[0], s[1], s[2], s[3], s[4]);
     }
-  }
+  __syncthreads();
+  const int op = a.tile_h << lg_tw;
+  for (int c = 0; c < a.C; ++c)
+    for (int j = threadIdx.x; j < op; j += nt) {
+      const int y = j >> lg_tw, x = j & (tw - 1);
+      const int ox = x0 + x, oy = y0 + y;
+      if (ox >= a.out.w || oy >= a.out.h) continue;
+      const float* h = HX + c * hxp + 2 * y * tw + x;
+      const float v = round_storage(a.st_out, tap5_binomial16(h[0], h[tw], h[2 * tw], h[3 * tw], h[4 * tw]));
+      if (F32) {
+        reinterpret_cast<float*>((char*)a.out.data + (long long)c * a.out.ps + (long long)oy * a.out.rs)[ox] = v;
+      } else {
+        store_px(a.out, c, ox, oy, v);
+      }
+    }
 }
 
 // Upsample of channel c of a coarse image at fine (X, Y): taps per axis by

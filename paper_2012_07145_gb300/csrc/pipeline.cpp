@@ -752,8 +752,9 @@ hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   }
   a.tile_w = gp.tile_w;
   a.tile_h = gp.tile_h;
-  if (a.tile_w < 1 || a.tile_h < 1 || a.tile_w > 64 || a.tile_h > 64)
-    return fail(HP_ERR_SCHEDULE, "downsample tiles must be at most 64x64");
+  if (a.tile_w < 1 || a.tile_h < 1 || a.tile_w > 64 || a.tile_h > 64 || (a.tile_w & (a.tile_w - 1)))
+    return fail(HP_ERR_SCHEDULE, "downsample tile width must be a power of two and tiles at most 64x64");
+  if (a.remap && a.K > 2 * HP_MAX_PARAMS) return fail(HP_ERR_UNSUPPORTED, "too many intensity levels");
   Dom od = plan.dom[gp.output];
   a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
@@ -843,9 +844,9 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         // that the grid still covers the SMs
         Dom od = plan.dom[gp.output];
         int t = 16;
-        while (t > 4 && ((od.w + t - 1) / t) * ((od.h + t - 1) / t) < 256) t /= 2;
+        while (t > 4 && ((od.w + t - 1) / t) * ((od.h + t / 2 - 1) / (t / 2)) < 512) t /= 2;
         gp.tile_w = std::min(pick(p->tile_w, g, t), 64);
-        gp.tile_h = std::min(pick(p->tile_h, g, t), 64);
+        gp.tile_h = std::min(pick(p->tile_h, g, std::max(2, t / 2)), 64);
         const int c = p->stages[gp.output].channels;
         while (ll_down_smem_bytes(gp.tile_w, gp.tile_h, c, 1) > kSmemLimit && gp.tile_w > 4) {
           gp.tile_w /= 2;
