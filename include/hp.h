@@ -119,7 +119,12 @@ typedef struct {
  * shared memory or registers; only the group's output stage (the one stage read
  * outside the group, or the pipeline output) is written to memory.  Singleton
  * groups everywhere is the stage-per-kernel schedule ("compute root", Sec. 2). */
-enum { HP_IMPL_AUTO = 0, HP_IMPL_GENERIC = 1 };
+enum {
+  HP_IMPL_AUTO = 0,    /* the kernel the group's shape selects */
+  HP_IMPL_GENERIC = 1, /* the generic interpreter */
+  HP_IMPL_WAVE = 2     /* stencil chains: the streaming kernel (one warp per stage, rows through
+                          shared-memory rings); even depth <= 16, f32 input, tile_w <= 128 - 4(d-1) */
+};
 
 typedef struct {
   int n_stages;                /* must equal the pipeline's stage count */
@@ -129,7 +134,7 @@ typedef struct {
   const int* tile_h;           /* per group: output tile height (NULL: defaults) */
   const int* threads;          /* per group: threads per block  (NULL: defaults) */
   const int* serial_y;         /* per group: rows per thread segment (NULL: defaults) */
-  const int* impl;             /* per group: HP_IMPL_AUTO or HP_IMPL_GENERIC (NULL: auto) */
+  const int* impl;             /* per group: HP_IMPL_* (NULL: auto) */
 } hp_schedule;
 
 typedef struct {
@@ -161,7 +166,8 @@ enum {
   HP_KERNEL_HISTOGRAM = 7,
   HP_KERNEL_CDF_LUT = 8,
   HP_KERNEL_LUT_APPLY = 9,
-  HP_KERNEL_LL_LEVEL = 10      /* local-Laplacian level: two-level blend + collapse step (+ colour) */
+  HP_KERNEL_LL_LEVEL = 10,     /* local-Laplacian level: two-level blend + collapse step (+ colour) */
+  HP_KERNEL_STENCIL_WAVE = 11  /* streaming stencil chain (HP_IMPL_WAVE) */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -204,6 +204,9 @@ struct LutApplyArgs {
 
 // Launchers (defined in the .cu files).  Return a cudaError_t as int.
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream);
+int launch_wave(const ChainArgs& a, int smem_bytes, void* stream);
+int wave_smem_bytes(int depth);
+int wave_max_tile_w(int depth);
 int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype);
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream);
 int launch_pointwise(const PointwiseArgs& a, void* stream);

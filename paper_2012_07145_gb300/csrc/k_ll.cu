@@ -69,27 +69,55 @@ __global__ void __launch_bounds__(256) k_ll_down(const LLDownArgs a) {
           GR[i0 + u * nt] = round_storage(a.st_gray, op_gray(rgb[u][0], rgb[u][1], rgb[u][2], a.gray_scale));
     }
     __syncthreads();
-    // every channel of the remap stack of one fine pixel per thread
+    // every channel of the remap stack of one fine pixel per thread.  Outside
+    // the band |g - g_k| <= sigma the remap is a multiply-add; a pixel lies in
+    // the band of at most two levels when 2 sigma (K-1) < 2, so the power is
+    // evaluated for those two only (the general case evaluates every level).
     for (int i = threadIdx.x; i < plane; i += nt) {
       const float g = GR[i];
-      for (int c = 0; c < a.C; ++c)
-        S[c * plane + i] = round_storage(a.st_remap, c < a.K ? op_ll_remap(g, gk_level[c], a.sigma, a.alpha, a.beta) : g);
+      int ka = -1, kb = -1;
+      bool many = false;
+      for (int k = 0; k < a.K; ++k) {
+        if (fabsf(__fsub_rn(g, gk_level[k])) <= a.sigma) {
+          if (ka < 0) ka = k;
+          else if (kb < 0) kb = k;
+          else many = true;
+        }
+      }
+      const float pa = ka >= 0 ? op_ll_remap(g, gk_level[ka], a.sigma, a.alpha, a.beta) : 0.0f;
+      const float pb = kb >= 0 ? op_ll_remap(g, gk_level[kb], a.sigma, a.alpha, a.beta) : 0.0f;
+      for (int c = 0; c < a.C; ++c) {
+        float v;
+        if (c >= a.K) {
+          v = g;
+        } else if (many) {
+          v = op_ll_remap(g, gk_level[c], a.sigma, a.alpha, a.beta);
+        } else if (c == ka) {
+          v = pa;
+        } else if (c == kb) {
+          v = pb;
+        } else {
+          const float d = __fsub_rn(g, gk_level[c]);
+          v = op_ll_remap_outside(d, fabsf(d), gk_level[c], a.sigma, a.beta);
+        }
+        S[c * plane + i] = round_storage(a.st_remap, v);
+      }
     }
   } else {
-    // four loads in flight per thread before any store
-    for (int c = 0; c < a.C; ++c) {
-      for (int i0 = threadIdx.x; i0 < plane; i0 += 4 * nt) {
-        float v[4];
+    // every channel at once, four loads in flight per thread before any store
+    const int total = a.C * plane;
+    for (int i0 = threadIdx.x; i0 < total; i0 += 4 * nt) {
+      float v[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u * nt;
-          const int r = i / FW, q = i - r * FW;
-          v[u] = i < plane ? level_px<F32>(a.src, c, iclamp(fx0 + q, 0, Wf - 1), iclamp(fy0 + r, 0, Hf - 1)) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (i0 + u * nt < plane) S[c * plane + i0 + u * nt] = v[u];
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * nt;
+        const int c = i / plane, j = i - c * plane;
+        const int r = j / FW, q = j - r * FW;
+        v[u] = i < total ? level_px<F32>(a.src, c, iclamp(fx0 + q, 0, Wf - 1), iclamp(fy0 + r, 0, Hf - 1)) : 0.0f;
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i0 + u * nt < total) S[i0 + u * nt] = v[u];
     }
   }
   __syncthreads();

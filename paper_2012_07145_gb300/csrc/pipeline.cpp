@@ -515,7 +515,7 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     chain = is_r2_stencil(s) && (i == 0 ? (s.inputs[0] < 0 || std::find(m.begin(), m.end(), s.inputs[0]) == m.end())
                                        : s.inputs[0] == m[i - 1]);
   }
-  if (chain) return HP_KERNEL_STENCIL_CHAIN;
+  if (chain) return impl == HP_IMPL_WAVE ? HP_KERNEL_STENCIL_WAVE : HP_KERNEL_STENCIL_CHAIN;
   {
     int remap, gray, rm;
     if (match_down(p, m, &remap, &gray, &rm)) return HP_KERNEL_DOWNSAMPLE;
@@ -693,6 +693,40 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   return HP_OK;
 }
 
+hp_status build_wave(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  ChainArgs& a = gp.chain;
+  memset(&a, 0, sizeof a);
+  a.depth = (int)gp.members.size();
+  for (int i = 0; i < a.depth; ++i) {
+    const Stage& s = p->stages[gp.members[i]];
+    a.storage[i] = s.storage;
+    for (int k = 0; k < 5; ++k) {
+      a.w[i][k] = s.wx[k];
+      a.w[i][5 + k] = s.wy[k];
+    }
+  }
+  a.tile_w = gp.tile_w;
+  a.tile_h = gp.tile_h;
+  int in_ref = p->stages[gp.members[0]].inputs[0];
+  if (stage_dtype_of_ref(p, in_ref) != HP_F32)
+    return fail(HP_ERR_SCHEDULE, "the streaming stencil kernel needs an f32 chain input");
+  if (a.depth < 2 || a.depth > 16 || (a.depth & 1))
+    return fail(HP_ERR_SCHEDULE, "the streaming stencil kernel fuses an even number of stages, 2..16");
+  if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_w > wave_max_tile_w(a.depth) || a.tile_h < 1)
+    return fail(HP_ERR_SCHEDULE, "streaming stencil tile width must be a multiple of 8 up to %d for depth %d",
+                wave_max_tile_w(a.depth), a.depth);
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  a.threads = 32 * a.depth;
+  a.seg = 1;
+  gp.smem = wave_smem_bytes(a.depth);
+  gp.grid_x = a.tiles_x;
+  gp.grid_y = a.tiles_y;
+  gp.grid_z = p->stages[gp.members[0]].channels;
+  return HP_OK;
+}
+
 hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   int roles[10];
   match_harris(p, gp.members, roles);
@@ -831,6 +865,13 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
     gp.kernel = choose_kernel(p, shapes[g], impl);
     if (gp.kernel < 0) return fail(HP_ERR_UNSUPPORTED, "group %d mixes reductions with other stages", g);
     switch (gp.kernel) {
+      case HP_KERNEL_STENCIL_WAVE:
+        gp.tile_w = pick(p->tile_w, g, 96);
+        gp.tile_h = pick(p->tile_h, g, 128);
+        gp.threads = 32 * (int)gp.members.size();
+        gp.seg = 1;
+        s = build_wave(p, plan, gp);
+        break;
       case HP_KERNEL_STENCIL_CHAIN:
       case HP_KERNEL_UNSHARP:
         gp.tile_w = pick(p->tile_w, g, 64);
@@ -969,13 +1010,14 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
     int e = 0;
     switch (gp.kernel) {
       case HP_KERNEL_STENCIL_CHAIN:
-      case HP_KERNEL_UNSHARP: {
+      case HP_KERNEL_UNSHARP:
+      case HP_KERNEL_STENCIL_WAVE: {
         ChainArgs a = gp.chain;
         int first = gp.members[0];
         a.in = ref_view(p, plan, p->stages[first].inputs[0], inputs, output);
         a.out = out;
         a.err = p->d_err;
-        e = launch_chain(a, gp.smem, stream);
+        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_wave(a, gp.smem, stream) : launch_chain(a, gp.smem, stream);
         break;
       }
       case HP_KERNEL_DOWNSAMPLE: {
@@ -1201,7 +1243,7 @@ hp_status hp_schedule_set(hp_pipeline* p, const hp_schedule* s) {
   if ((st = per_group(s->tile_w, tmp.tile_w, 1, 4096, "tile_w")) || (st = per_group(s->tile_h, tmp.tile_h, 1, 4096, "tile_h")) ||
       (st = per_group(s->threads, tmp.threads, 32, 1024, "threads")) ||
       (st = per_group(s->serial_y, tmp.serial_y, 1, 256, "serial_y")) ||
-      (st = per_group(s->impl, tmp.impl, 0, 1, "impl")))
+      (st = per_group(s->impl, tmp.impl, 0, 2, "impl")))
     return st;
   std::vector<GroupShape> shapes;
   if ((st = group_shapes(&tmp, shapes))) return st;

@@ -132,6 +132,11 @@ __device__ __forceinline__ float op_ll_remap(float i, float g, float sigma, floa
   return ad == 0.0f ? g : __fadd_rn(g, copysignf(mag, d));
 }
 
+// The remap outside the band (|d| > sigma), bit-identical to op_ll_remap there.
+__device__ __forceinline__ float op_ll_remap_outside(float d, float ad, float g, float sigma, float beta) {
+  return __fadd_rn(g, copysignf(__fmaf_rn(beta, __fsub_rn(ad, sigma), sigma), d));
+}
+
 __device__ __forceinline__ float ll_level(int k, int K) { return __fdiv_rn((float)k, (float)(K - 1)); }
 
 __device__ __forceinline__ void ll_interp_index(float gk, int K, int* k0, float* f) {

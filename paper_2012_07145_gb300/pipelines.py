@@ -35,13 +35,15 @@ def stencil_chain(n_stages: int = 32, pattern: str = "alternate", storage: int =
 
 
 def chain_schedule(p: hp.Pipeline, depth: int, tile_w: int = 64, tile_h: int = 32, threads: int = 256,
-                   serial_y: int = 8):
-    """Fuse consecutive runs of `depth` stages into one kernel each."""
+                   serial_y: int = 8, impl: int = hp.HP_IMPL_AUTO):
+    """Fuse consecutive runs of `depth` stages into one kernel each.  With
+    impl = HP_IMPL_WAVE the groups run on the streaming kernel (one warp per
+    stage; threads and serial_y do not apply)."""
     n = len(p.stages)
     groups = [k // depth for k in range(n)]
     ng = groups[-1] + 1
     p.schedule(groups, tile_w=[tile_w] * ng, tile_h=[tile_h] * ng, threads=[threads] * ng,
-               serial_y=[serial_y] * ng)
+               serial_y=[serial_y] * ng, impl=[impl] * ng)
 
 
 def root_schedule(p: hp.Pipeline, impl=None):

@@ -108,3 +108,27 @@ def test_cuda_graph_replay_matches_and_counts_launches():
         assert hp.launch_count() - n0 == 4
         assert torch.equal(bits(y), bits(ref))
         y.zero_()
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (3, 7), (17, 33), (65, 129), (200, 300)])
+@pytest.mark.parametrize("depth,tw,th", [(2, 120, 64), (4, 112, 32), (8, 96, 128), (16, 64, 16)])
+def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th):
+    img = synth.stencil_input(h, w, seed=h * 7 + w)
+    p = pipelines.stencil_chain(16, "alternate")
+    base = chain_run(p, img)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, impl=hp.HP_IMPL_WAVE)
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_WAVE
+    n0 = hp.launch_count()
+    y = chain_run(p, img)
+    assert hp.launch_count() - n0 == 16 // depth
+    assert torch.equal(bits(y), bits(base))
+
+
+def test_streaming_kernel_full_size_against_oracle():
+    H, W = 1536, 2560
+    img = synth.stencil_input(H, W, seed=0)
+    p = pipelines.stencil_chain(32, "alternate")
+    plain = chain_run(p, img)
+    pipelines.chain_schedule(p, depth=8, tile_w=96, tile_h=128, impl=hp.HP_IMPL_WAVE)
+    fused = chain_run(p, img)
+    assert torch.equal(bits(fused), bits(plain))
