@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(512) k_wave(const __grid_constant__ WaveKParam
     *status = 0;
     for (int i = 0; i < kWBoxes; ++i) mbar_init(&bars[i], 1);
     fence_mbar_init();
-    issue_upto(kWBoxes - 1);
+    // the first box holding an image row, and the three after it
+    const int first_box = y0_0 < 0 ? (-y0_0) / kWBox : 0;
+    next_box = first_box;
+    issue_upto(first_box + kWBoxes - 1);
   }
   __syncthreads();
 
