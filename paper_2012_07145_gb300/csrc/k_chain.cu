@@ -78,19 +78,21 @@ __device__ __forceinline__ float rnd(float v, int dtype) {
   return round_storage(dtype, v);
 }
 
-// x pass of one producer row for 4 output columns: columns (0,1) and (2,3)
-// each go through one paired FMA chain.
-__device__ __forceinline__ float4 xpass(const float* p, const float2* wx) {
+// x pass of one producer row for 4 output columns (scalar fma chains: the
+// column pairs would need register moves to use the paired instructions).
+__device__ __forceinline__ float4 xpass(const float* p, const float* wx) {
   const float4 lo = *reinterpret_cast<const float4*>(p);
   const float4 hi = *reinterpret_cast<const float4*>(p + 4);
-  const float2 p01 = make_float2(lo.x, lo.y), p12 = make_float2(lo.y, lo.z), p23 = make_float2(lo.z, lo.w);
-  const float2 p34 = make_float2(lo.w, hi.x), p45 = make_float2(hi.x, hi.y), p56 = make_float2(hi.y, hi.z);
-  const float2 p67 = make_float2(hi.z, hi.w);
-  const float2 a = tap5x2(wx, p01, p12, p23, p34, p45);
-  const float2 b = tap5x2(wx, p23, p34, p45, p56, p67);
-  return make_float4(a.x, a.y, b.x, b.y);
+  float4 h;
+  h.x = tap5(wx, lo.x, lo.y, lo.z, lo.w, hi.x);
+  h.y = tap5(wx, lo.y, lo.z, lo.w, hi.x, hi.y);
+  h.z = tap5(wx, lo.z, lo.w, hi.x, hi.y, hi.z);
+  h.w = tap5(wx, lo.w, hi.x, hi.y, hi.z, hi.w);
+  return h;
 }
 
+// y pass of a 5-row window for 4 columns: columns (0,1) and (2,3) are register
+// pairs, so each pair is one chain of paired FP32 FMAs (FMUL2/FFMA2).
 template <int RND>
 __device__ __forceinline__ float4 ypass(const float2* wy, const float4& a, const float4& b, const float4& c,
                                         const float4& d, const float4& e, int dtype) {
@@ -124,7 +126,7 @@ struct SmemSink {
 // in the buffer (it is allocated for that) and are never read by valid outputs.
 template <int SEG, int RND, class Sink>
 __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int Ws, int Hs,
-                                      const float2* wx, const float2* wy, int dtype, const Sink& sink) {
+                                      const float* wx, const float2* wy, int dtype, const Sink& sink) {
   const int nb = Ws >> 2;
   const int nseg = (Hs + SEG - 1) / SEG;
   // work item (b, sg) = (4-column block, row segment); walked without divisions
@@ -245,10 +247,11 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
     float* dst = (s & 1) ? bufB : bufA;
     const int Ws = a.tile_w + 4 * (d - s);
     const int Hs = a.tile_h + 4 * (d - s);
-    float2 wx[5], wy[5];
+    float wx[5];
+    float2 wy[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      wx[k] = make_float2(a.w[s - 1][k], a.w[s - 1][k]);
+      wx[k] = a.w[s - 1][k];
       wy[k] = make_float2(a.w[s - 1][5 + k], a.w[s - 1][5 + k]);
     }
     const int dt = a.storage[s - 1];
