@@ -74,17 +74,6 @@ __device__ __forceinline__ float tap3(const float* w, float a, float b, float c)
   return __fmaf_rn(w[2], c, s);
 }
 
-// The same 5-tap pass on two independent columns at once with the paired FP32
-// instructions of sm_100+ (FMUL2/FFMA2).  Each component is computed exactly
-// as tap5 computes it (same operations, same order, round to nearest even).
-__device__ __forceinline__ float2 tap5x2(const float2* w, float2 a, float2 b, float2 c, float2 d, float2 e) {
-  float2 s = __fmul2_rn(w[0], a);
-  s = __ffma2_rn(w[1], b, s);
-  s = __ffma2_rn(w[2], c, s);
-  s = __ffma2_rn(w[3], d, s);
-  return __ffma2_rn(w[4], e, s);
-}
-
 // Binomial [1,4,6,4,1]/16 (exact in float), the per-axis taps of the pyramid
 // downsample.
 __device__ __forceinline__ float tap5_binomial16(float a, float b, float c, float d, float e) {
