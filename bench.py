@@ -94,8 +94,8 @@ def config_table():
     cfgs["harris"] = dict(workload=f"harris_rgb_{W}x{H}_f32", h=H, w=W,
                           inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_F32)], out=(1, H, W, hp.HP_F32),
                           build=lambda: pipelines.harris(),
-                          fused=lambda p: pipelines.fused_schedule(p, tile_w=64, tile_h=32),
-                          flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris", dtype="f32",
+                          fused=lambda p: pipelines.fused_schedule(p, tile_w=120, tile_h=14, threads=256),
+                          flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris_rows", dtype="f32",
                           oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
     UH, UW = 3072, 4096
 
@@ -513,7 +513,7 @@ def run_serving(args):
     un = pipelines.unsharp()
     pipelines.fused_schedule(un, tile_w=64, tile_h=32)
     hr = pipelines.harris()
-    pipelines.fused_schedule(hr, tile_w=64, tile_h=32)
+    pipelines.fused_schedule(hr, tile_w=120, tile_h=32, threads=256)
     he = pipelines.histeq()
     kinds = [("unsharp", un, 3, hp.HP_F32, 3, torch.float32), ("harris", hr, 3, hp.HP_F32, 1, torch.float32),
              ("histeq", he, 1, hp.HP_U8, 1, torch.uint8)]

@@ -122,8 +122,12 @@ typedef struct {
 enum {
   HP_IMPL_AUTO = 0,    /* the kernel the group's shape selects */
   HP_IMPL_GENERIC = 1, /* the generic interpreter */
-  HP_IMPL_WAVE = 2     /* stencil chains: the streaming kernel (one warp per stage, rows through
-                          shared-memory rings); even depth <= 16, f32 input, tile_w <= 128 - 4(d-1) */
+  HP_IMPL_WAVE = 2     /* streaming kernels.  Stencil chains: one warp per stage, rows through
+                          shared-memory rings; even depth <= 16, f32 input, tile_w <= 128 - 4(d-1).
+                          Harris: one warp per column strip of exactly 120 columns (4-byte input) or
+                          112 (2-byte input), tile_h rows per run (>= 4), threads <= 256.  Under
+                          HP_IMPL_AUTO a Harris group whose tile_w is that strip width (the default)
+                          also takes the streaming kernel; other widths take the tiled one. */
 };
 
 typedef struct {
@@ -167,7 +171,9 @@ enum {
   HP_KERNEL_CDF_LUT = 8,
   HP_KERNEL_LUT_APPLY = 9,
   HP_KERNEL_LL_LEVEL = 10,     /* local-Laplacian level: two-level blend + collapse step (+ colour) */
-  HP_KERNEL_STENCIL_WAVE = 11  /* streaming stencil chain (HP_IMPL_WAVE) */
+  HP_KERNEL_STENCIL_WAVE = 11, /* streaming stencil chain (HP_IMPL_WAVE) */
+  HP_KERNEL_HARRIS_ROWS = 12   /* whole Harris DAG, streaming: one warp per column strip, rows
+                                  through a per-warp TMA ring, intermediates in registers */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -214,6 +214,11 @@ int launch_downsample(const ResampleArgs& a, void* stream);
 int launch_upsample(const ResampleArgs& a, void* stream);
 int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream);
 int harris_smem_bytes(int tile_w, int tile_h, int in_dtype);
+// streaming Harris: one warp per strip of harris_rows_strip_w columns, a.tile_h rows per run
+int harris_rows_strip_w(int in_dtype);
+int harris_rows_smem_bytes(int threads, int in_dtype);
+int harris_rows_grid(const HarrisArgs& a, int units, int threads, int smem_bytes);
+int launch_harris_rows(const HarrisArgs& a, int rows, int grid, int smem_bytes, void* stream);
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
 int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);

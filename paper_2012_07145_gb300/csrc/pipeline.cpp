@@ -727,8 +727,7 @@ hp_status build_wave(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   return HP_OK;
 }
 
-hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
-  int roles[10];
+void harris_common_args(const hp_pipeline* p, GroupPlan& gp, int roles[10]) {
   match_harris(p, gp.members, roles);
   HarrisArgs& a = gp.harris;
   memset(&a, 0, sizeof a);
@@ -745,6 +744,12 @@ hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   a.tile_h = gp.tile_h;
   a.threads = gp.threads;
   a.seg = gp.seg;
+}
+
+hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  int roles[10];
+  harris_common_args(p, gp, roles);
+  HarrisArgs& a = gp.harris;
   if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_w > 232 || a.tile_h < 1 || a.tile_h > 252)
     return fail(HP_ERR_SCHEDULE, "Harris tile width must be a multiple of 8 in [8, 232], height in [1, 252]");
   if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 512)
@@ -757,6 +762,29 @@ hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "Harris tile needs %d bytes of shared memory", gp.smem);
   gp.grid_x = a.tiles_x;
   gp.grid_y = a.tiles_y;
+  gp.ext_refs.assign(1, p->stages[roles[0]].inputs[0]);
+  return HP_OK;
+}
+
+hp_status build_harris_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  int roles[10];
+  harris_common_args(p, gp, roles);
+  HarrisArgs& a = gp.harris;
+  const int in_dt = stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]);
+  const int sw = harris_rows_strip_w(in_dt);
+  if (a.tile_w != sw)
+    return fail(HP_ERR_SCHEDULE, "streaming Harris strips are %d columns wide for this input type (tile_w %d)", sw,
+                a.tile_w);
+  if (a.tile_h < 4 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming Harris needs tile_h >= 4 rows per run");
+  if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 256)
+    return fail(HP_ERR_SCHEDULE, "streaming Harris threads per block must be a multiple of 32 in [32, 256]");
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + sw - 1) / sw;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  gp.smem = harris_rows_smem_bytes(a.threads, in_dt);
+  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "streaming Harris needs %d bytes of shared memory", gp.smem);
+  gp.grid_x = harris_rows_grid(a, a.tiles_x * a.tiles_y, a.threads, gp.smem);
+  gp.grid_y = 1;
   gp.ext_refs.assign(1, p->stages[roles[0]].inputs[0]);
   return HP_OK;
 }
@@ -899,13 +927,22 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
       case HP_KERNEL_LL_LEVEL:
         s = build_ll_level(p, plan, gp);
         break;
-      case HP_KERNEL_HARRIS:
-        gp.tile_w = pick(p->tile_w, g, 64);
+      case HP_KERNEL_HARRIS: {
+        int roles[10];
+        match_harris(p, gp.members, roles);
+        const int sw = harris_rows_strip_w(stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]));
+        gp.tile_w = pick(p->tile_w, g, sw);
         gp.tile_h = pick(p->tile_h, g, 32);
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
-        s = build_harris(p, plan, gp);
+        if (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw)) {
+          gp.kernel = HP_KERNEL_HARRIS_ROWS;
+          s = build_harris_rows(p, plan, gp);
+        } else {
+          s = build_harris(p, plan, gp);
+        }
         break;
+      }
       case HP_KERNEL_HISTOGRAM: case HP_KERNEL_CDF_LUT: case HP_KERNEL_LUT_APPLY:
         gp.threads = 256;
         break;
@@ -1047,6 +1084,14 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.out = out;
         a.err = p->d_err;
         e = launch_harris(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_HARRIS_ROWS: {
+        HarrisArgs a = gp.harris;
+        a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        a.err = p->d_err;
+        e = launch_harris_rows(a, a.tile_h, gp.grid_x, gp.smem, stream);
         break;
       }
       case HP_KERNEL_HISTOGRAM: {

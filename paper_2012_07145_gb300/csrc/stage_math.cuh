@@ -68,10 +68,13 @@ __device__ __forceinline__ float tap5(const float* w, float a, float b, float c,
   return __fmaf_rn(w[4], e, s);
 }
 
+__device__ __forceinline__ float tap3v(float w0, float w1, float w2, float a, float b, float c) {
+  float s = __fmul_rn(w0, a);
+  s = __fmaf_rn(w1, b, s);
+  return __fmaf_rn(w2, c, s);
+}
 __device__ __forceinline__ float tap3(const float* w, float a, float b, float c) {
-  float s = __fmul_rn(w[0], a);
-  s = __fmaf_rn(w[1], b, s);
-  return __fmaf_rn(w[2], c, s);
+  return tap3v(w[0], w[1], w[2], a, b, c);
 }
 
 // Binomial [1,4,6,4,1]/16 (exact in float), the per-axis taps of the pyramid

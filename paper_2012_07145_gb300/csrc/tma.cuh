@@ -68,6 +68,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase,
   }
 }
 
+// Bounded wait by polling: try_wait without a suspend hint (the hardware's own
+// short wait per poll), with the wall clock read every 32 polls.
+__device__ __forceinline__ bool mbar_wait_poll(uint64_t* bar, unsigned phase, unsigned long long limit_ns) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+#pragma unroll 1
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try_wait(bar, phase)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
 // 3-D tiled load of one box into shared memory; completion is signalled on bar.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
   asm volatile(

@@ -86,6 +86,20 @@ def test_lowering_picks_kernels():
     pipelines.fused_schedule(hr, inline_pointwise=True)
     info = hr.group_info([(64, 48)], 0)
     assert info.kernel == hp.HP_KERNEL_HARRIS and info.n_members == 10
+    # the streaming Harris kernel: 120-column strips for 4-byte input, 112 for 2-byte
+    pipelines.fused_schedule(hr, tile_w=120, tile_h=28, threads=256)
+    info = hr.group_info([(2560, 1536)], 0)
+    assert info.kernel == hp.HP_KERNEL_HARRIS_ROWS and info.grid_x >= 1
+    pipelines.fused_schedule(hr, tile_w=112, tile_h=28, impl=hp.HP_IMPL_WAVE)
+    with pytest.raises(hp.HPError) as e:
+        hr.group_info([(64, 48)], 0)
+    assert e.value.status == hp.HP_ERR_SCHEDULE
+    hb = pipelines.harris(io_storage=hp.HP_BF16)
+    pipelines.fused_schedule(hb, tile_w=112, tile_h=3, impl=hp.HP_IMPL_WAVE)
+    with pytest.raises(hp.HPError):
+        hb.group_info([(64, 48)], 0)
+    pipelines.fused_schedule(hb, tile_w=112, tile_h=8)
+    assert hb.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_HARRIS_ROWS
 
 
 def test_bounds_inference_stencil_chain():

@@ -62,6 +62,78 @@ def test_harris_bf16_io_error_is_stated():
     assert e_rounded < 0.05
 
 
+@pytest.mark.parametrize("h,w", [(1536, 2560), (37, 53), (1, 1), (2, 5), (130, 245), (9, 121), (6, 361)])
+def test_harris_streaming_kernel_bit_identical(h, w):
+    """The streaming kernel (one warp per 120-column strip, rows through a TMA
+    ring) against the stage-per-kernel schedule, over runs of rows that cut the
+    image at every offset against the 4-row boxes, strips with one to four
+    warps per block, and images narrower and shorter than one strip."""
+    img = synth.rgb_f32(h, w, seed=7)
+    x = to_device(img, hp.HP_F32)
+    p = pipelines.harris()
+    plain = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+    if 4 < h * w <= 100000:
+        assert rel_err(to_numpy(plain)[0], ohr.harris(img.astype(np.float64))) <= TOL
+    for th, thr in [(4, 32), (5, 64), (7, 128), (28, 256), (32, 96), (61, 256)]:
+        pipelines.fused_schedule(p, tile_w=120, tile_h=th, threads=thr)
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_HARRIS_ROWS
+        got = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+        assert torch.equal(bits(got), bits(plain)), (th, thr)
+        assert p.device_error() == 0
+
+
+def _harris_like(wd, ws, wb, scale, k=0.05):
+    """A pipeline with Harris's structure and other weights (not the Sobel and
+    box constants) and gray scale, so kernels take their runtime-weight path."""
+    p = hp.Pipeline([hp.HP_F32], [3])
+    g = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, hp.HP_F32, op=hp.HP_OP_GRAY, params=[scale])
+    ix = p.add_stage(hp.HP_STENCIL, [g], 1, hp.HP_F32, rx=1, ry=1, wx=wd, wy=ws)
+    iy = p.add_stage(hp.HP_STENCIL, [g], 1, hp.HP_F32, rx=1, ry=1, wx=ws, wy=wd)
+    ixx = p.add_stage(hp.HP_POINTWISE, [ix, ix], 1, hp.HP_F32, op=hp.HP_OP_MUL)
+    iyy = p.add_stage(hp.HP_POINTWISE, [iy, iy], 1, hp.HP_F32, op=hp.HP_OP_MUL)
+    ixy = p.add_stage(hp.HP_POINTWISE, [ix, iy], 1, hp.HP_F32, op=hp.HP_OP_MUL)
+    sxx = p.add_stage(hp.HP_STENCIL, [ixx], 1, hp.HP_F32, rx=1, ry=1, wx=wb, wy=wb)
+    syy = p.add_stage(hp.HP_STENCIL, [iyy], 1, hp.HP_F32, rx=1, ry=1, wx=wb, wy=wb)
+    sxy = p.add_stage(hp.HP_STENCIL, [ixy], 1, hp.HP_F32, rx=1, ry=1, wx=wb, wy=wb)
+    r = p.add_stage(hp.HP_POINTWISE, [sxx, syy, sxy], 1, hp.HP_F32, op=hp.HP_OP_HARRIS, params=[k])
+    p.set_output(r)
+    return p
+
+
+@pytest.mark.parametrize("h,w", [(97, 250), (1, 3)])
+def test_harris_kernels_with_other_weights(h, w):
+    """Scaled Sobel, a 1/3 box and a gray scale of 1/2: the runtime-weight
+    instantiations of the tiled and streaming kernels against stage-per-kernel."""
+    img = synth.rgb_f32(h, w, seed=9)
+    x = to_device(img, hp.HP_F32)
+    p = _harris_like([-0.5, 0.0, 0.5], [0.25, 0.5, 0.25], [1 / 3, 1 / 3, 1 / 3], 0.5)
+    plain = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+    for kw, kern in [(dict(tile_w=120, tile_h=8, threads=128), hp.HP_KERNEL_HARRIS_ROWS),
+                     (dict(tile_w=64, tile_h=32), hp.HP_KERNEL_HARRIS)]:
+        pipelines.fused_schedule(p, **kw)
+        assert p.group_info([(w, h)], 0).kernel == kern
+        assert torch.equal(bits(run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)), bits(plain)), kw
+
+
+@pytest.mark.parametrize("io,inner", [(hp.HP_BF16, hp.HP_F32), (hp.HP_F16, hp.HP_F32), (hp.HP_F32, hp.HP_BF16),
+                                      (hp.HP_BF16, hp.HP_BF16)])
+def test_harris_streaming_kernel_16bit_storage(io, inner):
+    """2-byte inputs take 112-column strips (the TMA box starts 8 columns left
+    of the strip); 16-bit intermediates round every stage as the other
+    schedules do."""
+    h, w = 131, 250
+    img = synth.rgb_f32(h, w, seed=8)
+    p = pipelines.harris(io_storage=io, inner_storage=inner)
+    x = to_device(img, io)
+    plain = run(p, [x], [io], (1, h, w), io)
+    sw = 120 if io == hp.HP_F32 else 112
+    for th in (4, 9, 33):
+        pipelines.fused_schedule(p, tile_w=sw, tile_h=th, threads=128, impl=hp.HP_IMPL_WAVE)
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_HARRIS_ROWS
+        got = run(p, [x], [io], (1, h, w), io)
+        assert torch.equal(bits(got), bits(plain)), th
+
+
 # ---------------------------------------------------------------- unsharp ---
 @pytest.mark.parametrize("h,w", [(480, 640), (3, 9), (1, 1)])
 def test_unsharp_against_oracle_and_schedules(h, w):

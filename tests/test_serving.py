@@ -25,7 +25,7 @@ def _kinds():
     un = pipelines.unsharp()
     pipelines.fused_schedule(un, tile_w=64, tile_h=32)
     hr = pipelines.harris()
-    pipelines.fused_schedule(hr, tile_w=64, tile_h=32)
+    pipelines.fused_schedule(hr, tile_w=120, tile_h=16, threads=128)
     he = pipelines.histeq()
     return {
         "unsharp": (un, lambda h, w, s: (synth.rgb_f32(h, w, seed=s), hp.HP_F32), (3, hp.HP_F32, torch.float32)),
