@@ -113,8 +113,8 @@ def config_table():
     cfgs["unsharp"] = dict(workload=f"unsharp_rgb_{UW}x{UH}_f32", h=UH, w=UW,
                            inputs=lambda seed: [(synth.rgb_f32(UH, UW, seed=seed), hp.HP_F32)],
                            out=(3, UH, UW, hp.HP_F32), build=lambda: pipelines.unsharp(),
-                           fused=lambda p: pipelines.fused_schedule(p, tile_w=64, tile_h=32),
-                           flops_px=63, bytes_px=24, bound="hbm", kernel="k_chain", dtype="f32",
+                           fused=lambda p: pipelines.fused_schedule(p, tile_w=120, tile_h=96, threads=256),
+                           flops_px=63, bytes_px=24, bound="hbm", kernel="k_stencil_rows", dtype="f32",
                            oracle_sample=unsharp_sample, parity=unsharp_parity, sample_rows=96)
 
     def histeq_sample(rows):
@@ -511,7 +511,7 @@ def run_serving(args):
     import __graft_entry__
     __graft_entry__.build()
     un = pipelines.unsharp()
-    pipelines.fused_schedule(un, tile_w=64, tile_h=32)
+    pipelines.fused_schedule(un, tile_w=120, tile_h=32, threads=256)
     hr = pipelines.harris()
     pipelines.fused_schedule(hr, tile_w=120, tile_h=32, threads=256)
     he = pipelines.histeq()

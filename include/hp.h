@@ -127,7 +127,10 @@ enum {
                           Harris: one warp per column strip of exactly 120 columns (4-byte input) or
                           112 (2-byte input), tile_h rows per run (>= 4), threads <= 256.  Under
                           HP_IMPL_AUTO a Harris group whose tile_w is that strip width (the default)
-                          also takes the streaming kernel; other widths take the tiled one. */
+                          also takes the streaming kernel; other widths take the tiled one.
+                          A single 5x5 stencil, alone or with the unsharp combine: the same strips
+                          (120 / 112 columns), tile_h rows per run, threads <= 256; again the default
+                          under HP_IMPL_AUTO when tile_w is the strip width. */
 };
 
 typedef struct {
@@ -172,8 +175,10 @@ enum {
   HP_KERNEL_LUT_APPLY = 9,
   HP_KERNEL_LL_LEVEL = 10,     /* local-Laplacian level: two-level blend + collapse step (+ colour) */
   HP_KERNEL_STENCIL_WAVE = 11, /* streaming stencil chain (HP_IMPL_WAVE) */
-  HP_KERNEL_HARRIS_ROWS = 12   /* whole Harris DAG, streaming: one warp per column strip, rows
+  HP_KERNEL_HARRIS_ROWS = 12,  /* whole Harris DAG, streaming: one warp per column strip, rows
                                   through a per-warp TMA ring, intermediates in registers */
+  HP_KERNEL_STENCIL_ROWS = 13  /* one 5x5 stencil (+ unsharp combine), streaming: one warp per
+                                  column strip of one plane, rows through a per-warp TMA ring */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

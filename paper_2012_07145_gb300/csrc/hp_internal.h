@@ -219,6 +219,11 @@ int harris_rows_strip_w(int in_dtype);
 int harris_rows_smem_bytes(int threads, int in_dtype);
 int harris_rows_grid(const HarrisArgs& a, int units, int threads, int smem_bytes);
 int launch_harris_rows(const HarrisArgs& a, int rows, int grid, int smem_bytes, void* stream);
+// streaming single 5x5 stencil (+ unsharp combine): one warp per strip of one plane
+int stencil_rows_strip_w(int in_dtype);
+int stencil_rows_smem_bytes(int threads, int in_dtype);
+int stencil_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes);
+int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream);
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
 int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);

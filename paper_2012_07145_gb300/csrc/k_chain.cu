@@ -124,10 +124,10 @@ __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int 
                                       const float* wx, const float* wy, int dtype, const Sink& sink) {
   const int nb = Ws >> 2;
   const int nseg = (Hs + SEG - 1) / SEG;
-  // work item (b, sg) = (4-column block, row segment); walked without divisions
-  int sg = threadIdx.x / nb, b = threadIdx.x - sg * nb;
-  const int dsg = blockDim.x / nb, db = blockDim.x - dsg * nb;
-  while (sg < nseg) {
+  const int items = nb * nseg;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int sg = it / nb;
+    const int b = it - sg * nb;
     const int r0 = sg * SEG;
     const float* p = src + r0 * P + 4 * b;
     float4 h[SEG + 4];
@@ -135,12 +135,6 @@ __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int 
     for (int k = 0; k < SEG + 4; ++k) {
       h[k] = xpass(p + k * P, wx);
       if (k >= 4) sink.put(b, r0 + k - 4, ypass<RND>(wy, h[k - 4], h[k - 3], h[k - 2], h[k - 1], h[k], dtype));
-    }
-    b += db;
-    sg += dsg;
-    if (b >= nb) {
-      b -= nb;
-      ++sg;
     }
   }
 }
@@ -150,24 +144,25 @@ __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int 
 __device__ void fixup(float* buf, int P, int x0, int y0, int Ws, int Hs, int W, int H) {
   const int cx0 = max(0, -x0), cx1 = min(Ws, W - x0);
   const int cy0 = max(0, -y0), cy1 = min(Hs, H - y0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // rows above and below the image: whole rows from the nearest image row
   const int band_rows = cy0 + (Hs - cy1);
-  for (int r = warp; r < band_rows; r += nw) {
-    const int y = r < cy0 ? r : cy1 + (r - cy0);
-    const float* from = buf + min(max(y, cy0), cy1 - 1) * P;
-    float* to = buf + y * P;
-    for (int x = lane; x < Ws; x += 32) to[x] = from[min(max(x, cx0), cx1 - 1)];
-  }
-  // columns left and right of the image on the image rows (these never read
-  // what the band loop writes, nor write what it reads)
+  const int n1 = band_rows * Ws;
   const int side = cx0 + (Ws - cx1);
-  if (side > 0)
-    for (int y = cy0 + warp; y < cy1; y += nw)
-      for (int k = lane; k < side; k += 32) {
-        const int x = k < cx0 ? k : cx1 + (k - cx0);
-        buf[y * P + x] = buf[y * P + min(max(x, cx0), cx1 - 1)];
-      }
+  const int n2 = (cy1 - cy0) * side;
+  for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+    int x, y;
+    if (i < n1) {
+      int r = i / Ws;
+      x = i - r * Ws;
+      y = r < cy0 ? r : cy1 + (r - cy0);
+    } else {
+      int j = i - n1;
+      int r = j / side;
+      int k = j - r * side;
+      y = cy0 + r;
+      x = k < cx0 ? k : cx1 + (k - cx0);
+    }
+    buf[y * P + x] = buf[min(max(y, cy0), cy1 - 1) * P + min(max(x, cx0), cx1 - 1)];
+  }
 }
 
 __device__ __forceinline__ float staged_value(const unsigned char* st, int idx, int dtype) {
@@ -263,14 +258,9 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
   const int nb4 = a.tile_w >> 2;
   char* plane = (char*)a.out.data + (long long)ch * a.out.ps;
   const int odt = a.out.dtype;
-  int y = threadIdx.x / nb4, xb = threadIdx.x - y * nb4;
-  const int dy = blockDim.x / nb4, dxb = blockDim.x - dy * nb4;
-  for (; y < hlim; y += dy, xb += dxb) {
-    if (xb >= nb4) {
-      xb -= nb4;
-      if (++y >= hlim) break;
-    }
-    const int x = 4 * xb;
+  for (int i = threadIdx.x; i < hlim * nb4; i += blockDim.x) {
+    const int y = i / nb4;
+    const int x = 4 * (i - y * nb4);
     if (x >= wlim) continue;
     float4 v = *reinterpret_cast<const float4*>(last + y * g.P + x);
     if (a.epilogue == 1) {

@@ -27,6 +27,8 @@ namespace hp {
 
 namespace {
 
+// Box heights stay a power of two: boxes of 3 or 5 rows measured several
+// times slower to arrive than boxes of 2 or 4.
 constexpr int kBoxRows = 2;       // rows per TMA box
 constexpr int kRing = 4;          // boxes per warp ring
 constexpr int kBarBytes = 512;    // mbarriers of up to 16 warps x kRing
@@ -459,8 +461,7 @@ int harris_rows_smem_bytes(int threads, int in_dtype) {
 }
 
 // Persistent grid: enough CTAs to fill every SM at the kernel's occupancy, or
-// fewer when there are fewer units.  Falls back to one CTA per group of units
-// when the device cannot be queried.
+// fewer when there are fewer units.
 int harris_rows_grid(const HarrisArgs& a, int units, int threads, int smem_bytes) {
   const int nw = threads / 32;
   const int need = (units + nw - 1) / nw;
@@ -470,7 +471,7 @@ int harris_rows_grid(const HarrisArgs& a, int units, int threads, int smem_bytes
       allow_max_dynamic_smem((const void*)kern) != 0 ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem_bytes) != cudaSuccess || per_sm < 1) {
     cudaGetLastError();
-    return need;
+    return need < 2 * 152 ? need : 2 * 152;  // no device to ask: two CTAs on each of 152 SMs
   }
   return need < sms * per_sm ? need : sms * per_sm;
 }

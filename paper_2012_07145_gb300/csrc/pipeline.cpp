@@ -515,7 +515,7 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     chain = is_r2_stencil(s) && (i == 0 ? (s.inputs[0] < 0 || std::find(m.begin(), m.end(), s.inputs[0]) == m.end())
                                        : s.inputs[0] == m[i - 1]);
   }
-  if (chain) return impl == HP_IMPL_WAVE ? HP_KERNEL_STENCIL_WAVE : HP_KERNEL_STENCIL_CHAIN;
+  if (chain) return impl == HP_IMPL_WAVE && m.size() > 1 ? HP_KERNEL_STENCIL_WAVE : HP_KERNEL_STENCIL_CHAIN;
   {
     int remap, gray, rm;
     if (match_down(p, m, &remap, &gray, &rm)) return HP_KERNEL_DOWNSAMPLE;
@@ -569,6 +569,17 @@ size_t scratch_bytes(const Stage& s, Dom d) {
 
 int pick(const std::vector<int>& v, int g, int dflt) {
   return g < (int)v.size() && v[g] > 0 ? v[g] : dflt;
+}
+
+// Default run length of the streaming kernels: about one run per resident warp
+// over the image (strip_units = strips x planes), at least 8 rows so that the
+// 4 warm-up rows of a run stay a modest overhead.
+int default_run_rows(int h, int strip_units, long long resident_warps) {
+  if (resident_warps < 1) resident_warps = 1;
+  long long r = ((long long)h * strip_units + resident_warps - 1) / resident_warps;
+  if (r < 8) r = 8;
+  if (r > h) r = h < 8 ? 8 : h;
+  return (int)r;
 }
 
 // Builds the generic plan (GPlan) of a group: nodes in member order, the
@@ -652,7 +663,7 @@ hp_status build_gplan(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   return HP_OK;
 }
 
-hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, bool unsharp) {
+void chain_common_args(const hp_pipeline* p, GroupPlan& gp, bool unsharp) {
   ChainArgs& a = gp.chain;
   memset(&a, 0, sizeof a);
   std::vector<int> st = gp.members;
@@ -670,6 +681,45 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   a.amount = unsharp ? p->stages[gp.members[1]].params[0] : 0.0f;
   a.tile_w = gp.tile_w;
   a.tile_h = gp.tile_h;
+  a.threads = gp.threads;
+  a.seg = gp.seg;
+}
+
+// A single 5x5 stencil (optionally with the unsharp combine) on the streaming
+// kernel: strips of stencil_rows_strip_w columns, tile_h rows per run.
+hp_status build_stencil_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, bool unsharp) {
+  chain_common_args(p, gp, unsharp);
+  ChainArgs& a = gp.chain;
+  const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
+  const int sw = stencil_rows_strip_w(in_dt);
+  if (a.tile_w != sw)
+    return fail(HP_ERR_SCHEDULE, "streaming stencil strips are %d columns wide for this input type (tile_w %d)", sw,
+                a.tile_w);
+  if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 256)
+    return fail(HP_ERR_SCHEDULE, "streaming stencil threads per block must be a multiple of 32 in [32, 256]");
+  Dom od = plan.dom[gp.output];
+  const int planes = p->stages[gp.output].channels;
+  a.tiles_x = (od.w + sw - 1) / sw;
+  gp.smem = stencil_rows_smem_bytes(a.threads, in_dt);
+  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "streaming stencil needs %d bytes of shared memory", gp.smem);
+  a.in.dtype = in_dt;
+  a.out.dtype = p->stages[gp.output].storage;
+  if (a.tile_h == 0)
+    gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x * planes,
+                                            (long long)stencil_rows_grid(a, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
+  if (a.tile_h < 1 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming stencil needs tile_h >= 1 rows per run");
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  gp.grid_x = stencil_rows_grid(a, a.tiles_x * a.tiles_y * planes, a.threads, gp.smem);
+  gp.grid_y = 1;
+  gp.grid_z = 1;
+  return HP_OK;
+}
+
+hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, bool unsharp) {
+  chain_common_args(p, gp, unsharp);
+  ChainArgs& a = gp.chain;
+  std::vector<int> st = gp.members;
+  if (unsharp) st.resize(1);
   if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_h < 1)
     return fail(HP_ERR_SCHEDULE, "stencil-chain tile width must be a positive multiple of 8");
   Dom od = plan.dom[gp.output];
@@ -775,14 +825,19 @@ hp_status build_harris_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& g
   if (a.tile_w != sw)
     return fail(HP_ERR_SCHEDULE, "streaming Harris strips are %d columns wide for this input type (tile_w %d)", sw,
                 a.tile_w);
-  if (a.tile_h < 4 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming Harris needs tile_h >= 4 rows per run");
   if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 256)
     return fail(HP_ERR_SCHEDULE, "streaming Harris threads per block must be a multiple of 32 in [32, 256]");
   Dom od = plan.dom[gp.output];
   a.tiles_x = (od.w + sw - 1) / sw;
-  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
   gp.smem = harris_rows_smem_bytes(a.threads, in_dt);
   if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "streaming Harris needs %d bytes of shared memory", gp.smem);
+  a.in.dtype = in_dt;
+  a.out.dtype = p->stages[gp.output].storage;
+  if (a.tile_h == 0)
+    gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x,
+                                            (long long)harris_rows_grid(a, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
+  if (a.tile_h < 4 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming Harris needs tile_h >= 4 rows per run");
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
   gp.grid_x = harris_rows_grid(a, a.tiles_x * a.tiles_y, a.threads, gp.smem);
   gp.grid_y = 1;
   gp.ext_refs.assign(1, p->stages[roles[0]].inputs[0]);
@@ -901,13 +956,25 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         s = build_wave(p, plan, gp);
         break;
       case HP_KERNEL_STENCIL_CHAIN:
-      case HP_KERNEL_UNSHARP:
-        gp.tile_w = pick(p->tile_w, g, 64);
-        gp.tile_h = pick(p->tile_h, g, 32);
+      case HP_KERNEL_UNSHARP: {
+        // one stencil (+ unsharp combine): the streaming kernel at its strip
+        // width (the default) or under HP_IMPL_WAVE; else the tiled chain kernel
+        const bool unsharp = gp.kernel == HP_KERNEL_UNSHARP;
+        const bool single = unsharp || gp.members.size() == 1;
+        const int sw = stencil_rows_strip_w(stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]));
+        gp.tile_w = pick(p->tile_w, g, single ? sw : 64);
+        gp.tile_h = pick(p->tile_h, g, single ? 0 : 32);
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
-        s = build_chain(p, plan, gp, gp.kernel == HP_KERNEL_UNSHARP);
+        if (single && (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw))) {
+          gp.kernel = HP_KERNEL_STENCIL_ROWS;
+          s = build_stencil_rows(p, plan, gp, unsharp);
+        } else {
+          if (gp.tile_h == 0) gp.tile_h = 32;
+          s = build_chain(p, plan, gp, unsharp);
+        }
         break;
+      }
       case HP_KERNEL_DOWNSAMPLE: {
         // default: 16x16 coarse tiles, halved (down to 4x4) for small levels so
         // that the grid still covers the SMs
@@ -932,13 +999,14 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         match_harris(p, gp.members, roles);
         const int sw = harris_rows_strip_w(stage_dtype_of_ref(p, p->stages[roles[0]].inputs[0]));
         gp.tile_w = pick(p->tile_w, g, sw);
-        gp.tile_h = pick(p->tile_h, g, 32);
+        gp.tile_h = pick(p->tile_h, g, 0);
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
         if (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw)) {
           gp.kernel = HP_KERNEL_HARRIS_ROWS;
           s = build_harris_rows(p, plan, gp);
         } else {
+          if (gp.tile_h == 0) gp.tile_h = 32;
           s = build_harris(p, plan, gp);
         }
         break;
@@ -1055,6 +1123,14 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.out = out;
         a.err = p->d_err;
         e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_wave(a, gp.smem, stream) : launch_chain(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_STENCIL_ROWS: {
+        ChainArgs a = gp.chain;
+        a.in = ref_view(p, plan, p->stages[gp.members[0]].inputs[0], inputs, output);
+        a.out = out;
+        a.err = p->d_err;
+        e = launch_stencil_rows(a, a.tile_h, gp.grid_x, gp.smem, stream);
         break;
       }
       case HP_KERNEL_DOWNSAMPLE: {

@@ -66,8 +66,16 @@ def test_schedule_validation():
 def test_lowering_picks_kernels():
     p = pipelines.stencil_chain(32, "alternate")
     assert p.group_count() == 32
+    # a single 5x5 stencil defaults to the streaming kernel (120-column strips);
+    # another tile width selects the tiled chain kernel
     info = p.group_info([(2560, 1536)], 0)
-    assert info.kernel == hp.HP_KERNEL_STENCIL_CHAIN and info.n_members == 1
+    assert info.kernel == hp.HP_KERNEL_STENCIL_ROWS and info.n_members == 1 and info.tile_w == 120
+    p.schedule(list(range(32)), tile_w=[64] * 32, tile_h=[32] * 32)
+    assert p.group_info([(2560, 1536)], 0).kernel == hp.HP_KERNEL_STENCIL_CHAIN
+    p.schedule(list(range(32)), tile_w=[64] * 32, impl=[hp.HP_IMPL_WAVE] * 32)
+    with pytest.raises(hp.HPError) as e:   # the streaming kernel's strip width is fixed
+        p.group_info([(2560, 1536)], 0)
+    assert e.value.status == hp.HP_ERR_SCHEDULE
     pipelines.chain_schedule(p, depth=8, tile_w=64, tile_h=32)
     info = p.group_info([(2560, 1536)], 0)
     assert info.kernel == hp.HP_KERNEL_STENCIL_CHAIN and info.n_members == 8
@@ -75,6 +83,8 @@ def test_lowering_picks_kernels():
     u = pipelines.unsharp()
     pipelines.fused_schedule(u)
     assert u.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_UNSHARP
+    pipelines.fused_schedule(u, tile_w=120, tile_h=96)
+    assert u.group_info([(4096, 3072)], 0).kernel == hp.HP_KERNEL_STENCIL_ROWS
     h = pipelines.histeq()
     kinds = [h.group_info([(100, 50)], g).kernel for g in range(3)]
     assert kinds == [hp.HP_KERNEL_HISTOGRAM, hp.HP_KERNEL_CDF_LUT, hp.HP_KERNEL_LUT_APPLY]

@@ -153,6 +153,45 @@ def test_unsharp_against_oracle_and_schedules(h, w):
     assert torch.equal(bits(gen), bits(plain))
 
 
+@pytest.mark.parametrize("h,w", [(480, 640), (77, 131), (3, 9), (1, 1), (130, 250), (5, 361)])
+def test_unsharp_streaming_kernel_bit_identical(h, w):
+    """The streaming stencil kernel (one warp per 120-column strip of a plane,
+    rows through a TMA ring) with the unsharp combine, against the generic
+    interpreter and the tiled kernel, over run lengths that cut the image at
+    every offset against the 4-row boxes and 1..8 warps per block."""
+    img = synth.rgb_f32(h, w, seed=15)
+    x = to_device(img, hp.HP_F32)
+    p = pipelines.unsharp()
+    pipelines.fused_schedule(p, impl=hp.HP_IMPL_GENERIC)
+    ref = run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)
+    if h * w > 1:
+        assert rel_err(to_numpy(ref), ous.unsharp(img.astype(np.float64))) <= TOL
+    pipelines.fused_schedule(p, tile_w=64, tile_h=32)
+    assert torch.equal(bits(run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)), bits(ref))
+    for th, thr in [(1, 32), (3, 64), (7, 128), (96, 256), (45, 96)]:
+        pipelines.fused_schedule(p, tile_w=120, tile_h=th, threads=thr)
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_ROWS
+        got = run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)
+        assert torch.equal(bits(got), bits(ref)), (th, thr)
+        assert p.device_error() == 0
+
+
+@pytest.mark.parametrize("st", [hp.HP_BF16, hp.HP_F16])
+def test_unsharp_streaming_kernel_16bit(st):
+    """2-byte storage: 112-column strips, every stage rounded as in the other
+    schedules."""
+    h, w = 99, 250
+    img = synth.rgb_f32(h, w, seed=16)
+    x = to_device(img, st)
+    p = pipelines.unsharp(storage=st)
+    pipelines.fused_schedule(p, impl=hp.HP_IMPL_GENERIC)
+    ref = run(p, [x], [st], (3, h, w), st)
+    for th in (2, 33):
+        pipelines.fused_schedule(p, tile_w=112, tile_h=th, threads=128, impl=hp.HP_IMPL_WAVE)
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_ROWS
+        assert torch.equal(bits(run(p, [x], [st], (3, h, w), st)), bits(ref)), th
+
+
 # -------------------------------------------------------- histogram equalize -
 @pytest.mark.parametrize("h,w", [(256, 256), (480, 640), (1080, 1920), (3072, 4096), (33, 17), (1, 1), (5, 3)])
 def test_histeq_bit_exact(h, w):
