@@ -129,8 +129,9 @@ def config_table():
 
     cfgs["histeq"] = dict(workload=f"histeq_u8_{UW}x{UH}", h=UH, w=UW,
                           inputs=lambda seed: [(synth.gray_u8_lowcontrast(UH, UW, seed=seed), hp.HP_U8)],
-                          out=(1, UH, UW, hp.HP_U8), build=lambda: pipelines.histeq(), fused=lambda p: None,
-                          flops_px=0, bytes_px=3, bound="hbm", kernel="k_hist", dtype="u8",
+                          out=(1, UH, UW, hp.HP_U8), build=lambda: pipelines.histeq(),
+                          fused=lambda p: pipelines.fused_schedule(p),
+                          flops_px=0, bytes_px=2, bound="hbm", kernel="k_histeq", dtype="u8",
                           oracle_sample=histeq_sample, parity=histeq_parity, sample_rows=256)
 
     def ll_build():
@@ -515,6 +516,7 @@ def run_serving(args):
     hr = pipelines.harris()
     pipelines.fused_schedule(hr, tile_w=120, tile_h=32, threads=256)
     he = pipelines.histeq()
+    pipelines.fused_schedule(he)
     kinds = [("unsharp", un, 3, hp.HP_F32, 3, torch.float32), ("harris", hr, 3, hp.HP_F32, 1, torch.float32),
              ("histeq", he, 1, hp.HP_U8, 1, torch.uint8)]
     ring = 3

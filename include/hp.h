@@ -177,8 +177,10 @@ enum {
   HP_KERNEL_STENCIL_WAVE = 11, /* streaming stencil chain (HP_IMPL_WAVE) */
   HP_KERNEL_HARRIS_ROWS = 12,  /* whole Harris DAG, streaming: one warp per column strip, rows
                                   through a per-warp TMA ring, intermediates in registers */
-  HP_KERNEL_STENCIL_ROWS = 13  /* one 5x5 stencil (+ unsharp combine), streaming: one warp per
+  HP_KERNEL_STENCIL_ROWS = 13, /* one 5x5 stencil (+ unsharp combine), streaming: one warp per
                                   column strip of one plane, rows through a per-warp TMA ring */
+  HP_KERNEL_HISTEQ = 14        /* histogram + CDF/table + lookup in one group: one cooperative
+                                  kernel, a grid-wide barrier between counting and lookup */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -224,6 +224,10 @@ int stencil_rows_strip_w(int in_dtype);
 int stencil_rows_smem_bytes(int threads, int in_dtype);
 int stencil_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes);
 int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream);
+// histogram equalization in one cooperative kernel; `state` is histeq_state_bytes() of zeroed device memory
+size_t histeq_state_bytes();
+int histeq_grid(int w, int h);
+int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, int grid, void* stream);
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
 int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);

@@ -14,6 +14,7 @@
 
 #include <mutex>
 
+#include "hist_common.cuh"
 #include "hp_internal.h"
 
 namespace hp {
@@ -22,16 +23,6 @@ namespace {
 
 constexpr int kHistThreads = 512;
 constexpr int kHistWarps = kHistThreads / 32;
-
-__device__ __forceinline__ void count_byte(unsigned int* wh, unsigned int v, unsigned int active) {
-  const int first = __ffs(active) - 1;
-  const bool uniform = __all_sync(active, v == __shfl_sync(active, v, first));
-  if (uniform) {
-    if ((int)(threadIdx.x & 31) == first) atomicAdd(&wh[v], (unsigned int)__popc(active));
-  } else {
-    atomicAdd(&wh[v], 1u);
-  }
-}
 
 constexpr int kChunksPerIter = 4;
 
@@ -87,50 +78,9 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigne
   }
 }
 
-// One CTA of 256 threads: inclusive scan of the counts, then the table
-//   N == cmin: LUT[v] = v;  cdf[v] < cmin: 0;
-//   else ((cdf[v]-cmin)*510 + (N-cmin)) / (2*(N-cmin)) in 64-bit integers.
+// One CTA of 256 threads: the CDF and the equalization table.
 __global__ void __launch_bounds__(256) k_cdf_lut(const unsigned int* __restrict__ hist, unsigned char* __restrict__ lut) {
-  __shared__ unsigned int warp_tot[8];
-  __shared__ unsigned int s_cmin, s_first;
-  const int v = threadIdx.x;
-  const int lane = v & 31, w = v >> 5;
-  unsigned int h = hist[v];
-  unsigned int c = h;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned int t = __shfl_up_sync(0xffffffffu, c, o);
-    if (lane >= o) c += t;
-  }
-  if (lane == 31) warp_tot[w] = c;
-  if (v == 0) s_first = 256;
-  __syncthreads();
-  unsigned int off = 0;
-  for (int i = 0; i < w; ++i) off += warp_tot[i];
-  c += off;
-  if (h > 0) atomicMin(&s_first, (unsigned int)v);
-  __syncthreads();
-  if (v == (int)s_first) s_cmin = c;
-  if (s_first == 256 && v == 0) s_cmin = 0;
-  __syncthreads();
-  unsigned long long n = 0;
-  for (int i = 0; i < 8; ++i) n += warp_tot[i];
-  unsigned long long cmin = s_cmin;
-  unsigned int out;
-  if (n == cmin) {
-    out = (unsigned int)v;
-  } else if (c < cmin) {
-    out = 0;
-  } else {
-    unsigned long long den = n - cmin;
-    out = (unsigned int)((((unsigned long long)c - cmin) * 510ull + den) / (2ull * den));
-  }
-  lut[v] = (unsigned char)out;
-}
-
-__device__ __forceinline__ unsigned int lut4(const unsigned char* t, unsigned int a) {
-  return (unsigned int)t[a & 0xff] | ((unsigned int)t[(a >> 8) & 0xff] << 8) |
-         ((unsigned int)t[(a >> 16) & 0xff] << 16) | ((unsigned int)t[a >> 24] << 24);
+  cdf_lut_cta(hist[threadIdx.x], lut);
 }
 
 __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out,

@@ -89,6 +89,8 @@ struct GroupPlan {
   LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
+  size_t aux_bytes = 0;       // kernel state kept across launches (zeroed once at allocation)
+  void* aux = nullptr;
 };
 
 struct Scratch {
@@ -502,6 +504,14 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
       case HP_CDF_LUT: return HP_KERNEL_CDF_LUT;
       case HP_LUT_APPLY: return HP_KERNEL_LUT_APPLY;
     }
+  }
+  if (m.size() == 3) {  // histogram -> table -> lookup of the same u8 image
+    const Stage& h = p->stages[m[0]];
+    const Stage& t = p->stages[m[1]];
+    const Stage& l = p->stages[m[2]];
+    if (h.kind == HP_HISTOGRAM && t.kind == HP_CDF_LUT && l.kind == HP_LUT_APPLY && t.inputs[0] == m[0] &&
+        l.inputs[1] == m[1] && l.inputs[0] == h.inputs[0] && impl != HP_IMPL_GENERIC)
+      return HP_KERNEL_HISTEQ;
   }
   for (int s : m) {
     int k = p->stages[s].kind;
@@ -1011,6 +1021,14 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         }
         break;
       }
+      case HP_KERNEL_HISTEQ: {
+        Dom od = plan.dom[gp.output];
+        gp.threads = 1024;
+        gp.grid_x = histeq_grid(od.w, od.h);
+        gp.aux_bytes = histeq_state_bytes();
+        gp.ext_refs.assign(1, p->stages[gp.members[0]].inputs[0]);
+        break;
+      }
       case HP_KERNEL_HISTOGRAM: case HP_KERNEL_CDF_LUT: case HP_KERNEL_LUT_APPLY:
         gp.threads = 256;
         break;
@@ -1031,6 +1049,15 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
 
 hp_status ensure_scratch(hp_pipeline* p, Plan& plan) {
   if (plan.allocated) return HP_OK;
+  for (GroupPlan& gp : plan.groups) {
+    if (gp.aux_bytes && !gp.aux) {
+      if (cudaMalloc(&gp.aux, gp.aux_bytes) != cudaSuccess || cudaMemset(gp.aux, 0, gp.aux_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        gp.aux = nullptr;
+        return fail(HP_ERR_OOM, "cudaMalloc of %zu bytes of kernel state failed", gp.aux_bytes);
+      }
+    }
+  }
   for (const GroupPlan& gp : plan.groups) {
     if (gp.output == p->output) continue;
     const Stage& st = p->stages[gp.output];
@@ -1091,6 +1118,11 @@ void free_plan(Plan& plan) {
   plan.graphs.clear();
   plan.seen.clear();
   for (auto& kv : plan.bufs) cudaFree(kv.second.ptr);
+  for (auto& gp : plan.groups)
+    if (gp.aux) {
+      cudaFree(gp.aux);
+      gp.aux = nullptr;
+    }
   for (auto& sc : plan.staging) cudaFree(sc.ptr);
   plan.bufs.clear();
   plan.staging.clear();
@@ -1170,6 +1202,9 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         e = launch_harris_rows(a, a.tile_h, gp.grid_x, gp.smem, stream);
         break;
       }
+      case HP_KERNEL_HISTEQ:
+        e = launch_histeq(ref_view(p, plan, gp.ext_refs[0], inputs, output), out, gp.aux, p->d_err, gp.grid_x, stream);
+        break;
       case HP_KERNEL_HISTOGRAM: {
         HistArgs a{};
         a.in = ref_view(p, plan, p->stages[gp.output].inputs[0], inputs, output);

@@ -88,6 +88,10 @@ def test_lowering_picks_kernels():
     h = pipelines.histeq()
     kinds = [h.group_info([(100, 50)], g).kernel for g in range(3)]
     assert kinds == [hp.HP_KERNEL_HISTOGRAM, hp.HP_KERNEL_CDF_LUT, hp.HP_KERNEL_LUT_APPLY]
+    pipelines.fused_schedule(h)   # all three in one group: one cooperative kernel
+    info = h.group_info([(4096, 3072)], 0)
+    assert h.group_count() == 1 and info.kernel == hp.HP_KERNEL_HISTEQ and info.threads == 1024
+    assert 1 <= info.grid_x <= 4096 * 3072 // 16 // 2048 + 1
     hr = pipelines.harris()
     pipelines.fused_schedule(hr, impl=hp.HP_IMPL_GENERIC)
     assert hr.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_GENERIC

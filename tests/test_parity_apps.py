@@ -203,6 +203,41 @@ def test_histeq_bit_exact(h, w):
     assert np.array_equal(to_numpy(y)[0], ref)
 
 
+@pytest.mark.parametrize("h,w", [(256, 256), (480, 640), (1080, 1920), (3072, 4096), (33, 17), (1, 1), (5, 3),
+                                 (4500, 5000)])
+def test_histeq_fused_kernel_bit_exact(h, w):
+    """Histogram, table and lookup in one cooperative kernel.  Three launches in
+    a row on different images exercise the self-resetting device state; 4500 x
+    5000 holds more chunks than the grid keeps in registers (counting in rounds
+    and reading the image again for the lookup)."""
+    p = pipelines.histeq()
+    pipelines.fused_schedule(p)
+    assert p.group_count() == 1 and p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_HISTEQ
+    for seed in range(3):
+        img = synth.gray_u8_lowcontrast(h, w, seed=seed * 31 + h)
+        ref = ohe.equalize(img[0])[2]
+        n0 = hp.launch_count()
+        y = run(p, [to_device(img, hp.HP_U8)], [hp.HP_U8], (1, h, w), hp.HP_U8)
+        assert hp.launch_count() - n0 == 1
+        assert np.array_equal(to_numpy(y)[0], ref), seed
+
+
+def test_histeq_fused_kernel_graph_replay_and_special_images():
+    p = pipelines.histeq()
+    pipelines.fused_schedule(p)
+    p.use_cuda_graph(True)
+    h, w = 300, 496   # rows a multiple of 16 bytes, so plain tensors serve as buffers
+    x = torch.zeros((1, h, w), dtype=torch.uint8, device="cuda")
+    y = torch.zeros((1, h, w), dtype=torch.uint8, device="cuda")
+    imgs = [synth.gray_u8_lowcontrast(h, w, seed=s) for s in range(3)]
+    imgs.append(np.full((1, h, w), 77, dtype=np.uint8))                              # constant
+    imgs.append(np.where(np.arange(w)[None, None, :] % 2 == 0, 10, 200).astype(np.uint8).repeat(h, 1))
+    for img in imgs + imgs:   # uncaptured, captured, then replays of the same addresses
+        x.copy_(torch.from_numpy(img))
+        run(p, [x], [hp.HP_U8], None, hp.HP_U8, out=y)
+        assert np.array_equal(to_numpy(y)[0], ohe.equalize(img[0])[2])
+
+
 def test_histeq_constant_and_two_value_images():
     p = pipelines.histeq()
     const = np.full((1, 40, 50), 77, dtype=np.uint8)
