@@ -2,22 +2,24 @@
 // read from memory once and written once.
 //
 // Each CTA takes a contiguous range of 16-pixel chunks (row-major over the
-// image, a row's last chunk possibly partial) and holds them in registers
-// (kEqK chunks per thread) while it counts them into per-warp sub-histograms
-// (four interleaved copies per warp, one per lane mod 4, against same-address
-// serialisation of the shared-memory atomics).  The CTA adds its counts to a device-wide histogram with
+// image, a row's last chunk possibly partial), keeps them in shared memory
+// while it counts them into per-warp sub-histograms (four interleaved copies
+// per warp, one per lane mod 4, against same-address serialisation of the
+// shared-memory atomics).  The loops stay compact: each runs once or twice per
+// thread, so its code must not be long (the instruction cache is cold).  The CTA adds its counts to a device-wide histogram with
 // one atomic per bin, then all CTAs meet at a grid-wide barrier -- they are
 // co-resident because the launch is cooperative, and the wait is bounded --
 // after which every CTA forms the CDF and the table itself (256 bins: cheaper
-// than another launch) and writes its equalized chunks.  When an image has
-// more chunks than the grid holds in registers, the CTA counts in rounds and
-// reads its chunks again for the lookup.
+// than another launch) and writes its equalized chunks.  When a CTA's slice
+// does not fit in shared memory it reads its chunks again for the lookup.
 //
-// The device-wide state (two histograms, an arrival counter and a generation
-// number) lives in a zero-initialised scratch that resets itself: launch g
-// counts into histogram g & 1, and the last CTA to arrive clears the other
-// histogram and the counter before it releases the others by bumping the
-// generation, so the next launch (a CUDA-graph replay included) starts clean.
+// The device-wide state (two histograms of kEqCopies copies each -- CTA b adds
+// into copy b % kEqCopies, so no counter takes more than a few atomics -- an
+// arrival counter and a generation number) lives in a zero-initialised
+// scratch that resets itself: launch g counts into histogram g & 1, and the
+// last CTA to arrive clears the other histogram and the counter before it
+// releases the others by bumping the generation, so the next launch (a
+// CUDA-graph replay included) starts clean.
 #include <cuda_runtime.h>
 
 #include "hist_common.cuh"
@@ -30,12 +32,16 @@ namespace {
 
 constexpr int kEqThreads = 1024;
 constexpr int kEqWarps = kEqThreads / 32;
-constexpr int kEqK = 8;  // chunks of 16 pixels per thread per round
-constexpr int kEqSmem = kEqWarps * 256 * 4 * 4;
+constexpr int kEqU = 4;  // chunk loads in flight per thread
+constexpr int kEqHistBytes = kEqWarps * 256 * 4 * 4;     // per warp: 4 copies of 256 bins
+constexpr int kEqSmemMax = 227 * 1024 - 8 * 1024;        // dynamic shared memory limit used here
+constexpr int kEqStageMax = kEqSmemMax - kEqHistBytes;    // bytes of image a CTA can keep
+
+constexpr int kEqCopies = 8;  // device histogram copies (CTA b adds into copy b % 8)
 
 struct EqState {
   unsigned int gen, count, pad[2];
-  unsigned int hist[2][256];
+  unsigned int hist[2][kEqCopies][256];
 };
 
 struct EqParams {
@@ -44,6 +50,7 @@ struct EqParams {
   int* err;
   long long n_chunks, per_cta;  // chunks in the image; chunks per CTA
   int cpr;                      // chunks per row
+  int staged;                   // per_cta chunks fit in shared memory: no second read
 };
 
 __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* a) {
@@ -68,16 +75,22 @@ __device__ __forceinline__ uint4 load_chunk(const unsigned char* src, int nb) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Counts a chunk into the lane's copy of the warp's sub-histogram: copy c of
-// bin v is word 4 v + c, so lanes that hold the same value but use different
-// copies hit different banks instead of serialising on one address.
-__device__ __forceinline__ void count_chunk(unsigned int* wh, const uint4& q, int nb) {
+// Word of copy c of bin v in a warp's sub-histogram: 4 v + (c ^ ((v >> 3) & 3)).
+// Lanes that hold the same value but use different copies hit different banks
+// instead of serialising on one address, and the swizzle spreads values eight
+// apart (same bank otherwise) over different banks.
+__device__ __forceinline__ unsigned int bin_word(unsigned int v, unsigned int c) {
+  return (v << 2) + (c ^ ((v >> 3) & 3u));
+}
+
+// Counts a chunk into the lane's copy (lane mod 4) of the warp's sub-histogram.
+__device__ __forceinline__ void count_chunk(unsigned int* wh, unsigned int c, const uint4& q, int nb) {
   const unsigned int w[4] = {q.x, q.y, q.z, q.w};
   if (nb == 16) {
 #pragma unroll
-    for (int b = 0; b < 16; ++b) atomicAdd(&wh[((w[b >> 2] >> (8 * (b & 3))) & 0xffu) << 2], 1u);
+    for (int b = 0; b < 16; ++b) atomicAdd(&wh[bin_word((w[b >> 2] >> (8 * (b & 3))) & 0xffu, c)], 1u);
   } else {
-    for (int b = 0; b < nb; ++b) atomicAdd(&wh[((w[b >> 2] >> (8 * (b & 3))) & 0xffu) << 2], 1u);
+    for (int b = 0; b < nb; ++b) atomicAdd(&wh[bin_word((w[b >> 2] >> (8 * (b & 3))) & 0xffu, c)], 1u);
   }
 }
 
@@ -91,47 +104,63 @@ __device__ __forceinline__ void store_chunk(const unsigned char* t, const uint4&
 }
 
 __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant__ EqParams p) {
-  extern __shared__ unsigned int sh_dyn[];  // per warp: 4 copies of 256 bins, interleaved
-  unsigned int (*sh)[256 * 4] = reinterpret_cast<unsigned int (*)[256 * 4]>(sh_dyn);
+  // dynamic shared memory: the warps' sub-histograms, then (when the slice
+  // fits) the CTA's slice of the image
+  extern __shared__ uint4 smem_dyn[];
+  unsigned int (*sh)[256 * 4] = reinterpret_cast<unsigned int (*)[256 * 4]>(smem_dyn);
+  uint4* stage = smem_dyn + kEqHistBytes / 16;
   __shared__ unsigned char table[256];
+  __shared__ unsigned int red[kEqThreads / 256][256];
   __shared__ unsigned int s_gen;
   __shared__ int s_last, s_ok;
   for (int i = threadIdx.x; i < kEqWarps * 256 * 4; i += blockDim.x) (&sh[0][0])[i] = 0;
   if (threadIdx.x == 0) s_gen = ld_relaxed(&p.st->gen);
   __syncthreads();
   const unsigned int gen = s_gen, buf = gen & 1u;
-  unsigned int* wh = sh[threadIdx.x >> 5] + (threadIdx.x & 3);
+  unsigned int* wh = sh[threadIdx.x >> 5];
+  const unsigned int copy = threadIdx.x & 3u;
   const long long c0 = (long long)blockIdx.x * p.per_cta;
   const long long c1 = min(p.n_chunks, c0 + p.per_cta);
-  const long long round_span = (long long)kEqK * blockDim.x;
-  const bool resident = c1 - c0 <= round_span;  // one round: the chunks stay in registers
+  const bool staged = p.staged != 0;  // the slice is kept in shared memory for the lookup
 
-  // ---- count ----
-  uint4 q[kEqK];
-  int nb[kEqK];
+  // ---- count (kEqU loads in flight per thread) ----
+  const long long step = (long long)kEqU * blockDim.x;
+#pragma unroll 1
+  for (long long base = c0 + threadIdx.x; base < c1; base += step) {
+    uint4 q[kEqU];
+    int nb[kEqU];
 #pragma unroll
-  for (int k = 0; k < kEqK; ++k) nb[k] = 0;
-  for (long long base = c0; base < c1; base += round_span) {
-#pragma unroll
-    for (int k = 0; k < kEqK; ++k) {
-      const long long ch = base + (long long)k * blockDim.x + threadIdx.x;
-      nb[k] = 0;
-      q[k] = make_uint4(0u, 0u, 0u, 0u);
+    for (int u = 0; u < kEqU; ++u) {
+      const long long ch = base + (long long)u * blockDim.x;
+      nb[u] = 0;
       if (ch < c1) {
         const unsigned char* src;
         unsigned char* dst;
-        nb[k] = chunk_bytes(p, ch, &src, &dst);
-        q[k] = load_chunk(src, nb[k]);
+        nb[u] = chunk_bytes(p, ch, &src, &dst);
+        q[u] = load_chunk(src, nb[u]);
       }
     }
 #pragma unroll
-    for (int k = 0; k < kEqK; ++k) count_chunk(wh, q[k], nb[k]);
+    for (int u = 0; u < kEqU; ++u) {
+      if (nb[u] == 0) continue;
+      if (staged) stage[base + (long long)u * blockDim.x - c0] = q[u];
+      count_chunk(wh, copy, q[u], nb[u]);
+    }
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < 256; v += blockDim.x) {
+  {
+    // all threads reduce: thread t sums bin t % 256 over a quarter of the
+    // warps (all four copies), then threads 0..255 add the quarters
+    const int v = threadIdx.x & 255, part = threadIdx.x >> 8, nparts = kEqThreads / 256;
     unsigned int s = 0;
-    for (int w = 0; w < kEqWarps; ++w) s += sh[w][4 * v] + sh[w][4 * v + 1] + sh[w][4 * v + 2] + sh[w][4 * v + 3];
-    if (s) atomicAdd(&p.st->hist[buf][v], s);
+    for (int w = part * (kEqWarps / nparts); w < (part + 1) * (kEqWarps / nparts); ++w)
+      s += sh[w][4 * v] + sh[w][4 * v + 1] + sh[w][4 * v + 2] + sh[w][4 * v + 3];
+    red[part][v] = s;
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      s = red[0][v] + red[1][v] + red[2][v] + red[3][v];
+      if (s) atomicAdd(&p.st->hist[buf][blockIdx.x % kEqCopies][v], s);
+    }
   }
 
   // ---- grid-wide barrier (bounded) ----
@@ -145,7 +174,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   if (s_last) {
     // every CTA's counts are in: clear the other histogram and the counter for
     // the next launch, then release the others
-    for (int v = threadIdx.x; v < 256; v += blockDim.x) p.st->hist[buf ^ 1u][v] = 0;
+    for (int v = threadIdx.x; v < kEqCopies * 256; v += blockDim.x) (&p.st->hist[buf ^ 1u][0][0])[v] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
       p.st->count = 0;
@@ -160,7 +189,6 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
         atomicExch(p.err, 3);
         break;
       }
-      __nanosleep(32);
     }
     __threadfence();
   }
@@ -168,25 +196,18 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   if (!s_ok) return;
 
   // ---- table, then the lookup ----
-  cdf_lut_cta(threadIdx.x < 256 ? __ldcg(&p.st->hist[buf][threadIdx.x]) : 0u, table);
-  __syncthreads();
-  if (resident) {
+  unsigned int h = 0;
+  if (threadIdx.x < 256)
 #pragma unroll
-    for (int k = 0; k < kEqK; ++k) {
-      if (nb[k] == 0) continue;
-      const long long ch = c0 + (long long)k * blockDim.x + threadIdx.x;
-      const unsigned char* src;
-      unsigned char* dst;
-      chunk_bytes(p, ch, &src, &dst);
-      store_chunk(table, q[k], nb[k], dst);
-    }
-    return;
-  }
+    for (int c = 0; c < kEqCopies; ++c) h += __ldcg(&p.st->hist[buf][c][threadIdx.x]);
+  cdf_lut_cta(h, table);
+  __syncthreads();
+#pragma unroll 1
   for (long long ch = c0 + threadIdx.x; ch < c1; ch += blockDim.x) {
     const unsigned char* src;
     unsigned char* dst;
     const int n = chunk_bytes(p, ch, &src, &dst);
-    store_chunk(table, load_chunk(src, n), n, dst);
+    store_chunk(table, staged ? stage[ch - c0] : load_chunk(src, n), n, dst);
   }
 }
 
@@ -197,7 +218,8 @@ int max_coop_ctas() {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         allow_max_dynamic_smem((const void*)k_histeq) != 0 ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_histeq, kEqThreads, kEqSmem) != cudaSuccess || per < 1) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_histeq, kEqThreads, kEqSmemMax) != cudaSuccess ||
+        per < 1) {
       cudaGetLastError();
       return 152;
     }
@@ -235,10 +257,11 @@ int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, 
   p.cpr = (in.w + 15) / 16;
   p.n_chunks = (long long)p.cpr * in.h;
   p.per_cta = (p.n_chunks + grid - 1) / grid;
+  p.staged = p.per_cta * 16 <= kEqStageMax;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid, 1, 1);
   cfg.blockDim = dim3(kEqThreads, 1, 1);
-  cfg.dynamicSmemBytes = kEqSmem;
+  cfg.dynamicSmemBytes = kEqHistBytes + (p.staged ? (int)p.per_cta * 16 : 0);
   cfg.stream = (cudaStream_t)stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
