@@ -72,11 +72,11 @@ def config_table():
         "chain32_bf16": _chain_cfg("chain32", 32, "alternate", 1536, 2560, "bf16"),
         "chain4": _chain_cfg("chain4", 4, "binomial", 512, 512),
     }
-    # the same 32-stage chain on the streaming kernel (one warp per stage)
+    # the same 32-stage chain on the streaming kernel (4 stages in registers per warp strip)
     wave = _chain_cfg("chain32", 32, "alternate", 1536, 2560)
     wave["workload"] += "_streaming"
-    wave["kernel"] = "k_wave"
-    wave["fused"] = lambda p: pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=32, impl=hp.HP_IMPL_WAVE)
+    wave["kernel"] = "k_chain_rows"
+    wave["fused"] = lambda p: pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=0, impl=hp.HP_IMPL_WAVE)
     cfgs["chain32_wave"] = wave
     H, W = 1536, 2560
 

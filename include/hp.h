@@ -122,8 +122,10 @@ typedef struct {
 enum {
   HP_IMPL_AUTO = 0,    /* the kernel the group's shape selects */
   HP_IMPL_GENERIC = 1, /* the generic interpreter */
-  HP_IMPL_WAVE = 2     /* streaming kernels.  Stencil chains: one warp per stage, rows through
-                          shared-memory rings; even depth <= 16, f32 input, tile_w <= 128 - 4(d-1).
+  HP_IMPL_WAVE = 2     /* streaming kernels: a warp walks down a strip of columns, rows arrive
+                          through a per-warp TMA ring.  Stencil chains of 2 or 4 stages: every stage
+                          in registers; strips of 120 columns (2 stages, 4-byte input) or 112 (4
+                          stages, or a 2-byte input), tile_h rows per run, threads <= 256.
                           Harris: one warp per column strip of exactly 120 columns (4-byte input) or
                           112 (2-byte input), tile_h rows per run (>= 4), threads <= 256.  Under
                           HP_IMPL_AUTO a Harris group whose tile_w is that strip width (the default)
@@ -174,7 +176,7 @@ enum {
   HP_KERNEL_CDF_LUT = 8,
   HP_KERNEL_LUT_APPLY = 9,
   HP_KERNEL_LL_LEVEL = 10,     /* local-Laplacian level: two-level blend + collapse step (+ colour) */
-  HP_KERNEL_STENCIL_WAVE = 11, /* streaming stencil chain (HP_IMPL_WAVE) */
+  HP_KERNEL_STENCIL_WAVE = 11, /* streaming stencil chain of 2 or 4 stages, all in registers */
   HP_KERNEL_HARRIS_ROWS = 12,  /* whole Harris DAG, streaming: one warp per column strip, rows
                                   through a per-warp TMA ring, intermediates in registers */
   HP_KERNEL_STENCIL_ROWS = 13, /* one 5x5 stencil (+ unsharp combine), streaming: one warp per

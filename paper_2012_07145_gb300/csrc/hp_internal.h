@@ -204,9 +204,12 @@ struct LutApplyArgs {
 
 // Launchers (defined in the .cu files).  Return a cudaError_t as int.
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream);
-int launch_wave(const ChainArgs& a, int smem_bytes, void* stream);
-int wave_smem_bytes(int depth);
-int wave_max_tile_w(int depth);
+// streaming stencil chain (2 or 4 stages in registers): one warp per strip of one plane
+bool chain_rows_depth_ok(int depth);
+int chain_rows_strip_w(int depth, int in_dtype);
+int chain_rows_smem_bytes(int depth, int threads, int in_dtype);
+int chain_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes);
+int launch_chain_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream);
 int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype);
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream);
 int launch_pointwise(const PointwiseArgs& a, void* stream);

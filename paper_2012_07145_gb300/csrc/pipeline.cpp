@@ -525,7 +525,7 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     chain = is_r2_stencil(s) && (i == 0 ? (s.inputs[0] < 0 || std::find(m.begin(), m.end(), s.inputs[0]) == m.end())
                                        : s.inputs[0] == m[i - 1]);
   }
-  if (chain) return impl == HP_IMPL_WAVE && m.size() > 1 ? HP_KERNEL_STENCIL_WAVE : HP_KERNEL_STENCIL_CHAIN;
+  if (chain) return HP_KERNEL_STENCIL_CHAIN;  // the builder picks the tiled or the streaming kernel
   {
     int remap, gray, rm;
     if (match_down(p, m, &remap, &gray, &rm)) return HP_KERNEL_DOWNSAMPLE;
@@ -753,37 +753,35 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   return HP_OK;
 }
 
-hp_status build_wave(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+// A chain of 2 or 4 stencils on the streaming kernel: strips of
+// chain_rows_strip_w columns, tile_h rows per run, every stage in registers.
+hp_status build_chain_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  chain_common_args(p, gp, false);
   ChainArgs& a = gp.chain;
-  memset(&a, 0, sizeof a);
-  a.depth = (int)gp.members.size();
-  for (int i = 0; i < a.depth; ++i) {
-    const Stage& s = p->stages[gp.members[i]];
-    a.storage[i] = s.storage;
-    for (int k = 0; k < 5; ++k) {
-      a.w[i][k] = s.wx[k];
-      a.w[i][5 + k] = s.wy[k];
-    }
-  }
-  a.tile_w = gp.tile_w;
-  a.tile_h = gp.tile_h;
-  int in_ref = p->stages[gp.members[0]].inputs[0];
-  if (stage_dtype_of_ref(p, in_ref) != HP_F32)
-    return fail(HP_ERR_SCHEDULE, "the streaming stencil kernel needs an f32 chain input");
-  if (a.depth < 2 || a.depth > 16 || (a.depth & 1))
-    return fail(HP_ERR_SCHEDULE, "the streaming stencil kernel fuses an even number of stages, 2..16");
-  if (a.tile_w % 8 != 0 || a.tile_w < 8 || a.tile_w > wave_max_tile_w(a.depth) || a.tile_h < 1)
-    return fail(HP_ERR_SCHEDULE, "streaming stencil tile width must be a multiple of 8 up to %d for depth %d",
-                wave_max_tile_w(a.depth), a.depth);
+  if (!chain_rows_depth_ok(a.depth))
+    return fail(HP_ERR_SCHEDULE, "the streaming chain kernel fuses 2 or 4 stencils (group of %d)", a.depth);
+  const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
+  const int sw = chain_rows_strip_w(a.depth, in_dt);
+  if (a.tile_w != sw)
+    return fail(HP_ERR_SCHEDULE, "streaming chain strips of %d stages are %d columns wide for this input type (tile_w %d)",
+                a.depth, sw, a.tile_w);
+  if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 256)
+    return fail(HP_ERR_SCHEDULE, "streaming chain threads per block must be a multiple of 32 in [32, 256]");
   Dom od = plan.dom[gp.output];
-  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  const int planes = p->stages[gp.output].channels;
+  a.tiles_x = (od.w + sw - 1) / sw;
+  gp.smem = chain_rows_smem_bytes(a.depth, a.threads, in_dt);
+  if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "streaming chain needs %d bytes of shared memory", gp.smem);
+  a.in.dtype = in_dt;
+  a.out.dtype = p->stages[gp.output].storage;
+  if (a.tile_h == 0)
+    gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x * planes,
+                                            (long long)chain_rows_grid(a, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
+  if (a.tile_h < 1 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming chain needs tile_h >= 1 rows per run");
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
-  a.threads = 32 * a.depth;
-  a.seg = 1;
-  gp.smem = wave_smem_bytes(a.depth);
-  gp.grid_x = a.tiles_x;
-  gp.grid_y = a.tiles_y;
-  gp.grid_z = p->stages[gp.members[0]].channels;
+  gp.grid_x = chain_rows_grid(a, a.tiles_x * a.tiles_y * planes, a.threads, gp.smem);
+  gp.grid_y = 1;
+  gp.grid_z = 1;
   return HP_OK;
 }
 
@@ -958,29 +956,28 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
     gp.kernel = choose_kernel(p, shapes[g], impl);
     if (gp.kernel < 0) return fail(HP_ERR_UNSUPPORTED, "group %d mixes reductions with other stages", g);
     switch (gp.kernel) {
-      case HP_KERNEL_STENCIL_WAVE:
-        gp.tile_w = pick(p->tile_w, g, 96);
-        gp.tile_h = pick(p->tile_h, g, 128);
-        gp.threads = 32 * (int)gp.members.size();
-        gp.seg = 1;
-        s = build_wave(p, plan, gp);
-        break;
       case HP_KERNEL_STENCIL_CHAIN:
       case HP_KERNEL_UNSHARP: {
         // one stencil (+ unsharp combine): the streaming kernel at its strip
         // width (the default) or under HP_IMPL_WAVE; else the tiled chain kernel
+        // a chain of 2 or 4: the streaming chain kernel likewise at its strip width
         const bool unsharp = gp.kernel == HP_KERNEL_UNSHARP;
         const bool single = unsharp || gp.members.size() == 1;
-        const int sw = stencil_rows_strip_w(stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]));
+        const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
+        const int depth = (int)gp.members.size();
+        const int sw = single ? stencil_rows_strip_w(in_dt) : chain_rows_depth_ok(depth) ? chain_rows_strip_w(depth, in_dt) : -1;
         gp.tile_w = pick(p->tile_w, g, single ? sw : 64);
-        gp.tile_h = pick(p->tile_h, g, single ? 0 : 32);
+        const bool streaming = impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw);
+        gp.tile_h = pick(p->tile_h, g, streaming ? 0 : 32);  // 0: the streaming kernels' adaptive run length
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
-        if (single && (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw))) {
+        if (single && streaming) {
           gp.kernel = HP_KERNEL_STENCIL_ROWS;
           s = build_stencil_rows(p, plan, gp, unsharp);
+        } else if (streaming) {
+          gp.kernel = HP_KERNEL_STENCIL_WAVE;
+          s = build_chain_rows(p, plan, gp);
         } else {
-          if (gp.tile_h == 0) gp.tile_h = 32;
           s = build_chain(p, plan, gp, unsharp);
         }
         break;
@@ -1154,7 +1151,8 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.in = ref_view(p, plan, p->stages[first].inputs[0], inputs, output);
         a.out = out;
         a.err = p->d_err;
-        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_wave(a, gp.smem, stream) : launch_chain(a, gp.smem, stream);
+        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_chain_rows(a, a.tile_h, gp.grid_x, gp.smem, stream)
+                                                : launch_chain(a, gp.smem, stream);
         break;
       }
       case HP_KERNEL_STENCIL_ROWS: {

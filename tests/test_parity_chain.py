@@ -110,13 +110,19 @@ def test_cuda_graph_replay_matches_and_counts_launches():
         y.zero_()
 
 
-@pytest.mark.parametrize("h,w", [(1, 1), (3, 7), (17, 33), (65, 129), (200, 300)])
-@pytest.mark.parametrize("depth,tw,th", [(2, 120, 64), (4, 112, 32), (8, 96, 128), (16, 64, 16)])
-def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th):
+@pytest.mark.parametrize("h,w", [(1, 1), (3, 7), (17, 33), (65, 129), (200, 300), (77, 250)])
+@pytest.mark.parametrize("depth,tw,th,thr", [(2, 120, 64, 256), (2, 120, 5, 64), (4, 112, 32, 256), (4, 112, 7, 96),
+                                             (4, 112, 1, 32)])
+def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th, thr):
+    """The streaming chain kernel (2 or 4 stages in registers per warp strip)
+    against the generic interpreter run stage by stage, over images narrower
+    and shorter than a strip or a run, runs cut at every offset against the
+    4-row boxes, and 1..8 warps per block."""
     img = synth.stencil_input(h, w, seed=h * 7 + w)
     p = pipelines.stencil_chain(16, "alternate")
+    p.schedule(list(range(16)), impl=[hp.HP_IMPL_GENERIC] * 16)
     base = chain_run(p, img)
-    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, impl=hp.HP_IMPL_WAVE)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, threads=thr, impl=hp.HP_IMPL_WAVE)
     assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_WAVE
     n0 = hp.launch_count()
     y = chain_run(p, img)
@@ -124,11 +130,24 @@ def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th):
     assert torch.equal(bits(y), bits(base))
 
 
+@pytest.mark.parametrize("st", ["f16", "bf16"])
+def test_streaming_kernel_16bit_storage(st):
+    dt = {"f16": hp.HP_F16, "bf16": hp.HP_BF16}[st]
+    h, w = 150, 333
+    img = synth.stencil_input(h, w, seed=3)
+    p = pipelines.stencil_chain(8, "alternate", storage=dt)
+    p.schedule(list(range(8)), impl=[hp.HP_IMPL_GENERIC] * 8)
+    base = chain_run(p, img, dt)
+    for depth in (2, 4):
+        pipelines.chain_schedule(p, depth=depth, tile_w=112, tile_h=19, impl=hp.HP_IMPL_WAVE)
+        assert torch.equal(bits(chain_run(p, img, dt)), bits(base)), depth
+
+
 def test_streaming_kernel_full_size_against_oracle():
     H, W = 1536, 2560
     img = synth.stencil_input(H, W, seed=0)
     p = pipelines.stencil_chain(32, "alternate")
     plain = chain_run(p, img)
-    pipelines.chain_schedule(p, depth=8, tile_w=96, tile_h=128, impl=hp.HP_IMPL_WAVE)
+    pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=0, impl=hp.HP_IMPL_WAVE)
     fused = chain_run(p, img)
     assert torch.equal(bits(fused), bits(plain))
