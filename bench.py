@@ -168,21 +168,21 @@ def tuned(name):
 
 
 # ------------------------------------------------------------------ helpers --
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
-    for f in ("k_chain.cu", "stage_math.cuh", "tma.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2012_07145_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current source of that kernel (the files the record lists); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(f"{kernel}:{workload}")
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("source_hash") != kernel_source_hash(rec.get("sources", [])):
         return None
     return rec["dram_bytes_per_launch"]
 

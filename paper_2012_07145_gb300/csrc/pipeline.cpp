@@ -1044,11 +1044,14 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
   return HP_OK;
 }
 
-hp_status ensure_scratch(hp_pipeline* p, Plan& plan) {
+// First realize of a plan: its buffers.  Kernel state is cleared on the
+// realize's own stream (a synchronous memset would wait for every stream).
+hp_status ensure_scratch(hp_pipeline* p, Plan& plan, cudaStream_t stream) {
   if (plan.allocated) return HP_OK;
   for (GroupPlan& gp : plan.groups) {
     if (gp.aux_bytes && !gp.aux) {
-      if (cudaMalloc(&gp.aux, gp.aux_bytes) != cudaSuccess || cudaMemset(gp.aux, 0, gp.aux_bytes) != cudaSuccess) {
+      if (cudaMalloc(&gp.aux, gp.aux_bytes) != cudaSuccess ||
+          cudaMemsetAsync(gp.aux, 0, gp.aux_bytes, stream) != cudaSuccess) {
         cudaGetLastError();
         gp.aux = nullptr;
         return fail(HP_ERR_OOM, "cudaMalloc of %zu bytes of kernel state failed", gp.aux_bytes);
@@ -1434,9 +1437,9 @@ hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, cons
   if (!p->d_err) {
     int e = cudaMalloc(&p->d_err, 16);
     if (e) return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
-    cudaMemset(p->d_err, 0, 16);
+    cudaMemsetAsync(p->d_err, 0, 16, (cudaStream_t)stream);  // on the caller's stream: no device-wide wait
   }
-  if ((s = ensure_scratch(p, *plan))) return s;
+  if ((s = ensure_scratch(p, *plan, (cudaStream_t)stream))) return s;
   if (!p->use_graph) return run_groups(p, *plan, inputs, output, stream);
   return run_graph(p, *plan, inputs, n_inputs, output, stream);
 }
