@@ -94,7 +94,8 @@ def config_table():
     cfgs["harris"] = dict(workload=f"harris_rgb_{W}x{H}_f32", h=H, w=W,
                           inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_F32)], out=(1, H, W, hp.HP_F32),
                           build=lambda: pipelines.harris(),
-                          fused=lambda p: pipelines.fused_schedule(p, tile_w=120, tile_h=14, threads=256),
+                          fused=app_schedule("harris", W, H, dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120,
+                                                                  tile_h=14, threads=256))[0],
                           flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris_rows", dtype="f32",
                           oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
     UH, UW = 3072, 4096
@@ -113,7 +114,8 @@ def config_table():
     cfgs["unsharp"] = dict(workload=f"unsharp_rgb_{UW}x{UH}_f32", h=UH, w=UW,
                            inputs=lambda seed: [(synth.rgb_f32(UH, UW, seed=seed), hp.HP_F32)],
                            out=(3, UH, UW, hp.HP_F32), build=lambda: pipelines.unsharp(),
-                           fused=lambda p: pipelines.fused_schedule(p, tile_w=120, tile_h=96, threads=256),
+                           fused=app_schedule("unsharp", UW, UH, dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
+                                                                      tile_w=120, tile_h=16, threads=128))[0],
                            flops_px=63, bytes_px=24, bound="hbm", kernel="k_stencil_rows", dtype="f32",
                            oracle_sample=unsharp_sample, parity=unsharp_parity, sample_rows=96)
 
@@ -130,7 +132,7 @@ def config_table():
     cfgs["histeq"] = dict(workload=f"histeq_u8_{UW}x{UH}", h=UH, w=UW,
                           inputs=lambda seed: [(synth.gray_u8_lowcontrast(UH, UW, seed=seed), hp.HP_U8)],
                           out=(1, UH, UW, hp.HP_U8), build=lambda: pipelines.histeq(),
-                          fused=lambda p: pipelines.fused_schedule(p),
+                          fused=app_schedule("histeq", UW, UH, dict(schedule="fused"))[0],
                           flops_px=0, bytes_px=2, bound="hbm", kernel="k_histeq", dtype="u8",
                           oracle_sample=histeq_sample, parity=histeq_parity, sample_rows=256)
 
@@ -157,14 +159,33 @@ def config_table():
     return cfgs
 
 
-def tuned(name):
-    """Schedule parameters chosen by the autotuner (schedules.json), else defaults."""
+def tuned(name, default=None):
+    """Schedule parameters chosen by the autotuner (schedules.json), else the default."""
     path = os.path.join(ROOT, "paper_2012_07145_gb300", "schedules.json")
     if name and os.path.exists(path):
         db = json.load(open(path))
         if name in db:
             return db[name]["params"]
-    return dict(depth=8, tile_w=64, tile_h=32, threads=256, serial_y=8)
+    return default if default is not None else dict(depth=8, tile_w=64, tile_h=32, threads=256, serial_y=8)
+
+
+def app_schedule(app, w, h, default):
+    """A function applying the tuned schedule of an application at w x h
+    (schedules.json, written by tuner.py), else the given default entry."""
+    from paper_2012_07145_gb300 import tuner
+    entry = tuned(f"{app}_{w}x{h}", default)
+    return (lambda p: tuner.apply_schedule(p, entry)), entry
+
+
+def schedule_of(cfg_name, cfg):
+    """The schedule a bench line ran, for its config record."""
+    if cfg_name in ("chain32", "chain32_f16", "chain32_bf16"):
+        return dict(tuned("chain32"), source="schedules.json chain32 (tuner.py)")
+    app = cfg["workload"].split("_")[0]
+    key = f"{app}_{cfg['w']}x{cfg['h']}"
+    if app in ("harris", "unsharp", "histeq"):
+        return dict(tuned(key, {}), source=f"schedules.json {key} (tuner.py)")
+    return "fused (see pipelines.py)"
 
 
 # ------------------------------------------------------------------ helpers --
@@ -429,7 +450,7 @@ def run_ours(args, cfg_name):
         "dtype": cfg["dtype"],
         "data": "synthetic (seeded images with the workload's shape and value distribution; no dataset)",
         "config": {"workload": cfg["workload"],
-                   "schedule": tuned(cfg_name) if cfg_name == "chain32" else "fused (see pipelines.py)",
+                   "schedule": schedule_of(cfg_name, cfg),
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
                    "launch": "CUDA graph replay"},
         "plain": {"value": round(npx / (plain_ms * 1e-3) / 1e6, 2), "unit": "MPix/s", "ms_per_step": round(plain_ms, 5),
@@ -511,18 +532,19 @@ def run_serving(args):
     from paper_2012_07145_gb300 import hp, pipelines, synth
     import __graft_entry__
     __graft_entry__.build()
-    un = pipelines.unsharp()
-    pipelines.fused_schedule(un, tile_w=120, tile_h=32, threads=256)
-    hr = pipelines.harris()
-    pipelines.fused_schedule(hr, tile_w=120, tile_h=32, threads=256)
-    he = pipelines.histeq()
-    pipelines.fused_schedule(he)
-    kinds = [("unsharp", un, 3, hp.HP_F32, 3, torch.float32), ("harris", hr, 3, hp.HP_F32, 1, torch.float32),
-             ("histeq", he, 1, hp.HP_U8, 1, torch.uint8)]
+    # one pipeline per kind and size, each with the autotuned schedule of that size
+    defaults = {"unsharp": dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=16, threads=128),
+                "harris": dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=14, threads=128),
+                "histeq": dict(schedule="fused")}
+    kinds = [("unsharp", pipelines.unsharp, 3, hp.HP_F32, 3, torch.float32),
+             ("harris", pipelines.harris, 3, hp.HP_F32, 1, torch.float32),
+             ("histeq", pipelines.histeq, 1, hp.HP_U8, 1, torch.uint8)]
     ring = 3
     bufs = {}
-    for name, p, ic, idt, oc, tdt in kinds:
+    for name, build, ic, idt, oc, tdt in kinds:
         for (h, w) in SERVING_SIZES:
+            p = build()
+            app_schedule(name, w, h, defaults[name])[0](p)
             arr = synth.rgb_f32(h, w, seed=7) if idt == hp.HP_F32 else synth.gray_u8_lowcontrast(h, w, seed=7)
             hin = torch.from_numpy(arr).pin_memory()
             outs = [torch.empty((oc, h, w), dtype=tdt).pin_memory() for _ in range(ring)]
@@ -535,14 +557,14 @@ def run_serving(args):
         picks = [(kinds[rng.integers(3)][0],) + SERVING_SIZES[rng.integers(len(SERVING_SIZES))] for _ in range(n)]
         gaps = rng.exponential(1.0 / lam, n)
         srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
-        # warm the slots' pipeline copies (scratch, kernel attributes) outside the measured stream
-        warm = [srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][0]) for k in bufs for _ in range(2)]
+        # make the slots' pipeline copies resident for every kind and size
+        # (lowering, scratch, kernel state), then one request per slot and key
+        # (kernel attributes are set on a kernel's first launch)
+        for k in bufs:
+            srv.prepare(bufs[k][0], [bufs[k][1]])
+        warm = [srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][j % ring]) for k in bufs for j in range(8)]
         for t in warm:
             srv.wait(t, 120000)
-        srv.close()
-        srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
-        for k in bufs:
-            srv.wait(srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][0]), 120000)
         base = srv.stats()
         t0 = time.perf_counter()
         due = t0
@@ -578,6 +600,7 @@ def run_serving(args):
             "dtype": "mixed (f32 RGB, u8)", "data": "synthetic",
             "config": {"workload": "serving_mix_unsharp_harris_histeq_poisson",
                        "sizes": ["%dx%d" % (w, h) for h, w in SERVING_SIZES], "slots": 8, "max_batch": 8,
+                       "schedules": "per kind and size from schedules.json (tuner.py)",
                        "hbm_budget_bytes": 8 << 30,
                        "latency": "host submit to completion observed by the server (includes host copies)"},
             "serving": per_rate}

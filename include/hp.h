@@ -209,6 +209,11 @@ hp_status hp_schedule_set(hp_pipeline* p, const hp_schedule* s);
 hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
                      const hp_buffer* output, void* stream);
 
+/* Lowers p for inputs of the given sizes and allocates its buffers and kernel
+ * state (on `stream`), without running anything: the first hp_realize for
+ * those sizes then starts at once.  Optional; hp_realize does the same on
+ * first use. */
+hp_status hp_prepare(hp_pipeline* p, const int* widths, const int* heights, int n_inputs, void* stream);
 /* Same as hp_realize with HOST buffers: copies the inputs to device staging
  * owned by the pipeline, runs, copies the output back and synchronises the
  * stream before returning.  Pinned host memory gives asynchronous copies. */
@@ -273,6 +278,11 @@ hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs
  * by then (it stays queued or running), else the request's status. */
 hp_status hp_server_wait(hp_server* s, unsigned long long ticket, int timeout_ms, double* latency_us);
 hp_status hp_server_stats_get(hp_server* s, hp_server_stats* stats);
+/* Makes every slot's copy of pipeline p ready for requests whose inputs have
+ * the sizes of `inputs` (only width, height, dtype and channels are read):
+ * lowering, scratch and kernel state, so the first such request does no
+ * allocation or lowering on the worker thread.  Call before traffic. */
+hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs);
 /* Finishes queued and running requests, then frees the server. */
 hp_status hp_server_destroy(hp_server* s);
 

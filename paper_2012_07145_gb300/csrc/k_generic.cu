@@ -37,8 +37,11 @@ __device__ __forceinline__ float fetch(const Ctx& k, int ref, int c, int x, int 
   y = iclamp(y, 0, p.dom_h - 1);
   const Rect r = k.rects[ref];
   const int ly = y - r.y0, lx = x - r.x0;
-  if ((unsigned)ly >= (unsigned)p.rows || (unsigned)lx >= (unsigned)p.pitch || (unsigned)c >= (unsigned)p.channels) {
-    // bounds inference guarantees this never happens; record it instead of reading outside the tile
+  // bounds inference guarantees the read lies in the rectangle this tile
+  // computed for the producer (not only in its allocation, which is the
+  // largest rectangle over all tiles); record a miss instead of reading
+  if ((unsigned)ly >= (unsigned)(r.y1 - r.y0) || (unsigned)lx >= (unsigned)(r.x1 - r.x0) ||
+      (unsigned)c >= (unsigned)p.channels) {
     atomicExch(k.g->err, 2);
     return 0.0f;
   }

@@ -1425,6 +1425,27 @@ static hp_status collect_in_dom(hp_pipeline* p, const hp_buffer* inputs, int n_i
   return HP_OK;
 }
 
+hp_status hp_prepare(hp_pipeline* p, const int* widths, const int* heights, int n_inputs, void* stream) {
+  if (!p || !widths || !heights || n_inputs != (int)p->in_dtypes.size())
+    return fail(HP_ERR_INVALID_ARG, "hp_prepare: expected %d input sizes", p ? (int)p->in_dtypes.size() : 0);
+  std::vector<Dom> in_dom;
+  for (int i = 0; i < n_inputs; ++i) {
+    if (widths[i] < 1 || heights[i] < 1) return fail(HP_ERR_INVALID_ARG, "hp_prepare: empty input %d", i);
+    in_dom.push_back(Dom{widths[i], heights[i]});
+  }
+  Plan* plan = nullptr;
+  hp_status s = get_plan(p, in_dom, &plan);
+  if (s) return s;
+  if (!p->d_err) {
+    if (cudaMalloc(&p->d_err, 16) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
+    }
+    cudaMemsetAsync(p->d_err, 0, 16, (cudaStream_t)stream);
+  }
+  return ensure_scratch(p, *plan, (cudaStream_t)stream);
+}
+
 hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output, void* stream) {
   std::vector<Dom> in_dom;
   hp_status s = collect_in_dom(p, inputs, n_inputs, in_dom);

@@ -397,6 +397,24 @@ hp_status hp_server_stats_get(hp_server* s, hp_server_stats* st) {
   return HP_OK;
 }
 
+hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs) {
+  if (!s || !p || !inputs || n_inputs < 1 || n_inputs > 16)
+    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: bad arguments");
+  std::vector<int> ws(n_inputs), hs(n_inputs);
+  for (int i = 0; i < n_inputs; ++i) {
+    ws[i] = inputs[i].width;
+    hs[i] = inputs[i].height;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);  // the worker touches slot copies only under the lock
+  for (Slot& sl : s->slots) {
+    hp_pipeline* c = slot_clone(sl, p, 1);
+    if (!c) return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: pipeline cannot be copied");
+    hp_status st = hp_prepare(c, ws.data(), hs.data(), n_inputs, sl.stream);
+    if (st) return st;
+  }
+  return HP_OK;
+}
+
 hp_status hp_server_destroy(hp_server* s) {
   if (!s) return hp::report_error(HP_ERR_INVALID_ARG, "null server");
   {

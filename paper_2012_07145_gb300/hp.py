@@ -69,7 +69,8 @@ class ServerStats(ctypes.Structure):
 EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_set", "hp_realize",
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
-           "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy"]
+           "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy",
+           "hp_prepare", "hp_server_prepare"]
 
 _lib = None
 
@@ -102,6 +103,8 @@ def lib():
         L.hp_server_wait.argtypes = [P, ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.hp_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
         L.hp_server_destroy.argtypes = [P]
+        L.hp_prepare.argtypes = [P, _IP, _IP, ctypes.c_int, P]
+        L.hp_server_prepare.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
         for name in EXPORTS:
@@ -144,7 +147,9 @@ def buffer_from_tensor(t, dtype: int) -> Buffer:
         rs, ps = t.stride(1), t.stride(0)
     es = t.element_size()
     assert t.stride(-1) == 1, "x must be the unit-stride dimension"
-    return Buffer(t.data_ptr(), dtype, c, w, h, rs * es, ps * es)
+    b = Buffer(t.data_ptr(), dtype, c, w, h, rs * es, ps * es)
+    b._tensor = t  # the descriptor keeps its memory alive (it holds only the address)
+    return b
 
 
 def padded_empty(c: int, h: int, w: int, torch_dtype, device="cuda"):
@@ -220,6 +225,11 @@ class Pipeline:
         arr = (Buffer * len(inputs))(*inputs)
         check(lib().hp_realize(self.h, arr, len(inputs), ctypes.byref(output), ctypes.c_void_p(stream or 0)))
 
+    def prepare(self, sizes, stream=None):
+        """Lowers and allocates for inputs of the given (w, h) sizes without running."""
+        check(lib().hp_prepare(self.h, _ints([s[0] for s in sizes]), _ints([s[1] for s in sizes]), len(sizes),
+                               ctypes.c_void_p(stream or 0)))
+
     def realize_host(self, inputs, output, stream=None):
         arr = (Buffer * len(inputs))(*inputs)
         check(lib().hp_realize_host(self.h, arr, len(inputs), ctypes.byref(output), ctypes.c_void_p(stream or 0)))
@@ -271,6 +281,11 @@ class Server:
         t = ctypes.c_ulonglong()
         check(lib().hp_server_submit(self.h, pipeline.h, arr, len(inputs), ctypes.byref(output), ctypes.byref(t)))
         return t.value
+
+    def prepare(self, pipeline: "Pipeline", inputs):
+        """Makes every slot's copy of the pipeline ready for inputs shaped like these."""
+        arr = (Buffer * len(inputs))(*inputs)
+        check(lib().hp_server_prepare(self.h, pipeline.h, arr, len(inputs)))
 
     def wait(self, ticket: int, timeout_ms: int = 60000):
         """(status, latency_us); status HP_ERR_TIMEOUT if not done in time."""

@@ -17,6 +17,14 @@ and thread counts that leave most threads idle.  Every timed candidate's
 output is compared bit for bit with the stage-per-kernel result, so tuning
 also checks schedule invariance.  Results go to schedules.json, keyed by
 workload.
+
+For the application pipelines (Harris, unsharp mask, histogram equalize) the
+space is the grouping -- every stage its own kernel, or the whole pipeline in
+one group -- crossed with the kernels that can run the one group: the tiled
+kernel over its tile shapes, threads and serial rows, the streaming kernel
+over run lengths and threads, and the generic interpreter.  Those results
+are keyed by application and image size ("harris_2560x1536"), since the best
+run length and tile depend on how many tiles or runs the image has per SM.
 """
 
 import argparse
@@ -117,6 +125,91 @@ def tune_chain(name, n_stages=32, pattern="alternate", W=2560, H=1536, quick=Fal
                 top5=[dict(ms=m, **c) for m, c in results[:5]], device=torch.cuda.get_device_name())
 
 
+# ------------------------------------------------------------ applications --
+def apply_schedule(p, entry):
+    """Applies a schedule entry of schedules.json (an application's) to p."""
+    from . import pipelines
+    kind = entry["schedule"]
+    if kind == "root":
+        pipelines.root_schedule(p)
+    elif kind == "fused":
+        pipelines.fused_schedule(p, tile_w=entry.get("tile_w", 32), tile_h=entry.get("tile_h", 32),
+                                 threads=entry.get("threads", 256), impl=entry.get("impl"))
+        if entry.get("serial_y"):
+            n = len(p.stages)
+            p.schedule([0] * n, tile_w=[entry["tile_w"]], tile_h=[entry["tile_h"]], threads=[entry["threads"]],
+                       serial_y=[entry["serial_y"]], impl=[entry["impl"]] if entry.get("impl") is not None else None)
+    else:
+        raise ValueError(f"unknown schedule kind {kind}")
+
+
+def app_candidates(app):
+    from . import hp
+    out = [dict(schedule="root")]
+    if app == "histeq":
+        return out + [dict(schedule="fused")]
+    out.append(dict(schedule="fused", impl=hp.HP_IMPL_GENERIC, tile_w=32, tile_h=32, threads=256))
+    tiled_w = (32, 64, 96) if app == "harris" else (64, 128)
+    for tw, th, t, sy in itertools.product(tiled_w, (16, 32, 64), (128, 256), (4, 8)):
+        out.append(dict(schedule="fused", impl=hp.HP_IMPL_AUTO, tile_w=tw, tile_h=th, threads=t, serial_y=sy))
+    runs = (8, 11, 14, 17, 20, 26, 32) if app == "harris" else (16, 32, 48, 64, 96, 128, 192)
+    for th, t in itertools.product(runs, (128, 256)):
+        out.append(dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=th, threads=t))
+    return out
+
+
+def app_io(app, H, W):
+    """Seeded input and output buffers of an application at H x W."""
+    import torch
+    from . import hp, pipelines, synth
+    if app == "harris":
+        p, img, idt, oc, odt, tdt = pipelines.harris(), synth.rgb_f32(H, W, seed=0), hp.HP_F32, 1, hp.HP_F32, torch.float32
+    elif app == "unsharp":
+        p, img, idt, oc, odt, tdt = pipelines.unsharp(), synth.rgb_f32(H, W, seed=0), hp.HP_F32, 3, hp.HP_F32, torch.float32
+    elif app == "histeq":
+        p, img, idt, oc, odt, tdt = (pipelines.histeq(), synth.gray_u8_lowcontrast(H, W, seed=0), hp.HP_U8, 1, hp.HP_U8,
+                                     torch.uint8)
+    else:
+        raise ValueError(app)
+    x = hp.padded_copy(torch.from_numpy(img), "cuda")
+    ref = hp.padded_empty(oc, H, W, tdt, "cuda")
+    y = hp.padded_empty(oc, H, W, tdt, "cuda")
+    return p, [hp.buffer_from_tensor(x, idt)], ref, y, odt   # the buffer keeps x alive
+
+
+def tune_app(app, W, H, log=print):
+    import torch
+    from . import hp
+    p, bi, ref, y, odt = app_io(app, H, W)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    p.use_cuda_graph(True)
+    p.realize(bi, hp.buffer_from_tensor(ref, odt), stream.cuda_stream)   # the default (stage-per-kernel) result
+    torch.cuda.synchronize()
+    as_bits = (lambda t: t.view(torch.int32)) if ref.dtype == torch.float32 else (lambda t: t)
+    results = []
+    plain_ms = None
+    for c in app_candidates(app):
+        try:
+            apply_schedule(p, c)
+            ms = time_candidate(p, bi, hp.buffer_from_tensor(y, odt), stream, flush)
+        except hp.HPError as e:
+            log(f"skip {c}: {e}")
+            continue
+        if not torch.equal(as_bits(y), as_bits(ref)):
+            raise RuntimeError(f"schedule {c} changed the result: schedules must be bit-identical")
+        if p.device_error():
+            raise RuntimeError(f"schedule {c} reported a device error")
+        if c["schedule"] == "root":
+            plain_ms = ms
+        results.append((ms, c))
+        log(f"{ms:.4f} ms {c}")
+    results.sort(key=lambda r: r[0])
+    best = results[0]
+    return dict(params=best[1], ms=best[0], plain_ms=plain_ms, candidates=len(results),
+                top5=[dict(ms=m, **c) for m, c in results[:5]], device=torch.cuda.get_device_name())
+
+
 def save(name, entry):
     db = json.load(open(DB_PATH)) if os.path.exists(DB_PATH) else {}
     db[name] = entry
@@ -129,20 +222,27 @@ def main():
     ap.add_argument("--config", default="chain32")
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--out", default=None, help="also write the entry to this JSON file")
+    ap.add_argument("--sizes", default="2560x1536", help="applications: comma-separated WxH image sizes")
     args = ap.parse_args()
     sys.path.insert(0, os.path.dirname(PKG))
     import __graft_entry__
     __graft_entry__.build()
+    entries = {}
     if args.config == "chain32":
-        e = tune_chain("chain32", 32, "alternate", 2560, 1536, args.quick)
+        entries["chain32"] = tune_chain("chain32", 32, "alternate", 2560, 1536, args.quick)
     elif args.config == "chain4":
-        e = tune_chain("chain4", 4, "binomial", 512, 512, args.quick)
+        entries["chain4"] = tune_chain("chain4", 4, "binomial", 512, 512, args.quick)
+    elif args.config in ("harris", "unsharp", "histeq"):
+        sizes = [(int(a), int(b)) for a, b in (s.split("x") for s in args.sizes.split(","))]
+        for W, H in sizes:
+            entries[f"{args.config}_{W}x{H}"] = tune_app(args.config, W, H)
     else:
         raise SystemExit(f"unknown config {args.config}")
-    save(args.config, e)
+    for k, e in entries.items():
+        save(k, e)
     if args.out:
-        json.dump({args.config: e}, open(args.out, "w"), indent=1)
-    print(json.dumps({args.config: e}))
+        json.dump(entries, open(args.out, "w"), indent=1)
+    print(json.dumps(entries))
 
 
 if __name__ == "__main__":

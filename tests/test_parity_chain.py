@@ -151,3 +151,17 @@ def test_streaming_kernel_full_size_against_oracle():
     pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=0, impl=hp.HP_IMPL_WAVE)
     fused = chain_run(p, img)
     assert torch.equal(bits(fused), bits(plain))
+
+
+def test_prepare_then_realize():
+    """hp_prepare lowers and allocates ahead; the realize that follows launches
+    the same kernels with the same result."""
+    img = synth.stencil_input(130, 90, seed=11)
+    p = pipelines.stencil_chain(8, "alternate")
+    ref = chain_run(p, img)
+    q = pipelines.stencil_chain(8, "alternate")
+    q.prepare([(90, 130)], torch.cuda.current_stream().cuda_stream)
+    n0 = hp.launch_count()
+    y = chain_run(q, img)
+    assert hp.launch_count() - n0 == 8
+    assert torch.equal(bits(y), bits(ref))
