@@ -54,7 +54,10 @@ def chain_candidates(n_stages, W, H, quick=False):
     depths = [d for d in (1, 2, 4, 8, 16, 32) if n_stages % d == 0]
     tws = (32, 64, 128) if not quick else (64, 128)
     ths = (16, 32, 64, 128) if not quick else (32, 64)
-    threads = (128, 256, 512) if not quick else (256,)
+    # thread counts that are not powers of two too: a stage's work items
+    # (4-column blocks x row segments) rarely divide 256, and the threads left
+    # over wait at the stage barrier
+    threads = (96, 128, 160, 192, 224, 256, 320, 384, 512) if not quick else (192, 256)
     serials = (4, 8, 16) if not quick else (8, 16)
     out = []
     for d, tw, th, t, s in itertools.product(depths, tws, ths, threads, serials):
