@@ -135,19 +135,24 @@ def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, al
     return p, ids
 
 
-def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None):
+def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None,
+                                   down_tile: int = 0):
     """Per-level fusion: level 1 of the remapped pyramid from the input in one
     kernel (gray and remap inlined); one downsample kernel per coarser level;
     one kernel per level for Laplacian + interpolation + collapse step; the
-    finest level fused with the colour reconstruction."""
+    finest level fused with the colour reconstruction.  down_tile = 0 lets the
+    downsample kernels size their tiles per level (smaller tiles on the coarse
+    levels, so that they still spread over the SMs)."""
     J = len(ids["G"])
     n = len(p.stages)
     groups = [None] * n
     gid = 0
     groups[ids["gray"]] = hp.HP_INLINE
     groups[ids["G"][0]] = hp.HP_INLINE
+    down_groups = []
     for l in range(1, J):
         groups[ids["G"][l]] = gid
+        down_groups.append(gid)
         gid += 1
     groups[ids["R"][J - 1]] = hp.HP_INLINE
     for l in range(J - 2, -1, -1):
@@ -157,5 +162,7 @@ def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, th
             groups[ids["out"]] = gid
         gid += 1
     assert all(g is not None for g in groups)
-    p.schedule(groups, tile_w=[tile] * gid, tile_h=[tile] * gid, threads=[threads] * gid,
+    generic = impl == hp.HP_IMPL_GENERIC
+    tiles = [down_tile if (g in down_groups and not generic) else tile for g in range(gid)]
+    p.schedule(groups, tile_w=tiles, tile_h=tiles, threads=[threads] * gid,
                impl=[impl] * gid if impl is not None else None)
