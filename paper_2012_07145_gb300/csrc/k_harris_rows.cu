@@ -201,6 +201,7 @@ struct StripRun {
   const int lane, stride, c0, esize;
   const Weights<SPEC> w;
   Edges e;
+  const bool vedge;          // the run reads rows outside the image
   bool st_full, st_part;     // the lane stores four columns / some of its columns
   char* out_row;             // the next output row
   float hA[3][4], hB[3][4];  // x passes of gray with the Ix and Iy x-weights
@@ -212,7 +213,8 @@ struct StripRun {
   __device__ __forceinline__ StripRun(const RowsParams& kp_, const StripGeom& g_, Ring& R_, const Unit& U_, int lane_,
                                       int stride_)
       : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + 4 * lane_),
-        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), w(kp_.a.w), q(R_.released), rr(0), slot(nullptr) {
+        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), w(kp_.a.w), vedge(U_.oy < 2 || U_.oy + U_.n_in - 2 > kp_.a.in.h),
+        q(R_.released), rr(0), slot(nullptr) {
     const int W = kp.a.in.w;
     e.left = c0 == 0;
 #pragma unroll
@@ -356,7 +358,7 @@ struct StripRun {
   template <int M>
   __device__ __forceinline__ bool step(int t) {
     const int r = U.oy - 2 + t;
-    const bool edge = r < 2 || r >= kp.a.in.h;  // a window row outside the image may need a copy
+    const bool edge = vedge && (r < 2 || r >= kp.a.in.h);  // a window row outside the image may need a copy
     if (!row_in<M>(r, edge)) return false;
     if (t >= 2) row_grad<M>(r, edge);
     if (t >= 4) row_out<M>();

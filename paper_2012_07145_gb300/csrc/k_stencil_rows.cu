@@ -144,7 +144,7 @@ __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (
 // run.  Windows are indexed by row mod 5, so a loop unrolled five times keeps
 // them in fixed registers.  F32 = every storage type is f32 (no rounding, one
 // 128-bit store per lane and row).
-template <bool F32>
+template <bool F32, bool EPI>
 struct StripRun {
   const SRowsParams& kp;
   const StripGeom& g;
@@ -152,6 +152,7 @@ struct StripRun {
   const Unit U;
   const int lane, stride, c0, esize;
   const bool hb;             // the strip touches the left or right image edge
+  const bool vedge;          // the run reads rows outside the image
   float wx[5], wy[5];
   float hx[5][4];            // x-pass results
   float raw[5][4];           // input values (for the unsharp combine)
@@ -164,7 +165,8 @@ struct StripRun {
   __device__ __forceinline__ StripRun(const SRowsParams& kp_, const StripGeom& g_, Ring& R_, const Unit& U_,
                                       int lane_, int stride_)
       : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + 4 * lane_),
-        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), hb(U_.x0 < 0 || U_.x0 + 128 > kp_.a.in.w), q(R_.released),
+        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), hb(U_.x0 < 0 || U_.x0 + 128 > kp_.a.in.w),
+        vedge(U_.oy < 2 || U_.oy + U_.n_in - 2 > kp_.a.in.h), q(R_.released),
         rr(0), slot(nullptr) {
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -200,7 +202,7 @@ struct StripRun {
     const int r = U.oy - 2 + t;
     if (rr == 0 && !wait_box()) return false;
     float v[4];
-    load4(slot + rr * 128 * esize, a.in.dtype, v);
+    load4(slot + rr * 128 * esize, F32 ? HP_F32 : a.in.dtype, v);
     if (++rr == kBoxRows) {
       rr = 0;
       release_box();
@@ -215,7 +217,7 @@ struct StripRun {
     hx[M][1] = tap5(wx, l1, v[0], v[1], v[2], v[3]);
     hx[M][2] = tap5(wx, v[0], v[1], v[2], v[3], r1);
     hx[M][3] = tap5(wx, v[1], v[2], v[3], r1, r2);
-    if (r < 1 || r >= a.in.h) {
+    if (vedge && (r < 1 || r >= a.in.h)) {
       if (r == 0) {  // rows -2 and -1 are row 0
 #pragma unroll
         for (int k = 0; k < 4; ++k) { hx[(M + 3) % 5][k] = hx[M][k]; hx[(M + 4) % 5][k] = hx[M][k]; }
@@ -233,7 +235,7 @@ struct StripRun {
       for (int k = 0; k < 4; ++k) {
         float b = tap5(wy, hx[J0][k], hx[J1][k], hx[J2][k], hx[J3][k], hx[M][k]);
         if (!F32) b = round_storage(a.storage[0], b);
-        if (a.epilogue == 1) {
+        if (EPI) {
           b = op_unsharp(raw[J2][k], b, a.amount);
           if (!F32) b = round_storage(a.out.dtype, b);
         }
@@ -276,7 +278,7 @@ struct StripRun {
   }
 };
 
-template <bool F32>
+template <bool F32, bool EPI>
 __global__ void __launch_bounds__(256, 3) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(256, 3) k_stencil_rows(const __grid_constant__
   R.IU = unit_geom(kp, g, gw);
   for (int i = 0; i < kRing; ++i) issue_one(kp, g, R, stride, lane);
   for (int u = gw; u < kp.units; u += stride) {
-    StripRun<F32> run(kp, g, R, unit_geom(kp, g, u), lane, stride);
+    StripRun<F32, EPI> run(kp, g, R, unit_geom(kp, g, u), lane, stride);
     if (!run.run()) {
       // a box never arrived: report, wait (bounded) for the copies still in
       // flight into this warp's slots, and stop
@@ -318,8 +320,10 @@ typedef void (*SRowsKernel)(SRowsParams);
 
 SRowsKernel pick_kernel(const ChainArgs& a, int* variant) {
   const bool f32 = a.in.dtype == HP_F32 && a.storage[0] == HP_F32 && a.out.dtype == HP_F32;
-  *variant = f32 ? 0 : 1;
-  return f32 ? k_stencil_rows<true> : k_stencil_rows<false>;
+  const bool epi = a.epilogue == 1;
+  *variant = (f32 ? 0 : 1) + (epi ? 2 : 0);
+  if (epi) return f32 ? k_stencil_rows<true, true> : k_stencil_rows<false, true>;
+  return f32 ? k_stencil_rows<true, false> : k_stencil_rows<false, false>;
 }
 
 }  // namespace
@@ -352,7 +356,7 @@ int stencil_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes
 int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream) {
   int variant;
   SRowsKernel kern = pick_kernel(a, &variant);
-  static bool configured[2] = {false, false};
+  static bool configured[4] = {false, false, false, false};
   if (!configured[variant]) {
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
