@@ -98,6 +98,22 @@ def config_table():
                                                                   tile_h=14, threads=256))[0],
                           flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris_rows", dtype="f32",
                           oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
+    def harris_bf16_parity(out, inputs):
+        import torch
+        from oracle import harris as ohr
+        # the oracle on the bf16-rounded input (the storage error of the stages is what is stated)
+        rgb = torch.from_numpy(inputs[0][0][:, :64, :64]).to(torch.bfloat16).double().numpy()
+        ref = ohr.harris(rgb)[:62, :62]
+        return float(np.abs(out[0][:62, :62] - ref).max() / (ref.max() - ref.min()))
+
+    cfgs["harris_bf16"] = dict(workload=f"harris_rgb_{W}x{H}_bf16", h=H, w=W,
+                               inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_BF16)],
+                               out=(1, H, W, hp.HP_BF16),
+                               build=lambda: pipelines.harris(io_storage=hp.HP_BF16, inner_storage=hp.HP_BF16),
+                               fused=app_schedule("harris_bf16", W, H, dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
+                                                                           tile_w=112, tile_h=14, threads=128))[0],
+                               flops_px=68, bytes_px=8, bound="hbm", kernel="k_harris_rows", dtype="bf16",
+                               oracle_sample=harris_sample, parity=harris_bf16_parity, sample_rows=128)
     UH, UW = 3072, 4096
 
     def unsharp_sample(rows):
@@ -182,8 +198,10 @@ def schedule_of(cfg_name, cfg):
     if cfg_name in ("chain32", "chain32_f16", "chain32_bf16"):
         return dict(tuned("chain32"), source="schedules.json chain32 (tuner.py)")
     app = cfg["workload"].split("_")[0]
+    if cfg["workload"].endswith("_bf16") and app == "harris":
+        app = "harris_bf16"
     key = f"{app}_{cfg['w']}x{cfg['h']}"
-    if app in ("harris", "unsharp", "histeq"):
+    if app in ("harris", "harris_bf16", "unsharp", "histeq"):
         return dict(tuned(key, {}), source=f"schedules.json {key} (tuner.py)")
     return "fused (see pipelines.py)"
 

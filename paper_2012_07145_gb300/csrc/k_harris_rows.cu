@@ -162,9 +162,13 @@ __device__ __forceinline__ void xpass3(const Weights<SPEC>& w, int q, const floa
   for (int k = 0; k < 4; ++k) h[k] = tapw(w, q, 0, l[k], v[k], r[k]);
 }
 
+// A stage value rounded to its storage: RND 0 = every stage f32 (nothing to
+// do), 2 = every stage bf16 (known at compile time), 3 = per stage.
 template <int RND>
 __device__ __forceinline__ float rs(float v, int dtype) {
-  return RND == 0 ? v : round_storage(dtype, v);
+  if (RND == 0) return v;
+  if (RND == 2) return __bfloat162float(__float2bfloat16_rn(v));
+  return round_storage(dtype, v);
 }
 
 __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (&v)[4]) {
@@ -449,6 +453,12 @@ RowsKernel pick_kernel(const HarrisArgs& a, int* variant) {
     *variant = spec ? 2 : 3;
     return spec ? k_harris_rows<0, 2, true> : k_harris_rows<0, 2, false>;
   }
+  bool inner_bf16 = true;
+  for (int i = 0; i < 9; ++i) inner_bf16 &= a.st[i] == HP_BF16;
+  if (inner_bf16 && a.out.dtype == HP_BF16) {  // the bf16-storage pipeline
+    *variant = spec ? 5 : 6;
+    return spec ? k_harris_rows<2, 2, true> : k_harris_rows<2, 2, false>;
+  }
   *variant = 4;
   return k_harris_rows<3, 3, false>;
 }
@@ -481,7 +491,7 @@ int harris_rows_grid(const HarrisArgs& a, int units, int threads, int smem_bytes
 int launch_harris_rows(const HarrisArgs& a, int rows, int grid, int smem_bytes, void* stream) {
   int variant;
   RowsKernel kern = pick_kernel(a, &variant);
-  static bool configured[5] = {false, false, false, false, false};
+  static bool configured[7] = {};
   if (!configured[variant]) {
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;

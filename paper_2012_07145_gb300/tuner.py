@@ -152,12 +152,13 @@ def app_candidates(app):
     if app == "histeq":
         return out + [dict(schedule="fused")]
     out.append(dict(schedule="fused", impl=hp.HP_IMPL_GENERIC, tile_w=32, tile_h=32, threads=256))
-    tiled_w = (32, 64, 96) if app == "harris" else (64, 128)
+    tiled_w = (32, 64, 96) if app.startswith("harris") else (64, 128)
     for tw, th, t, sy in itertools.product(tiled_w, (16, 32, 64), (128, 256), (4, 8)):
         out.append(dict(schedule="fused", impl=hp.HP_IMPL_AUTO, tile_w=tw, tile_h=th, threads=t, serial_y=sy))
-    runs = (8, 11, 14, 17, 20, 26, 32) if app == "harris" else (16, 32, 48, 64, 96, 128, 192)
+    runs = (8, 11, 14, 17, 20, 26, 32) if app.startswith("harris") else (16, 32, 48, 64, 96, 128, 192)
+    strip = 112 if app.endswith("bf16") else 120      # 2-byte inputs take 112-column strips
     for th, t in itertools.product(runs, (128, 256)):
-        out.append(dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=th, threads=t))
+        out.append(dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=strip, tile_h=th, threads=t))
     return out
 
 
@@ -167,6 +168,9 @@ def app_io(app, H, W):
     from . import hp, pipelines, synth
     if app == "harris":
         p, img, idt, oc, odt, tdt = pipelines.harris(), synth.rgb_f32(H, W, seed=0), hp.HP_F32, 1, hp.HP_F32, torch.float32
+    elif app == "harris_bf16":   # bf16 input, intermediates and output; f32 arithmetic
+        p = pipelines.harris(io_storage=hp.HP_BF16, inner_storage=hp.HP_BF16)
+        img, idt, oc, odt, tdt = synth.rgb_f32(H, W, seed=0), hp.HP_BF16, 1, hp.HP_BF16, torch.bfloat16
     elif app == "unsharp":
         p, img, idt, oc, odt, tdt = pipelines.unsharp(), synth.rgb_f32(H, W, seed=0), hp.HP_F32, 3, hp.HP_F32, torch.float32
     elif app == "histeq":
@@ -174,7 +178,8 @@ def app_io(app, H, W):
                                      torch.uint8)
     else:
         raise ValueError(app)
-    x = hp.padded_copy(torch.from_numpy(img), "cuda")
+    t = torch.from_numpy(img)
+    x = hp.padded_copy(t.to(tdt) if tdt in (torch.bfloat16, torch.float16) else t, "cuda")
     ref = hp.padded_empty(oc, H, W, tdt, "cuda")
     y = hp.padded_empty(oc, H, W, tdt, "cuda")
     return p, [hp.buffer_from_tensor(x, idt)], ref, y, odt   # the buffer keeps x alive
@@ -189,7 +194,8 @@ def tune_app(app, W, H, log=print):
     p.use_cuda_graph(True)
     p.realize(bi, hp.buffer_from_tensor(ref, odt), stream.cuda_stream)   # the default (stage-per-kernel) result
     torch.cuda.synchronize()
-    as_bits = (lambda t: t.view(torch.int32)) if ref.dtype == torch.float32 else (lambda t: t)
+    as_bits = ((lambda t: t.view(torch.int32)) if ref.dtype == torch.float32 else
+               (lambda t: t.view(torch.int16)) if ref.dtype in (torch.bfloat16, torch.float16) else (lambda t: t))
     results = []
     plain_ms = None
     for c in app_candidates(app):
@@ -235,7 +241,7 @@ def main():
         entries["chain32"] = tune_chain("chain32", 32, "alternate", 2560, 1536, args.quick)
     elif args.config == "chain4":
         entries["chain4"] = tune_chain("chain4", 4, "binomial", 512, 512, args.quick)
-    elif args.config in ("harris", "unsharp", "histeq"):
+    elif args.config in ("harris", "harris_bf16", "unsharp", "histeq"):
         sizes = [(int(a), int(b)) for a, b in (s.split("x") for s in args.sizes.split(","))]
         for W, H in sizes:
             entries[f"{args.config}_{W}x{H}"] = tune_app(args.config, W, H)
