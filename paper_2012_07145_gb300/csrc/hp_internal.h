@@ -234,6 +234,10 @@ int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, 
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
 int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);
+int ll_remap_rows_strip_w();
+int ll_remap_rows_ok(const LLDownArgs& a, int in_dtype);
+int ll_remap_rows_grid(int in_dtype, int units, int threads);
+int launch_ll_remap_rows(const LLDownArgs& a, int rows, int threads, int grid, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

@@ -852,7 +852,8 @@ hp_status build_harris_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& g
   return HP_OK;
 }
 
-hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+// Arguments shared by the tiled and the streaming downsample kernels.
+void down_common_args(const hp_pipeline* p, GroupPlan& gp) {
   int remap = 0, gray = -1, rm = -1;
   match_down(p, gp.members, &remap, &gray, &rm);
   LLDownArgs& a = gp.lldown;
@@ -875,6 +876,11 @@ hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   } else {
     gp.ext_refs.assign(1, d.inputs[0]);
   }
+}
+
+hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  down_common_args(p, gp);
+  LLDownArgs& a = gp.lldown;
   a.tile_w = gp.tile_w;
   a.tile_h = gp.tile_h;
   if (a.tile_w < 1 || a.tile_h < 1 || a.tile_w > 64 || a.tile_h > 64 || (a.tile_w & (a.tile_w - 1)))
@@ -890,6 +896,33 @@ hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
                 a.tile_w, a.tile_h, gp.smem);
   gp.grid_x = a.tiles_x;
   gp.grid_y = a.tiles_y;
+  return HP_OK;
+}
+
+// Streaming first level of the remap pyramid: strips of 30 coarse columns,
+// tile_h coarse rows per run (0: about one run per resident warp).
+hp_status build_ll_remap_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  down_common_args(p, gp);
+  LLDownArgs& a = gp.lldown;
+  const int in_dt = stage_dtype_of_ref(p, gp.ext_refs[0]);
+  if (!ll_remap_rows_ok(a, in_dt))
+    return fail(HP_ERR_SCHEDULE, "the streaming remap downsample needs K = 8, u16 or f32 input and 0 < 2 sigma < 1/7");
+  if (gp.tile_w != ll_remap_rows_strip_w())
+    return fail(HP_ERR_SCHEDULE, "streaming remap downsample strips are %d coarse columns wide (tile_w %d)",
+                ll_remap_rows_strip_w(), gp.tile_w);
+  if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256)
+    return fail(HP_ERR_SCHEDULE, "streaming remap downsample threads per block must be a multiple of 32 in [32, 256]");
+  Dom od = plan.dom[gp.output];
+  a.tile_w = gp.tile_w;
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  if (gp.tile_h == 0)
+    gp.tile_h = default_run_rows(od.h, a.tiles_x, (long long)ll_remap_rows_grid(in_dt, 1 << 30, gp.threads) * (gp.threads / 32));
+  if (gp.tile_h < 1 || gp.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming remap downsample needs tile_h >= 1");
+  a.tile_h = gp.tile_h;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  gp.smem = 0;
+  gp.grid_x = ll_remap_rows_grid(in_dt, a.tiles_x * a.tiles_y, gp.threads);
+  gp.grid_y = 1;
   return HP_OK;
 }
 
@@ -983,6 +1016,26 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         break;
       }
       case HP_KERNEL_DOWNSAMPLE: {
+        // the first remap level: the streaming kernel at its strip width (the
+        // default) or under HP_IMPL_WAVE, where it covers the group
+        {
+          GroupPlan probe;
+          probe.members = gp.members;
+          probe.output = gp.output;
+          down_common_args(p, probe);
+          const int sw = ll_remap_rows_strip_w();
+          if (ll_remap_rows_ok(probe.lldown, stage_dtype_of_ref(p, probe.ext_refs[0]))) {
+            gp.tile_w = pick(p->tile_w, g, sw);
+            if (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw)) {
+              gp.kernel = HP_KERNEL_LL_REMAP_ROWS;
+              gp.tile_w = sw;
+              gp.tile_h = pick(p->tile_h, g, 0);
+              gp.threads = pick(p->threads, g, 256);
+              s = build_ll_remap_rows(p, plan, gp);
+              break;
+            }
+          }
+        }
         // default: 16x16 coarse tiles, halved (down to 4x4) for small levels so
         // that the grid still covers the SMs
         Dom od = plan.dom[gp.output];
@@ -1171,6 +1224,13 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
         e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_LL_REMAP_ROWS: {
+        LLDownArgs a = gp.lldown;
+        a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        e = launch_ll_remap_rows(a, a.tile_h, gp.threads, gp.grid_x, stream);
         break;
       }
       case HP_KERNEL_LL_LEVEL: {

@@ -297,3 +297,58 @@ def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha):
     assert np.array_equal(_ll_run(p, img), plain)
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
     assert np.array_equal(_ll_run(p, img), plain)
+    pipelines.local_laplacian_fused_schedule(p, ids, tile=16, down_tile=16)   # tiled first downsample
+    assert np.array_equal(_ll_run(p, img), plain)
+
+
+def _remap_down(in_dtype, st_gray, st_remap, st_out, sigma, alpha, beta, scale):
+    """gray -> K = 8 remaps + gray -> one downsample, the first level of the
+    local-Laplacian remap pyramid, as its own pipeline."""
+    p = hp.Pipeline([in_dtype], [3])
+    g = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, st_gray, op=hp.HP_OP_GRAY, params=[scale])
+    r = p.add_stage(hp.HP_POINTWISE, [g], 9, st_remap, op=hp.HP_OP_LL_REMAP, params=[sigma, alpha, beta, 8])
+    d = p.add_stage(hp.HP_DOWNSAMPLE2, [r], 9, st_out)
+    p.set_output(d)
+    return p
+
+
+def _remap_input(in_dtype, h, w, seed):
+    rng = np.random.default_rng(seed)
+    if in_dtype == hp.HP_U16:
+        return rng.integers(0, 65536, size=(3, h, w), dtype=np.uint16), 1.0 / 65535.0
+    x = rng.random((3, h, w), dtype=np.float32)
+    # grey pixels at, and a hair off, the level values and the band edges
+    lv = np.array([k / 7.0 + e for k in range(8) for e in (0.0, 0.1, -0.1, 1e-7, 0.1 + 1e-7, -0.1 - 1e-7)],
+                  dtype=np.float32)
+    n = min(lv.size, w)
+    x[:, 0, :n] = lv[:n]
+    return x, 1.0
+
+
+# The streaming first remap downsample against the tiled kernel and the
+# generic interpreter: every channel bit-identical, over run lengths, block
+# sizes, ragged strips (coarse widths not a multiple of 30), clamped edges,
+# u16 and f32 input, all-f32 and 16-bit storages, and remap parameters with
+# one or two levels in the band.
+@pytest.mark.parametrize("in_dtype,st", [(hp.HP_U16, (hp.HP_F32,) * 3), (hp.HP_F32, (hp.HP_F32,) * 3),
+                                         (hp.HP_U16, (hp.HP_BF16, hp.HP_F16, hp.HP_BF16)),
+                                         (hp.HP_F32, (hp.HP_F32, hp.HP_BF16, hp.HP_F16))])
+@pytest.mark.parametrize("h,w", [(45, 61), (53, 37), (130, 250), (1, 1), (2, 3), (768, 1280)])
+def test_ll_remap_downsample_streaming_bit_identical(in_dtype, st, h, w):
+    img, scale = _remap_input(in_dtype, h, w, seed=h * 7 + w)
+    x = to_device(img, in_dtype)
+    oh, ow = (h + 1) // 2, (w + 1) // 2
+    for sigma, alpha, beta in [(0.1, 0.25, 1.0), (0.14, 0.5, 1.7), (0.1, 1.0, 1.0)]:
+        p = _remap_down(in_dtype, st[0], st[1], st[2], sigma, alpha, beta, scale)
+        groups = [hp.HP_INLINE, hp.HP_INLINE, 0]
+        p.schedule(groups, impl=[hp.HP_IMPL_GENERIC])
+        ref = bits(run(p, [x], [in_dtype], (9, oh, ow), st[2]))
+        p.schedule(groups, tile_w=[16], tile_h=[8])
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_DOWNSAMPLE
+        assert torch.equal(bits(run(p, [x], [in_dtype], (9, oh, ow), st[2])), ref)
+        for rows, threads in [(0, 256), (1, 32), (3, 96), (8, 256), (64, 128)]:
+            p.schedule(groups, tile_h=[rows], threads=[threads])
+            info = p.group_info([(w, h)], 0)
+            assert info.kernel == hp.HP_KERNEL_LL_REMAP_ROWS and info.tile_w == 30
+            got = bits(run(p, [x], [in_dtype], (9, oh, ow), st[2]))
+            assert torch.equal(got, ref), f"rows {rows} threads {threads} sigma {sigma}"
