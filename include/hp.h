@@ -133,11 +133,12 @@ enum {
                           A single 5x5 stencil, alone or with the unsharp combine: the same strips
                           (120 / 112 columns), tile_h rows per run, threads <= 256; again the default
                           under HP_IMPL_AUTO when tile_w is the strip width.
-                          The first local-Laplacian downsample with gray and the remap inlined (K = 8,
-                          u16 or f32 input, 2 sigma below the level spacing 1/7): strips of 30 coarse
-                          columns, tile_h coarse rows per run, threads <= 256; the default under
-                          HP_IMPL_AUTO when tile_w is 30 (other groups ignore HP_IMPL_WAVE's request
-                          when they have no streaming kernel). */
+                          A pyramid downsample of f32 planes, and the first local-Laplacian
+                          downsample with gray and the remap inlined (K = 8, u16 or f32 input, 2 sigma
+                          below the level spacing 1/7): strips of 30 coarse columns, tile_h coarse rows
+                          per run, threads <= 256; the default under HP_IMPL_AUTO when tile_w is 30
+                          (other groups ignore HP_IMPL_WAVE's request when they have no streaming
+                          kernel). */
 };
 
 typedef struct {
@@ -188,9 +189,11 @@ enum {
                                   column strip of one plane, rows through a per-warp TMA ring */
   HP_KERNEL_HISTEQ = 14,       /* histogram + CDF/table + lookup in one group: one cooperative
                                   kernel, a grid-wide barrier between counting and lookup */
-  HP_KERNEL_LL_REMAP_ROWS = 15 /* level 1 of the local-Laplacian remap pyramid from the input
+  HP_KERNEL_LL_REMAP_ROWS = 15, /* level 1 of the local-Laplacian remap pyramid from the input
                                   (gray, K = 8 remaps, downsample), streaming: one warp per strip
                                   of 30 coarse columns, everything in registers */
+  HP_KERNEL_LL_DOWN_ROWS = 16   /* one pyramid level down of a stack of f32 planes, streaming: one
+                                  warp per strip of 30 coarse columns and 3 (or 1) planes */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -238,6 +238,10 @@ int ll_remap_rows_strip_w();
 int ll_remap_rows_ok(const LLDownArgs& a, int in_dtype);
 int ll_remap_rows_grid(int in_dtype, int units, int threads);
 int launch_ll_remap_rows(const LLDownArgs& a, int rows, int threads, int grid, void* stream);
+int ll_down_rows_ok(const LLDownArgs& a, int src_dtype);
+int ll_down_rows_groups(int C);
+int ll_down_rows_grid(int C, int units, int threads);
+int launch_ll_down_rows(const LLDownArgs& a, int rows, int threads, int grid, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

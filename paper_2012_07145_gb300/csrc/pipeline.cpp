@@ -899,29 +899,40 @@ hp_status build_down(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   return HP_OK;
 }
 
-// Streaming first level of the remap pyramid: strips of 30 coarse columns,
-// tile_h coarse rows per run (0: about one run per resident warp).
-hp_status build_ll_remap_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+// Streaming downsample (the first level of the remap pyramid, or a stack of
+// f32 planes): strips of 30 coarse columns, tile_h coarse rows per run (0:
+// about one run per resident warp; the plane kernel, light per row, down to
+// one row so that small levels still spread over the SMs).
+hp_status build_ll_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   down_common_args(p, gp);
   LLDownArgs& a = gp.lldown;
-  const int in_dt = stage_dtype_of_ref(p, gp.ext_refs[0]);
-  if (!ll_remap_rows_ok(a, in_dt))
-    return fail(HP_ERR_SCHEDULE, "the streaming remap downsample needs K = 8, u16 or f32 input and 0 < 2 sigma < 1/7");
+  const bool remap = gp.kernel == HP_KERNEL_LL_REMAP_ROWS;
+  const int src_dt = stage_dtype_of_ref(p, gp.ext_refs[0]);
+  if (remap ? !ll_remap_rows_ok(a, src_dt) : !ll_down_rows_ok(a, src_dt))
+    return fail(HP_ERR_SCHEDULE, remap ? "the streaming remap downsample needs K = 8, u16 or f32 input and 0 < 2 sigma < 1/7"
+                                       : "the streaming downsample needs f32 planes");
   if (gp.tile_w != ll_remap_rows_strip_w())
-    return fail(HP_ERR_SCHEDULE, "streaming remap downsample strips are %d coarse columns wide (tile_w %d)",
+    return fail(HP_ERR_SCHEDULE, "streaming downsample strips are %d coarse columns wide (tile_w %d)",
                 ll_remap_rows_strip_w(), gp.tile_w);
   if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256)
-    return fail(HP_ERR_SCHEDULE, "streaming remap downsample threads per block must be a multiple of 32 in [32, 256]");
+    return fail(HP_ERR_SCHEDULE, "streaming downsample threads per block must be a multiple of 32 in [32, 256]");
   Dom od = plan.dom[gp.output];
   a.tile_w = gp.tile_w;
   a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
-  if (gp.tile_h == 0)
-    gp.tile_h = default_run_rows(od.h, a.tiles_x, (long long)ll_remap_rows_grid(in_dt, 1 << 30, gp.threads) * (gp.threads / 32));
-  if (gp.tile_h < 1 || gp.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming remap downsample needs tile_h >= 1");
+  const int units_per_row = a.tiles_x * (remap ? 1 : ll_down_rows_groups(a.C));
+  auto grid_for = [&](int units) {
+    return remap ? ll_remap_rows_grid(src_dt, units, gp.threads) : ll_down_rows_grid(a.C, units, gp.threads);
+  };
+  if (gp.tile_h == 0) {
+    const long long warps = (long long)grid_for(1 << 30) * (gp.threads / 32);
+    gp.tile_h = remap ? default_run_rows(od.h, units_per_row, warps)
+                      : (int)std::max(1LL, ((long long)od.h * units_per_row + warps - 1) / warps);
+  }
+  if (gp.tile_h < 1 || gp.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming downsample needs tile_h >= 1");
   a.tile_h = gp.tile_h;
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
   gp.smem = 0;
-  gp.grid_x = ll_remap_rows_grid(in_dt, a.tiles_x * a.tiles_y, gp.threads);
+  gp.grid_x = grid_for(units_per_row * a.tiles_y);
   gp.grid_y = 1;
   return HP_OK;
 }
@@ -1018,20 +1029,24 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
       case HP_KERNEL_DOWNSAMPLE: {
         // the first remap level: the streaming kernel at its strip width (the
         // default) or under HP_IMPL_WAVE, where it covers the group
+        // the first remap level and f32 plane stacks: the streaming kernels at
+        // their strip width (the default) or under HP_IMPL_WAVE
         {
           GroupPlan probe;
           probe.members = gp.members;
           probe.output = gp.output;
           down_common_args(p, probe);
           const int sw = ll_remap_rows_strip_w();
-          if (ll_remap_rows_ok(probe.lldown, stage_dtype_of_ref(p, probe.ext_refs[0]))) {
+          const int src_dt = stage_dtype_of_ref(p, probe.ext_refs[0]);
+          const bool remap_ok = ll_remap_rows_ok(probe.lldown, src_dt);
+          if (remap_ok || ll_down_rows_ok(probe.lldown, src_dt)) {
             gp.tile_w = pick(p->tile_w, g, sw);
             if (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw)) {
-              gp.kernel = HP_KERNEL_LL_REMAP_ROWS;
+              gp.kernel = remap_ok ? HP_KERNEL_LL_REMAP_ROWS : HP_KERNEL_LL_DOWN_ROWS;
               gp.tile_w = sw;
               gp.tile_h = pick(p->tile_h, g, 0);
               gp.threads = pick(p->threads, g, 256);
-              s = build_ll_remap_rows(p, plan, gp);
+              s = build_ll_rows(p, plan, gp);
               break;
             }
           }
@@ -1226,11 +1241,13 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         e = launch_ll_down(a, gp.smem, stream);
         break;
       }
-      case HP_KERNEL_LL_REMAP_ROWS: {
+      case HP_KERNEL_LL_REMAP_ROWS:
+      case HP_KERNEL_LL_DOWN_ROWS: {
         LLDownArgs a = gp.lldown;
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
-        e = launch_ll_remap_rows(a, a.tile_h, gp.threads, gp.grid_x, stream);
+        e = gp.kernel == HP_KERNEL_LL_REMAP_ROWS ? launch_ll_remap_rows(a, a.tile_h, gp.threads, gp.grid_x, stream)
+                                                 : launch_ll_down_rows(a, a.tile_h, gp.threads, gp.grid_x, stream);
         break;
       }
       case HP_KERNEL_LL_LEVEL: {

@@ -352,3 +352,34 @@ def test_ll_remap_downsample_streaming_bit_identical(in_dtype, st, h, w):
             assert info.kernel == hp.HP_KERNEL_LL_REMAP_ROWS and info.tile_w == 30
             got = bits(run(p, [x], [in_dtype], (9, oh, ow), st[2]))
             assert torch.equal(got, ref), f"rows {rows} threads {threads} sigma {sigma}"
+
+
+# The streaming plane downsample against the tiled kernel, the generic
+# interpreter and the oracle: C planes (3 per warp unit where C allows, else 1),
+# run lengths, block sizes, ragged strips and clamped edges, f32 and bf16
+# output storage.
+@pytest.mark.parametrize("C", [1, 2, 3, 9])
+@pytest.mark.parametrize("h,w", [(45, 61), (53, 37), (96, 160), (1, 1), (2, 3), (3, 2), (768, 1280)])
+@pytest.mark.parametrize("st", [hp.HP_F32, hp.HP_BF16])
+def test_downsample_streaming_bit_identical(C, h, w, st):
+    from oracle import pyramid as opy
+    rng = np.random.default_rng(C * 1000 + h + w)
+    img = rng.standard_normal((C, h, w)).astype(np.float32)
+    x = to_device(img, hp.HP_F32)
+    oh, ow = (h + 1) // 2, (w + 1) // 2
+    p = hp.Pipeline([hp.HP_F32], [C])
+    d = p.add_stage(hp.HP_DOWNSAMPLE2, [p.input(0)], C, st)
+    p.set_output(d)
+    p.schedule([0], impl=[hp.HP_IMPL_GENERIC])
+    ref = bits(run(p, [x], [hp.HP_F32], (C, oh, ow), st))
+    p.schedule([0], tile_w=[16], tile_h=[8])
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_DOWNSAMPLE
+    assert torch.equal(bits(run(p, [x], [hp.HP_F32], (C, oh, ow), st)), ref)
+    for rows, threads in [(0, 256), (1, 32), (2, 96), (5, 256), (64, 128)]:
+        p.schedule([0], tile_h=[rows], threads=[threads])
+        assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_LL_DOWN_ROWS
+        got = run(p, [x], [hp.HP_F32], (C, oh, ow), st)
+        assert torch.equal(bits(got), ref), f"rows {rows} threads {threads}"
+    if st == hp.HP_F32 and h * w <= 1 << 14:
+        exp = np.stack([opy.downsample(img[c].astype(np.float64)) for c in range(C)])
+        assert rel_err(to_numpy(got), exp) <= 1e-6
