@@ -136,9 +136,10 @@ enum {
                           A pyramid downsample of f32 planes, and the first local-Laplacian
                           downsample with gray and the remap inlined (K = 8, u16 or f32 input, 2 sigma
                           below the level spacing 1/7): strips of 30 coarse columns, tile_h coarse rows
-                          per run, threads <= 256; the default under HP_IMPL_AUTO when tile_w is 30
-                          (other groups ignore HP_IMPL_WAVE's request when they have no streaming
-                          kernel). */
+                          per run, threads <= 256; the default under HP_IMPL_AUTO when tile_w is 30.
+                          A local-Laplacian level (K = 8, f32 stages; level 0 from u16 RGB): the same
+                          30-column strips (of the coarser level), tile_h coarse rows per run.  Other
+                          groups ignore HP_IMPL_WAVE's request when they have no streaming kernel. */
 };
 
 typedef struct {
@@ -192,8 +193,10 @@ enum {
   HP_KERNEL_LL_REMAP_ROWS = 15, /* level 1 of the local-Laplacian remap pyramid from the input
                                   (gray, K = 8 remaps, downsample), streaming: one warp per strip
                                   of 30 coarse columns, everything in registers */
-  HP_KERNEL_LL_DOWN_ROWS = 16   /* one pyramid level down of a stack of f32 planes, streaming: one
+  HP_KERNEL_LL_DOWN_ROWS = 16,  /* one pyramid level down of a stack of f32 planes, streaming: one
                                   warp per strip of 30 coarse columns and 3 (or 1) planes */
+  HP_KERNEL_LL_LEVEL_ROWS = 17  /* local-Laplacian level (K = 8, f32 stages), streaming: one warp per
+                                  strip of 30 coarse (60 fine) columns, upsample windows in registers */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

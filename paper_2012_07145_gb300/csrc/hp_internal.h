@@ -242,6 +242,10 @@ int ll_down_rows_ok(const LLDownArgs& a, int src_dtype);
 int ll_down_rows_groups(int C);
 int ll_down_rows_grid(int C, int units, int threads);
 int launch_ll_down_rows(const LLDownArgs& a, int rows, int threads, int grid, void* stream);
+int ll_level_rows_strip_w();
+int ll_level_rows_ok(const LLLevelArgs& a);
+int ll_level_rows_grid(const LLLevelArgs& a, int units, int threads);
+int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

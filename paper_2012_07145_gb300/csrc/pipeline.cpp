@@ -980,6 +980,49 @@ hp_status build_ll_level(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) 
   return HP_OK;
 }
 
+// The level kernel's arguments with the element types and channel counts of
+// its views filled in from the stages they come from (at realize the views
+// carry the same).
+LLLevelArgs ll_level_view_types(const hp_pipeline* p, const GroupPlan& gp) {
+  LLLevelArgs a = gp.lllevel;
+  const LLRoles& r = gp.llroles;
+  auto set = [&](ImgView& v, int ref) {
+    v.dtype = stage_dtype_of_ref(p, ref);
+    v.c = stage_channels_of_ref(p, ref);
+  };
+  if (a.level0) {
+    set(a.in, p->stages[r.gray].inputs[0]);
+  } else {
+    set(a.G, r.Gl);
+  }
+  set(a.Gn, r.Gn);
+  set(a.Rn, r.select >= 0 ? p->stages[r.select].inputs[0] : r.Rn);
+  a.out.dtype = p->stages[gp.output].storage;
+  a.out.c = p->stages[gp.output].channels;
+  return a;
+}
+
+// Streaming level kernel: strips of 30 coarse columns (60 fine), tile_h coarse
+// rows per run (0: about one run per resident warp, at least 2).
+hp_status build_ll_level_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, const LLLevelArgs& probe) {
+  if (gp.tile_w != ll_level_rows_strip_w())
+    return fail(HP_ERR_SCHEDULE, "streaming level strips are %d coarse columns wide (tile_w %d)", ll_level_rows_strip_w(),
+                gp.tile_w);
+  if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256)
+    return fail(HP_ERR_SCHEDULE, "streaming level threads per block must be a multiple of 32 in [32, 256]");
+  const Dom cd = plan.dom[gp.llroles.Gn];
+  const int strips = (cd.w + gp.tile_w - 1) / gp.tile_w;
+  if (gp.tile_h == 0) {
+    const long long warps = (long long)ll_level_rows_grid(probe, 1 << 30, gp.threads) * (gp.threads / 32);
+    gp.tile_h = (int)std::max(2LL, ((long long)cd.h * strips + warps - 1) / warps);
+  }
+  if (gp.tile_h < 1 || gp.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming level needs tile_h >= 1");
+  gp.grid_x = ll_level_rows_grid(probe, strips * ((cd.h + gp.tile_h - 1) / gp.tile_h), gp.threads);
+  gp.grid_y = 1;
+  gp.smem = 0;
+  return HP_OK;
+}
+
 hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
   plan.in_dom = in_dom;
   hp_status s = infer_domains(p, in_dom, plan.dom);
@@ -1066,9 +1109,25 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
       }
         s = build_down(p, plan, gp);
         break;
-      case HP_KERNEL_LL_LEVEL:
+      case HP_KERNEL_LL_LEVEL: {
         s = build_ll_level(p, plan, gp);
+        if (s) break;
+        // the streaming kernel at its strip width (the default) or under
+        // HP_IMPL_WAVE, where it covers the group
+        const int sw = ll_level_rows_strip_w();
+        LLLevelArgs probe = ll_level_view_types(p, gp);
+        if (ll_level_rows_ok(probe)) {
+          gp.tile_w = pick(p->tile_w, g, sw);
+          if (impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw)) {
+            gp.kernel = HP_KERNEL_LL_LEVEL_ROWS;
+            gp.tile_w = sw;
+            gp.tile_h = pick(p->tile_h, g, 0);
+            gp.threads = pick(p->threads, g, 256);
+            s = build_ll_level_rows(p, plan, gp, probe);
+          }
+        }
         break;
+      }
       case HP_KERNEL_HARRIS: {
         int roles[10];
         match_harris(p, gp.members, roles);
@@ -1250,7 +1309,8 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
                                                  : launch_ll_down_rows(a, a.tile_h, gp.threads, gp.grid_x, stream);
         break;
       }
-      case HP_KERNEL_LL_LEVEL: {
+      case HP_KERNEL_LL_LEVEL:
+      case HP_KERNEL_LL_LEVEL_ROWS: {
         LLLevelArgs a = gp.lllevel;
         const LLRoles& r = gp.llroles;
         if (a.level0) {
@@ -1261,7 +1321,8 @@ hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const 
         a.Gn = ref_view(p, plan, r.Gn, inputs, output);
         a.Rn = ref_view(p, plan, r.select >= 0 ? p->stages[r.select].inputs[0] : r.Rn, inputs, output);
         a.out = out;
-        e = launch_ll_level(a, stream);
+        e = gp.kernel == HP_KERNEL_LL_LEVEL_ROWS ? launch_ll_level_rows(a, gp.tile_h, gp.threads, gp.grid_x, stream)
+                                                 : launch_ll_level(a, stream);
         break;
       }
       case HP_KERNEL_HARRIS: {

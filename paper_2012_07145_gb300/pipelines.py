@@ -136,13 +136,16 @@ def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, al
 
 
 def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None,
-                                   down_tile: int = 0):
+                                   down_tile: int = 0, level_tile: int = 0, rows: int = 0):
     """Per-level fusion: level 1 of the remapped pyramid from the input in one
     kernel (gray and remap inlined); one downsample kernel per coarser level;
     one kernel per level for Laplacian + interpolation + collapse step; the
-    finest level fused with the colour reconstruction.  down_tile = 0 lets the
-    downsample kernels size their tiles per level (smaller tiles on the coarse
-    levels, so that they still spread over the SMs)."""
+    finest level fused with the colour reconstruction.  down_tile and
+    level_tile = 0 take each kernel's default (the streaming kernels, with run
+    lengths sized per level so that small levels still spread over the SMs);
+    another value picks the tiled downsample / per-pixel level kernel.  rows
+    sets the streaming kernels' coarse rows per run (0: their default).  tile
+    sizes the groups under the generic interpreter."""
     J = len(ids["G"])
     n = len(p.stages)
     groups = [None] * n
@@ -163,6 +166,7 @@ def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, th
         gid += 1
     assert all(g is not None for g in groups)
     generic = impl == hp.HP_IMPL_GENERIC
-    tiles = [down_tile if (g in down_groups and not generic) else tile for g in range(gid)]
-    p.schedule(groups, tile_w=tiles, tile_h=tiles, threads=[threads] * gid,
+    tiles = [tile if generic else (down_tile if g in down_groups else level_tile) for g in range(gid)]
+    heights = [t if (generic or t) else rows for t in tiles]
+    p.schedule(groups, tile_w=tiles, tile_h=heights, threads=[threads] * gid,
                impl=[impl] * gid if impl is not None else None)

@@ -159,13 +159,15 @@ def test_local_laplacian_lowering():
     assert n == 2 * J - 2
     kinds = [pl.group_info([(160, 96)], g).kernel for g in range(n)]
     # level 1 straight from the input: the streaming remap downsample by default
-    assert kinds == [hp.HP_KERNEL_LL_REMAP_ROWS] + [hp.HP_KERNEL_LL_DOWN_ROWS] * (J - 2) + [hp.HP_KERNEL_LL_LEVEL] * (J - 1)
+    assert kinds == ([hp.HP_KERNEL_LL_REMAP_ROWS] + [hp.HP_KERNEL_LL_DOWN_ROWS] * (J - 2) +
+                     [hp.HP_KERNEL_LL_LEVEL_ROWS] * (J - 1))
     assert pl.group_info([(160, 96)], 0).n_members == 3          # gray and remap inlined
     info = pl.group_info([(160, 96)], 0)
     assert info.tile_w == 30 and info.tile_h >= 1 and info.threads == 256
     # an explicit power-of-two tile takes the tiled kernel
-    pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, down_tile=16)
+    pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, down_tile=16, level_tile=32)
     assert all(pl.group_info([(160, 96)], g).kernel == hp.HP_KERNEL_DOWNSAMPLE for g in range(J - 1))
+    assert all(pl.group_info([(160, 96)], g).kernel == hp.HP_KERNEL_LL_LEVEL for g in range(J - 1, n))
     pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, impl=hp.HP_IMPL_WAVE, down_tile=16)
     assert pl.group_info([(160, 96)], 0).kernel == hp.HP_KERNEL_LL_REMAP_ROWS
     # a band as wide as the level spacing: three levels could hold one gray value

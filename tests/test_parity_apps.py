@@ -297,8 +297,30 @@ def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha):
     assert np.array_equal(_ll_run(p, img), plain)
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
     assert np.array_equal(_ll_run(p, img), plain)
-    pipelines.local_laplacian_fused_schedule(p, ids, tile=16, down_tile=16)   # tiled first downsample
+    pipelines.local_laplacian_fused_schedule(p, ids, tile=16, down_tile=16, level_tile=32)   # tiled / per-pixel
     assert np.array_equal(_ll_run(p, img), plain)
+    pipelines.local_laplacian_fused_schedule(pf, ids_f)     # streaming, f32 output
+    assert np.array_equal(to_numpy(run(pf, [x], [hp.HP_U16], (3, h, w), hp.HP_F32)), yf)
+
+
+# The streaming level kernels (and the streaming downsamples) over run
+# lengths, block sizes and sizes with ragged strips and odd levels: every
+# output bit-identical to the stage-per-kernel pipeline, u16 and f32 output.
+@pytest.mark.parametrize("h,w,levels", [(45, 61, 4), (130, 250, 5), (1, 1, 2), (2, 3, 2), (97, 67, 6)])
+def test_local_laplacian_streaming_levels_bit_identical(h, w, levels):
+    img = synth.rgb_u16_gradient_noise(h, w, seed=3)
+    x = to_device(img, hp.HP_U16)
+    for out_st in (hp.HP_U16, hp.HP_F32):
+        p, ids = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=0.5, beta=1.2,
+                                           out_storage=out_st)
+        plain = run(p, [x], [hp.HP_U16], (3, h, w), out_st)
+        for rows, threads in [(0, 256), (1, 32), (2, 96), (5, 256), (64, 128)]:
+            pipelines.local_laplacian_fused_schedule(p, ids, threads=threads, rows=rows)
+            n = p.group_count()
+            kinds = [p.group_info([(w, h)], g).kernel for g in range(n)]
+            assert kinds[n - 1] == hp.HP_KERNEL_LL_LEVEL_ROWS
+            got = run(p, [x], [hp.HP_U16], (3, h, w), out_st)
+            assert torch.equal(bits(got), bits(plain)), f"rows {rows} threads {threads} out {out_st}"
 
 
 def _remap_down(in_dtype, st_gray, st_remap, st_out, sigma, alpha, beta, scale):
