@@ -135,6 +135,23 @@ def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, al
     return p, ids
 
 
+def remap_pyramid_level1(k_levels: int = 8, sigma_r: float = 0.1, alpha: float = 1.0, beta: float = 1.0,
+                         in_dtype: int = hp.HP_U16, scale: float = 1.0 / 65535.0,
+                         storages=(hp.HP_F32, hp.HP_F32, hp.HP_F32)) -> hp.Pipeline:
+    """Level 1 of the local-Laplacian remap pyramid on its own: gray of an RGB
+    input, its K remaps and gray (K+1 channels), one downsample; gray and the
+    remap inlined into the downsample group (the first group of the local
+    Laplacian pipeline).  storages: (gray, remap, downsample)."""
+    p = hp.Pipeline([in_dtype], [3])
+    g = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, storages[0], op=hp.HP_OP_GRAY, params=[scale])
+    r = p.add_stage(hp.HP_POINTWISE, [g], k_levels + 1, storages[1], op=hp.HP_OP_LL_REMAP,
+                    params=[sigma_r, alpha, beta, k_levels])
+    d = p.add_stage(hp.HP_DOWNSAMPLE2, [r], k_levels + 1, storages[2])
+    p.set_output(d)
+    p.schedule([hp.HP_INLINE, hp.HP_INLINE, 0])
+    return p
+
+
 def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None,
                                    down_tile: int = 0, level_tile: int = 0, rows: int = 0):
     """Per-level fusion: level 1 of the remapped pyramid from the input in one

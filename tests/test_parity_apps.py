@@ -324,14 +324,7 @@ def test_local_laplacian_streaming_levels_bit_identical(h, w, levels):
 
 
 def _remap_down(in_dtype, st_gray, st_remap, st_out, sigma, alpha, beta, scale):
-    """gray -> K = 8 remaps + gray -> one downsample, the first level of the
-    local-Laplacian remap pyramid, as its own pipeline."""
-    p = hp.Pipeline([in_dtype], [3])
-    g = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, st_gray, op=hp.HP_OP_GRAY, params=[scale])
-    r = p.add_stage(hp.HP_POINTWISE, [g], 9, st_remap, op=hp.HP_OP_LL_REMAP, params=[sigma, alpha, beta, 8])
-    d = p.add_stage(hp.HP_DOWNSAMPLE2, [r], 9, st_out)
-    p.set_output(d)
-    return p
+    return pipelines.remap_pyramid_level1(8, sigma, alpha, beta, in_dtype, scale, (st_gray, st_remap, st_out))
 
 
 def _remap_input(in_dtype, h, w, seed):
