@@ -3,10 +3,12 @@
 //
 // Each CTA takes a contiguous range of 16-pixel chunks (row-major over the
 // image, a row's last chunk possibly partial), keeps them in shared memory
-// while it counts them into per-warp sub-histograms (four interleaved copies
-// per warp, one per lane mod 4, against same-address serialisation of the
-// shared-memory atomics).  The loops stay compact: each runs once or twice per
-// thread, so its code must not be long (the instruction cache is cold).  The CTA adds its counts to a device-wide histogram with
+// while it counts them into a lane-private histogram: counter (v, l) is word
+// 32 v + l, so the 32 lanes of a shared-memory atomic always hit 32 different
+// banks and never the same address, whatever the values (a low-contrast image
+// puts most lanes of a warp on a few values).  The loops stay compact: each
+// runs once or twice per thread, so its code must not be long (the instruction
+// cache is cold).  The CTA adds its counts to a device-wide histogram with
 // one atomic per bin, then all CTAs meet at a grid-wide barrier -- they are
 // co-resident because the launch is cooperative, and the wait is bounded --
 // after which every CTA forms the CDF and the table itself (256 bins: cheaper
@@ -31,9 +33,8 @@ namespace hp {
 namespace {
 
 constexpr int kEqThreads = 1024;
-constexpr int kEqWarps = kEqThreads / 32;
 constexpr int kEqU = 4;  // chunk loads in flight per thread
-constexpr int kEqHistBytes = kEqWarps * 256 * 4 * 4;     // per warp: 4 copies of 256 bins
+constexpr int kEqHistBytes = 256 * 32 * 4;               // 256 bins x 32 lanes
 constexpr int kEqSmemMax = 227 * 1024 - 8 * 1024;        // dynamic shared memory limit used here
 constexpr int kEqStageMax = kEqSmemMax - kEqHistBytes;    // bytes of image a CTA can keep
 
@@ -70,27 +71,32 @@ __device__ __forceinline__ int chunk_bytes(const EqParams& p, long long ch, cons
 
 __device__ __forceinline__ uint4 load_chunk(const unsigned char* src, int nb) {
   if (nb == 16) return __ldcs(reinterpret_cast<const uint4*>(src));
-  unsigned int w[4] = {0u, 0u, 0u, 0u};
-  for (int b = 0; b < nb; ++b) w[b >> 2] |= (unsigned int)src[b] << (8 * (b & 3));
-  return make_uint4(w[0], w[1], w[2], w[3]);
+  uint4 q = make_uint4(0u, 0u, 0u, 0u);
+  for (int b = 0; b < nb; ++b) {
+    const unsigned int v = (unsigned int)src[b] << (8 * (b & 3));
+    if (b < 4) q.x |= v;
+    else if (b < 8) q.y |= v;
+    else if (b < 12) q.z |= v;
+    else q.w |= v;
+  }
+  return q;
 }
 
-// Word of copy c of bin v in a warp's sub-histogram: 4 v + (c ^ ((v >> 3) & 3)).
-// Lanes that hold the same value but use different copies hit different banks
-// instead of serialising on one address, and the swizzle spreads values eight
-// apart (same bank otherwise) over different banks.
-__device__ __forceinline__ unsigned int bin_word(unsigned int v, unsigned int c) {
-  return (v << 2) + (c ^ ((v >> 3) & 3u));
+// Word b / 4 of a chunk without indexing a local array (a partial chunk's
+// loop index is not a compile-time constant).
+__device__ __forceinline__ unsigned int word_of(const uint4& q, int b) {
+  return b < 8 ? (b < 4 ? q.x : q.y) : (b < 12 ? q.z : q.w);
 }
 
-// Counts a chunk into the lane's copy (lane mod 4) of the warp's sub-histogram.
-__device__ __forceinline__ void count_chunk(unsigned int* wh, unsigned int c, const uint4& q, int nb) {
+// Counts a chunk into the lane's column (hl = hist + lane) of the CTA's
+// lane-private histogram: bin v of this lane is word 32 v.
+__device__ __forceinline__ void count_chunk(unsigned int* hl, const uint4& q, int nb) {
   const unsigned int w[4] = {q.x, q.y, q.z, q.w};
   if (nb == 16) {
 #pragma unroll
-    for (int b = 0; b < 16; ++b) atomicAdd(&wh[bin_word((w[b >> 2] >> (8 * (b & 3))) & 0xffu, c)], 1u);
+    for (int b = 0; b < 16; ++b) atomicAdd(&hl[((w[b >> 2] >> (8 * (b & 3))) & 0xffu) << 5], 1u);
   } else {
-    for (int b = 0; b < nb; ++b) atomicAdd(&wh[bin_word((w[b >> 2] >> (8 * (b & 3))) & 0xffu, c)], 1u);
+    for (int b = 0; b < nb; ++b) atomicAdd(&hl[((word_of(q, b) >> (8 * (b & 3))) & 0xffu) << 5], 1u);
   }
 }
 
@@ -99,26 +105,23 @@ __device__ __forceinline__ void store_chunk(const unsigned char* t, const uint4&
     __stcs(reinterpret_cast<uint4*>(dst), make_uint4(lut4(t, q.x), lut4(t, q.y), lut4(t, q.z), lut4(t, q.w)));
     return;
   }
-  const unsigned int w[4] = {q.x, q.y, q.z, q.w};
-  for (int b = 0; b < nb; ++b) dst[b] = t[(w[b >> 2] >> (8 * (b & 3))) & 0xffu];
+  for (int b = 0; b < nb; ++b) dst[b] = t[(word_of(q, b) >> (8 * (b & 3))) & 0xffu];
 }
 
 __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant__ EqParams p) {
-  // dynamic shared memory: the warps' sub-histograms, then (when the slice
+  // dynamic shared memory: the lane-private histogram, then (when the slice
   // fits) the CTA's slice of the image
   extern __shared__ uint4 smem_dyn[];
-  unsigned int (*sh)[256 * 4] = reinterpret_cast<unsigned int (*)[256 * 4]>(smem_dyn);
+  unsigned int* sh = reinterpret_cast<unsigned int*>(smem_dyn);
   uint4* stage = smem_dyn + kEqHistBytes / 16;
   __shared__ unsigned char table[256];
-  __shared__ unsigned int red[kEqThreads / 256][256];
   __shared__ unsigned int s_gen;
   __shared__ int s_last, s_ok;
-  for (int i = threadIdx.x; i < kEqWarps * 256 * 4; i += blockDim.x) (&sh[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) sh[i] = 0;
   if (threadIdx.x == 0) s_gen = ld_relaxed(&p.st->gen);
   __syncthreads();
   const unsigned int gen = s_gen, buf = gen & 1u;
-  unsigned int* wh = sh[threadIdx.x >> 5];
-  const unsigned int copy = threadIdx.x & 3u;
+  unsigned int* hl = sh + (threadIdx.x & 31);
   const long long c0 = (long long)blockIdx.x * p.per_cta;
   const long long c1 = min(p.n_chunks, c0 + p.per_cta);
   const bool staged = p.staged != 0;  // the slice is kept in shared memory for the lookup
@@ -144,23 +147,23 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
     for (int u = 0; u < kEqU; ++u) {
       if (nb[u] == 0) continue;
       if (staged) stage[base + (long long)u * blockDim.x - c0] = q[u];
-      count_chunk(wh, copy, q[u], nb[u]);
+      count_chunk(hl, q[u], nb[u]);
     }
   }
   __syncthreads();
   {
-    // all threads reduce: thread t sums bin t % 256 over a quarter of the
-    // warps (all four copies), then threads 0..255 add the quarters
-    const int v = threadIdx.x & 255, part = threadIdx.x >> 8, nparts = kEqThreads / 256;
+    // all threads reduce: thread t sums bin t / 4 over 8 of the 32 lane
+    // columns (8 (t % 4) .. 8 (t % 4) + 7, visited from a bin-dependent start
+    // so that a warp's reads hit 32 different banks); the four partial sums of
+    // a bin are adjacent lanes and are added by shuffles
+    const int v = threadIdx.x >> 2, part = threadIdx.x & 3;
+    const unsigned int* row = sh + v * 32 + 8 * part;
     unsigned int s = 0;
-    for (int w = part * (kEqWarps / nparts); w < (part + 1) * (kEqWarps / nparts); ++w)
-      s += sh[w][4 * v] + sh[w][4 * v + 1] + sh[w][4 * v + 2] + sh[w][4 * v + 3];
-    red[part][v] = s;
-    __syncthreads();
-    if (threadIdx.x < 256) {
-      s = red[0][v] + red[1][v] + red[2][v] + red[3][v];
-      if (s) atomicAdd(&p.st->hist[buf][blockIdx.x % kEqCopies][v], s);
-    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += row[(j + v) & 7];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (part == 0 && s) atomicAdd(&p.st->hist[buf][blockIdx.x % kEqCopies][v], s);
   }
 
   // ---- grid-wide barrier (bounded) ----
