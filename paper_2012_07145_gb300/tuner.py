@@ -155,7 +155,7 @@ def app_candidates(app):
     tiled_w = (32, 64, 96) if app.startswith("harris") else (64, 128)
     for tw, th, t, sy in itertools.product(tiled_w, (16, 32, 64), (128, 256), (4, 8)):
         out.append(dict(schedule="fused", impl=hp.HP_IMPL_AUTO, tile_w=tw, tile_h=th, threads=t, serial_y=sy))
-    runs = (8, 11, 14, 17, 20, 26, 32) if app.startswith("harris") else (16, 32, 48, 64, 96, 128, 192)
+    runs = (8, 11, 14, 17, 20, 26, 32) if app.startswith("harris") else (12, 16, 20, 24, 32, 48, 64, 96)
     strip = 112 if app.endswith("bf16") else 120      # 2-byte inputs take 112-column strips
     for th, t in itertools.product(runs, (128, 256)):
         out.append(dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=strip, tile_h=th, threads=t))
