@@ -257,8 +257,13 @@ hp_status hp_infer_bounds(hp_pipeline* p, const int* in_widths, const int* in_he
  *   uncaptured, the second captures and instantiates a graph, later ones launch
  *   it with one cudaGraphLaunch on the caller's stream.  Up to 16 graphs are
  *   kept per input size (least recently used evicted).  Capture happens on a
- *   private stream, so the caller's stream may be the legacy default stream. */
-enum { HP_OPT_CUDA_GRAPH = 1 };
+ *   private stream, so the caller's stream may be the legacy default stream.
+ * HP_OPT_OVERLAP (0/1, default 1): launch the kernels of a realize with
+ *   programmatic dependent launch, so that a kernel's blocks may be scheduled
+ *   while its predecessor's last blocks drain.  Every kernel waits for its
+ *   predecessor to complete before it touches memory, so results are the same
+ *   either way. */
+enum { HP_OPT_CUDA_GRAPH = 1, HP_OPT_OVERLAP = 2 };
 hp_status hp_set_option(hp_pipeline* p, int option, long long value);
 
 /* ---- Serving loop ---------------------------------------------------------

@@ -5,12 +5,29 @@
 
 #include <stdint.h>
 
+#include <cuda_runtime.h>
+
 #include "../../include/hp.h"
 
 #if defined(__CUDACC__)
 #define HPHD __host__ __device__ __forceinline__
 #else
 #define HPHD inline
+#endif
+
+#if defined(__CUDACC__)
+// First statement of every kernel launched by launch_kernel: wait until the
+// grid it depends on has completed (a no-op for a plain launch).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// The same, then let the next kernel's launch begin at once: its blocks take
+// the SMs this grid's last wave leaves free (and wait there).  For kernels
+// that run in several waves; a persistent grid (one wave) gains nothing, and
+// the local-Laplacian sequence measured slower with it.
+__device__ __forceinline__ void grid_dep_sync() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 #endif
 
 namespace hp {
@@ -255,6 +272,29 @@ const char* cuda_error_string(int e);
 int allow_max_dynamic_smem(const void* func);
 
 extern unsigned long long g_launches;
+
+// Programmatic dependent launch: when t_overlap is set (by the realize of a
+// pipeline with HP_OPT_OVERLAP on, for its own thread), kernels are launched
+// so that the next one's blocks may be scheduled while the previous kernel's
+// last blocks finish.  Every such kernel first waits for its predecessor grid
+// to complete and its memory to be visible (grid_dep_sync), before any global
+// memory access, so the order of reads and writes is that of plain launches.
+extern thread_local int t_overlap;
+
+template <typename... KArgs, typename... Args>
+inline int launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, void* stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = (cudaStream_t)stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = t_overlap ? 1 : 0;
+  return (int)cudaLaunchKernelEx(&cfg, kern, args...);
+}
 
 // Sets the thread's hp_last_error() message and returns s.
 hp_status report_error(hp_status s, const char* msg);

@@ -173,6 +173,7 @@ __device__ __forceinline__ float staged_value(const unsigned char* st, int idx, 
 
 template <int RND, int ODT, int SEG>
 __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKParams kp) {
+  grid_dep_sync();
   const ChainArgs& a = kp.a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // align to 128 bytes by offsetting the shared array itself (not through an
@@ -372,7 +373,7 @@ int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
     }
   }
   dim3 grid(a.tiles_x, a.tiles_y, a.in.c);
-  kern<<<grid, a.threads, smem_bytes, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(kern, dim3(grid), dim3(a.threads), smem_bytes, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

@@ -119,6 +119,7 @@ __device__ float eval_node(const Ctx& k, const GNode& nd, int c, int x, int y) {
 }
 
 __global__ void __launch_bounds__(1024) k_generic(const __grid_constant__ GPlan g) {
+  grid_dep_sync();
   extern __shared__ float4 smem4[];
   __shared__ Rect rects[kMaxGNodes];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -160,7 +161,7 @@ int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream) {
     configured = true;
   }
   dim3 grid(g.tiles_x, g.tiles_y, 1);
-  k_generic<<<grid, threads, smem_bytes, (cudaStream_t)stream>>>(g);
+  { const int le_ = launch_kernel(k_generic, dim3(grid), dim3(threads), smem_bytes, stream, g); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

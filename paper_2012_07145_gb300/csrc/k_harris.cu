@@ -98,6 +98,7 @@ __device__ void fixup_rect(float* buf, int P, int x0, int y0, int Ws, int Hs, in
 
 template <int RND, int ODT>
 __global__ void __launch_bounds__(512) k_harris(const __grid_constant__ HarrisKParams kp) {
+  grid_dep_sync();
   const HarrisArgs& a = kp.a;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -330,7 +331,7 @@ int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream) {
       encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, g.bw, g.GH, 3))
     return (int)cudaErrorInvalidValue;
   dim3 grid(a.tiles_x, a.tiles_y, 1);
-  kern<<<grid, a.threads, smem_bytes, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(kern, dim3(grid), dim3(a.threads), smem_bytes, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

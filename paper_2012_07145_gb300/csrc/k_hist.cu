@@ -27,6 +27,7 @@ constexpr int kHistWarps = kHistThreads / 32;
 constexpr int kChunksPerIter = 4;
 
 __global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigned int* __restrict__ hist) {
+  grid_dep_sync();
   __shared__ unsigned int sh[kHistWarps][256];
   for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
@@ -80,11 +81,13 @@ __global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigne
 
 // One CTA of 256 threads: the CDF and the equalization table.
 __global__ void __launch_bounds__(256) k_cdf_lut(const unsigned int* __restrict__ hist, unsigned char* __restrict__ lut) {
+  grid_dep_sync();
   cdf_lut_cta(hist[threadIdx.x], lut);
 }
 
 __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out,
                                                    const unsigned char* __restrict__ lut) {
+  grid_dep_sync();
   __shared__ unsigned char t[256];
   if (threadIdx.x < 256) t[threadIdx.x] = lut[threadIdx.x];
   __syncthreads();
@@ -145,13 +148,13 @@ int launch_hist(const HistArgs& a, void* stream) {
   long long want = (chunks + kHistThreads * kChunksPerIter - 1) / (kHistThreads * kChunksPerIter);
   int blocks = (int)(want < 4LL * sm_count() ? want : 4LL * sm_count());
   if (blocks < 1) blocks = 1;
-  k_hist<<<blocks, kHistThreads, 0, s>>>(a.in, a.hist);
+  { const int le_ = launch_kernel(k_hist, dim3(blocks), dim3(kHistThreads), 0, (void*)s, a.in, a.hist); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
 
 int launch_cdf_lut(const LutArgs& a, void* stream) {
-  k_cdf_lut<<<1, 256, 0, (cudaStream_t)stream>>>(a.hist, a.lut);
+  { const int le_ = launch_kernel(k_cdf_lut, dim3(1), dim3(256), 0, stream, a.hist, a.lut); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
@@ -161,7 +164,7 @@ int launch_lut_apply(const LutApplyArgs& a, void* stream) {
   long long want = (chunks + 256 * kChunksPerIter - 1) / (256 * kChunksPerIter);
   int blocks = (int)(want < 8LL * sm_count() ? want : 8LL * sm_count());
   if (blocks < 1) blocks = 1;
-  k_lut_apply<<<blocks, 256, 0, (cudaStream_t)stream>>>(a.in, a.out, a.lut);
+  { const int le_ = launch_kernel(k_lut_apply, dim3(blocks), dim3(256), 0, stream, a.in, a.out, a.lut); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

@@ -38,6 +38,7 @@ __device__ __forceinline__ float level_px(const ImgView& v, int c, int x, int y)
 // Tile widths are powers of two (checked on the host): lg_tw = log2(tile_w).
 template <bool REMAP, bool F32>
 __global__ void __launch_bounds__(256) k_ll_down(const LLDownArgs a) {
+  grid_dep_wait();
   extern __shared__ __align__(16) float sm[];
   __shared__ float gk_level[HP_MAX_PARAMS * 2 + 1];
   const int tw = a.tile_w, lg_tw = 31 - __clz(tw);
@@ -169,6 +170,7 @@ __device__ __forceinline__ float upsample_at(const ImgView& v, int c, int X, int
 // F32: every level buffer and every stage stored as f32 (no rounding steps).
 template <bool LEVEL0, bool F32>
 __global__ void __launch_bounds__(256) k_ll_level(const LLLevelArgs a) {
+  grid_dep_wait();
   const int X = blockIdx.x * 32 + (threadIdx.x & 31);
   const int Y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (X >= a.W || Y >= a.H) return;
@@ -226,7 +228,7 @@ int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream) {
     configured[variant] = true;
   }
   dim3 grid(a.tiles_x, a.tiles_y, 1);
-  kernels[variant]<<<grid, 256, smem_bytes, (cudaStream_t)stream>>>(a);
+  { const int le_ = launch_kernel(kernels[variant], dim3(grid), dim3(256), smem_bytes, stream, a); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
@@ -237,12 +239,12 @@ int launch_ll_level(const LLLevelArgs& a, void* stream) {
              a.st_U == HP_F32 && a.st_L == HP_F32 && a.st_Lout == HP_F32 && a.st_UR == HP_F32 && a.st_R == HP_F32;
   if (a.level0) {
     f32 = f32 && a.st_gray == HP_F32;
-    if (f32) k_ll_level<true, true><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else k_ll_level<true, false><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    if (f32) { const int le_ = launch_kernel(k_ll_level<true, true>, dim3(grid), dim3(256), 0, stream, a); if (le_) return le_; }
+    else { const int le_ = launch_kernel(k_ll_level<true, false>, dim3(grid), dim3(256), 0, stream, a); if (le_) return le_; }
   } else {
     f32 = f32 && a.G.dtype == HP_F32;
-    if (f32) k_ll_level<false, true><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
-    else k_ll_level<false, false><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+    if (f32) { const int le_ = launch_kernel(k_ll_level<false, true>, dim3(grid), dim3(256), 0, stream, a); if (le_) return le_; }
+    else { const int le_ = launch_kernel(k_ll_level<false, false>, dim3(grid), dim3(256), 0, stream, a); if (le_) return le_; }
   }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();

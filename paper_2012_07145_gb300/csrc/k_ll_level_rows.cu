@@ -246,6 +246,7 @@ struct LevelRun {
 
 template <bool LEVEL0, int ODT>
 __global__ void __launch_bounds__(256, 2) k_ll_level_rows(const LevelRowsParams P) {
+  grid_dep_wait();
   __shared__ float gks[kK];
   if (threadIdx.x < kK) gks[threadIdx.x] = P.gk[threadIdx.x];
   __syncthreads();
@@ -308,7 +309,7 @@ int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, 
   kp.vec_in = a.level0 ? al(a.in, 4) : 0;
   kp.vec_out = al(a.out, a.out.dtype == HP_U16 ? 4 : 8);
   kp.vec_g = a.level0 ? 0 : al(a.G, 8);
-  pick_kernel(a)<<<grid, threads, 0, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(pick_kernel(a), dim3(grid), dim3(threads), 0, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

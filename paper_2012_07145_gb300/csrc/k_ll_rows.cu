@@ -289,6 +289,7 @@ struct PlaneRun {
 
 template <int IDT, bool F32S>
 __global__ void __launch_bounds__(256, 2) k_ll_remap_rows(const LLRowsParams P) {
+  grid_dep_wait();
   __shared__ float gks[kK];
   if (threadIdx.x < kK) gks[threadIdx.x] = P.gk[threadIdx.x];
   __syncthreads();
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(256, 2) k_ll_remap_rows(const LLRowsParams P) 
 // One level down of C f32 planes, CG channels per warp unit.
 template <int CG, bool F32S>
 __global__ void __launch_bounds__(256, 2) k_ll_down_rows(const LLRowsParams P) {
+  grid_dep_wait();
   const int groups = P.a.C / CG;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.units; u += nw) {
@@ -388,7 +390,7 @@ int launch_ll_down_rows(const LLDownArgs& a, int rows, int threads, int grid, vo
   kp.units = kp.strips * ll_down_rows_groups(a.C) * ((a.out.h + rows - 1) / rows);
   kp.vec = ((long long)(size_t)a.src.data % 8 == 0) && a.src.rs % 8 == 0 && a.src.ps % 8 == 0;
   const bool f32s = a.st_out == HP_F32 && a.out.dtype == HP_F32;
-  pick_down_kernel(a.C, f32s)<<<grid, threads, 0, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(pick_down_kernel(a.C, f32s), dim3(grid), dim3(threads), 0, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
@@ -409,7 +411,7 @@ int launch_ll_remap_rows(const LLDownArgs& a, int rows, int threads, int grid, v
   kp.vec = ((long long)(size_t)a.src.data % al == 0) && a.src.rs % al == 0 && a.src.ps % al == 0;
   int variant;
   RemapKernel kern = pick_kernel(a.src.dtype, all_f32(a), &variant);
-  kern<<<grid, threads, 0, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(kern, dim3(grid), dim3(threads), 0, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

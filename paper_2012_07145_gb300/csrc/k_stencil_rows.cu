@@ -280,6 +280,7 @@ struct StripRun {
 
 template <bool F32, bool EPI>
 __global__ void __launch_bounds__(256, 3) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -376,7 +377,7 @@ int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, 
                             : dt == HP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   if (encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, 128, kBoxRows, 1))
     return (int)cudaErrorInvalidValue;
-  kern<<<grid, a.threads, smem_bytes, (cudaStream_t)stream>>>(kp);
+  { const int le_ = launch_kernel(kern, dim3(grid), dim3(a.threads), smem_bytes, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

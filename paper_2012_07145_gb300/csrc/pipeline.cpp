@@ -22,6 +22,7 @@
 namespace hp {
 
 unsigned long long g_launches = 0;
+thread_local int t_overlap = 0;
 
 namespace {
 
@@ -137,6 +138,7 @@ struct hp_pipeline {
   std::map<std::vector<int>, std::unique_ptr<hp::Plan>> plans;
   int* d_err = nullptr;
   bool use_graph = false;
+  bool overlap = true;   // programmatic dependent launch between the realize's kernels
   cudaStream_t capture_stream = nullptr;
   unsigned long long uses = 0;
 };
@@ -1268,7 +1270,21 @@ void default_schedule(hp_pipeline* p) {
   p->tile_w.clear(); p->tile_h.clear(); p->threads.clear(); p->serial_y.clear(); p->impl.clear();
 }
 
+hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const hp_buffer* output, void* stream);
+
+// Launches every group's kernel in order on `stream`; with the overlap option
+// each launch may begin while the previous kernel drains (every kernel waits
+// for its predecessor before touching memory).
 hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const hp_buffer* output, void* stream) {
+  struct Overlap {
+    int saved;
+    explicit Overlap(int on) : saved(t_overlap) { t_overlap = on; }
+    ~Overlap() { t_overlap = saved; }
+  } guard(p->overlap ? 1 : 0);
+  return run_groups_impl(p, plan, inputs, output, stream);
+}
+
+hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const hp_buffer* output, void* stream) {
   for (GroupPlan& gp : plan.groups) {
     ImgView out = ref_view(p, plan, gp.output, inputs, output);
     int e = 0;
@@ -1808,6 +1824,16 @@ hp_status hp_set_option(hp_pipeline* p, int option, long long value) {
         }
       }
       p->use_graph = value != 0;
+      return HP_OK;
+    case HP_OPT_OVERLAP:
+      if (p->overlap != (value != 0)) {  // captured graphs hold the old launch attributes
+        for (auto& kv : p->plans) {
+          for (auto& g : kv.second->graphs) cudaGraphExecDestroy(g.exec);
+          kv.second->graphs.clear();
+          kv.second->seen.clear();
+        }
+      }
+      p->overlap = value != 0;
       return HP_OK;
     default:
       return fail(HP_ERR_INVALID_ARG, "unknown option %d", option);

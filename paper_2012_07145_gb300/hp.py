@@ -21,6 +21,7 @@ HP_STENCIL, HP_POINTWISE, HP_DOWNSAMPLE2, HP_UPSAMPLE2, HP_HISTOGRAM, HP_CDF_LUT
  HP_OP_LL_COLOUR, HP_OP_SELECT, HP_OP_SCALE) = range(11)
 HP_INLINE = -1
 HP_OPT_CUDA_GRAPH = 1
+HP_OPT_OVERLAP = 2
 HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE = 0, 1, 2
 (HP_KERNEL_STENCIL_CHAIN, HP_KERNEL_UNSHARP, HP_KERNEL_HARRIS, HP_KERNEL_GENERIC, HP_KERNEL_POINTWISE,
  HP_KERNEL_DOWNSAMPLE, HP_KERNEL_UPSAMPLE, HP_KERNEL_HISTOGRAM, HP_KERNEL_CDF_LUT, HP_KERNEL_LUT_APPLY,
@@ -240,6 +241,10 @@ class Pipeline:
 
     def use_cuda_graph(self, on: bool = True):
         self.set_option(HP_OPT_CUDA_GRAPH, 1 if on else 0)
+
+    def overlap_launches(self, on: bool = True):
+        """Programmatic dependent launch between the realize's kernels (the default)."""
+        self.set_option(HP_OPT_OVERLAP, 1 if on else 0)
 
     def device_error(self) -> int:
         """Reads and clears the device error word (0 = none); synchronises."""

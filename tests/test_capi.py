@@ -179,3 +179,14 @@ def test_local_laplacian_lowering():
     assert pl.group_info([(160, 96)], n - 1).n_members == 8      # level 0: + colour, gray, remap
     pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
     assert all(pl.group_info([(160, 96)], g).kernel == hp.HP_KERNEL_GENERIC for g in range(n))
+
+
+def test_options():
+    """Options need no GPU to set; unknown ones are rejected."""
+    p = pipelines.stencil_chain(4, "binomial")
+    p.use_cuda_graph(True)
+    p.overlap_launches(False)
+    p.overlap_launches(True)
+    p.set_option(hp.HP_OPT_OVERLAP, 0)
+    with pytest.raises(hp.HPError):
+        p.set_option(99, 1)

@@ -165,3 +165,24 @@ def test_prepare_then_realize():
     y = chain_run(q, img)
     assert hp.launch_count() - n0 == 8
     assert torch.equal(bits(y), bits(ref))
+
+
+def test_overlapped_launches_match_plain_launches():
+    """Programmatic dependent launch (the default) against plain launches, in
+    eager realizes and in graph replays: the same bits, for a fused chain (the
+    tiled kernel, which lets its successor launch early) and the stage-per-
+    kernel schedule (streaming single-stencil kernels)."""
+    img = synth.stencil_input(300, 500, seed=12)
+    for fused in (True, False):
+        p = pipelines.stencil_chain(16, "alternate")
+        if fused:
+            pipelines.chain_schedule(p, depth=4, tile_w=64, tile_h=32, threads=256, serial_y=8)
+        p.overlap_launches(False)
+        ref = chain_run(p, img)
+        p.overlap_launches(True)
+        assert torch.equal(bits(chain_run(p, img)), bits(ref))
+        p.use_cuda_graph(True)
+        x = to_device(img, hp.HP_F32)
+        for _ in range(3):   # uncaptured, captured, replayed
+            y = run(p, [x], [hp.HP_F32], (1, 300, 500), hp.HP_F32)
+            assert torch.equal(bits(y), bits(ref))
