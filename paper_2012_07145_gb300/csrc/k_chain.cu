@@ -46,7 +46,7 @@ __host__ __device__ inline ChainGeom chain_geom(int depth, int tw, int th) {
   ChainGeom g;
   g.W0 = tw + 4 * depth;
   g.H0 = th + 4 * depth;
-  g.P = ((g.W0 + 3) & ~3) + 4;
+  g.P = (g.W0 + 3) & ~3;
   g.BH = g.H0 < 256 ? g.H0 : 256;
   g.nby = (g.H0 + g.BH - 1) / g.BH;
   // rows: the stacked TMA boxes, and the overshoot of a last row segment

@@ -43,7 +43,7 @@ SMEM_LIMIT = 227 * 1024 - 1024
 def chain_smem_bytes(depth, tile_w, tile_h):
     """Mirror of the kernel's shared-memory plan (two ping-pong buffers)."""
     W0, H0 = tile_w + 4 * depth, tile_h + 4 * depth
-    P = ((W0 + 3) & ~3) + 4
+    P = (W0 + 3) & ~3
     BH = min(H0, 256)
     R = max((H0 + BH - 1) // BH * BH, ((H0 + 15) & ~15) + 4)
     buf = (P * R + 31) & ~31
