@@ -14,9 +14,11 @@
 // neighbours m-1, m+1 by warp shuffles): even fine columns 1/8, 6/8, 1/8 over
 // m-1, m, m+1; odd ones 1/2, 1/2 over m, m+1.  A window of three x-passed
 // coarse rows gives the y pass of fine rows 2n (1/8, 6/8, 1/8 over n-1, n, n+1)
-// and 2n+1 (1/2, 1/2 over n, n+1).  The upsample is formed for all K levels
-// and the two a pixel needs are selected afterwards, so no load depends on the
-// pixel's level.  Lanes 0 and 31 only feed their neighbours.  The operations
+// and 2n+1 (1/2, 1/2 over n, n+1).  The window of the K levels sits in shared
+// memory, lane-private (word (slot, level, column) x 32 + lane: every access
+// of a warp hits 32 banks), so a pixel reads just the two levels it blends; no
+// global load depends on the pixel's level.  R_{l+1}'s window stays in
+// registers.  Lanes 0 and 31 only feed their neighbours.  The operations
 // are those of the per-pixel expression (x pass over each coarse row, then the
 // y pass, in tap order), so results are bit-identical to the other kernels.
 // All stages are stored as f32 in the pipelines this kernel takes (the host
@@ -35,6 +37,9 @@ namespace {
 constexpr int kK = 8;        // intensity levels
 constexpr int kNC = kK + 1;  // x-passed channels per coarse row: the K levels of G_{l+1}, then R_{l+1}
 constexpr int kStripW = 30;  // coarse columns per warp
+constexpr int kSlotF = kK * 2 * 32;      // floats per window slot of a warp: K levels x 2 columns x 32 lanes
+constexpr int kWarpF = 3 * kSlotF;       // floats per warp: three slots
+constexpr int kMaxWarps = 8;             // 256 threads
 
 struct LevelRowsParams {
   LLLevelArgs a;
@@ -55,14 +60,15 @@ template <bool LEVEL0, int ODT>
 struct LevelRun {
   const LevelRowsParams& P;
   const float* gks;  // the level table in shared memory (dynamic index)
+  float* win;        // this lane's column of the warp's window: word (slot, level, column) x 32
   int m, cm, X0, X1, n0, nrun;
   bool pair, prod, ok1;  // pair: both fine columns inside the image; ok1: fine column 2m+1 exists
-  float hx[3][kNC][2];   // x-passed coarse rows (window slot, channel, fine column)
+  float hr[3][2];        // x-passed coarse rows of R_{l+1} (window slot, fine column)
   float raw[kNC];        // the next coarse row, in flight
   RGBPair pin[2], pin_nxt[2];   // level 0: input rows 2n, 2n+1 of this step and the next
   float2 gkp[2], gkp_nxt[2];    // above level 0: G_l[K] at rows 2n, 2n+1
 
-  __device__ __forceinline__ LevelRun(const LevelRowsParams& p, const float* g) : P(p), gks(g) {}
+  __device__ __forceinline__ LevelRun(const LevelRowsParams& p, const float* g, float* w) : P(p), gks(g), win(w) {}
 
   __device__ __forceinline__ void load_raw(int q) {
     const LLLevelArgs& a = P.a;
@@ -82,8 +88,15 @@ struct LevelRun {
     for (int c = 0; c < kNC; ++c) {
       const float l = __shfl_up_sync(0xffffffffu, raw[c], 1);
       const float r = __shfl_down_sync(0xffffffffu, raw[c], 1);
-      hx[S][c][0] = __fmaf_rn(0.125f, r, __fmaf_rn(0.75f, raw[c], __fmul_rn(0.125f, l)));
-      hx[S][c][1] = __fmaf_rn(0.5f, r, __fmul_rn(0.5f, raw[c]));
+      const float h0 = __fmaf_rn(0.125f, r, __fmaf_rn(0.75f, raw[c], __fmul_rn(0.125f, l)));
+      const float h1 = __fmaf_rn(0.5f, r, __fmul_rn(0.5f, raw[c]));
+      if (c < kK) {
+        win[S * kSlotF + (2 * c) * 32] = h0;
+        win[S * kSlotF + (2 * c + 1) * 32] = h1;
+      } else {
+        hr[S][0] = h0;
+        hr[S][1] = h1;
+      }
     }
   }
 
@@ -143,21 +156,22 @@ struct LevelRun {
         g0 = __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(q) + (long long)k0 * a.G.ps));
         g1 = __ldg(reinterpret_cast<const float*>(reinterpret_cast<const char*>(q) + (long long)(k0 + 1) * a.G.ps));
       }
-      // y pass of every level's upsample, then the two this pixel needs
-      float u[kNC];
-#pragma unroll
-      for (int c = 0; c < kNC; ++c)
-        u[c] = ODD ? __fmaf_rn(0.5f, hx[C][c][j], __fmul_rn(0.5f, hx[B][c][j]))
-                   : __fmaf_rn(0.125f, hx[C][c][j], __fmaf_rn(0.75f, hx[B][c][j], __fmul_rn(0.125f, hx[A][c][j])));
-      float ulo = u[0], uhi = u[1];
-#pragma unroll
-      for (int c = 1; c < kK - 1; ++c) {
-        ulo = k0 == c ? u[c] : ulo;
-        uhi = k0 == c ? u[c + 1] : uhi;
+      // y pass of the two levels this pixel blends (k0 and k0 + 1), and of R
+      const float* wl = win + (2 * k0 + j) * 32;  // level k0, this column; level k0 + 1 is 64 further
+      float ulo, uhi, ur;
+      if (ODD) {
+        ulo = __fmaf_rn(0.5f, wl[C * kSlotF], __fmul_rn(0.5f, wl[B * kSlotF]));
+        uhi = __fmaf_rn(0.5f, wl[C * kSlotF + 64], __fmul_rn(0.5f, wl[B * kSlotF + 64]));
+        ur = __fmaf_rn(0.5f, hr[C][j], __fmul_rn(0.5f, hr[B][j]));
+      } else {
+        ulo = __fmaf_rn(0.125f, wl[C * kSlotF], __fmaf_rn(0.75f, wl[B * kSlotF], __fmul_rn(0.125f, wl[A * kSlotF])));
+        uhi = __fmaf_rn(0.125f, wl[C * kSlotF + 64],
+                        __fmaf_rn(0.75f, wl[B * kSlotF + 64], __fmul_rn(0.125f, wl[A * kSlotF + 64])));
+        ur = __fmaf_rn(0.125f, hr[C][j], __fmaf_rn(0.75f, hr[B][j], __fmul_rn(0.125f, hr[A][j])));
       }
       const float L0 = __fsub_rn(g0, ulo);
       const float L1 = __fsub_rn(g1, uhi);
-      res[j] = __fadd_rn(op_ll_blend(L0, L1, f), u[kK]);
+      res[j] = __fadd_rn(op_ll_blend(L0, L1, f), ur);
     }
     if (!prod) return;
     const ImgView& o = a.out;
@@ -245,14 +259,16 @@ struct LevelRun {
 };
 
 template <bool LEVEL0, int ODT>
-__global__ void __launch_bounds__(256, 2) k_ll_level_rows(const LevelRowsParams P) {
+__global__ void __launch_bounds__(256, 3) k_ll_level_rows(const LevelRowsParams P) {
   grid_dep_wait();
   __shared__ float gks[kK];
+  extern __shared__ float wins[];  // kWarpF floats per warp (dynamic: 48 KB for 8 warps)
   if (threadIdx.x < kK) gks[threadIdx.x] = P.gk[threadIdx.x];
   __syncthreads();
+  float* win = wins + (threadIdx.x >> 5) * kWarpF + (threadIdx.x & 31);
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.units; u += nw) {
-    LevelRun<LEVEL0, ODT> r(P, gks);
+    LevelRun<LEVEL0, ODT> r(P, gks, win);
     r.run(u % P.strips, u / P.strips);
   }
 }
@@ -279,12 +295,16 @@ int ll_level_rows_ok(const LLLevelArgs& a) {
   return a.G.dtype == HP_F32 && a.G.c >= kK + 1 && a.out.dtype == HP_F32;
 }
 
+static int level_smem_bytes(int threads) { return (threads / 32) * kWarpF * 4; }
+
 int ll_level_rows_grid(const LLLevelArgs& a, int units, int threads) {
   const int nw = threads / 32;
   const int need = (units + nw - 1) / nw;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(a), threads, 0) != cudaSuccess || per_sm < 1) {
+      allow_max_dynamic_smem((const void*)pick_kernel(a)) != 0 ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pick_kernel(a), threads, level_smem_bytes(threads)) != cudaSuccess ||
+      per_sm < 1) {
     cudaGetLastError();
     return need < 2 * 152 ? need : 2 * 152;  // no device to ask: two CTAs on each of 152 SMs
   }
@@ -309,7 +329,14 @@ int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, 
   kp.vec_in = a.level0 ? al(a.in, 4) : 0;
   kp.vec_out = al(a.out, a.out.dtype == HP_U16 ? 4 : 8);
   kp.vec_g = a.level0 ? 0 : al(a.G, 8);
-  { const int le_ = launch_kernel(pick_kernel(a), dim3(grid), dim3(threads), 0, stream, kp); if (le_) return le_; }
+  static bool configured[3] = {};
+  const int variant = !a.level0 ? 0 : a.out.dtype == HP_U16 ? 1 : 2;
+  if (!configured[variant]) {  // the window (48 KB for 8 warps) and the level table pass the default 48 KB
+    const int e = allow_max_dynamic_smem((const void*)pick_kernel(a));
+    if (e) return e;
+    configured[variant] = true;
+  }
+  { const int le_ = launch_kernel(pick_kernel(a), dim3(grid), dim3(threads), level_smem_bytes(threads), stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
