@@ -511,6 +511,7 @@ def run_ours(args, cfg_name):
     }
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, seconds=args.cpu_seconds)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg_name, seconds=args.cpu_seconds)
     if world > 1:
         dist.destroy_process_group()
     return line
@@ -532,6 +533,40 @@ def cpu_baseline(cfg, seconds=15.0):
     return {"value": round(rows * cfg["w"] / dt / 1e6, 4), "unit": "MPix/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} run(s) of the oracle on a {cfg['w']}x{rows} band of the workload (same per-pixel "
                       f"work), numpy, 1 thread"}
+
+
+def _oracle_worker(cfg_name, seconds):
+    """One host process of the all-cores oracle timing: its own band, as many
+    runs as fit in `seconds` (at least one).  Returns (pixels, elapsed)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    cfg = config_table()[cfg_name]
+    rows = cfg["sample_rows"]
+    fn = cfg["oracle_sample"](rows)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        fn()
+        n += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    return rows * cfg["w"] * n, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(cfg_name, seconds=15.0):
+    """The oracle on every host core at once: one process per core (spawned, so
+    no CUDA state is inherited), each on its own band of the workload; rate =
+    all pixels / the slowest process's wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.starmap(_oracle_worker, [(cfg_name, seconds * 0.5)] * cores)
+    px = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    cfg = config_table()[cfg_name]
+    return {"value": round(px / wall / 1e6, 4), "unit": "MPix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each running the oracle on a {cfg['w']}x{cfg['sample_rows']} band of the "
+                      f"workload for about {seconds * 0.5:.0f} s (numpy, 1 thread each)"}
 
 
 def run_reference(args, cfg_name):
