@@ -67,7 +67,10 @@ typedef enum {
                           size reference whose domain the output takes (it is not read) */
   HP_HISTOGRAM = 4,    /* 256-bin counts of a 1-channel u8 image; output 256 x 1 u32 */
   HP_CDF_LUT = 5,      /* equalization LUT (256 x 1 u8) from a histogram stage */
-  HP_LUT_APPLY = 6     /* out = lut[in] for a 1-channel u8 image */
+  HP_LUT_APPLY = 6,    /* out = lut[in] for a 1-channel u8 image */
+  HP_MAX_STENCIL = 7   /* per channel, the maximum over the (2rx+1) x (2ry+1) window at clamped
+                          coordinates (the max filter app of Sec. 6; exact in any order);
+                          rx, ry <= HP_MAX_RADIUS, no taps */
 } hp_kind;
 
 /* Point-wise operations (HP_POINTWISE).  The float expression of each is fixed
@@ -89,7 +92,10 @@ typedef enum {
   HP_OP_LL_COLOUR = 8, /* (in 3 ch, gray, out_gray) -> 3 ch: v = in*params[0];
                           (gray > 0 ? v * out_gray / gray : out_gray) * params[1] */
   HP_OP_SELECT = 9,    /* 1 input -> 1 ch: channel params[0] */
-  HP_OP_SCALE = 10     /* a * params[0] + params[1], per channel (also dtype conversion) */
+  HP_OP_SCALE = 10,    /* a * params[0] + params[1], per channel (also dtype conversion) */
+  HP_OP_PREMUL = 11,   /* 1 input, 4 ch (RGBA) -> 4 ch: (R a, G a, B a, a) (the interpolate app) */
+  HP_OP_OVER = 12,     /* (front 4 ch, back 4 ch) -> 4 ch, premultiplied: front + (1 - front.a) back */
+  HP_OP_UNPREMUL = 13  /* 1 input, 4 ch -> 3 ch: a > 0 ? c / a : 0 */
 } hp_op;
 
 #define HP_MAX_RADIUS 4
@@ -195,8 +201,11 @@ enum {
                                   of 30 coarse columns, everything in registers */
   HP_KERNEL_LL_DOWN_ROWS = 16,  /* one pyramid level down of a stack of f32 planes, streaming: one
                                   warp per strip of 30 coarse columns and 3 (or 1) planes */
-  HP_KERNEL_LL_LEVEL_ROWS = 17  /* local-Laplacian level (K = 8, f32 stages), streaming: one warp per
-                                  strip of 30 coarse (60 fine) columns, upsample windows in registers */
+  HP_KERNEL_LL_LEVEL_ROWS = 17, /* local-Laplacian level (K = 8, f32 stages), streaming: one warp per
+                                  strip of 30 coarse (60 fine) columns, upsample window in shared memory */
+  HP_KERNEL_MAX_ROWS = 18       /* max filter (one square window-maximum stage of radius 1..4, or a
+                                  horizontal and a vertical one), streaming: one warp per strip of 120
+                                  columns of one plane, a ring of row maxima in registers */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -90,7 +90,7 @@ struct GPlan {
 // expressed in the producer's coordinates, before clamping.
 HPHD Rect footprint(int kind, int slot, int rx, int ry, Rect r) {
   Rect f = r;
-  if (kind == HP_STENCIL) {
+  if (kind == HP_STENCIL || kind == HP_MAX_STENCIL) {
     f.x0 = r.x0 - rx; f.x1 = r.x1 + rx; f.y0 = r.y0 - ry; f.y1 = r.y1 + ry;
   } else if (kind == HP_DOWNSAMPLE2) {
     f.x0 = 2 * r.x0 - 2; f.x1 = 2 * r.x1 + 1; f.y0 = 2 * r.y0 - 2; f.y1 = 2 * r.y1 + 1;
@@ -150,6 +150,14 @@ struct ChainArgs {
   int epilogue;            // 0: none; 1: unsharp out = in + amount*(in - chain(in))
   float amount;
   int* err;                // device error word (bounded waits)
+};
+
+// Max filter group (k_max_rows.cu): window of radius 1..4, square (shape 0),
+// horizontal (1) or vertical (2).
+struct MaxArgs {
+  ImgView in, out;
+  int radius, shape, rows, threads;
+  int st_mid, st_out;  // storages of the two stages (the same for a one-stage group)
 };
 
 struct PointwiseArgs {
@@ -263,6 +271,9 @@ int ll_level_rows_strip_w();
 int ll_level_rows_ok(const LLLevelArgs& a);
 int ll_level_rows_grid(const LLLevelArgs& a, int units, int threads);
 int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, void* stream);
+int max_rows_strip_w();
+int max_rows_grid(const MaxArgs& a, int units, int threads);
+int launch_max_rows(const MaxArgs& a, int grid, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

@@ -63,6 +63,12 @@ __device__ float eval_node(const Ctx& k, const GNode& nd, int c, int x, int y) {
       }
       return tapn(wy, hs, 2 * nd.ry + 1);
     }
+    case HP_MAX_STENCIL: {  // exact: the maximum is the same in any order
+      float mv = fetch(k, nd.in[0], c, x - nd.rx, y - nd.ry);
+      for (int j = -nd.ry; j <= nd.ry; ++j)
+        for (int i = -nd.rx; i <= nd.rx; ++i) mv = fmaxf(mv, fetch(k, nd.in[0], c, x + i, y + j));
+      return mv;
+    }
     case HP_DOWNSAMPLE2: {
       float hs[5];
       for (int j = 0; j < 5; ++j) {
@@ -113,6 +119,12 @@ __device__ float eval_node(const Ctx& k, const GNode& nd, int c, int x, int y) {
                           P[1]);
     case HP_OP_SELECT:
       return fetch(k, nd.in[0], (int)P[0], x, y);
+    case HP_OP_PREMUL:
+      return op_premul(fetch(k, nd.in[0], c, x, y), fetch(k, nd.in[0], 3, x, y), c);
+    case HP_OP_OVER:
+      return op_over(fetch(k, nd.in[0], c, x, y), fetch(k, nd.in[0], 3, x, y), fetch(k, nd.in[1], c, x, y));
+    case HP_OP_UNPREMUL:
+      return op_unpremul(fetch(k, nd.in[0], c, x, y), fetch(k, nd.in[0], 3, x, y));
     default:  // HP_OP_SCALE
       return op_scale(fetch(k, nd.in[0], c, x, y), P[0], P[1]);
   }

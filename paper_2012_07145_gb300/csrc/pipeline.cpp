@@ -87,6 +87,7 @@ struct GroupPlan {
   HarrisArgs harris{};
   LLDownArgs lldown{};
   LLLevelArgs lllevel{};
+  MaxArgs maxa{};
   LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
@@ -183,6 +184,12 @@ hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
         return fail(HP_ERR_INVALID_ARG, "stencil radii must be in [0,%d] with taps", HP_MAX_RADIUS);
       if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
       return HP_OK;
+    case HP_MAX_STENCIL:
+      if ((s = need(1, c0))) return s;
+      if (d->rx < 0 || d->ry < 0 || d->rx > HP_MAX_RADIUS || d->ry > HP_MAX_RADIUS)
+        return fail(HP_ERR_INVALID_ARG, "max-stencil radii must be in [0,%d]", HP_MAX_RADIUS);
+      if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
+      return HP_OK;
     case HP_DOWNSAMPLE2:
       if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
       return need(1, c0);
@@ -253,6 +260,18 @@ hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
         return fail(HP_ERR_INVALID_ARG, "interp needs a K+1-channel G stack and a K-channel L stack");
       return HP_OK;
     }
+    case HP_OP_PREMUL:
+      if ((s = need(1, 4))) return s;
+      if (c0 != 4) return fail(HP_ERR_INVALID_ARG, "premultiply needs a 4-channel (RGBA) input");
+      return HP_OK;
+    case HP_OP_OVER:
+      if ((s = need(2, 4))) return s;
+      if (chan(0) != 4 || chan(1) != 4) return fail(HP_ERR_INVALID_ARG, "over needs two 4-channel inputs");
+      return HP_OK;
+    case HP_OP_UNPREMUL:
+      if ((s = need(1, 3))) return s;
+      if (c0 != 4) return fail(HP_ERR_INVALID_ARG, "unpremultiply needs a 4-channel input");
+      return HP_OK;
     case HP_OP_LL_COLOUR:
       if ((s = need(3, 3)) || (s = nparams(2))) return s;
       if (chan(0) != 3 || chan(1) != 1 || chan(2) != 1) return fail(HP_ERR_INVALID_ARG, "colour inputs: 3, 1, 1 ch");
@@ -499,6 +518,11 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     const Stage& s = p->stages[m[0]];
     switch (s.kind) {
       case HP_STENCIL: return is_r2_stencil(s) && impl != HP_IMPL_GENERIC ? HP_KERNEL_STENCIL_CHAIN : HP_KERNEL_GENERIC;
+      case HP_MAX_STENCIL: {  // square, horizontal or vertical window of radius 1..4
+        const int r = s.rx > s.ry ? s.rx : s.ry;
+        const bool shape_ok = s.rx == s.ry || s.rx == 0 || s.ry == 0;
+        return shape_ok && r >= 1 && r <= 4 && impl != HP_IMPL_GENERIC ? HP_KERNEL_MAX_ROWS : HP_KERNEL_GENERIC;
+      }
       case HP_POINTWISE: return HP_KERNEL_POINTWISE;
       case HP_DOWNSAMPLE2: return impl == HP_IMPL_GENERIC ? HP_KERNEL_GENERIC : HP_KERNEL_DOWNSAMPLE;
       case HP_UPSAMPLE2: return HP_KERNEL_UPSAMPLE;
@@ -520,6 +544,16 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY) return -1;
   }
   if (impl == HP_IMPL_GENERIC) return HP_KERNEL_GENERIC;
+  // a horizontal and a vertical window maximum of one radius (either order)
+  if (m.size() == 2) {
+    const Stage& a = p->stages[m[0]];
+    const Stage& b = p->stages[m[1]];
+    if (a.kind == HP_MAX_STENCIL && b.kind == HP_MAX_STENCIL && b.inputs[0] == m[0] && a.inputs[0] != m[1]) {
+      const int r = a.rx + a.ry;
+      if (r >= 1 && r <= 4 && a.rx * a.ry == 0 && b.rx * b.ry == 0 && b.rx + b.ry == r && a.rx != b.rx)
+        return HP_KERNEL_MAX_ROWS;
+    }
+  }
   // linear chain of 5x5 stencils
   bool chain = (int)m.size() <= kChainMax;
   for (size_t i = 0; i < m.size() && chain; ++i) {
@@ -1147,6 +1181,44 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         }
         break;
       }
+      case HP_KERNEL_MAX_ROWS: {
+        const Stage& first = p->stages[gp.members[0]];
+        const Stage& last = p->stages[gp.output];
+        MaxArgs& a = gp.maxa;
+        memset(&a, 0, sizeof a);
+        if (gp.members.size() == 1) {
+          a.radius = first.rx > first.ry ? first.rx : first.ry;
+          a.shape = first.rx == first.ry ? 0 : first.ry == 0 ? 1 : 2;
+        } else {
+          a.radius = first.rx + first.ry;
+          a.shape = 0;
+        }
+        a.st_mid = first.storage;
+        a.st_out = last.storage;
+        gp.ext_refs.assign(1, first.inputs[0]);
+        gp.tile_w = max_rows_strip_w();
+        gp.threads = pick(p->threads, g, 256);
+        if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256) {
+          s = fail(HP_ERR_SCHEDULE, "streaming max filter threads per block must be a multiple of 32 in [32, 256]");
+          break;
+        }
+        a.threads = gp.threads;
+        Dom od = plan.dom[gp.output];
+        const int planes = last.channels;
+        const int strips = (od.w + gp.tile_w - 1) / gp.tile_w;
+        gp.tile_h = pick(p->tile_h, g, 0);
+        if (gp.tile_h == 0) {
+          a.in.dtype = stage_dtype_of_ref(p, first.inputs[0]);
+          gp.tile_h = default_run_rows(od.h, strips * planes,
+                                       (long long)max_rows_grid(a, 1 << 30, gp.threads) * (gp.threads / 32));
+        }
+        a.rows = gp.tile_h;
+        a.in.dtype = stage_dtype_of_ref(p, first.inputs[0]);
+        gp.grid_x = max_rows_grid(a, strips * planes * ((od.h + a.rows - 1) / a.rows), gp.threads);
+        gp.grid_y = 1;
+        gp.smem = 0;
+        break;
+      }
       case HP_KERNEL_HISTEQ: {
         Dom od = plan.dom[gp.output];
         gp.threads = 1024;
@@ -1314,6 +1386,13 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
         e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_MAX_ROWS: {
+        MaxArgs a = gp.maxa;
+        a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        e = launch_max_rows(a, gp.grid_x, stream);
         break;
       }
       case HP_KERNEL_LL_REMAP_ROWS:
@@ -1766,7 +1845,7 @@ namespace hp {
 // stacked plane-wise into one image of B times the channels.
 bool pipeline_stackable(const hp_pipeline* p) {
   for (const Stage& s : p->stages) {
-    if (s.kind == HP_STENCIL || s.kind == HP_DOWNSAMPLE2 || s.kind == HP_UPSAMPLE2) continue;
+    if (s.kind == HP_STENCIL || s.kind == HP_MAX_STENCIL || s.kind == HP_DOWNSAMPLE2 || s.kind == HP_UPSAMPLE2) continue;
     if (s.kind == HP_POINTWISE && (s.op == HP_OP_MUL || s.op == HP_OP_ADD || s.op == HP_OP_SUB ||
                                    s.op == HP_OP_UNSHARP || s.op == HP_OP_SCALE))
       continue;

@@ -171,4 +171,14 @@ __device__ __forceinline__ float op_binary(int op, float a, float b) {
 
 __device__ __forceinline__ float op_scale(float a, float s, float o) { return __fmaf_rn(a, s, o); }
 
+// Interpolate app: premultiplied colour, compositing of a level over the
+// upsampled coarser result, and the final division by coverage.
+__device__ __forceinline__ float op_premul(float v, float a, int c) { return c < 3 ? __fmul_rn(v, a) : a; }
+
+__device__ __forceinline__ float op_over(float front, float front_a, float back) {
+  return __fmaf_rn(__fsub_rn(1.0f, front_a), back, front);
+}
+
+__device__ __forceinline__ float op_unpremul(float v, float a) { return a > 0.0f ? __fdiv_rn(v, a) : 0.0f; }
+
 }  // namespace hp

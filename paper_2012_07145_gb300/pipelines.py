@@ -187,3 +187,86 @@ def local_laplacian_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, th
     heights = [t if (generic or t) else rows for t in tiles]
     p.schedule(groups, tile_w=tiles, tile_h=heights, threads=[threads] * gid,
                impl=[impl] * gid if impl is not None else None)
+
+
+def max_filter(radius: int = 4, channels: int = 3, storage: int = hp.HP_F32, io_storage: int = None) -> hp.Pipeline:
+    """Max filter (Sec. 6 app list): per channel, the maximum over the
+    (2 radius + 1)^2 window at clamped coordinates, as a horizontal and a
+    vertical window-maximum stage (radius <= HP_MAX_RADIUS each)."""
+    io = storage if io_storage is None else io_storage
+    p = hp.Pipeline([io], [channels])
+    h = p.add_stage(hp.HP_MAX_STENCIL, [p.input(0)], channels, storage, rx=radius, ry=0)
+    v = p.add_stage(hp.HP_MAX_STENCIL, [h], channels, io, rx=0, ry=radius)
+    p.set_output(v)
+    return p
+
+
+def interpolate(levels: int = 10) -> tuple:
+    """Interpolate (Sec. 6 app list): fill the uncovered pixels of an RGBA f32
+    image (alpha = coverage) from premultiplied pyramids:
+    D_0 = premultiply(in), D_l = downsample(D_{l-1}); I_{J-1} = D_{J-1},
+    I_l = D_l over upsample(I_{l+1}); out = I_0.rgb / I_0.a (0 where a = 0).
+    Returns (pipeline, stage-id map)."""
+    J = levels
+    F = hp.HP_F32
+    p = hp.Pipeline([F], [4])
+    D = [p.add_stage(hp.HP_POINTWISE, [p.input(0)], 4, F, op=hp.HP_OP_PREMUL)]
+    for _ in range(1, J):
+        D.append(p.add_stage(hp.HP_DOWNSAMPLE2, [D[-1]], 4, F))
+    I = [None] * J
+    U = [None] * J
+    I[J - 1] = D[J - 1]
+    for l in range(J - 2, -1, -1):
+        U[l] = p.add_stage(hp.HP_UPSAMPLE2, [I[l + 1], D[l]], 4, F)
+        I[l] = p.add_stage(hp.HP_POINTWISE, [D[l], U[l]], 4, F, op=hp.HP_OP_OVER)
+    out = p.add_stage(hp.HP_POINTWISE, [I[0]], 3, F, op=hp.HP_OP_UNPREMUL)
+    p.set_output(out)
+    return p, dict(D=D, U=U, I=I, out=out)
+
+
+def interpolate_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None,
+                               down_tile: int = 0):
+    """Per level: the premultiplied image in its own kernel (read by the first
+    downsample and the finest composite); one downsample kernel per coarser
+    level (default: the streaming plane kernel); one kernel per level for the
+    upsample and the composite, the finest one with the final division."""
+    D, U, I, out = ids["D"], ids["U"], ids["I"], ids["out"]
+    J = len(D)
+    n = len(p.stages)
+    groups = [None] * n
+    groups[D[0]] = 0
+    gid = 1
+    down_groups = []
+    for l in range(1, J):
+        groups[D[l]] = gid
+        down_groups.append(gid)
+        gid += 1
+    for l in range(J - 2, -1, -1):
+        groups[U[l]] = gid
+        groups[I[l]] = gid
+        if l == 0:
+            groups[out] = gid
+        gid += 1
+    if J == 1:   # no pyramid: the premultiply and the division
+        groups[out] = gid
+        gid += 1
+    assert all(g is not None for g in groups)
+    generic = impl == hp.HP_IMPL_GENERIC
+    tiles = [tile if (generic or g not in down_groups) else down_tile for g in range(gid)]
+    p.schedule(groups, tile_w=tiles, tile_h=tiles, threads=[threads] * gid,
+               impl=[impl] * gid if impl is not None else None)
+
+
+def interpolate_finest(levels_below: int = 1) -> hp.Pipeline:
+    """The finest group of the interpolate pipeline on its own: inputs the
+    RGBA image and I_1 (4 channels at half size); premultiply (inlined),
+    upsample of I_1, composite, division by coverage (one kernel)."""
+    F = hp.HP_F32
+    p = hp.Pipeline([F, F], [4, 4])
+    d0 = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 4, F, op=hp.HP_OP_PREMUL)
+    u0 = p.add_stage(hp.HP_UPSAMPLE2, [p.input(1), d0], 4, F)
+    i0 = p.add_stage(hp.HP_POINTWISE, [d0, u0], 4, F, op=hp.HP_OP_OVER)
+    out = p.add_stage(hp.HP_POINTWISE, [i0], 3, F, op=hp.HP_OP_UNPREMUL)
+    p.set_output(out)
+    p.schedule([hp.HP_INLINE, 0, 0, 0], tile_w=[32], tile_h=[32], threads=[256])
+    return p

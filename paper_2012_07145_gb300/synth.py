@@ -83,3 +83,12 @@ def gray_u8_lowcontrast(h: int, w: int, seed: int = 0) -> np.ndarray:
     """uint8 [1][H][W]: clamp(rint(N(100, 20)), 0, 255) (histogram-equalize workload)."""
     v = 100.0 + 20.0 * gaussian_f64((1, h, w), seed, stream=5)
     return np.clip(np.rint(v), 0, 255).astype(np.uint8)
+
+
+def rgba_sparse_f32(h: int, w: int, seed: int = 0, coverage: float = 0.25) -> np.ndarray:
+    """Planar float32 RGBA [4][H][W] for the interpolate workload: RGB uniform
+    [0,1); alpha 1 on a seeded random fraction `coverage` of the pixels (the
+    samples to interpolate between), 0 elsewhere."""
+    rgb = uniform_f32((3, h, w), seed, stream=6)
+    a = (uniform_f32((1, h, w), seed, stream=7) < coverage).astype(np.float32)
+    return np.concatenate([rgb, a])
