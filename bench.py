@@ -219,18 +219,22 @@ def config_table():
     # dominant kernel: the finest group (premultiply, upsample of I_1, composite,
     # division by coverage) timed alone; algorithmic bytes per fine pixel: the
     # RGBA input 16, I_1 at a quarter of the pixels 4, the RGB output 12
-    interp_dominant = dict(kernel="k_generic", bound="hbm", bytes_per_launch=32 * W * H,
-                           algorithmic="32 bytes per fine pixel (RGBA input 16, the 4-channel level 1 at a quarter "
-                                       "of the pixels 4, RGB output 12)",
+    def premultiplied(seed):
+        x = synth.rgba_sparse_f32(H, W, seed=seed)
+        return np.concatenate([x[:3] * x[3:4], x[3:4]]).astype(np.float32)
+
+    interp_dominant = dict(kernel="k_interp_rows", bound="hbm", bytes_per_launch=32 * W * H,
+                           algorithmic="32 bytes per fine pixel (premultiplied RGBA level 0 16, the 4-channel level 1 "
+                                       "at a quarter of the pixels 4, RGB output 12)",
                            build=lambda: pipelines.interpolate_finest(),
-                           inputs=lambda seed: [(synth.rgba_sparse_f32(H, W, seed=seed), hp.HP_F32),
+                           inputs=lambda seed: [(premultiplied(seed), hp.HP_F32),
                                                 (synth.uniform_f32((4, (H + 1) // 2, (W + 1) // 2), seed, stream=8),
                                                  hp.HP_F32)],
                            out=(3, H, W, hp.HP_F32))
     cfgs["interpolate"] = dict(workload=f"interpolate_rgba_{W}x{H}_J10_f32", h=H, w=W,
                                inputs=lambda seed: [(synth.rgba_sparse_f32(H, W, seed=seed), hp.HP_F32)],
                                out=(3, H, W, hp.HP_F32), build=interp_build, fused=interp_fused,
-                               flops_px=0, bytes_px=28, bound="hbm", kernel="k_generic", dtype="f32",
+                               flops_px=0, bytes_px=28, bound="hbm", kernel="k_interp_rows", dtype="f32",
                                dominant=interp_dominant, oracle_sample=interp_sample, parity=interp_parity,
                                sample_rows=64)
     return cfgs

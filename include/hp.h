@@ -203,9 +203,15 @@ enum {
                                   warp per strip of 30 coarse columns and 3 (or 1) planes */
   HP_KERNEL_LL_LEVEL_ROWS = 17, /* local-Laplacian level (K = 8, f32 stages), streaming: one warp per
                                   strip of 30 coarse (60 fine) columns, upsample window in shared memory */
-  HP_KERNEL_MAX_ROWS = 18       /* max filter (one square window-maximum stage of radius 1..4, or a
+  HP_KERNEL_MAX_ROWS = 18,      /* max filter (one square window-maximum stage of radius 1..4, or a
                                   horizontal and a vertical one), streaming: one warp per strip of 120
                                   columns of one plane, a ring of row maxima in registers */
+  HP_KERNEL_INTERP_ROWS = 19,   /* interpolate level (upsample, composite, optional division by
+                                  coverage; f32 RGBA), streaming: one warp per strip of 30 coarse
+                                  columns, upsample window in registers */
+  HP_KERNEL_PW_ROWS = 20        /* one point-wise stage over f32 images (add, sub, mul, scale,
+                                  unsharp combine, premultiply, over, unpremultiply): 4 pixels per
+                                  thread, 128-bit loads and stores */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -160,6 +160,21 @@ struct MaxArgs {
   int st_mid, st_out;  // storages of the two stages (the same for a one-stage group)
 };
 
+// Interpolate level group (k_interp_rows.cu): I = D over U(coarse), optionally
+// followed by the division by coverage.
+struct InterpArgs {
+  ImgView fine, coarse, out;  // D_l (4 ch), I_{l+1} (4 ch), the group's output
+  int rows, threads, final_div, vec;
+};
+
+// One point-wise stage over f32 images (k_pointwise.cu).
+struct PwArgs {
+  ImgView in[HP_MAX_INPUTS];
+  ImgView out;
+  int n_in, op;
+  float p0, p1;
+};
+
 struct PointwiseArgs {
   int op, n_in, channels, storage;
   ImgView in[HP_MAX_INPUTS];
@@ -274,6 +289,11 @@ int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, 
 int max_rows_strip_w();
 int max_rows_grid(const MaxArgs& a, int units, int threads);
 int launch_max_rows(const MaxArgs& a, int grid, void* stream);
+int interp_rows_strip_w();
+int interp_rows_grid(const InterpArgs& a, int units, int threads);
+int launch_interp_rows(const InterpArgs& a, int grid, void* stream);
+int pw_rows_op_ok(int op);
+int launch_pw_rows(const PwArgs& p, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

@@ -88,6 +88,8 @@ struct GroupPlan {
   LLDownArgs lldown{};
   LLLevelArgs lllevel{};
   MaxArgs maxa{};
+  InterpArgs interp{};
+  PwArgs pw{};
   LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
@@ -523,7 +525,11 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
         const bool shape_ok = s.rx == s.ry || s.rx == 0 || s.ry == 0;
         return shape_ok && r >= 1 && r <= 4 && impl != HP_IMPL_GENERIC ? HP_KERNEL_MAX_ROWS : HP_KERNEL_GENERIC;
       }
-      case HP_POINTWISE: return HP_KERNEL_POINTWISE;
+      case HP_POINTWISE: {  // f32 per-channel and RGBA ops: the vectorised point-wise kernel
+        bool f32 = s.storage == HP_F32 && impl != HP_IMPL_GENERIC && pw_rows_op_ok(s.op);
+        for (int r : s.inputs) f32 = f32 && stage_dtype_of_ref(p, r) == HP_F32;
+        return f32 ? HP_KERNEL_PW_ROWS : HP_KERNEL_POINTWISE;
+      }
       case HP_DOWNSAMPLE2: return impl == HP_IMPL_GENERIC ? HP_KERNEL_GENERIC : HP_KERNEL_DOWNSAMPLE;
       case HP_UPSAMPLE2: return HP_KERNEL_UPSAMPLE;
       case HP_HISTOGRAM: return HP_KERNEL_HISTOGRAM;
@@ -544,6 +550,21 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY) return -1;
   }
   if (impl == HP_IMPL_GENERIC) return HP_KERNEL_GENERIC;
+  // interpolate level: upsample of a coarse image, composite with the fine
+  // level (and the division by coverage), every stage f32
+  if (m.size() == 2 || m.size() == 3) {
+    const Stage& u = p->stages[m[0]];
+    const Stage& o = p->stages[m[1]];
+    bool ok = u.kind == HP_UPSAMPLE2 && o.kind == HP_POINTWISE && o.op == HP_OP_OVER && o.inputs[1] == m[0] &&
+              o.inputs[0] == u.inputs[1] && o.inputs[0] != m[0] && u.inputs[0] != m[1] && u.channels == 4 &&
+              u.storage == HP_F32 && o.storage == HP_F32 && stage_dtype_of_ref(p, u.inputs[0]) == HP_F32 &&
+              stage_dtype_of_ref(p, o.inputs[0]) == HP_F32 && stage_channels_of_ref(p, u.inputs[0]) == 4;
+    if (ok && m.size() == 3) {
+      const Stage& d = p->stages[m[2]];
+      ok = d.kind == HP_POINTWISE && d.op == HP_OP_UNPREMUL && d.inputs[0] == m[1] && d.storage == HP_F32;
+    }
+    if (ok) return HP_KERNEL_INTERP_ROWS;
+  }
   // a horizontal and a vertical window maximum of one radius (either order)
   if (m.size() == 2) {
     const Stage& a = p->stages[m[0]];
@@ -612,6 +633,9 @@ size_t scratch_bytes(const Stage& s, Dom d) {
   ImgView v = scratch_view(s, d, nullptr);
   return (size_t)(v.ps * v.c);
 }
+
+// Domain of a reference: a stage's, or a pipeline input's (ref < 0).
+Dom dom_of_ref(const Plan& plan, int ref) { return ref < 0 ? plan.in_dom[-1 - ref] : plan.dom[ref]; }
 
 int pick(const std::vector<int>& v, int g, int dflt) {
   return g < (int)v.size() && v[g] > 0 ? v[g] : dflt;
@@ -1046,7 +1070,7 @@ hp_status build_ll_level_rows(const hp_pipeline* p, const Plan& plan, GroupPlan&
                 gp.tile_w);
   if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256)
     return fail(HP_ERR_SCHEDULE, "streaming level threads per block must be a multiple of 32 in [32, 256]");
-  const Dom cd = plan.dom[gp.llroles.Gn];
+  const Dom cd = dom_of_ref(plan, gp.llroles.Gn);
   const int strips = (cd.w + gp.tile_w - 1) / gp.tile_w;
   if (gp.tile_h == 0) {
     const long long warps = (long long)ll_level_rows_grid(probe, 1 << 30, gp.threads) * (gp.threads / 32);
@@ -1219,6 +1243,45 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.smem = 0;
         break;
       }
+      case HP_KERNEL_PW_ROWS: {
+        const Stage& st = p->stages[gp.output];
+        PwArgs& a = gp.pw;
+        memset(&a, 0, sizeof a);
+        a.op = st.op;
+        a.n_in = (int)st.inputs.size();
+        a.p0 = st.params.size() > 0 ? st.params[0] : 0.0f;
+        a.p1 = st.params.size() > 1 ? st.params[1] : 0.0f;
+        gp.ext_refs = st.inputs;
+        gp.threads = 256;
+        break;
+      }
+      case HP_KERNEL_INTERP_ROWS: {
+        const Stage& u = p->stages[gp.members[0]];
+        const Stage& o = p->stages[gp.members[1]];
+        InterpArgs& a = gp.interp;
+        memset(&a, 0, sizeof a);
+        a.final_div = gp.members.size() == 3;
+        gp.ext_refs.assign({o.inputs[0], u.inputs[0]});  // the fine level, the coarse image
+        gp.tile_w = interp_rows_strip_w();
+        gp.threads = pick(p->threads, g, 256);
+        if (gp.threads % 32 != 0 || gp.threads < 32 || gp.threads > 256) {
+          s = fail(HP_ERR_SCHEDULE, "streaming interpolate threads per block must be a multiple of 32 in [32, 256]");
+          break;
+        }
+        a.threads = gp.threads;
+        const Dom cd = dom_of_ref(plan, u.inputs[0]);
+        const int strips = (cd.w + gp.tile_w - 1) / gp.tile_w;
+        gp.tile_h = pick(p->tile_h, g, 0);
+        if (gp.tile_h == 0) {
+          const long long warps = (long long)interp_rows_grid(a, 1 << 30, gp.threads) * (gp.threads / 32);
+          gp.tile_h = (int)std::max(2LL, ((long long)cd.h * strips + warps - 1) / warps);
+        }
+        a.rows = gp.tile_h;
+        gp.grid_x = interp_rows_grid(a, strips * ((cd.h + a.rows - 1) / a.rows), gp.threads);
+        gp.grid_y = 1;
+        gp.smem = 0;
+        break;
+      }
       case HP_KERNEL_HISTEQ: {
         Dom od = plan.dom[gp.output];
         gp.threads = 1024;
@@ -1386,6 +1449,21 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
         e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_PW_ROWS: {
+        PwArgs a = gp.pw;
+        for (int i = 0; i < a.n_in; ++i) a.in[i] = ref_view(p, plan, gp.ext_refs[i], inputs, output);
+        a.out = out;
+        e = launch_pw_rows(a, stream);
+        break;
+      }
+      case HP_KERNEL_INTERP_ROWS: {
+        InterpArgs a = gp.interp;
+        a.fine = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.coarse = ref_view(p, plan, gp.ext_refs[1], inputs, output);
+        a.out = out;
+        e = launch_interp_rows(a, gp.grid_x, stream);
         break;
       }
       case HP_KERNEL_MAX_ROWS: {

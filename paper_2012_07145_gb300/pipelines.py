@@ -225,11 +225,14 @@ def interpolate(levels: int = 10) -> tuple:
 
 
 def interpolate_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, threads: int = 256, impl=None,
-                               down_tile: int = 0):
+                               down_tile: int = 0, level_tile: int = 0):
     """Per level: the premultiplied image in its own kernel (read by the first
     downsample and the finest composite); one downsample kernel per coarser
     level (default: the streaming plane kernel); one kernel per level for the
-    upsample and the composite, the finest one with the final division."""
+    upsample and the composite, the finest one with the final division.
+    down_tile / level_tile = 0 take each kernel's default (the streaming
+    kernels with run lengths sized per level); tile sizes the premultiply and,
+    under the generic interpreter, every group."""
     D, U, I, out = ids["D"], ids["U"], ids["I"], ids["out"]
     J = len(D)
     n = len(p.stages)
@@ -252,21 +255,20 @@ def interpolate_fused_schedule(p: hp.Pipeline, ids: dict, tile: int = 32, thread
         gid += 1
     assert all(g is not None for g in groups)
     generic = impl == hp.HP_IMPL_GENERIC
-    tiles = [tile if (generic or g not in down_groups) else down_tile for g in range(gid)]
+    tiles = [tile if (generic or g == 0) else (down_tile if g in down_groups else level_tile) for g in range(gid)]
     p.schedule(groups, tile_w=tiles, tile_h=tiles, threads=[threads] * gid,
                impl=[impl] * gid if impl is not None else None)
 
 
-def interpolate_finest(levels_below: int = 1) -> hp.Pipeline:
-    """The finest group of the interpolate pipeline on its own: inputs the
-    RGBA image and I_1 (4 channels at half size); premultiply (inlined),
-    upsample of I_1, composite, division by coverage (one kernel)."""
+def interpolate_finest() -> hp.Pipeline:
+    """The finest group of the interpolate pipeline on its own: inputs D_0
+    (the premultiplied RGBA image) and I_1 (4 channels at half size); upsample
+    of I_1, composite, division by coverage, in one kernel."""
     F = hp.HP_F32
     p = hp.Pipeline([F, F], [4, 4])
-    d0 = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 4, F, op=hp.HP_OP_PREMUL)
-    u0 = p.add_stage(hp.HP_UPSAMPLE2, [p.input(1), d0], 4, F)
-    i0 = p.add_stage(hp.HP_POINTWISE, [d0, u0], 4, F, op=hp.HP_OP_OVER)
+    u0 = p.add_stage(hp.HP_UPSAMPLE2, [p.input(1), p.input(0)], 4, F)
+    i0 = p.add_stage(hp.HP_POINTWISE, [p.input(0), u0], 4, F, op=hp.HP_OP_OVER)
     out = p.add_stage(hp.HP_POINTWISE, [i0], 3, F, op=hp.HP_OP_UNPREMUL)
     p.set_output(out)
-    p.schedule([hp.HP_INLINE, 0, 0, 0], tile_w=[32], tile_h=[32], threads=[256])
+    p.schedule([0, 0, 0])
     return p

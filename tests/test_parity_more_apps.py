@@ -90,8 +90,11 @@ def test_interpolate_against_oracle_and_schedules(h, w, levels):
     err = float(np.abs(to_numpy(plain).astype(np.float64) - ref).max())
     print(f"interpolate {w}x{h} J={levels}: max abs err {err:.3e}")
     assert err <= INTERP_TOL
-    for kw in (dict(), dict(down_tile=16), dict(impl=hp.HP_IMPL_GENERIC, tile=16), dict(tile=64, threads=128)):
+    for kw in (dict(), dict(down_tile=16), dict(impl=hp.HP_IMPL_GENERIC, tile=16), dict(tile=64, threads=128),
+               dict(level_tile=1, threads=32), dict(level_tile=3, threads=96), dict(level_tile=40)):
         pipelines.interpolate_fused_schedule(p, ids, **kw)
+        if levels > 1 and not kw.get("impl"):   # the composites run on the streaming level kernel
+            assert p.group_info([(w, h)], p.group_count() - 1).kernel == hp.HP_KERNEL_INTERP_ROWS
         assert torch.equal(bits(run(p, [x], [hp.HP_F32], (3, h, w), hp.HP_F32)), bits(plain)), kw
 
 
