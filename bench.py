@@ -231,6 +231,37 @@ def config_table():
                                                 (synth.uniform_f32((4, (H + 1) // 2, (W + 1) // 2), seed, stream=8),
                                                  hp.HP_F32)],
                            out=(3, H, W, hp.HP_F32))
+    def bg_sample(rows):
+        from oracle import bilateral_grid as ob
+        img = synth.gray_f32_gradient_noise(rows, W, seed=0)[0]
+        return lambda: ob.bilateral_grid(img, 8, 0.1)
+
+    def bg_parity(out, inputs):
+        from oracle import bilateral_grid as ob
+        ref = ob.bilateral_grid(inputs[0][0][0][:96], 8, 0.1)[:64]   # rows whose grid cells lie inside the band
+        return float(np.abs(out[0][:64].astype(np.float64) - ref).max())
+
+    def bg_grid(seed):
+        # a blurred-grid-like input for the slice alone: values in [0, w], weights in [1, 64]
+        gx, gy = (W + 7) // 8 + 1, (H + 7) // 8 + 1
+        wts = 1.0 + 63.0 * synth.uniform_f32((11, gy, gx), seed, stream=10)
+        vals = wts * synth.uniform_f32((11, gy, gx), seed, stream=11)
+        return np.stack([vals, wts], axis=1).reshape(22, gy, gx).astype(np.float32)
+
+    bg_dominant = dict(kernel="k_grid_slice", bound="hbm", bytes_per_launch=8 * W * H + 22 * 4 * ((W + 7) // 8 + 1) * ((H + 7) // 8 + 1),
+                       algorithmic="8 bytes per pixel (the image read, the output written) plus the grid "
+                                   "(22 channels x 321 x 193 cells x 4 bytes) read once",
+                       build=lambda: pipelines.bilateral_grid_slice_only(8, 0.1),
+                       inputs=lambda seed: [(bg_grid(seed), hp.HP_F32),
+                                            (synth.gray_f32_gradient_noise(H, W, seed=seed), hp.HP_F32)],
+                       out=(1, H, W, hp.HP_F32))
+    cfgs["bilateral"] = dict(workload=f"bilateral_grid_gray_{W}x{H}_s8_r0.1_f32", h=H, w=W,
+                             inputs=lambda seed: [(synth.gray_f32_gradient_noise(H, W, seed=seed), hp.HP_F32)],
+                             out=(1, H, W, hp.HP_F32), build=lambda: pipelines.bilateral_grid(8, 0.1),
+                             fused=lambda p: pipelines.bilateral_grid_fused_schedule(p),
+                             flops_px=0, bytes_px=8, bound="hbm", kernel="k_grid_slice", dtype="f32",
+                             dominant=bg_dominant, oracle_sample=bg_sample, parity=bg_parity, sample_rows=64)
+
     cfgs["interpolate"] = dict(workload=f"interpolate_rgba_{W}x{H}_J10_f32", h=H, w=W,
                                inputs=lambda seed: [(synth.rgba_sparse_f32(H, W, seed=seed), hp.HP_F32)],
                                out=(3, H, W, hp.HP_F32), build=interp_build, fused=interp_fused,

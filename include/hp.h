@@ -68,9 +68,19 @@ typedef enum {
   HP_HISTOGRAM = 4,    /* 256-bin counts of a 1-channel u8 image; output 256 x 1 u32 */
   HP_CDF_LUT = 5,      /* equalization LUT (256 x 1 u8) from a histogram stage */
   HP_LUT_APPLY = 6,    /* out = lut[in] for a 1-channel u8 image */
-  HP_MAX_STENCIL = 7   /* per channel, the maximum over the (2rx+1) x (2ry+1) window at clamped
+  HP_MAX_STENCIL = 7,  /* per channel, the maximum over the (2rx+1) x (2ry+1) window at clamped
                           coordinates (the max filter app of Sec. 6; exact in any order);
                           rx, ry <= HP_MAX_RADIUS, no taps */
+  HP_GRID_SPLAT = 8,   /* bilateral grid (the bilateral grid app of Sec. 6): a 1-channel image
+                          v -> a grid of (ceil(W/s)+1) x (ceil(H/s)+1) cells x 2 GZ channels,
+                          GZ = floor(1/r + 1/2) + 1; cell (gx, gy) takes the s x s pixels
+                          (clamp(gx s + i - s/2), clamp(gy s + j - s/2)) and adds (v, 1),
+                          v = clamp(I, 0, 1), to channels 2z and 2z+1, z = floor(v (1/r) + 1/2)
+                          in f32, clamped; params = {s, r} */
+  HP_GRID_SLICE = 9    /* (grid, 1-channel image) -> 1 channel at the image's size: trilinear
+                          interpolation of the grid's value and weight at (x/s, y/s, v/r),
+                          indices clamped; out = value / weight (v where the weight is 0);
+                          params = {s, r} */
 } hp_kind;
 
 /* Point-wise operations (HP_POINTWISE).  The float expression of each is fixed
@@ -95,7 +105,9 @@ typedef enum {
   HP_OP_SCALE = 10,    /* a * params[0] + params[1], per channel (also dtype conversion) */
   HP_OP_PREMUL = 11,   /* 1 input, 4 ch (RGBA) -> 4 ch: (R a, G a, B a, a) (the interpolate app) */
   HP_OP_OVER = 12,     /* (front 4 ch, back 4 ch) -> 4 ch, premultiplied: front + (1 - front.a) back */
-  HP_OP_UNPREMUL = 13  /* 1 input, 4 ch -> 3 ch: a > 0 ? c / a : 0 */
+  HP_OP_UNPREMUL = 13, /* 1 input, 4 ch -> 3 ch: a > 0 ? c / a : 0 */
+  HP_OP_ZBLUR = 14     /* bilateral grid, 2 GZ ch -> 2 GZ ch: [1,4,6,4,1]/16 along the range
+                          levels (channel 2z + k from channels 2 clamp(z + j) + k), params = {GZ} */
 } hp_op;
 
 #define HP_MAX_RADIUS 4
@@ -209,9 +221,12 @@ enum {
   HP_KERNEL_INTERP_ROWS = 19,   /* interpolate level (upsample, composite, optional division by
                                   coverage; f32 RGBA), streaming: one warp per strip of 30 coarse
                                   columns, upsample window in registers */
-  HP_KERNEL_PW_ROWS = 20        /* one point-wise stage over f32 images (add, sub, mul, scale,
+  HP_KERNEL_PW_ROWS = 20,       /* one point-wise stage over f32 images (add, sub, mul, scale,
                                   unsharp combine, premultiply, over, unpremultiply): 4 pixels per
                                   thread, 128-bit loads and stores */
+  HP_KERNEL_GRID_SPLAT = 21,    /* bilateral grid splat: one thread per cell, accumulators in
+                                  shared memory */
+  HP_KERNEL_GRID_SLICE = 22     /* bilateral grid slice: one thread per pixel, trilinear */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -23,8 +23,13 @@ import numpy as np
 B5 = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
 
 
+def _r32(r: float) -> float:
+    """The range cell size as the f32 parameter the pipeline is given."""
+    return float(np.float32(r))
+
+
 def levels(r: float) -> int:
-    return int(np.floor(1.0 / r + 0.5)) + 1
+    return int(np.floor(1.0 / _r32(r) + 0.5)) + 1
 
 
 def grid_size(w: int, h: int, s: int):
@@ -34,7 +39,7 @@ def grid_size(w: int, h: int, s: int):
 def range_level(v: np.ndarray, r: float, gz: int) -> np.ndarray:
     """floor(v * (1/r) + 1/2) with the product and the sum rounded once to f32
     (the exact product of two f32 values fits in f64)."""
-    inv_r = np.float64(np.float32(1.0 / r))
+    inv_r = np.float64(np.float32(1.0 / _r32(r)))
     zf = (np.asarray(v, dtype=np.float32).astype(np.float64) * inv_r + 0.5).astype(np.float32)
     return np.clip(np.floor(zf.astype(np.float64)).astype(np.int64), 0, gz - 1)
 

@@ -167,6 +167,15 @@ struct InterpArgs {
   int rows, threads, final_div, vec;
 };
 
+// Bilateral grid splat / slice (k_grid.cu).
+struct GridArgs {
+  ImgView in;    // the 1-channel image
+  ImgView grid;  // (ceil(W/s)+1) x (ceil(H/s)+1), 2 gz channels
+  ImgView out;   // slice: the 1-channel output
+  int s, gz;
+  float inv_s, inv_r;
+};
+
 // One point-wise stage over f32 images (k_pointwise.cu).
 struct PwArgs {
   ImgView in[HP_MAX_INPUTS];
@@ -294,6 +303,9 @@ int interp_rows_grid(const InterpArgs& a, int units, int threads);
 int launch_interp_rows(const InterpArgs& a, int grid, void* stream);
 int pw_rows_op_ok(int op);
 int launch_pw_rows(const PwArgs& p, void* stream);
+int grid_max_levels();
+int launch_grid_splat(const GridArgs& a, void* stream);
+int launch_grid_slice(const GridArgs& a, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

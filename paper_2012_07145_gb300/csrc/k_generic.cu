@@ -125,6 +125,12 @@ __device__ float eval_node(const Ctx& k, const GNode& nd, int c, int x, int y) {
       return op_over(fetch(k, nd.in[0], c, x, y), fetch(k, nd.in[0], 3, x, y), fetch(k, nd.in[1], c, x, y));
     case HP_OP_UNPREMUL:
       return op_unpremul(fetch(k, nd.in[0], c, x, y), fetch(k, nd.in[0], 3, x, y));
+    case HP_OP_ZBLUR: {  // along the range levels: channel 2z + q from 2 clamp(z + j) + q
+      const int gz = (int)P[0], z = c >> 1, q = c & 1;
+      float t[5];
+      for (int j = 0; j < 5; ++j) t[j] = fetch(k, nd.in[0], 2 * iclamp(z + j - 2, 0, gz - 1) + q, x, y);
+      return tap5_binomial16(t[0], t[1], t[2], t[3], t[4]);
+    }
     default:  // HP_OP_SCALE
       return op_scale(fetch(k, nd.in[0], c, x, y), P[0], P[1]);
   }

@@ -1,0 +1,114 @@
+// Bilateral grid (the bilateral grid app of Sec. 6, after Chen, Paris and
+// Durand): the splat of a gray image into a grid of s x s pixel cells and
+// range levels of size r, and the trilinear slice of the blurred grid back to
+// the image.  The grid is a (ceil(W/s)+1) x (ceil(H/s)+1) image of 2 GZ
+// channels: channel 2z holds the sum of the values of range level z, channel
+// 2z+1 their count.  (The blur between them is a point-wise op along the range
+// levels and two 5-tap stencils: the generic kernels.)
+//
+// k_grid_splat: one thread per cell; it walks the cell's s x s pixels in row
+//   order and adds each to its range level's pair of accumulators, which sit
+//   in shared memory (word channel x 128 + thread: every access of a warp hits
+//   32 banks), so the sums are formed in the same order every time.
+// k_grid_slice: one thread per pixel; trilinear interpolation (x, then y, then
+//   the range level) of the value and the weight, then their ratio.
+#include <cuda_runtime.h>
+
+#include "hp_internal.h"
+#include "stage_math.cuh"
+
+namespace hp {
+
+namespace {
+
+constexpr int kSplatThreads = 128;
+constexpr int kMaxGZ = 31;
+
+__device__ __forceinline__ float gray_at(const ImgView& v, int x, int y) {
+  return fminf(fmaxf(load_px(v, 0, x, y), 0.0f), 1.0f);
+}
+
+__device__ __forceinline__ int range_level(float v, float inv_r, int gz) {
+  return iclamp((int)floorf(__fmaf_rn(v, inv_r, 0.5f)), 0, gz - 1);
+}
+
+__global__ void __launch_bounds__(kSplatThreads) k_grid_splat(const GridArgs a) {
+  grid_dep_sync();
+  __shared__ float acc[2 * kMaxGZ * kSplatThreads];
+  const int t = threadIdx.x;
+  const int gx = blockIdx.x * kSplatThreads + t, gy = blockIdx.y;
+  if (gx >= a.grid.w) return;  // no barrier below: each thread owns its column of acc
+  for (int j = 0; j < 2 * a.gz; ++j) acc[j * kSplatThreads + t] = 0.0f;
+  const int W = a.in.w, H = a.in.h, s = a.s;
+  for (int j = 0; j < s; ++j) {
+    const int y = iclamp(gy * s + j - s / 2, 0, H - 1);
+    for (int i = 0; i < s; ++i) {
+      const float v = gray_at(a.in, iclamp(gx * s + i - s / 2, 0, W - 1), y);
+      const int z = range_level(v, a.inv_r, a.gz);
+      float* p = acc + 2 * z * kSplatThreads + t;
+      p[0] = __fadd_rn(p[0], v);
+      p[kSplatThreads] = __fadd_rn(p[kSplatThreads], 1.0f);
+    }
+  }
+  for (int j = 0; j < 2 * a.gz; ++j)
+    reinterpret_cast<float*>((char*)a.grid.data + (long long)j * a.grid.ps + (long long)gy * a.grid.rs)[gx] =
+        acc[j * kSplatThreads + t];
+}
+
+__device__ __forceinline__ float lerp(float a, float b, float f) { return __fmaf_rn(f, __fsub_rn(b, a), a); }
+
+__device__ __forceinline__ float grid_at(const ImgView& g, int c, int x, int y) {
+  return __ldg(reinterpret_cast<const float*>((const char*)g.data + (long long)c * g.ps + (long long)y * g.rs) + x);
+}
+
+__global__ void __launch_bounds__(256) k_grid_slice(const GridArgs a) {
+  grid_dep_sync();
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= a.in.w || y >= a.in.h) return;
+  const ImgView& g = a.grid;
+  const float v = gray_at(a.in, x, y);
+  const float gxf = __fmul_rn((float)x, a.inv_s), gyf = __fmul_rn((float)y, a.inv_s), gzf = __fmul_rn(v, a.inv_r);
+  const float flx = floorf(gxf), fly = floorf(gyf), flz = floorf(gzf);
+  const float fx = __fsub_rn(gxf, flx), fy = __fsub_rn(gyf, fly), fz = __fsub_rn(gzf, flz);
+  const int x0 = iclamp((int)flx, 0, g.w - 1), x1 = iclamp((int)flx + 1, 0, g.w - 1);
+  const int y0 = iclamp((int)fly, 0, g.h - 1), y1 = iclamp((int)fly + 1, 0, g.h - 1);
+  const int z0 = iclamp((int)flz, 0, a.gz - 1), z1 = iclamp((int)flz + 1, 0, a.gz - 1);
+  float r[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {  // value, weight
+    float zs[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int c = 2 * (d ? z1 : z0) + k;
+      const float a0 = lerp(grid_at(g, c, x0, y0), grid_at(g, c, x1, y0), fx);
+      const float a1 = lerp(grid_at(g, c, x0, y1), grid_at(g, c, x1, y1), fx);
+      zs[d] = lerp(a0, a1, fy);
+    }
+    r[k] = lerp(zs[0], zs[1], fz);
+  }
+  const float out = r[1] > 0.0f ? __fdiv_rn(r[0], r[1]) : v;
+  reinterpret_cast<float*>((char*)a.out.data + (long long)y * a.out.rs)[x] = out;
+}
+
+}  // namespace
+
+int grid_max_levels() { return kMaxGZ; }
+
+int launch_grid_splat(const GridArgs& a, void* stream) {
+  if (a.gz < 1 || a.gz > kMaxGZ || a.s < 1 || a.grid.dtype != HP_F32 || a.grid.c < 2 * a.gz) return (int)cudaErrorInvalidValue;
+  dim3 grid((a.grid.w + kSplatThreads - 1) / kSplatThreads, a.grid.h, 1);
+  { const int le_ = launch_kernel(k_grid_splat, grid, dim3(kSplatThreads), 0, stream, a); if (le_) return le_; }
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
+int launch_grid_slice(const GridArgs& a, void* stream) {
+  if (a.gz < 1 || a.grid.dtype != HP_F32 || a.out.dtype != HP_F32 || a.grid.c < 2 * a.gz) return (int)cudaErrorInvalidValue;
+  dim3 grid((a.in.w + 31) / 32, (a.in.h + 7) / 8, 1);
+  { const int le_ = launch_kernel(k_grid_slice, grid, dim3(256), 0, stream, a); if (le_) return le_; }
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace hp

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -90,6 +91,7 @@ struct GroupPlan {
   MaxArgs maxa{};
   InterpArgs interp{};
   PwArgs pw{};
+  GridArgs grid{};
   LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
@@ -157,6 +159,9 @@ int stage_dtype_of_ref(const hp_pipeline* p, int ref) {
   return ref < 0 ? p->in_dtypes[-1 - ref] : p->stages[ref].storage;
 }
 
+// Range levels of a bilateral grid with range cell r: floor(1/r + 1/2) + 1.
+int grid_levels(float r) { return (int)floor(1.0 / (double)r + 0.5) + 1; }
+
 hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
   int nst = (int)p->stages.size();
   if (d->n_inputs < 1 || d->n_inputs > HP_MAX_INPUTS || !d->inputs)
@@ -192,6 +197,26 @@ hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
         return fail(HP_ERR_INVALID_ARG, "max-stencil radii must be in [0,%d]", HP_MAX_RADIUS);
       if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
       return HP_OK;
+    case HP_GRID_SPLAT: {
+      if (d->n_params < 2 || !(d->params[0] >= 1.0f && d->params[0] <= 64.0f) || (float)(int)d->params[0] != d->params[0] ||
+          !(d->params[1] >= 1.0f / 30.0f && d->params[1] <= 1.0f))
+        return fail(HP_ERR_INVALID_ARG, "grid splat params: s an integer in [1, 64], r in [1/30, 1]");
+      const int gz = grid_levels(d->params[1]);
+      if ((s = need(1, 2 * gz))) return s;
+      if (c0 != 1) return fail(HP_ERR_INVALID_ARG, "grid splat input is 1-channel");
+      if (d->storage != HP_F32) return fail(HP_ERR_UNSUPPORTED, "the grid is stored as f32");
+      return HP_OK;
+    }
+    case HP_GRID_SLICE: {
+      if ((s = need(2, 1))) return s;
+      if (d->n_params < 2 || !(d->params[0] >= 1.0f) || !(d->params[1] > 0.0f))
+        return fail(HP_ERR_INVALID_ARG, "grid slice params: s >= 1, r > 0");
+      const int gz = grid_levels(d->params[1]);
+      if (c0 != 2 * gz || stage_channels_of_ref(p, d->inputs[1]) != 1)
+        return fail(HP_ERR_INVALID_ARG, "grid slice inputs: a 2 GZ-channel grid and a 1-channel image");
+      if (d->storage != HP_F32) return fail(HP_ERR_UNSUPPORTED, "the slice is stored as f32");
+      return HP_OK;
+    }
     case HP_DOWNSAMPLE2:
       if (d->storage == HP_U32) return fail(HP_ERR_UNSUPPORTED, "u32 storage is for histograms only");
       return need(1, c0);
@@ -274,6 +299,12 @@ hp_status validate_stage(const hp_pipeline* p, const hp_stage_desc* d) {
       if ((s = need(1, 3))) return s;
       if (c0 != 4) return fail(HP_ERR_INVALID_ARG, "unpremultiply needs a 4-channel input");
       return HP_OK;
+    case HP_OP_ZBLUR: {
+      if ((s = nparams(1))) return s;
+      const int gz = (int)d->params[0];
+      if (gz < 1 || (float)gz != d->params[0] || c0 != 2 * gz) return fail(HP_ERR_INVALID_ARG, "zblur: params {GZ}, 2 GZ channels");
+      return need(1, c0);
+    }
     case HP_OP_LL_COLOUR:
       if ((s = need(3, 3)) || (s = nparams(2))) return s;
       if (chan(0) != 3 || chan(1) != 1 || chan(2) != 1) return fail(HP_ERR_INVALID_ARG, "colour inputs: 3, 1, 1 ch");
@@ -309,6 +340,19 @@ hp_status infer_domains(const hp_pipeline* p, const std::vector<Dom>& in_dom, st
         break;
       }
       case HP_HISTOGRAM: case HP_CDF_LUT: dom[s] = Dom{256, 1}; break;
+      case HP_GRID_SPLAT: {
+        const int gs = (int)st.params[0];
+        dom[s] = Dom{(d0.w + gs - 1) / gs + 1, (d0.h + gs - 1) / gs + 1};
+        break;
+      }
+      case HP_GRID_SLICE: {
+        const int gs = (int)st.params[0];
+        const Dom im = of(st.inputs[1]);
+        if (d0.w != (im.w + gs - 1) / gs + 1 || d0.h != (im.h + gs - 1) / gs + 1)
+          return fail(HP_ERR_INVALID_ARG, "stage %zu: a %dx%d grid does not fit a %dx%d image", s, d0.w, d0.h, im.w, im.h);
+        dom[s] = im;
+        break;
+      }
       default: {
         dom[s] = d0;
         int first = st.kind == HP_LUT_APPLY ? 1 : (int)st.inputs.size();
@@ -533,6 +577,8 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
       case HP_DOWNSAMPLE2: return impl == HP_IMPL_GENERIC ? HP_KERNEL_GENERIC : HP_KERNEL_DOWNSAMPLE;
       case HP_UPSAMPLE2: return HP_KERNEL_UPSAMPLE;
       case HP_HISTOGRAM: return HP_KERNEL_HISTOGRAM;
+      case HP_GRID_SPLAT: return HP_KERNEL_GRID_SPLAT;
+      case HP_GRID_SLICE: return HP_KERNEL_GRID_SLICE;
       case HP_CDF_LUT: return HP_KERNEL_CDF_LUT;
       case HP_LUT_APPLY: return HP_KERNEL_LUT_APPLY;
     }
@@ -547,7 +593,7 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
   }
   for (int s : m) {
     int k = p->stages[s].kind;
-    if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY) return -1;
+    if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY || k == HP_GRID_SPLAT || k == HP_GRID_SLICE) return -1;
   }
   if (impl == HP_IMPL_GENERIC) return HP_KERNEL_GENERIC;
   // interpolate level: upsample of a coarse image, composite with the fine
@@ -1243,6 +1289,23 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.smem = 0;
         break;
       }
+      case HP_KERNEL_GRID_SPLAT:
+      case HP_KERNEL_GRID_SLICE: {
+        const Stage& st = p->stages[gp.output];
+        GridArgs& a = gp.grid;
+        memset(&a, 0, sizeof a);
+        a.s = (int)st.params[0];
+        a.gz = grid_levels(st.params[1]);
+        a.inv_s = (float)(1.0 / (double)a.s);
+        a.inv_r = (float)(1.0 / (double)st.params[1]);
+        if (a.gz > grid_max_levels()) {
+          s = fail(HP_ERR_UNSUPPORTED, "at most %d range levels", grid_max_levels());
+          break;
+        }
+        gp.ext_refs = st.inputs;
+        gp.threads = 256;
+        break;
+      }
       case HP_KERNEL_PW_ROWS: {
         const Stage& st = p->stages[gp.output];
         PwArgs& a = gp.pw;
@@ -1449,6 +1512,21 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
         e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_GRID_SPLAT: {
+        GridArgs a = gp.grid;
+        a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.grid = out;
+        e = launch_grid_splat(a, stream);
+        break;
+      }
+      case HP_KERNEL_GRID_SLICE: {
+        GridArgs a = gp.grid;
+        a.grid = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.in = ref_view(p, plan, gp.ext_refs[1], inputs, output);
+        a.out = out;
+        e = launch_grid_slice(a, stream);
         break;
       }
       case HP_KERNEL_PW_ROWS: {

@@ -17,9 +17,9 @@ HP_OK, HP_ERR_INVALID_ARG, HP_ERR_UNSUPPORTED, HP_ERR_SCHEDULE, HP_ERR_OOM, HP_E
     HP_ERR_STATE = range(8)
 HP_U8, HP_U16, HP_F16, HP_BF16, HP_F32, HP_U32 = range(6)
 (HP_STENCIL, HP_POINTWISE, HP_DOWNSAMPLE2, HP_UPSAMPLE2, HP_HISTOGRAM, HP_CDF_LUT, HP_LUT_APPLY,
- HP_MAX_STENCIL) = range(8)
+ HP_MAX_STENCIL, HP_GRID_SPLAT, HP_GRID_SLICE) = range(10)
 (HP_OP_GRAY, HP_OP_MUL, HP_OP_ADD, HP_OP_SUB, HP_OP_HARRIS, HP_OP_UNSHARP, HP_OP_LL_REMAP, HP_OP_LL_INTERP,
- HP_OP_LL_COLOUR, HP_OP_SELECT, HP_OP_SCALE, HP_OP_PREMUL, HP_OP_OVER, HP_OP_UNPREMUL) = range(14)
+ HP_OP_LL_COLOUR, HP_OP_SELECT, HP_OP_SCALE, HP_OP_PREMUL, HP_OP_OVER, HP_OP_UNPREMUL, HP_OP_ZBLUR) = range(15)
 HP_INLINE = -1
 HP_OPT_CUDA_GRAPH = 1
 HP_OPT_OVERLAP = 2
@@ -28,10 +28,12 @@ HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE = 0, 1, 2
  HP_KERNEL_DOWNSAMPLE, HP_KERNEL_UPSAMPLE, HP_KERNEL_HISTOGRAM, HP_KERNEL_CDF_LUT, HP_KERNEL_LUT_APPLY,
  HP_KERNEL_LL_LEVEL, HP_KERNEL_STENCIL_WAVE, HP_KERNEL_HARRIS_ROWS, HP_KERNEL_STENCIL_ROWS,
  HP_KERNEL_HISTEQ, HP_KERNEL_LL_REMAP_ROWS, HP_KERNEL_LL_DOWN_ROWS, HP_KERNEL_LL_LEVEL_ROWS,
- HP_KERNEL_MAX_ROWS, HP_KERNEL_INTERP_ROWS, HP_KERNEL_PW_ROWS) = range(21)
+ HP_KERNEL_MAX_ROWS, HP_KERNEL_INTERP_ROWS, HP_KERNEL_PW_ROWS, HP_KERNEL_GRID_SPLAT,
+ HP_KERNEL_GRID_SLICE) = range(23)
 KERNEL_NAMES = ["stencil_chain", "unsharp", "harris", "generic", "pointwise", "downsample", "upsample",
                 "histogram", "cdf_lut", "lut_apply", "ll_level", "stencil_wave", "harris_rows", "stencil_rows", "histeq",
-                "ll_remap_rows", "ll_down_rows", "ll_level_rows", "max_rows", "interp_rows", "pw_rows"]
+                "ll_remap_rows", "ll_down_rows", "ll_level_rows", "max_rows", "interp_rows", "pw_rows", "grid_splat",
+                "grid_slice"]
 DTYPE_BYTES = {HP_U8: 1, HP_U16: 2, HP_F16: 2, HP_BF16: 2, HP_F32: 4, HP_U32: 4}
 
 _IP = ctypes.POINTER(ctypes.c_int)

@@ -5,6 +5,8 @@ Each builder states the algorithm once (stages, footprints, storage types);
 schedules only regroup stages into kernels and retile them (Sec. 1, Sec. 4).
 """
 
+import numpy as np
+
 from . import hp
 
 BINOMIAL16 = [0.0625, 0.25, 0.375, 0.25, 0.0625]   # [1,4,6,4,1]/16, per axis
@@ -271,4 +273,36 @@ def interpolate_finest() -> hp.Pipeline:
     out = p.add_stage(hp.HP_POINTWISE, [i0], 3, F, op=hp.HP_OP_UNPREMUL)
     p.set_output(out)
     p.schedule([0, 0, 0])
+    return p
+
+
+def bilateral_grid(s: int = 8, r: float = 0.1) -> hp.Pipeline:
+    """Bilateral grid (Sec. 6 app list): splat the clamped gray values into
+    s x s pixel cells and range levels of size r, blur the grid with
+    [1,4,6,4,1]/16 along the range levels, then x, then y, and slice it back
+    (trilinear; value / weight).  Input and output: 1-channel f32."""
+    F = hp.HP_F32
+    gz = int(np.floor(1.0 / float(np.float32(r)) + 0.5)) + 1
+    p = hp.Pipeline([F], [1])
+    g = p.add_stage(hp.HP_GRID_SPLAT, [p.input(0)], 2 * gz, F, params=[s, r])
+    bz = p.add_stage(hp.HP_POINTWISE, [g], 2 * gz, F, op=hp.HP_OP_ZBLUR, params=[gz])
+    bx = p.add_stage(hp.HP_STENCIL, [bz], 2 * gz, F, rx=2, ry=0, wx=BINOMIAL16, wy=[1.0])
+    by = p.add_stage(hp.HP_STENCIL, [bx], 2 * gz, F, rx=0, ry=2, wx=[1.0], wy=BINOMIAL16)
+    out = p.add_stage(hp.HP_GRID_SLICE, [by, p.input(0)], 1, F, params=[s, r])
+    p.set_output(out)
+    return p
+
+
+def bilateral_grid_fused_schedule(p: hp.Pipeline, tile: int = 32, threads: int = 256):
+    """Splat, the three blurs fused in one kernel, slice."""
+    p.schedule([0, 1, 1, 1, 2], tile_w=[0, tile, 0], tile_h=[0, tile, 0], threads=[0, threads, 0])
+
+
+def bilateral_grid_slice_only(s: int = 8, r: float = 0.1) -> hp.Pipeline:
+    """The slice of the bilateral grid on its own: inputs the blurred grid
+    (2 GZ channels) and the image; one kernel."""
+    F = hp.HP_F32
+    gz = int(np.floor(1.0 / float(np.float32(r)) + 0.5)) + 1
+    p = hp.Pipeline([F, F], [2 * gz, 1])
+    p.set_output(p.add_stage(hp.HP_GRID_SLICE, [p.input(0), p.input(1)], 1, F, params=[s, r]))
     return p

@@ -92,3 +92,13 @@ def rgba_sparse_f32(h: int, w: int, seed: int = 0, coverage: float = 0.25) -> np
     rgb = uniform_f32((3, h, w), seed, stream=6)
     a = (uniform_f32((1, h, w), seed, stream=7) < coverage).astype(np.float32)
     return np.concatenate([rgb, a])
+
+
+def gray_f32_gradient_noise(h: int, w: int, seed: int = 0, sigma: float = 0.05) -> np.ndarray:
+    """float32 [1][H][W] for the bilateral-grid workload: (x/(W-1) + y/(H-1))/2
+    plus N(0, sigma) per pixel, clamped to [0, 1]."""
+    xs = np.arange(w, dtype=np.float64) / max(w - 1, 1)
+    ys = np.arange(h, dtype=np.float64) / max(h - 1, 1)
+    base = (xs[None, :] + ys[:, None]) / 2.0
+    noisy = base + sigma * gaussian_f64((1, h, w), seed, stream=9)[0]
+    return np.clip(noisy, 0.0, 1.0).astype(np.float32)[None]

@@ -1,11 +1,13 @@
-"""GPU parity of the max filter (exact) and interpolate (FP32 against the FP64
-oracle) apps, plus schedule invariance."""
+"""GPU parity of the max filter (exact), interpolate and bilateral grid (FP32
+against the FP64 oracle; the grid's counts exact) apps, plus schedule
+invariance."""
 
 import numpy as np
 import pytest
 import torch
 
 import __graft_entry__
+from oracle import bilateral_grid as ob
 from oracle import interpolate as oi
 from oracle import maxfilter as om
 from paper_2012_07145_gb300 import hp, pipelines, synth
@@ -122,3 +124,58 @@ def test_interpolate_full_coverage_is_identity():
     pipelines.interpolate_fused_schedule(p, ids)
     got = to_numpy(run(p, [to_device(img, hp.HP_F32)], [hp.HP_F32], (3, h, w), hp.HP_F32))
     assert np.array_equal(got, img[:3])
+
+
+# --------------------------------------------------------- bilateral grid --
+def _splat_only(s, r):
+    gz = ob.levels(r)
+    p = hp.Pipeline([hp.HP_F32], [1])
+    p.set_output(p.add_stage(hp.HP_GRID_SPLAT, [p.input(0)], 2 * gz, hp.HP_F32, params=[s, r]))
+    return p, gz
+
+
+@pytest.mark.parametrize("h,w,s,r", [(37, 53, 4, 0.2), (96, 160, 8, 0.1), (1, 1, 2, 0.5), (130, 250, 8, 0.05)])
+def test_grid_splat_counts_exact(h, w, s, r):
+    """The splat's counts are exact integers, so every cell's count per range
+    level (decided in f32 on both sides) must match the oracle's exactly; the
+    sums of values within FP32 rounding."""
+    img = synth.gray_f32_gradient_noise(h, w, seed=h + w)
+    p, gz = _splat_only(s, r)
+    GX, GY = ob.grid_size(w, h, s)
+    got = to_numpy(run(p, [to_device(img, hp.HP_F32)], [hp.HP_F32], (2 * gz, GY, GX), hp.HP_F32))
+    ref = ob.splat(img[0], s, r)                        # [GY][GX][GZ][2]
+    counts = got[1::2].transpose(1, 2, 0)
+    sums = got[0::2].transpose(1, 2, 0)
+    assert np.array_equal(counts, ref[..., 1])
+    assert np.abs(sums - ref[..., 0]).max() <= 1e-5 * s * s
+
+
+@pytest.mark.parametrize("h,w,s,r", [(37, 53, 4, 0.2), (96, 160, 8, 0.1), (1, 1, 2, 0.5), (257, 131, 8, 0.1)])
+def test_bilateral_grid_against_oracle_and_schedules(h, w, s, r):
+    img = synth.gray_f32_gradient_noise(h, w, seed=3 * h + w)
+    x = to_device(img, hp.HP_F32)
+    p = pipelines.bilateral_grid(s, r)
+    plain = run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)
+    ref = ob.bilateral_grid(img[0], s, r)
+    err = float(np.abs(to_numpy(plain)[0].astype(np.float64) - ref).max())
+    print(f"bilateral grid {w}x{h} s={s} r={r}: max abs err {err:.3e}")
+    assert err <= 1e-5
+    for tile, threads in ((32, 256), (16, 128), (64, 512)):
+        pipelines.bilateral_grid_fused_schedule(p, tile, threads)
+        assert torch.equal(bits(run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)), bits(plain))
+
+
+def test_bilateral_grid_full_size_and_edges():
+    h, w = 1536, 2560
+    img = synth.gray_f32_gradient_noise(h, w, seed=0)
+    p = pipelines.bilateral_grid(8, 0.1)
+    pipelines.bilateral_grid_fused_schedule(p)
+    got = to_numpy(run(p, [to_device(img, hp.HP_F32)], [hp.HP_F32], (1, h, w), hp.HP_F32))[0]
+    band = slice(0, 96)
+    ref = ob.bilateral_grid(img[0][band], 8, 0.1)
+    # the band's last grid rows see the clamped band edge instead of the image below
+    assert float(np.abs(got[band][:64].astype(np.float64) - ref[:64]).max()) <= 1e-5
+    step = np.full((1, 64, 96), 0.2, dtype=np.float32)
+    step[:, :, 48:] = 0.8     # six range cells apart: each side keeps its value
+    out = to_numpy(run(p, [to_device(step, hp.HP_F32)], [hp.HP_F32], (1, 64, 96), hp.HP_F32))[0]
+    assert np.abs(out[:, :48] - np.float32(0.2)).max() <= 1e-6 and np.abs(out[:, 48:] - np.float32(0.8)).max() <= 1e-6
