@@ -293,8 +293,9 @@ def bilateral_grid(s: int = 8, r: float = 0.1) -> hp.Pipeline:
     return p
 
 
-def bilateral_grid_fused_schedule(p: hp.Pipeline, tile: int = 32, threads: int = 256):
-    """Splat, the three blurs fused in one kernel, slice."""
+def bilateral_grid_fused_schedule(p: hp.Pipeline, tile: int = 16, threads: int = 256):
+    """Splat, the three blurs fused in one kernel (small tiles: the grid is
+    small, so they spread over the SMs), slice."""
     p.schedule([0, 1, 1, 1, 2], tile_w=[0, tile, 0], tile_h=[0, tile, 0], threads=[0, threads, 0])
 
 
