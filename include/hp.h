@@ -226,7 +226,9 @@ enum {
                                   thread, 128-bit loads and stores */
   HP_KERNEL_GRID_SPLAT = 21,    /* bilateral grid splat: one thread per cell, accumulators in
                                   shared memory */
-  HP_KERNEL_GRID_SLICE = 22     /* bilateral grid slice: one thread per pixel, trilinear */
+  HP_KERNEL_GRID_SLICE = 22,    /* bilateral grid slice: one thread per pixel, trilinear */
+  HP_KERNEL_GRID_BLUR = 23      /* bilateral grid blur (range levels, x, y; binomial/16), streaming:
+                                  one warp per 28 grid columns x 4 range levels, y taps in order */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

@@ -176,6 +176,13 @@ struct GridArgs {
   float inv_s, inv_r;
 };
 
+// Blur of a bilateral grid (k_grid.cu): [1,4,6,4,1]/16 along the range levels,
+// then x, then y; rows per run of the streaming kernel.
+struct GridBlurArgs {
+  ImgView in, out;
+  int gz, rows;
+};
+
 // One point-wise stage over f32 images (k_pointwise.cu).
 struct PwArgs {
   ImgView in[HP_MAX_INPUTS];
@@ -306,6 +313,8 @@ int launch_pw_rows(const PwArgs& p, void* stream);
 int grid_max_levels();
 int launch_grid_splat(const GridArgs& a, void* stream);
 int launch_grid_slice(const GridArgs& a, void* stream);
+int grid_blur_units(const GridBlurArgs& a);
+int launch_grid_blur(const GridBlurArgs& a, int grid, void* stream);
 int launch_hist(const HistArgs& a, void* stream);
 int launch_cdf_lut(const LutArgs& a, void* stream);
 int launch_lut_apply(const LutApplyArgs& a, void* stream);

@@ -141,4 +141,144 @@ int launch_grid_slice(const GridArgs& a, void* stream) {
   return (int)cudaGetLastError();
 }
 
+
+// ---- the blur of the grid (the group: range-level blur, x blur, y blur) ----
+//
+// k_grid_blur: one warp per strip of 28 grid columns (lanes 0, 1, 30, 31 only
+// feed their neighbours), one of the two halves of a cell (values or weights)
+// and a chunk of 4 range levels, walking down a run of grid rows.  Per row it
+// loads the chunk's levels and two more on each side (clamped), blurs along
+// the levels, then along x (neighbours by warp shuffles); the y blur is five
+// accumulators per level, each fed its taps in order as the rows arrive, so
+// the float operations are those of the three stages one after the other.
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kZC = 4;          // range levels per unit
+constexpr int kBlurStrip = 28;  // grid columns per warp
+
+struct GridBlurParams {
+  GridBlurArgs a;
+  int strips, zchunks, runs, units;
+};
+
+struct BlurRun {
+  const GridBlurParams& P;
+  int x, k, z0, y0, nout, T;
+  bool prod;
+  float acc[kZC][5];
+  float ld[kZC + 4];  // the row's levels z0-2 .. z0+kZC+1 (clamped), in flight
+
+  __device__ __forceinline__ explicit BlurRun(const GridBlurParams& p) : P(p) {}
+
+  __device__ __forceinline__ void fetch(int t) {
+    const ImgView& g = P.a.in;
+    const int y = iclamp(y0 - 2 + t, 0, g.h - 1);
+    const int xc = iclamp(x, 0, g.w - 1);
+    const char* row = (const char*)g.data + (long long)y * g.rs;
+#pragma unroll
+    for (int i = 0; i < kZC + 4; ++i) {
+      const int c = 2 * iclamp(z0 - 2 + i, 0, P.a.gz - 1) + k;
+      ld[i] = __ldg(reinterpret_cast<const float*>(row + c * g.ps) + xc);
+    }
+  }
+
+  // Input row t (grid row y0 - 2 + t) into the accumulators; PH = t mod 5.
+  // Row t is tap j of output row t - j (run-relative, outputs 0 .. nout-1):
+  // tap 0 starts output t, tap 4 completes output t - 4.
+  template <int PH>
+  __device__ __forceinline__ void row(int t) {
+    float v[kZC + 4];
+#pragma unroll
+    for (int i = 0; i < kZC + 4; ++i) v[i] = ld[i];
+    if (t + 1 < T) fetch(t + 1);
+    const float w[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+    const int ofin = t - 4;
+    const bool st = prod && ofin >= 0 && ofin < nout;
+#pragma unroll
+    for (int q = 0; q < kZC; ++q) {
+      const float zb = tap5_binomial16(v[q], v[q + 1], v[q + 2], v[q + 3], v[q + 4]);
+      const float l2 = __shfl_up_sync(kFull, zb, 2), l1 = __shfl_up_sync(kFull, zb, 1);
+      const float r1 = __shfl_down_sync(kFull, zb, 1), r2 = __shfl_down_sync(kFull, zb, 2);
+      const float h = tap5(w, l2, l1, zb, r1, r2);
+      // slot of output t - j is (t - j) mod 5 = (PH - j) mod 5
+      float& fin = acc[q][(PH + 1) % 5];                 // output t - 4: tap 4, complete
+      fin = __fmaf_rn(w[4], h, fin);
+      if (st && z0 + q < P.a.gz) {
+        const ImgView& o = P.a.out;
+        reinterpret_cast<float*>((char*)o.data + (long long)(2 * (z0 + q) + k) * o.ps +
+                                 (long long)(y0 + ofin) * o.rs)[x] = fin;
+      }
+      acc[q][(PH + 2) % 5] = __fmaf_rn(w[3], h, acc[q][(PH + 2) % 5]);  // output t - 3
+      acc[q][(PH + 3) % 5] = __fmaf_rn(w[2], h, acc[q][(PH + 3) % 5]);  // output t - 2
+      acc[q][(PH + 4) % 5] = __fmaf_rn(w[1], h, acc[q][(PH + 4) % 5]);  // output t - 1
+      acc[q][PH] = __fmul_rn(w[0], h);                                  // output t: tap 0
+    }
+  }
+
+  __device__ __forceinline__ void run(int u) {
+    const int lane = threadIdx.x & 31;
+    const int strip = u % P.strips;
+    int rest = u / P.strips;
+    const int zc = rest % P.zchunks;
+    rest /= P.zchunks;
+    k = rest & 1;
+    const int run_idx = rest >> 1;
+    x = strip * kBlurStrip + lane - 2;
+    prod = lane >= 2 && lane < 2 + kBlurStrip && x < P.a.in.w;
+    z0 = zc * kZC;
+    y0 = run_idx * P.a.rows;
+    nout = imin(P.a.rows, P.a.in.h - y0);
+    T = nout + 4;  // grid rows y0 - 2 .. y0 + nout + 1
+#pragma unroll
+    for (int q = 0; q < kZC; ++q)
+#pragma unroll
+      for (int s = 0; s < 5; ++s) acc[q][s] = 0.0f;
+    fetch(0);
+    for (int t = 0; t < T; t += 5) {
+      row<0>(t);
+      if (t + 1 >= T) break;
+      row<1>(t + 1);
+      if (t + 2 >= T) break;
+      row<2>(t + 2);
+      if (t + 3 >= T) break;
+      row<3>(t + 3);
+      if (t + 4 >= T) break;
+      row<4>(t + 4);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256, 2) k_grid_blur(const GridBlurParams P) {
+  grid_dep_wait();
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.units; u += nw) {
+    BlurRun r(P);
+    r.run(u);
+  }
+}
+
+}  // namespace
+
+int grid_blur_units(const GridBlurArgs& a) {
+  const int strips = (a.in.w + kBlurStrip - 1) / kBlurStrip;
+  const int zchunks = (a.gz + kZC - 1) / kZC;
+  return strips * zchunks * 2 * ((a.in.h + a.rows - 1) / a.rows);
+}
+
+int launch_grid_blur(const GridBlurArgs& a, int grid, void* stream) {
+  if (a.gz < 1 || a.rows < 1 || grid < 1 || a.in.dtype != HP_F32 || a.out.dtype != HP_F32 || a.in.c < 2 * a.gz ||
+      a.out.c < 2 * a.gz)
+    return (int)cudaErrorInvalidValue;
+  GridBlurParams kp;
+  kp.a = a;
+  kp.strips = (a.in.w + kBlurStrip - 1) / kBlurStrip;
+  kp.zchunks = (a.gz + kZC - 1) / kZC;
+  kp.runs = (a.in.h + a.rows - 1) / a.rows;
+  kp.units = kp.strips * kp.zchunks * 2 * kp.runs;
+  { const int le_ = launch_kernel(k_grid_blur, dim3(grid), dim3(256), 0, stream, kp); if (le_) return le_; }
+  __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
+  return (int)cudaGetLastError();
+}
+
 }  // namespace hp

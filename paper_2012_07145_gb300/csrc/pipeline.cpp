@@ -92,6 +92,7 @@ struct GroupPlan {
   InterpArgs interp{};
   PwArgs pw{};
   GridArgs grid{};
+  GridBlurArgs gblur{};
   LLRoles llroles{};
   std::unique_ptr<GPlan> gplan;
   std::vector<int> ext_refs;  // generic: external refs (stage id or -1-k)
@@ -596,6 +597,21 @@ int choose_kernel(const hp_pipeline* p, const GroupShape& gs, int impl) {
     if (k == HP_HISTOGRAM || k == HP_CDF_LUT || k == HP_LUT_APPLY || k == HP_GRID_SPLAT || k == HP_GRID_SLICE) return -1;
   }
   if (impl == HP_IMPL_GENERIC) return HP_KERNEL_GENERIC;
+  // bilateral grid blur: along the range levels, then x, then y (binomial/16)
+  if (m.size() == 3) {
+    const Stage& a = p->stages[m[0]];
+    const Stage& b = p->stages[m[1]];
+    const Stage& c = p->stages[m[2]];
+    auto is_b16 = [](const std::vector<float>& w) {
+      return w.size() == 5 && w[0] == 0.0625f && w[1] == 0.25f && w[2] == 0.375f && w[3] == 0.25f && w[4] == 0.0625f;
+    };
+    auto is_one = [](const std::vector<float>& w) { return w.size() == 1 && w[0] == 1.0f; };
+    if (a.kind == HP_POINTWISE && a.op == HP_OP_ZBLUR && b.kind == HP_STENCIL && c.kind == HP_STENCIL &&
+        b.inputs[0] == m[0] && c.inputs[0] == m[1] && b.rx == 2 && b.ry == 0 && c.rx == 0 && c.ry == 2 &&
+        is_b16(b.wx) && is_one(b.wy) && is_one(c.wx) && is_b16(c.wy) && a.storage == HP_F32 && b.storage == HP_F32 &&
+        c.storage == HP_F32 && stage_dtype_of_ref(p, a.inputs[0]) == HP_F32)
+      return HP_KERNEL_GRID_BLUR;
+  }
   // interpolate level: upsample of a coarse image, composite with the fine
   // level (and the division by coverage), every stage f32
   if (m.size() == 2 || m.size() == 3) {
@@ -1289,6 +1305,26 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.smem = 0;
         break;
       }
+      case HP_KERNEL_GRID_BLUR: {
+        const Stage& zb = p->stages[gp.members[0]];
+        GridBlurArgs& a = gp.gblur;
+        memset(&a, 0, sizeof a);
+        a.gz = (int)zb.params[0];
+        gp.ext_refs.assign(1, zb.inputs[0]);
+        gp.threads = 256;
+        const Dom gd = plan.dom[gp.output];
+        a.in.w = gd.w;
+        a.in.h = gd.h;
+        a.rows = 1;
+        const long long per_row = grid_blur_units(a) / gd.h;  // column units per grid row
+        gp.tile_h = pick(p->tile_h, g, 0);
+        if (gp.tile_h == 0) gp.tile_h = (int)std::max(1LL, ((long long)gd.h * per_row + 2431) / 2432);
+        a.rows = gp.tile_h;
+        const int units = grid_blur_units(a);
+        gp.grid_x = std::max(1, std::min((units + 7) / 8, 2 * 152));
+        gp.grid_y = 1;
+        break;
+      }
       case HP_KERNEL_GRID_SPLAT:
       case HP_KERNEL_GRID_SLICE: {
         const Stage& st = p->stages[gp.output];
@@ -1512,6 +1548,13 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.src = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
         e = launch_ll_down(a, gp.smem, stream);
+        break;
+      }
+      case HP_KERNEL_GRID_BLUR: {
+        GridBlurArgs a = gp.gblur;
+        a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
+        a.out = out;
+        e = launch_grid_blur(a, gp.grid_x, stream);
         break;
       }
       case HP_KERNEL_GRID_SPLAT: {

@@ -29,11 +29,11 @@ HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE = 0, 1, 2
  HP_KERNEL_LL_LEVEL, HP_KERNEL_STENCIL_WAVE, HP_KERNEL_HARRIS_ROWS, HP_KERNEL_STENCIL_ROWS,
  HP_KERNEL_HISTEQ, HP_KERNEL_LL_REMAP_ROWS, HP_KERNEL_LL_DOWN_ROWS, HP_KERNEL_LL_LEVEL_ROWS,
  HP_KERNEL_MAX_ROWS, HP_KERNEL_INTERP_ROWS, HP_KERNEL_PW_ROWS, HP_KERNEL_GRID_SPLAT,
- HP_KERNEL_GRID_SLICE) = range(23)
+ HP_KERNEL_GRID_SLICE, HP_KERNEL_GRID_BLUR) = range(24)
 KERNEL_NAMES = ["stencil_chain", "unsharp", "harris", "generic", "pointwise", "downsample", "upsample",
                 "histogram", "cdf_lut", "lut_apply", "ll_level", "stencil_wave", "harris_rows", "stencil_rows", "histeq",
                 "ll_remap_rows", "ll_down_rows", "ll_level_rows", "max_rows", "interp_rows", "pw_rows", "grid_splat",
-                "grid_slice"]
+                "grid_slice", "grid_blur"]
 DTYPE_BYTES = {HP_U8: 1, HP_U16: 2, HP_F16: 2, HP_BF16: 2, HP_F32: 4, HP_U32: 4}
 
 _IP = ctypes.POINTER(ctypes.c_int)

@@ -293,10 +293,13 @@ def bilateral_grid(s: int = 8, r: float = 0.1) -> hp.Pipeline:
     return p
 
 
-def bilateral_grid_fused_schedule(p: hp.Pipeline, tile: int = 16, threads: int = 256):
-    """Splat, the three blurs fused in one kernel (small tiles: the grid is
-    small, so they spread over the SMs), slice."""
-    p.schedule([0, 1, 1, 1, 2], tile_w=[0, tile, 0], tile_h=[0, tile, 0], threads=[0, threads, 0])
+def bilateral_grid_fused_schedule(p: hp.Pipeline, tile: int = 0, threads: int = 256, impl=None):
+    """Splat, the three blurs fused in one kernel (the streaming grid-blur
+    kernel; tile = its grid rows per run, 0: sized to spread over the SMs;
+    under the generic interpreter 16 x 16 tiles by default), slice."""
+    t = tile or (16 if impl == hp.HP_IMPL_GENERIC else 0)
+    p.schedule([0, 1, 1, 1, 2], tile_w=[0, t, 0], tile_h=[0, t, 0], threads=[0, threads, 0],
+               impl=[hp.HP_IMPL_AUTO, impl, hp.HP_IMPL_AUTO] if impl is not None else None)
 
 
 def bilateral_grid_slice_only(s: int = 8, r: float = 0.1) -> hp.Pipeline:

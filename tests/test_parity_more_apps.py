@@ -160,8 +160,11 @@ def test_bilateral_grid_against_oracle_and_schedules(h, w, s, r):
     err = float(np.abs(to_numpy(plain)[0].astype(np.float64) - ref).max())
     print(f"bilateral grid {w}x{h} s={s} r={r}: max abs err {err:.3e}")
     assert err <= 1e-5
-    for tile, threads in ((32, 256), (16, 128), (64, 512)):
-        pipelines.bilateral_grid_fused_schedule(p, tile, threads)
+    for tile, threads, impl in ((0, 256, None), (1, 256, None), (7, 256, None), (64, 256, None),
+                                (16, 128, hp.HP_IMPL_GENERIC), (32, 512, hp.HP_IMPL_GENERIC)):
+        pipelines.bilateral_grid_fused_schedule(p, tile, threads, impl)
+        blur = p.group_info([(w, h)], 1).kernel
+        assert blur == (hp.HP_KERNEL_GENERIC if impl else hp.HP_KERNEL_GRID_BLUR)
         assert torch.equal(bits(run(p, [x], [hp.HP_F32], (1, h, w), hp.HP_F32)), bits(plain))
 
 
