@@ -190,3 +190,42 @@ def test_options():
     p.set_option(hp.HP_OPT_OVERLAP, 0)
     with pytest.raises(hp.HPError):
         p.set_option(99, 1)
+
+
+def test_new_stage_kinds_validation_and_lowering():
+    """Max stencil, interpolate ops and the bilateral grid's stages: argument
+    rules, domains and kernel choice (no GPU needed)."""
+    p = hp.Pipeline([hp.HP_F32], [3])
+    with pytest.raises(hp.HPError):  # radius beyond HP_MAX_RADIUS
+        p.add_stage(hp.HP_MAX_STENCIL, [p.input(0)], 3, rx=5, ry=0)
+    with pytest.raises(hp.HPError):  # channel count must follow the input
+        p.add_stage(hp.HP_MAX_STENCIL, [p.input(0)], 1, rx=2, ry=2)
+    with pytest.raises(hp.HPError):  # premultiply needs RGBA
+        p.add_stage(hp.HP_POINTWISE, [p.input(0)], 4, op=hp.HP_OP_PREMUL)
+    m = pipelines.max_filter(2)
+    m.schedule([0, 0])
+    assert m.group_info([(50, 40)], 0).kernel == hp.HP_KERNEL_MAX_ROWS
+    m.schedule([0, 0], impl=[hp.HP_IMPL_GENERIC])
+    assert m.group_info([(50, 40)], 0).kernel == hp.HP_KERNEL_GENERIC
+
+    g = hp.Pipeline([hp.HP_F32], [1])
+    with pytest.raises(hp.HPError):  # s must be an integer in [1, 64]
+        g.add_stage(hp.HP_GRID_SPLAT, [g.input(0)], 22, params=[2.5, 0.1])
+    with pytest.raises(hp.HPError):  # 2 GZ channels: GZ = floor(1/r + 1/2) + 1 = 11
+        g.add_stage(hp.HP_GRID_SPLAT, [g.input(0)], 20, params=[8, 0.1])
+    b = pipelines.bilateral_grid(8, 0.1)
+    kinds = [b.group_info([(100, 70)], k).kernel for k in range(b.group_count())]
+    assert kinds == [hp.HP_KERNEL_GRID_SPLAT, hp.HP_KERNEL_POINTWISE, hp.HP_KERNEL_GENERIC, hp.HP_KERNEL_GENERIC,
+                     hp.HP_KERNEL_GRID_SLICE]
+    pipelines.bilateral_grid_fused_schedule(b)
+    assert [b.group_info([(100, 70)], k).kernel for k in range(3)] == [
+        hp.HP_KERNEL_GRID_SPLAT, hp.HP_KERNEL_GRID_BLUR, hp.HP_KERNEL_GRID_SLICE]
+    with pytest.raises(hp.HPError):  # the splat cannot share a kernel with other stages
+        b.schedule([0, 0, 1, 1, 2])
+        b.group_info([(100, 70)], 0)
+
+    q, ids = pipelines.interpolate(4)
+    pipelines.interpolate_fused_schedule(q, ids)
+    ks = [q.group_info([(64, 48)], k).kernel for k in range(q.group_count())]
+    assert ks[0] == hp.HP_KERNEL_PW_ROWS and ks[-1] == hp.HP_KERNEL_INTERP_ROWS
+    assert q.group_info([(64, 48)], q.group_count() - 1).n_members == 3   # upsample, over, division
