@@ -171,6 +171,23 @@ __device__ __forceinline__ float rs(float v, int dtype) {
   return round_storage(dtype, v);
 }
 
+// Four values rounded to the storage type; bf16 two at a time (one paired
+// conversion, round-to-nearest-even per value: the same values as rs).
+template <int RND>
+__device__ __forceinline__ void rs4(float (&v)[4], int dtype) {
+  if (RND == 2) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float2 f = __bfloat1622float2(__floats2bfloat162_rn(v[2 * q], v[2 * q + 1]));
+      v[2 * q] = f.x;
+      v[2 * q + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = rs<RND>(v[k], dtype);
+  }
+}
+
 __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (&v)[4]) {
   if (dtype == HP_F32) {
     const float4 q = *reinterpret_cast<const float4*>(p);
@@ -264,12 +281,12 @@ struct StripRun {
     }
     if (SPEC || a.gray_scale == 1.0f) {  // x * 1 is exact: the same value as op_gray with scale 1
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        gv[k] = rs<RND>(__fmaf_rn(0.114f, cb[k], __fmaf_rn(0.587f, cg[k], __fmul_rn(0.299f, cr[k]))), a.st[0]);
+      for (int k = 0; k < 4; ++k) gv[k] = __fmaf_rn(0.114f, cb[k], __fmaf_rn(0.587f, cg[k], __fmul_rn(0.299f, cr[k])));
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) gv[k] = rs<RND>(op_gray(cr[k], cg[k], cb[k], a.gray_scale), a.st[0]);
+      for (int k = 0; k < 4; ++k) gv[k] = op_gray(cr[k], cg[k], cb[k], a.gray_scale);
     }
+    rs4<RND>(gv, a.st[0]);
     float l[4], rt[4];
     neighbours(gv, e, l, rt);
     xpass3(w, 0, l, gv, rt, hA[M]);
@@ -294,15 +311,23 @@ struct StripRun {
     const HarrisArgs& a = kp.a;
     constexpr int I0 = (M + 1) % 3, I1 = (M + 2) % 3, I2 = M;
     constexpr int S = (M + 2) % 3, SP = (M + 1) % 3;  // this product row's slot; the previous one's
-    float pr[3][4];
+    float pr[3][4], ix[4], iy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float ix = rs<RND>(tapw(w, 0, 3, hA[I0][k], hA[I1][k], hA[I2][k]), a.st[1]);
-      const float iy = rs<RND>(tapw(w, 1, 3, hB[I0][k], hB[I1][k], hB[I2][k]), a.st[2]);
-      pr[0][k] = rs<RND>(__fmul_rn(ix, ix), a.st[3]);
-      pr[1][k] = rs<RND>(__fmul_rn(iy, iy), a.st[4]);
-      pr[2][k] = rs<RND>(__fmul_rn(ix, iy), a.st[5]);
+      ix[k] = tapw(w, 0, 3, hA[I0][k], hA[I1][k], hA[I2][k]);
+      iy[k] = tapw(w, 1, 3, hB[I0][k], hB[I1][k], hB[I2][k]);
     }
+    rs4<RND>(ix, a.st[1]);
+    rs4<RND>(iy, a.st[2]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pr[0][k] = __fmul_rn(ix[k], ix[k]);
+      pr[1][k] = __fmul_rn(iy[k], iy[k]);
+      pr[2][k] = __fmul_rn(ix[k], iy[k]);
+    }
+    rs4<RND>(pr[0], a.st[3]);
+    rs4<RND>(pr[1], a.st[4]);
+    rs4<RND>(pr[2], a.st[5]);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       float l[4], rt[4];
@@ -330,13 +355,19 @@ struct StripRun {
   __device__ __forceinline__ void row_out() {
     const HarrisArgs& a = kp.a;
     constexpr int J0 = M, J1 = (M + 1) % 3, J2 = (M + 2) % 3;
-    float o[4];
+    float o[4], sxx[4], syy[4], sxy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const float sxx = rs<RND>(tapw(w, 2, 3, sm[J0][0][k], sm[J1][0][k], sm[J2][0][k]), a.st[6]);
-      const float syy = rs<RND>(tapw(w, 3, 3, sm[J0][1][k], sm[J1][1][k], sm[J2][1][k]), a.st[7]);
-      const float sxy = rs<RND>(tapw(w, 4, 3, sm[J0][2][k], sm[J1][2][k], sm[J2][2][k]), a.st[8]);
-      const float v = op_harris(sxx, syy, sxy, a.k);
+      sxx[k] = tapw(w, 2, 3, sm[J0][0][k], sm[J1][0][k], sm[J2][0][k]);
+      syy[k] = tapw(w, 3, 3, sm[J0][1][k], sm[J1][1][k], sm[J2][1][k]);
+      sxy[k] = tapw(w, 4, 3, sm[J0][2][k], sm[J1][2][k], sm[J2][2][k]);
+    }
+    rs4<RND>(sxx, a.st[6]);
+    rs4<RND>(syy, a.st[7]);
+    rs4<RND>(sxy, a.st[8]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float v = op_harris(sxx[k], syy[k], sxy[k], a.k);
       o[k] = ODT == 3 ? round_storage(a.out.dtype, v) : v;
     }
     char* row = out_row;
