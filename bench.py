@@ -574,6 +574,8 @@ def run_ours(args, cfg_name):
                 "algorithmic": f"{cfg['bytes_px']} bytes per output pixel (input + output once), over the whole step"}
     roof.update({"traffic": recorded_traffic(cfg["kernel"], cfg["workload"]), "kernel": cfg["kernel"],
                  "kernel_ms": round(kernel_ms, 5), "launches_per_step": launches_per_step})
+    if roof["bound"] == "hbm":   # also against the nominal HBM3e bandwidth, for context
+        roof["frac_of_nominal_7900_gbs"] = round(roof["achieved"] / 7900.0, 4)
     in_bytes = int(sum(a.nbytes for a, _ in inputs))
     out_bytes = int(C * OH * OW * hp.DTYPE_BYTES[odt])
     line = {
