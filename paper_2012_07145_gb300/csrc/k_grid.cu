@@ -6,10 +6,11 @@
 // 2z+1 their count.  (The blur between them is a point-wise op along the range
 // levels and two 5-tap stencils: the generic kernels.)
 //
-// k_grid_splat: one thread per cell; it walks the cell's s x s pixels in row
-//   order and adds each to its range level's pair of accumulators, which sit
-//   in shared memory (word channel x 128 + thread: every access of a warp hits
-//   32 banks), so the sums are formed in the same order every time.
+// k_grid_splat: one thread per cell (any s) or four (s = 8, k_grid_splat8: two
+//   pixel rows each, their copies added in a fixed order); each walks its
+//   pixels in row order and adds them to its range level's pair of
+//   accumulators, which sit in lane-private shared memory (every access of a
+//   warp hits 32 banks), so the sums are formed in the same order every time.
 // k_grid_slice: one thread per pixel; trilinear interpolation (x, then y, then
 //   the range level) of the value and the weight, then their ratio.
 #include <cuda_runtime.h>
@@ -85,6 +86,51 @@ __global__ void __launch_bounds__(kSplatThreads) k_grid_splat(const GridArgs a) 
         acc[j * kSplatThreads + t];
 }
 
+// The splat of 8 x 8-pixel cells: a block of 4 warps takes 32 consecutive
+// cells of a grid row, lane = cell, warp w = the cell's pixel rows 2w and 2w+1
+// (two 128-bit loads per row for interior cells); each warp accumulates into
+// its own lane-private copy, then the four copies are added in warp order.
+__global__ void __launch_bounds__(128) k_grid_splat8(const GridArgs a) {
+  grid_dep_sync();
+  __shared__ float acc[4][2 * kMaxGZ][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int gx = blockIdx.x * 32 + lane, gy = blockIdx.y;
+  const bool valid = gx < a.grid.w;
+  for (int j = 0; j < 2 * a.gz; ++j) acc[w][j][lane] = 0.0f;
+  if (valid) {
+    const int W = a.in.w, H = a.in.h;
+    const int x0 = gx * 8 - 4;
+    const bool inner = x0 >= 0 && x0 + 7 <= W - 1 && a.in.dtype == HP_F32;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int y = iclamp(gy * 8 + 2 * w + jj - 4, 0, H - 1);
+      float v[8];
+      if (inner) {
+        const float4* row = reinterpret_cast<const float4*>((const char*)a.in.data + (long long)y * a.in.rs) + (x0 >> 2);
+        const float4 f0 = __ldg(row), f1 = __ldg(row + 1);
+        v[0] = f0.x; v[1] = f0.y; v[2] = f0.z; v[3] = f0.w; v[4] = f1.x; v[5] = f1.y; v[6] = f1.z; v[7] = f1.w;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fminf(fmaxf(v[i], 0.0f), 1.0f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = gray_at(a.in, iclamp(x0 + i, 0, W - 1), y);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int z = range_level(v[i], a.inv_r, a.gz);
+        acc[w][2 * z][lane] = __fadd_rn(acc[w][2 * z][lane], v[i]);
+        acc[w][2 * z + 1][lane] = __fadd_rn(acc[w][2 * z + 1][lane], 1.0f);
+      }
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  for (int j = w; j < 2 * a.gz; j += 4) {
+    const float t = __fadd_rn(__fadd_rn(__fadd_rn(acc[0][j][lane], acc[1][j][lane]), acc[2][j][lane]), acc[3][j][lane]);
+    reinterpret_cast<float*>((char*)a.grid.data + (long long)j * a.grid.ps + (long long)gy * a.grid.rs)[gx] = t;
+  }
+}
+
 __device__ __forceinline__ float lerp(float a, float b, float f) { return __fmaf_rn(f, __fsub_rn(b, a), a); }
 
 __device__ __forceinline__ float grid_at(const ImgView& g, int c, int x, int y) {
@@ -127,8 +173,13 @@ int grid_max_levels() { return kMaxGZ; }
 
 int launch_grid_splat(const GridArgs& a, void* stream) {
   if (a.gz < 1 || a.gz > kMaxGZ || a.s < 1 || a.grid.dtype != HP_F32 || a.grid.c < 2 * a.gz) return (int)cudaErrorInvalidValue;
-  dim3 grid((a.grid.w + kSplatThreads - 1) / kSplatThreads, a.grid.h, 1);
-  { const int le_ = launch_kernel(a.s == 8 ? k_grid_splat<8> : k_grid_splat<0>, grid, dim3(kSplatThreads), 0, stream, a); if (le_) return le_; }
+  if (a.s == 8) {
+    dim3 grid8((a.grid.w + 31) / 32, a.grid.h, 1);
+    { const int le_ = launch_kernel(k_grid_splat8, grid8, dim3(128), 0, stream, a); if (le_) return le_; }
+  } else {
+    dim3 grid((a.grid.w + kSplatThreads - 1) / kSplatThreads, a.grid.h, 1);
+    { const int le_ = launch_kernel(k_grid_splat<0>, grid, dim3(kSplatThreads), 0, stream, a); if (le_) return le_; }
+  }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
