@@ -11,8 +11,9 @@
 //   pixels in row order and adds them to its range level's pair of
 //   accumulators, which sit in lane-private shared memory (every access of a
 //   warp hits 32 banks), so the sums are formed in the same order every time.
-// k_grid_slice: one thread per pixel; trilinear interpolation (x, then y, then
-//   the range level) of the value and the weight, then their ratio.
+// k_grid_slice: per pixel, trilinear interpolation (x, then y, then the range
+//   level) of the value and the weight, then their ratio; four pixels of a row
+//   per thread.
 #include <cuda_runtime.h>
 
 #include "hp_internal.h"
@@ -133,38 +134,65 @@ __global__ void __launch_bounds__(128) k_grid_splat8(const GridArgs a) {
 
 __device__ __forceinline__ float lerp(float a, float b, float f) { return __fmaf_rn(f, __fsub_rn(b, a), a); }
 
-__device__ __forceinline__ float grid_at(const ImgView& g, int c, int x, int y) {
-  return __ldg(reinterpret_cast<const float*>((const char*)g.data + (long long)c * g.ps + (long long)y * g.rs) + x);
-}
-
+// Four consecutive pixels of one row per thread (a warp: 128 pixels; a block:
+// 8 rows): one 128-bit load of the image and one 128-bit store of the output
+// where the row allows, and the grid-row addresses shared by the four pixels.
+// Each pixel's arithmetic is the per-pixel expression above, unchanged.
 __global__ void __launch_bounds__(256) k_grid_slice(const GridArgs a) {
   grid_dep_sync();
-  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int xb = (blockIdx.x * 32 + (threadIdx.x & 31)) * 4;
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (x >= a.in.w || y >= a.in.h) return;
+  if (xb >= a.in.w || y >= a.in.h) return;
   const ImgView& g = a.grid;
-  const float v = gray_at(a.in, x, y);
-  const float gxf = __fmul_rn((float)x, a.inv_s), gyf = __fmul_rn((float)y, a.inv_s), gzf = __fmul_rn(v, a.inv_r);
-  const float flx = floorf(gxf), fly = floorf(gyf), flz = floorf(gzf);
-  const float fx = __fsub_rn(gxf, flx), fy = __fsub_rn(gyf, fly), fz = __fsub_rn(gzf, flz);
-  const int x0 = iclamp((int)flx, 0, g.w - 1), x1 = iclamp((int)flx + 1, 0, g.w - 1);
+  const float gyf = __fmul_rn((float)y, a.inv_s);
+  const float fly = floorf(gyf), fy = __fsub_rn(gyf, fly);
   const int y0 = iclamp((int)fly, 0, g.h - 1), y1 = iclamp((int)fly + 1, 0, g.h - 1);
-  const int z0 = iclamp((int)flz, 0, a.gz - 1), z1 = iclamp((int)flz + 1, 0, a.gz - 1);
-  float r[2];
+  const char* g0 = (const char*)g.data + (long long)y0 * g.rs;
+  const char* g1 = (const char*)g.data + (long long)y1 * g.rs;
+  const int n = imin(4, a.in.w - xb);
+  const bool vec = n == 4 && a.in.dtype == HP_F32 && (((size_t)a.in.data | (size_t)a.in.rs | (size_t)a.out.data | (size_t)a.out.rs) & 15) == 0;
+  float v[4];
+  if (vec) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>((const char*)a.in.data + (long long)y * a.in.rs) + (xb >> 2));
+    v[0] = fminf(fmaxf(q.x, 0.0f), 1.0f); v[1] = fminf(fmaxf(q.y, 0.0f), 1.0f);
+    v[2] = fminf(fmaxf(q.z, 0.0f), 1.0f); v[3] = fminf(fmaxf(q.w, 0.0f), 1.0f);
+  } else {
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {  // value, weight
-    float zs[2];
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const int c = 2 * (d ? z1 : z0) + k;
-      const float a0 = lerp(grid_at(g, c, x0, y0), grid_at(g, c, x1, y0), fx);
-      const float a1 = lerp(grid_at(g, c, x0, y1), grid_at(g, c, x1, y1), fx);
-      zs[d] = lerp(a0, a1, fy);
-    }
-    r[k] = lerp(zs[0], zs[1], fz);
+    for (int k = 0; k < 4; ++k) v[k] = gray_at(a.in, imin(xb + k, a.in.w - 1), y);
   }
-  const float out = r[1] > 0.0f ? __fdiv_rn(r[0], r[1]) : v;
-  reinterpret_cast<float*>((char*)a.out.data + (long long)y * a.out.rs)[x] = out;
+  float o[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float gxf = __fmul_rn((float)(xb + k), a.inv_s), gzf = __fmul_rn(v[k], a.inv_r);
+    const float flx = floorf(gxf), flz = floorf(gzf);
+    const float fx = __fsub_rn(gxf, flx), fz = __fsub_rn(gzf, flz);
+    const int x0 = iclamp((int)flx, 0, g.w - 1), x1 = iclamp((int)flx + 1, 0, g.w - 1);
+    const int z0 = iclamp((int)flz, 0, a.gz - 1), z1 = iclamp((int)flz + 1, 0, a.gz - 1);
+    float r[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {  // value, weight
+      float zs[2];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const long long off = (long long)(2 * (d ? z1 : z0) + q) * g.ps;
+        const float* p0 = reinterpret_cast<const float*>(g0 + off);
+        const float* p1 = reinterpret_cast<const float*>(g1 + off);
+        const float a0 = lerp(__ldg(p0 + x0), __ldg(p0 + x1), fx);
+        const float a1 = lerp(__ldg(p1 + x0), __ldg(p1 + x1), fx);
+        zs[d] = lerp(a0, a1, fy);
+      }
+      r[q] = lerp(zs[0], zs[1], fz);
+    }
+    o[k] = r[1] > 0.0f ? __fdiv_rn(r[0], r[1]) : v[k];
+  }
+  float* orow = reinterpret_cast<float*>((char*)a.out.data + (long long)y * a.out.rs);
+  if (vec) {
+    reinterpret_cast<float4*>(orow)[xb >> 2] = make_float4(o[0], o[1], o[2], o[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < n) orow[xb + k] = o[k];
+  }
 }
 
 }  // namespace
@@ -186,7 +214,7 @@ int launch_grid_splat(const GridArgs& a, void* stream) {
 
 int launch_grid_slice(const GridArgs& a, void* stream) {
   if (a.gz < 1 || a.grid.dtype != HP_F32 || a.out.dtype != HP_F32 || a.grid.c < 2 * a.gz) return (int)cudaErrorInvalidValue;
-  dim3 grid((a.in.w + 31) / 32, (a.in.h + 7) / 8, 1);
+  dim3 grid((a.in.w + 127) / 128, (a.in.h + 7) / 8, 1);
   { const int le_ = launch_kernel(k_grid_slice, grid, dim3(256), 0, stream, a); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
