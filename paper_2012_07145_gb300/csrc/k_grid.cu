@@ -3,8 +3,9 @@
 // range levels of size r, and the trilinear slice of the blurred grid back to
 // the image.  The grid is a (ceil(W/s)+1) x (ceil(H/s)+1) image of 2 GZ
 // channels: channel 2z holds the sum of the values of range level z, channel
-// 2z+1 their count.  (The blur between them is a point-wise op along the range
-// levels and two 5-tap stencils: the generic kernels.)
+// 2z+1 their count.  The blur between them (a point-wise op along the range
+// levels and two 5-tap stencils) is one streaming kernel, k_grid_blur, below;
+// any other grouping of those stages runs on the generic kernel.
 //
 // k_grid_splat: one thread per cell (any s) or four (s = 8, k_grid_splat8: two
 //   pixel rows each, their copies added in a fixed order); each walks its
