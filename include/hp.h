@@ -65,7 +65,8 @@ typedef enum {
   HP_DOWNSAMPLE2 = 2,  /* binomial [1,4,6,4,1]/16 per axis at (2x+i, 2y+j); size ceil(W/2) x ceil(H/2) */
   HP_UPSAMPLE2 = 3,    /* zero-stuff + [1,4,6,4,1]/8 per axis, coarse index clamped; inputs[1] is a
                           size reference whose domain the output takes (it is not read) */
-  HP_HISTOGRAM = 4,    /* 256-bin counts of a 1-channel u8 image; output 256 x 1 u32 */
+  HP_HISTOGRAM = 4,    /* 256-bin counts of a 1-channel u8 image; output 256 x 1 u32; images of
+                          more than 2^32 - 1 pixels are refused (HP_ERR_UNSUPPORTED) */
   HP_CDF_LUT = 5,      /* equalization LUT (256 x 1 u8) from a histogram stage */
   HP_LUT_APPLY = 6,    /* out = lut[in] for a 1-channel u8 image */
   HP_MAX_STENCIL = 7,  /* per channel, the maximum over the (2rx+1) x (2ry+1) window at clamped

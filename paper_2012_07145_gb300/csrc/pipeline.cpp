@@ -340,7 +340,14 @@ hp_status infer_domains(const hp_pipeline* p, const std::vector<Dom>& in_dom, st
         dom[s] = r;
         break;
       }
-      case HP_HISTOGRAM: case HP_CDF_LUT: dom[s] = Dom{256, 1}; break;
+      case HP_HISTOGRAM:
+        // the bin counters (and the table's running sums) are 32-bit
+        if ((unsigned long long)d0.w * (unsigned long long)d0.h > 4294967295ULL)
+          return fail(HP_ERR_UNSUPPORTED, "stage %zu: a histogram counts at most 2^32 - 1 pixels (%dx%d given)", s, d0.w,
+                      d0.h);
+        dom[s] = Dom{256, 1};
+        break;
+      case HP_CDF_LUT: dom[s] = Dom{256, 1}; break;
       case HP_GRID_SPLAT: {
         const int gs = (int)st.params[0];
         dom[s] = Dom{(d0.w + gs - 1) / gs + 1, (d0.h + gs - 1) / gs + 1};

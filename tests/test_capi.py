@@ -229,3 +229,16 @@ def test_new_stage_kinds_validation_and_lowering():
     ks = [q.group_info([(64, 48)], k).kernel for k in range(q.group_count())]
     assert ks[0] == hp.HP_KERNEL_PW_ROWS and ks[-1] == hp.HP_KERNEL_INTERP_ROWS
     assert q.group_info([(64, 48)], q.group_count() - 1).n_members == 3   # upsample, over, division
+
+
+def test_histogram_refuses_images_beyond_its_32_bit_counters():
+    """The bin counters and the table's running sums are 32-bit: an image of
+    2^32 - 1 pixels or fewer lowers, one of more is refused with a message."""
+    h = pipelines.histeq()
+    assert h.group_info([(65535, 65537)], 0).kernel == hp.HP_KERNEL_HISTOGRAM   # 2^32 - 1 pixels
+    with pytest.raises(hp.HPError) as e:
+        h.group_info([(65536, 65536)], 0)
+    assert e.value.status == hp.HP_ERR_UNSUPPORTED and "2^32 - 1" in str(e.value)
+    pipelines.fused_schedule(h)
+    with pytest.raises(hp.HPError):
+        h.group_info([(65536, 65536)], 0)
