@@ -679,7 +679,7 @@ def run_reference(args, cfg_name):
     t0 = time.perf_counter()
     fn()
     per_row = (time.perf_counter() - t0) / probe_rows
-    rows = int(max(4, min(cfg["h"], 120.0 / max(args.steps, 1) / per_row)))
+    rows = int(max(1, min(cfg["h"], 120.0 / max(args.steps, 1) / per_row)))   # a band of one row at least
     fn = cfg["oracle_sample"](rows)
     for _ in range(min(args.warmup, 1)):
         fn()
