@@ -27,6 +27,7 @@
 #include <thread>
 #include <vector>
 
+#include "arena.h"
 #include "hp_internal.h"
 
 namespace hp {
@@ -40,7 +41,8 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 int dtype_size(int d) { return d == HP_U8 ? 1 : (d == HP_U16 || d == HP_F16 || d == HP_BF16) ? 2 : 4; }
-long long r256(long long v) { return (v + 255) / 256 * 256; }
+using hp::Arena;
+long long r256(long long v) { return hp::round256(v); }
 
 struct Request {
   unsigned long long ticket = 0;
@@ -48,47 +50,6 @@ struct Request {
   std::vector<hp_buffer> in;
   hp_buffer out{};
   Clock::time_point t_submit;
-};
-
-// First-fit allocator over one device arena.
-struct Arena {
-  char* base = nullptr;
-  long long size = 0;
-  std::map<long long, long long> free_blocks;  // offset -> size
-  long long used = 0, peak = 0;
-
-  bool alloc(long long bytes, long long* off) {
-    bytes = r256(bytes);
-    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
-      if (it->second < bytes) continue;
-      *off = it->first;
-      long long rest = it->second - bytes;
-      long long at = it->first + bytes;
-      free_blocks.erase(it);
-      if (rest > 0) free_blocks[at] = rest;
-      used += bytes;
-      peak = std::max(peak, used);
-      return true;
-    }
-    return false;
-  }
-  void release(long long off, long long bytes) {
-    bytes = r256(bytes);
-    used -= bytes;
-    auto it = free_blocks.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_blocks.erase(nx);
-    }
-    if (it != free_blocks.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_blocks.erase(it);
-      }
-    }
-  }
 };
 
 struct Slot {
@@ -312,9 +273,7 @@ hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slot
     delete s;
     return hp::report_error(HP_ERR_OOM, "hp_server_create: cannot reserve the HBM budget");
   }
-  s->arena.base = (char*)base;
-  s->arena.size = hbm_budget_bytes;
-  s->arena.free_blocks[0] = hbm_budget_bytes / 256 * 256;
+  s->arena.init((char*)base, hbm_budget_bytes);
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
