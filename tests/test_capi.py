@@ -242,3 +242,20 @@ def test_histogram_refuses_images_beyond_its_32_bit_counters():
     pipelines.fused_schedule(h)
     with pytest.raises(hp.HPError):
         h.group_info([(65536, 65536)], 0)
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: with libhp.so absent, the first call raises and names the
+    build step (run in a child process so this process keeps its library)."""
+    import subprocess
+    import sys
+    code = ("from paper_2012_07145_gb300 import hp\n"
+            "hp.LIB_PATH = '/nonexistent/libhp.so'\n"
+            "try:\n"
+            "    hp.Pipeline([hp.HP_F32], [1])\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "else:\n"
+            "    print('no error')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert "raised:" in r.stdout and "build" in r.stdout, r.stdout + r.stderr
