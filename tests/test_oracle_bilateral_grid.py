@@ -78,3 +78,16 @@ def test_slice_of_a_linear_grid_is_the_linear_function():
     ys, xs = np.mgrid[0:H, 0:W]
     exp = 0.5 + 0.1 * np.minimum(xs / s, GX - 1) + 0.2 * np.minimum(ys / s, GY - 1) + 0.3 * (img / r)
     np.testing.assert_allclose(out, exp, rtol=0, atol=1e-12)
+
+
+def test_blur_is_the_separable_binomial_in_three_axes():
+    # an impulse far from every edge spreads into b(y) b(x) b(z), b = [1,4,6,4,1]/16,
+    # in the value channel only: the blur acts on all three grid axes
+    g = np.zeros((9, 10, 11, 2))
+    g[4, 5, 5, 0] = 1.0
+    out = ob.blur(g)
+    b = np.array([1.0, 4.0, 6.0, 4.0, 1.0]) / 16.0
+    exp = np.zeros((9, 10, 11))
+    exp[2:7, 3:8, 3:8] = b[:, None, None] * b[None, :, None] * b[None, None, :]
+    np.testing.assert_allclose(out[..., 0], exp, rtol=0, atol=1e-15)
+    assert not out[..., 1].any()
