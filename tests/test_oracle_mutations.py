@@ -164,6 +164,51 @@ def _slice_swapped_weights(g, img, s, r):
     return np.where(acc[..., 1] > 0, acc[..., 0] / np.where(acc[..., 1] > 0, acc[..., 1], 1.0), v)
 
 
+def _point_from_a_crop_too_small(img, kinds, x, y):
+    """A point evaluated on a crop of radius n (the chain's reach is 2n), whose
+    cut edges then act as clamp boundaries."""
+    img = np.asarray(img, dtype=np.float64)
+    n = len(kinds)
+    y0, x0 = max(y - n, 0), max(x - n, 0)
+    crop = img[y0:y + n + 1, x0:x + n + 1]
+    return float(ost.stencil_chain(crop, kinds)[y - y0, x - x0])
+
+
+def _upsample_wrapping(coarse, fine_shape):
+    """Upsample whose coarse index wraps around instead of clamping."""
+    coarse = np.asarray(coarse, dtype=np.float64)
+    hc, wc = coarse.shape
+    H, W = fine_shape
+    Y, X = np.arange(H), np.arange(W)
+    out = np.zeros((H, W))
+    for s in range(-2, 3):
+        row_ok = (Y - s) % 2 == 0
+        n = ((Y - s) // 2) % hc
+        for t in range(-2, 3):
+            col_ok = (X - t) % 2 == 0
+            m = ((X - t) // 2) % wc
+            out += np.where(row_ok[:, None] & col_ok[None, :], (pm.UP_TAPS[s] * pm.UP_TAPS[t]) * coarse[np.ix_(n, m)], 0.0)
+    return out
+
+
+def _histogram_off_by_one(img_u8):
+    h = [0] * 256
+    for v in np.asarray(img_u8, dtype=np.uint8).ravel().tolist():
+        h[min(v + 1, 255)] += 1
+    return h
+
+
+def _max_filter_wrapping(img, rx, ry):
+    img = np.asarray(img)
+    H, W = img.shape
+    out = None
+    for j in range(-ry, ry + 1):
+        for i in range(-rx, rx + 1):
+            v = img[np.ix_((np.arange(H) + j) % H, (np.arange(W) + i) % W)]
+            out = v.copy() if out is None else np.maximum(out, v)
+    return out
+
+
 MISTAKES = {
     # stencil chains
     "box weights 1/24": ([(ost, "box5_weights", lambda: np.full((5, 5), 1.0 / 24.0))], STENCIL_PINS),
@@ -174,6 +219,11 @@ MISTAKES = {
                                                                           for k in range(n)] if p == "alternate"
                                       else ["binomial"] * n)], STENCIL_PINS),
     "clamp on the input only": ([(ost, "stencil_chain", _chain_clamped_on_input_only)], STENCIL_PINS),
+    "point evaluated on too small a crop": ([(ost, "stencil_chain_point", _point_from_a_crop_too_small)], STENCIL_PINS),
+    "upsample index wraps": ([(pm, "upsample", _upsample_wrapping)], PYRAMID_PINS),
+    "histogram bin off by one": ([(oeq, "histogram", _histogram_off_by_one)], UNSHARP_HISTEQ_PINS),
+    "max window wraps around": ([(om, "max_filter", _max_filter_wrapping)], MAX_PINS),
+    "no division by coverage": ([(oi, "unpremultiply", lambda v: np.array(v[:3], dtype=np.float64))], INTERP_PINS),
     # pyramids
     "downsample at odd pixels": ([(pm, "downsample", _downsample_odd)], PYRAMID_PINS),
     "upsample taps over 16": ([(pm, "UP_TAPS", {k: v / 2.0 for k, v in pm.UP_TAPS.items()})], PYRAMID_PINS),
