@@ -209,6 +209,29 @@ def _max_filter_wrapping(img, rx, ry):
     return out
 
 
+def _ll_interp_weights_swapped(rgb_u16, levels=8, k_levels=8, sigma_r=0.1, alpha=1.0, beta=1.0):
+    """The local Laplacian with the two levels' weights exchanged (f on the
+    lower level, 1 - f on the upper)."""
+    inp = np.asarray(rgb_u16, dtype=np.float64) / 65535.0
+    gray = oll.GRAY_WEIGHTS[0] * inp[0] + oll.GRAY_WEIGHTS[1] * inp[1] + oll.GRAY_WEIGHTS[2] * inp[2]
+    g_pyr = pm.gaussian_pyramid(gray, levels)
+    lap_k = [pm.laplacian_pyramid(pm.gaussian_pyramid(oll.remap(gray, k / (k_levels - 1), sigma_r, alpha, beta), levels))
+             for k in range(k_levels)]
+    out_lap = []
+    for l in range(levels - 1):
+        t = g_pyr[l] * (k_levels - 1)
+        k0 = np.minimum(np.floor(t), k_levels - 2).astype(np.int64)
+        f = t - k0
+        stack = np.stack([lap_k[k][l] for k in range(k_levels)])
+        lo = np.take_along_axis(stack, k0[None], axis=0)[0]
+        hi = np.take_along_axis(stack, (k0 + 1)[None], axis=0)[0]
+        out_lap.append(f * lo + (1.0 - f) * hi)
+    out_lap.append(g_pyr[levels - 1])
+    out_gray = pm.collapse(out_lap)
+    safe = np.where(gray > 0, gray, 1.0)
+    return np.where((gray > 0)[None], inp * (out_gray / safe)[None], out_gray[None])
+
+
 MISTAKES = {
     # stencil chains
     "box weights 1/24": ([(ost, "box5_weights", lambda: np.full((5, 5), 1.0 / 24.0))], STENCIL_PINS),
@@ -238,6 +261,7 @@ MISTAKES = {
     # local Laplacian
     "remap detail branch sign": ([(oll, "remap", _remap_detail_sign)], LL_PINS),
     "collapse adds Laplacians (LL)": ([(oll, "collapse", _collapse_with_laplacians)], LL_PINS),
+    "LL level weights exchanged": ([(oll, "local_laplacian_float", _ll_interp_weights_swapped)], LL_PINS),
     "u16 by truncation": ([(oll, "quantize_u16", lambda x: np.clip(np.floor(np.asarray(x) * 65535.0), 0, 65535)
                             .astype(np.uint16))], LL_PINS),
     "LL gray weights R and B swapped": ([(oll, "GRAY_WEIGHTS", (0.114, 0.587, 0.299))], LL_PINS),
