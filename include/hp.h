@@ -225,9 +225,9 @@ enum {
   HP_KERNEL_PW_ROWS = 20,       /* one point-wise stage over f32 images (add, sub, mul, scale,
                                   unsharp combine, premultiply, over, unpremultiply): 4 pixels per
                                   thread, 128-bit loads and stores */
-  HP_KERNEL_GRID_SPLAT = 21,    /* bilateral grid splat: one thread per cell, accumulators in
-                                  shared memory */
-  HP_KERNEL_GRID_SLICE = 22,    /* bilateral grid slice: one thread per pixel, trilinear */
+  HP_KERNEL_GRID_SPLAT = 21,    /* bilateral grid splat: one thread per cell (four, two pixel rows
+                                  each, for 8 x 8 cells), accumulators in shared memory */
+  HP_KERNEL_GRID_SLICE = 22,    /* bilateral grid slice: four pixels of a row per thread, trilinear */
   HP_KERNEL_GRID_BLUR = 23      /* bilateral grid blur (range levels, x, y; binomial/16), streaming:
                                   one warp per 28 grid columns x 4 range levels, y taps in order */
 };
@@ -322,6 +322,10 @@ typedef struct {
   double busy_s;                        /* first submit to last completion */
 } hp_server_stats;
 
+/* Reserves the arena (cudaMalloc of hbm_budget_bytes, at least 1 MiB), creates
+ * `slots` streams (1..64) and the worker thread; max_batch is 1..64.
+ * HP_ERR_INVALID_ARG for arguments out of range, HP_ERR_OOM if the arena
+ * cannot be reserved. */
 hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slots, int max_batch);
 /* Enqueues a request; *ticket identifies it.  Never blocks on the GPU. */
 hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
@@ -341,7 +345,8 @@ hp_status hp_server_destroy(hp_server* s);
 /* Reads and clears the pipeline's device error word (synchronises the device).
  * *code: 0 = no error; 1 = a bounded TMA/mbarrier wait gave up; 2 = a fused
  * kernel's read fell outside the tile bounds inference gave it (the read was
- * skipped).  A non-zero code means the last outputs are not valid. */
+ * skipped); 3 = the fused histogram equalization's grid-wide barrier gave up.
+ * A non-zero code means the last outputs are not valid. */
 hp_status hp_check_device_error(hp_pipeline* p, int* code);
 
 hp_status hp_pipeline_destroy(hp_pipeline* p);
