@@ -259,3 +259,19 @@ def test_binding_fails_loudly_without_the_library():
             "    print('no error')\n")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
     assert "raised:" in r.stdout and "build" in r.stdout, r.stdout + r.stderr
+
+
+def test_server_argument_validation_needs_no_gpu():
+    """Out-of-range server arguments are refused before any CUDA call, and the
+    calls on a null server handle return errors instead of crashing."""
+    for budget, slots, batch in ((1 << 19, 4, 8), (1 << 30, 0, 8), (1 << 30, 65, 8), (1 << 30, 4, 0), (1 << 30, 4, 65)):
+        with pytest.raises(hp.HPError) as e:
+            hp.Server(budget, slots, batch)
+        assert e.value.status == hp.HP_ERR_INVALID_ARG
+    L = hp.lib()
+    t = ctypes.c_ulonglong()
+    assert L.hp_server_submit(None, None, None, 0, None, ctypes.byref(t)) == hp.HP_ERR_INVALID_ARG
+    stats = hp.ServerStats()
+    assert L.hp_server_stats_get(None, ctypes.byref(stats)) != hp.HP_OK
+    lat = ctypes.c_double()
+    assert L.hp_server_wait(None, 1, 0, ctypes.byref(lat)) != hp.HP_OK
