@@ -1,6 +1,7 @@
-"""Every benchmark workload lowers, on the CPU, to the kernels its schedules
-name, at its full size (no GPU needed): the fused and stage-per-kernel
-schedules, and the dominant group timed alone where a step has several."""
+"""Host logic of bench.py, on the CPU: every benchmark workload lowers to the
+kernels its schedules name, at its full size (the fused and stage-per-kernel
+schedules, and the dominant group timed alone where a step has several); the
+clocks record summarises the samples of the timed region."""
 
 import importlib.util
 import os
@@ -54,3 +55,50 @@ def test_fused_schedules_use_the_specialised_kernels(table):
         names = [hp.KERNEL_NAMES[p.group_info([(cfg["w"], cfg["h"])], g).kernel] for g in range(p.group_count())]
         assert kname in names, (name, names)
         assert "generic" not in names, (name, names)   # no group falls back to the interpreter
+
+
+def _bench_module():
+    spec = importlib.util.spec_from_file_location("bench_clk", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    return b
+
+
+class _DoneProcess:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_summary_takes_the_timed_region_and_names_throttle_reasons():
+    """The clocks record of a bench line: the median SM clock of the samples
+    inside the timed region, the maximum clock, and every throttle reason seen
+    active there (samples before or after the region are ignored)."""
+    b = _bench_module()
+    c = b.ClockSampler(0)
+    c.proc = _DoneProcess()
+    row = "0, {sm}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {pc}"
+    c.lines = [(0.0, row.format(sm=1000, hw="Active", pc="Not Active")),        # before the region
+               (1.0, row.format(sm=2070, hw="Not Active", pc="Not Active")),
+               (1.1, row.format(sm=1980, hw="Not Active", pc="Active")),
+               (1.2, row.format(sm=2070, hw="Not Active", pc="Not Active")),
+               (1.3, "garbage line"),
+               (9.0, row.format(sm=500, hw="Active", pc="Not Active"))]         # after the region
+    c.t0, c.t1 = 0.9, 1.25
+    out = b.ClockSampler.stop(c)
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append((1.15, row.format(sm=1400, hw="Active", pc="Not Active")))
+    out = b.ClockSampler.stop(c)
+    assert out["reasons"] == ["hw_slowdown", "sw_power_cap"] and out["samples"] == 4
+
+
+def test_clock_summary_of_a_region_shorter_than_the_sampling_period():
+    b = _bench_module()
+    c = b.ClockSampler(0)
+    c.proc = _DoneProcess()
+    c.lines = [(0.0, "0, 1500, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"),
+               (2.0, "0, 2070, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active")]
+    c.t0, c.t1 = 1.0, 1.01           # no sample inside: the first one after the region starts
+    assert b.ClockSampler.stop(c)["sm_mhz"] == 2070.0
