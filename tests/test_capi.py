@@ -275,3 +275,23 @@ def test_server_argument_validation_needs_no_gpu():
     assert L.hp_server_stats_get(None, ctypes.byref(stats)) != hp.HP_OK
     lat = ctypes.c_double()
     assert L.hp_server_wait(None, 1, 0, ctypes.byref(lat)) != hp.HP_OK
+
+
+def test_bounds_inference_max_filter_and_upsample():
+    # max filter fused: the horizontal stage is needed on the tile grown by the
+    # vertical radius in y only, clamped to the image
+    p = pipelines.max_filter(3)
+    p.schedule([0, 0])
+    r = p.infer_bounds([(100, 60)], 0, 32, 16, 16, 8)
+    assert r[1] == (32, 16, 48, 24)
+    assert r[0] == (32, 13, 48, 27)
+    r = p.infer_bounds([(100, 60)], 0, 0, 56, 16, 8)    # ragged bottom tile
+    assert r[1] == (0, 56, 16, 60) and r[0] == (0, 53, 16, 60)
+    # interpolate's finest level fused (upsample of I_1, composite, division):
+    # the point-wise consumers need the upsample exactly on the tile, and a
+    # ragged tile is clamped to the fine domain
+    q = pipelines.interpolate_finest()
+    out = q.infer_bounds([(64, 40), (32, 20)], 0, 16, 8, 16, 8)
+    assert out == [(16, 8, 32, 16)] * 3
+    out = q.infer_bounds([(63, 39), (32, 20)], 0, 48, 32, 16, 8)
+    assert out == [(48, 32, 63, 39)] * 3
