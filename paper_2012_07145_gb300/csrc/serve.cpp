@@ -298,6 +298,10 @@ hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs
       delete r;
       return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty input buffer");
     }
+  if (!r->out.data || r->out.width < 1 || r->out.height < 1 || r->out.channels < 1) {
+    delete r;
+    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty output buffer");
+  }
   if (request_bytes(*r) > s->arena.size) {
     delete r;
     return hp::report_error(HP_ERR_OOM, "hp_server_submit: request larger than the whole HBM budget");
