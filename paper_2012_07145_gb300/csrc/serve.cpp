@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -276,8 +277,20 @@ hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slot
   s->arena.init((char*)base, hbm_budget_bytes);
   s->slots.resize(slots);
   for (Slot& sl : s->slots) {
-    cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    const cudaError_t e1 = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) : e1;
+    if (e2 != cudaSuccess) {  // undo what was created so far
+      cudaGetLastError();
+      for (Slot& o : s->slots) {
+        if (o.stream) cudaStreamDestroy(o.stream);
+        if (o.done) cudaEventDestroy(o.done);
+      }
+      cudaFree(base);
+      delete s;
+      char msg[160];
+      snprintf(msg, sizeof msg, "hp_server_create: stream or event creation failed: %s", cudaGetErrorString(e2));
+      return hp::report_error(HP_ERR_CUDA, msg);
+    }
   }
   s->max_batch = max_batch;
   s->worker = std::thread(worker_loop, s);
