@@ -1864,6 +1864,24 @@ static hp_status collect_in_dom(hp_pipeline* p, const hp_buffer* inputs, int n_i
   return HP_OK;
 }
 
+// The pipeline's device error word: allocated once, cleared on the caller's
+// stream (no device-wide wait).
+static hp_status alloc_error_word(hp_pipeline* p, void* stream) {
+  if (cudaMalloc(&p->d_err, 16) != cudaSuccess) {
+    cudaGetLastError();
+    p->d_err = nullptr;
+    return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
+  }
+  const cudaError_t e = cudaMemsetAsync(p->d_err, 0, 16, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p->d_err);
+    p->d_err = nullptr;
+    return fail(HP_ERR_CUDA, "clearing the error word failed: %s", cudaGetErrorString(e));
+  }
+  return HP_OK;
+}
+
 hp_status hp_prepare(hp_pipeline* p, const int* widths, const int* heights, int n_inputs, void* stream) {
   if (!p || !widths || !heights || n_inputs != (int)p->in_dtypes.size())
     return fail(HP_ERR_INVALID_ARG, "hp_prepare: expected %d input sizes", p ? (int)p->in_dtypes.size() : 0);
@@ -1876,11 +1894,7 @@ hp_status hp_prepare(hp_pipeline* p, const int* widths, const int* heights, int 
   hp_status s = get_plan(p, in_dom, &plan);
   if (s) return s;
   if (!p->d_err) {
-    if (cudaMalloc(&p->d_err, 16) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
-    }
-    cudaMemsetAsync(p->d_err, 0, 16, (cudaStream_t)stream);
+    if ((s = alloc_error_word(p, stream))) return s;
   }
   return ensure_scratch(p, *plan, (cudaStream_t)stream);
 }
@@ -1894,11 +1908,7 @@ hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, cons
   if ((s = get_plan(p, in_dom, &plan))) return s;
   const Stage& os = p->stages[p->output];
   if ((s = check_buffer(*output, os.storage, os.channels, plan->dom[p->output], "output", 0))) return s;
-  if (!p->d_err) {
-    int e = cudaMalloc(&p->d_err, 16);
-    if (e) return fail(HP_ERR_OOM, "cudaMalloc of the error word failed");
-    cudaMemsetAsync(p->d_err, 0, 16, (cudaStream_t)stream);  // on the caller's stream: no device-wide wait
-  }
+  if (!p->d_err && (s = alloc_error_word(p, stream))) return s;
   if ((s = ensure_scratch(p, *plan, (cudaStream_t)stream))) return s;
   if (!p->use_graph) return run_groups(p, *plan, inputs, output, stream);
   return run_graph(p, *plan, inputs, n_inputs, output, stream);
