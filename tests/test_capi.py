@@ -295,3 +295,34 @@ def test_bounds_inference_max_filter_and_upsample():
     assert out == [(16, 8, 32, 16)] * 3
     out = q.infer_bounds([(63, 39), (32, 20)], 0, 48, 32, 16, 8)
     assert out == [(48, 32, 63, 39)] * 3
+
+
+def test_realize_rejects_bad_buffers_before_touching_the_device():
+    """Null, misaligned, wrongly typed, wrongly shaped or too tightly strided
+    buffers are refused with HP_ERR_INVALID_ARG by the host checks, before any
+    CUDA call (the addresses are never dereferenced)."""
+    p = pipelines.stencil_chain(2)
+    W, H = 40, 24
+    A = 1 << 20                      # a 16-byte-aligned address that is never read
+
+    def buf(data=A, dtype=hp.HP_F32, c=1, w=W, h=H, rs=192, ps=192 * H):
+        return hp.Buffer(data, dtype, c, w, h, rs, ps)
+
+    good = buf()
+    cases = {
+        "null input": ([buf(data=0)], good),
+        "misaligned input": ([buf(data=A + 4)], good),
+        "row stride not a multiple of 16": ([buf(rs=168, ps=168 * H)], good),
+        "row stride below the width": ([buf(rs=144, ps=144 * H)], good),
+        "input dtype": ([buf(dtype=hp.HP_F16)], good),
+        "input channels": ([buf(c=3, ps=192 * H)], good),
+        "empty input": ([buf(w=0)], good),
+        "output size": ([good], buf(w=W - 1)),
+        "output dtype": ([good], buf(dtype=hp.HP_U8)),
+        "null output": ([good], buf(data=0)),
+        "input count": ([good, good], good),
+    }
+    for name, (ins, out) in cases.items():
+        with pytest.raises(hp.HPError) as e:
+            p.realize(ins, out)
+        assert e.value.status == hp.HP_ERR_INVALID_ARG, (name, str(e.value))
