@@ -102,3 +102,18 @@ def test_clock_summary_of_a_region_shorter_than_the_sampling_period():
                (2.0, "0, 2070, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active")]
     c.t0, c.t1 = 1.0, 1.01           # no sample inside: the first one after the region starts
     assert b.ClockSampler.stop(c)["sm_mhz"] == 2070.0
+
+
+@pytest.mark.parametrize("size", [(1, 1), (2, 3), (7, 5), (33, 17), (250, 130)])
+def test_every_workload_lowers_at_tiny_and_ragged_sizes(table, size):
+    """Degenerate and ragged images lower under both schedules of every
+    workload (a pyramid of 1x1 levels, one partial tile or strip)."""
+    for name, cfg in table.items():
+        plain = cfg["build"]()
+        fused = cfg["build"]()
+        cfg["fused"](fused)
+        for p in (plain, fused):
+            for g in range(p.group_count()):
+                info = p.group_info([size], g)
+                assert 0 <= info.kernel < len(hp.KERNEL_NAMES), (name, size, g)
+                assert info.grid_x >= 1 and info.grid_y >= 1 and info.threads >= 32, (name, size, g)
