@@ -35,10 +35,7 @@ __device__ __forceinline__ int range_level(float v, float inv_r, int gz) {
   return iclamp((int)floorf(__fmaf_rn(v, inv_r, 0.5f)), 0, gz - 1);
 }
 
-// S: the cell size when it is known at compile time (8: the loads of a row are
-// two 128-bit loads, and every row's loads are issued before the sums); 0:
-// any size.
-template <int S>
+// Any cell size s: one thread per cell walks its s x s pixels in row order.
 __global__ void __launch_bounds__(kSplatThreads) k_grid_splat(const GridArgs a) {
   grid_dep_sync();
   __shared__ float acc[2 * kMaxGZ * kSplatThreads];
@@ -47,40 +44,15 @@ __global__ void __launch_bounds__(kSplatThreads) k_grid_splat(const GridArgs a) 
   if (gx >= a.grid.w) return;  // no barrier below: each thread owns its column of acc
   for (int j = 0; j < 2 * a.gz; ++j) acc[j * kSplatThreads + t] = 0.0f;
   const int W = a.in.w, H = a.in.h;
-  auto add = [&](float v) {
-    const int z = range_level(v, a.inv_r, a.gz);
-    float* p = acc + 2 * z * kSplatThreads + t;
-    p[0] = __fadd_rn(p[0], v);
-    p[kSplatThreads] = __fadd_rn(p[kSplatThreads], 1.0f);
-  };
-  if (S > 0) {
-    const int x0 = gx * S - S / 2;
-    const bool inner = x0 >= 0 && x0 + S - 1 <= W - 1 && a.in.dtype == HP_F32 && S % 4 == 0;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-      const int y = iclamp(gy * S + j - S / 2, 0, H - 1);
-      float v[S > 0 ? S : 1];
-      if (inner) {
-        const float4* row = reinterpret_cast<const float4*>((const char*)a.in.data + (long long)y * a.in.rs) + (x0 >> 2);
-#pragma unroll
-        for (int q = 0; q < S / 4; ++q) {
-          const float4 f = __ldg(row + q);
-          v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
-        }
-#pragma unroll
-        for (int i = 0; i < S; ++i) v[i] = fminf(fmaxf(v[i], 0.0f), 1.0f);
-      } else {
-#pragma unroll
-        for (int i = 0; i < S; ++i) v[i] = gray_at(a.in, iclamp(x0 + i, 0, W - 1), y);
-      }
-#pragma unroll
-      for (int i = 0; i < S; ++i) add(v[i]);
-    }
-  } else {
-    const int s = a.s;
-    for (int j = 0; j < s; ++j) {
-      const int y = iclamp(gy * s + j - s / 2, 0, H - 1);
-      for (int i = 0; i < s; ++i) add(gray_at(a.in, iclamp(gx * s + i - s / 2, 0, W - 1), y));
+  const int s = a.s;
+  for (int j = 0; j < s; ++j) {
+    const int y = iclamp(gy * s + j - s / 2, 0, H - 1);
+    for (int i = 0; i < s; ++i) {
+      const float v = gray_at(a.in, iclamp(gx * s + i - s / 2, 0, W - 1), y);
+      const int z = range_level(v, a.inv_r, a.gz);
+      float* p = acc + 2 * z * kSplatThreads + t;
+      p[0] = __fadd_rn(p[0], v);
+      p[kSplatThreads] = __fadd_rn(p[kSplatThreads], 1.0f);
     }
   }
   for (int j = 0; j < 2 * a.gz; ++j)
@@ -207,7 +179,7 @@ int launch_grid_splat(const GridArgs& a, void* stream) {
     { const int le_ = launch_kernel(k_grid_splat8, grid8, dim3(128), 0, stream, a); if (le_) return le_; }
   } else {
     dim3 grid((a.grid.w + kSplatThreads - 1) / kSplatThreads, a.grid.h, 1);
-    { const int le_ = launch_kernel(k_grid_splat<0>, grid, dim3(kSplatThreads), 0, stream, a); if (le_) return le_; }
+    { const int le_ = launch_kernel(k_grid_splat, grid, dim3(kSplatThreads), 0, stream, a); if (le_) return le_; }
   }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
