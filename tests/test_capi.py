@@ -326,3 +326,17 @@ def test_realize_rejects_bad_buffers_before_touching_the_device():
         with pytest.raises(hp.HPError) as e:
             p.realize(ins, out)
         assert e.value.status == hp.HP_ERR_INVALID_ARG, (name, str(e.value))
+
+
+def test_binding_constants_equal_the_header():
+    """Every enumerator of include/hp.h has the same value in the binding, and
+    the kernel names follow the HP_KERNEL_* ids."""
+    text = open(os.path.join(ROOT, "include", "hp.h")).read()
+    pairs = re.findall(r"\b(HP_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)
+    assert len(pairs) >= 60
+    for name, value in pairs:
+        assert getattr(hp, name) == int(value), name
+    assert hp.HP_INLINE == -1
+    kernels = sorted((int(v), n) for n, v in pairs if n.startswith("HP_KERNEL_"))
+    assert [v for v, _ in kernels] == list(range(len(hp.KERNEL_NAMES)))
+    assert [n[len("HP_KERNEL_"):].lower() for _, n in kernels] == list(hp.KERNEL_NAMES)
