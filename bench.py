@@ -30,8 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPix/s fused vs stage-per-kernel on 1 GB300 at stated tol; %HBM roofline; p50/p99"
 L2_FLUSH_BYTES = 256 << 20
-SMS = 152
 FP32_LANES_PER_SM = 128
+# the workloads the default line also reports, compactly, beside the headline
+DEFAULT_CONFIGS = "chain4,chain32_f16,chain32_bf16,harris,harris_bf16,unsharp,histeq,ll,serving"
 
 
 # ------------------------------------------------------------------ configs --
@@ -56,10 +57,18 @@ def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
         ref = [ost.stencil_chain_point(img, ost.chain_kinds(n, pattern), x, y) for x, y in pts]
         return max(abs(float(out[0][y, x]) - r) for (x, y), r in zip(pts, ref))
 
+    # the method's work per output pixel (a separable 5x5 stage, per pass):
+    # binomial ((a+e) + 4(b+d)) + 6c, then x 1/16: 7 flops (an fma counts 2);
+    # box (((a+b) + (c+d)) + e) x 1/5: 5 flops
+    n_binomial = sum(1 for k in range(n) if pattern == "binomial" or k % 2 == 0)
+    flops_px = 14 * n_binomial + 10 * (n - n_binomial)
+    algorithmic = (f"{flops_px} FP32 flops per output pixel: {n_binomial} binomial stages x 14 + "
+                   f"{n - n_binomial} box stages x 10 (2 separable passes each, fma = 2 flops)")
     return dict(workload=f"stencil_chain_{n}_{pattern}_{W}x{H}_{storage_name}", h=H, w=W,
                 inputs=lambda seed: [(synth.stencil_input(H, W, seed=seed), st)], out=(1, H, W, st),
                 build=lambda: pipelines.stencil_chain(n, pattern, storage=st), fused=fused,
-                flops_px=n * 18, bytes_px=2 * esize, bound="alu", kernel="k_chain", dtype=storage_name,
+                flops_px=flops_px, algorithmic=algorithmic, fp32_instr_px=10 * n,
+                bytes_px=2 * esize, bound="alu", kernel="k_chain", dtype=storage_name,
                 oracle_sample=oracle_sample, parity=parity, sample_rows=64)
 
 
@@ -452,6 +461,146 @@ def _to_numpy(t, dt):
     return t.cpu().numpy()
 
 
+def measure_fp32_peak(device_index):
+    """FP32 peak of this GPU, measured (hp_measure_fp32_peak): scalar fma and
+    paired fma.rn.f32x2 kernels on every SM, each timed with CUDA events over
+    about 0.3 s while nvidia-smi samples the SM clock.  The peak is the faster
+    form; flops per MHz normalise it to the clock it ran at."""
+    import torch
+    from paper_2012_07145_gb300 import hp
+    s = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for paired in (False, True):
+        f, ms, sms = hp.measure_fp32_peak(paired, iters=512, launches=4, stream=s)      # size the run
+        launches = max(10, int(300.0 / max(ms, 1e-3)))
+        sampler = ClockSampler(device_index)
+        sampler.start()
+        sampler.mark_begin()
+        f, ms, sms = hp.measure_fp32_peak(paired, iters=512, launches=launches, stream=s)
+        sampler.mark_end()
+        clk = sampler.stop()
+        out["paired" if paired else "scalar"] = {"tflops": round(f / 1e12, 3), "ms_per_launch": round(ms, 4),
+                                                 "launches": launches, "sm_mhz": clk["sm_mhz"],
+                                                 "reasons": clk["reasons"]}
+        out["sms"] = sms
+    best = max(("scalar", "paired"), key=lambda k: out[k]["tflops"])
+    out["peak_tflops"] = out[best]["tflops"]
+    out["peak_form"] = best
+    mhz = out[best]["sm_mhz"]
+    out["tflops_per_ghz"] = round(out[best]["tflops"] / (mhz / 1e3), 3) if mhz else None
+    out["nominal_tflops_at_2070_mhz"] = round(out["sms"] * FP32_LANES_PER_SM * 2 * 2.07e9 / 1e12, 2)
+    return out
+
+
+def measure_config(cfg_name, cfg, steps, warmup, flush, stream, peaks, peak_kind, fp32, local=0, world=1,
+                   headline=False):
+    """Times one workload: the stage-per-kernel comparator, the fused tuned
+    schedule (with clocks sampled during its timed region), the roofline of
+    its dominant kernel and a parity spot check.  Returns the measurements
+    and the objects the end-to-end timing needs."""
+    import torch
+    from paper_2012_07145_gb300 import hp
+    H, W = cfg["h"], cfg["w"]
+    C, OH, OW, odt = cfg["out"]
+    rank = int(os.environ.get("RANK", "0"))
+    inputs = cfg["inputs"](rank)
+    dev_in = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in inputs]
+    yout = hp.padded_empty(C, OH, OW, _torch_dtype(odt), "cuda")
+    bi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dev_in, inputs)]
+    bo = hp.buffer_from_tensor(yout, odt)
+    # stage-per-kernel comparator
+    p_plain = cfg["build"]()
+    p_plain.use_cuda_graph(True)
+    plain_steps = max(steps // 4, 3)
+    plain_ms, plain_launches, _ = time_steps(p_plain, bi, bo, plain_steps, warmup, flush, stream)
+    # fused, tuned schedule
+    p = cfg["build"]()
+    cfg["fused"](p)
+    p.use_cuda_graph(True)
+    sampler = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms, launches, ms_all = time_steps(p, bi, bo, steps, warmup, flush, stream, sampler)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    assert p.device_error() == 0, "a kernel reported a device-side error"
+    err = cfg["parity"](_to_numpy(yout, odt), inputs)
+
+    npx = OH * OW
+    fp32_peak = fp32["peak_tflops"]
+    fp32_src = (f"measured: hp_measure_fp32_peak, {fp32['peak_form']} fma on {fp32['sms']} SMs at "
+                f"{fp32[fp32['peak_form']]['sm_mhz']} MHz median")
+    launches_per_step = launches / steps
+    kernel_ms = ms / launches_per_step
+    if "dominant" in cfg:
+        # a multi-kernel step: its dominant kernel timed alone, on the same
+        # input, with the same L2 flush between launches
+        dom = cfg["dominant"]
+        dp = dom["build"]()
+        dc, dh, dw, ddt = dom["out"]
+        dout = hp.padded_empty(dc, dh, dw, _torch_dtype(ddt), "cuda")
+        dbi = bi
+        if "inputs" in dom:
+            dins = dom["inputs"](0)
+            dtens = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in dins]
+            dbi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dtens, dins)]
+        dms, dlaunches, _ = time_steps(dp, dbi, hp.buffer_from_tensor(dout, ddt), steps, warmup, flush, stream)
+        if dom.get("bound", "alu") == "hbm":
+            achieved = dom["bytes_per_launch"] / (dms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+        else:
+            achieved = dom["flops_per_launch"] / (dms * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": round(achieved / fp32_peak, 4), "peak_source": fp32_src}
+        roof.update({"algorithmic": dom["algorithmic"], "timed": "the dominant group alone, one launch per step",
+                     "launches_per_timed_step": dlaunches / steps})
+        kernel_ms = dms
+    elif cfg["bound"] == "alu":
+        achieved = cfg["flops_px"] * npx / launches_per_step / (kernel_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "peak_source": fp32_src,
+                "algorithmic": cfg["algorithmic"]}
+        if cfg.get("fp32_instr_px"):
+            # FP32 instructions the fixed per-stage expression issues (tap5: 1 mul
+            # + 4 fma per pass, 2 passes), against one FP32 instruction per lane
+            # and clock on every SM at the clock sampled during the timed region
+            mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+            issue = cfg["fp32_instr_px"] * npx / launches_per_step / (kernel_ms * 1e-3)
+            roof["fp32_issue_frac"] = round(issue / (fp32["sms"] * FP32_LANES_PER_SM * mhz * 1e6), 4)
+            roof["fp32_issue_basis"] = (f"{cfg['fp32_instr_px']} FP32 instructions per output pixel "
+                                        f"(10 per stage: 2 passes x (1 mul + 4 fma)) vs {fp32['sms']} SMs x "
+                                        f"{FP32_LANES_PER_SM} lanes x {mhz} MHz")
+    else:
+        achieved = cfg["bytes_px"] * npx / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "algorithmic": f"{cfg['bytes_px']} bytes per output pixel (input + output once), over the whole step"}
+    roof.update({"traffic": recorded_traffic(cfg["kernel"], cfg["workload"]), "kernel": cfg["kernel"],
+                 "kernel_ms": round(kernel_ms, 5), "launches_per_step": launches_per_step})
+    if roof["bound"] == "hbm":   # also against the nominal HBM3e bandwidth, for context
+        roof["frac_of_nominal_7900_gbs"] = round(roof["achieved"] / 7900.0, 4)
+    res = dict(npx=npx, ms=ms, ms_all=ms_all, launches=launches, plain_ms=plain_ms, plain_launches=plain_launches,
+               plain_steps=plain_steps, roof=roof, clocks=clocks, err=err, p=p, inputs=inputs)
+    return res
+
+
+def compact_entry(cfg_name, cfg, r):
+    return {"workload": cfg["workload"], "value": round(r["npx"] / (r["ms"] * 1e-3) / 1e6, 2), "unit": "MPix/s",
+            "ms_per_step": round(r["ms"], 5), "plain": round(r["npx"] / (r["plain_ms"] * 1e-3) / 1e6, 2),
+            "speedup_vs_plain": round(r["plain_ms"] / r["ms"], 3), "bound": r["roof"]["bound"],
+            "frac": r["roof"]["frac"], "kernel": r["roof"]["kernel"], "kernel_ms": r["roof"]["kernel_ms"],
+            "launches_per_step": r["launches"] / max(1, len(r["ms_all"])),
+            "clocks": {k: r["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "parity": r["err"], "parity_kind": cfg.get("parity_kind", "max |gpu - oracle| at sampled points"),
+            "schedule": schedule_of(cfg_name, cfg)}
+
+
 def run_ours(args, cfg_name):
     import torch
     import torch.distributed as dist
@@ -469,48 +618,36 @@ def run_ours(args, cfg_name):
     if world > 1:
         dist.barrier()
         __graft_entry__.build()
-    cfg = config_table()[cfg_name]
-    H, W = cfg["h"], cfg["w"]
-    C, OH, OW, odt = cfg["out"]
-    inputs = cfg["inputs"](rank)
+    table = config_table()
+    cfg = table[cfg_name]
     stream = torch.cuda.current_stream()
-    dev_in = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in inputs]
-    yout = hp.padded_empty(C, OH, OW, _torch_dtype(odt), "cuda")
-    bi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dev_in, inputs)]
-    bo = hp.buffer_from_tensor(yout, odt)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     if args.only_fused:   # profiling runs: the fused pipeline alone, nothing else on the GPU
+        inputs = cfg["inputs"](rank)
+        C, OH, OW, odt = cfg["out"]
+        dev_in = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in inputs]
+        yout = hp.padded_empty(C, OH, OW, _torch_dtype(odt), "cuda")
+        bi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dev_in, inputs)]
         p = cfg["build"]()
         cfg["fused"](p)
-        ms, launches, _ = time_steps(p, bi, bo, args.steps, args.warmup, flush, stream)
+        ms, launches, _ = time_steps(p, bi, hp.buffer_from_tensor(yout, odt), args.steps, args.warmup, flush, stream)
         if rank == 0:
             print(json.dumps({"only_fused": cfg["workload"], "ms_per_step": ms, "launches": launches}))
         return None
-    # stage-per-kernel comparator
-    p_plain = cfg["build"]()
-    p_plain.use_cuda_graph(True)
-    plain_steps = max(args.steps // 4, 3)
-    plain_ms, plain_launches, _ = time_steps(p_plain, bi, bo, plain_steps, args.warmup, flush, stream)
-    # fused, tuned schedule (the headline)
-    p = cfg["build"]()
-    cfg["fused"](p)
-    p.use_cuda_graph(True)
-    sampler = ClockSampler(local)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    ms, launches, ms_all = time_steps(p, bi, bo, args.steps, args.warmup, flush, stream, sampler)
-    clocks = sampler.stop()
-    torch.cuda.synchronize()
-    assert p.device_error() == 0, "a kernel reported a device-side error"
+    peaks, peak_kind = measured_peaks()
+    fp32 = measure_fp32_peak(local)
+    r = measure_config(cfg_name, cfg, args.steps, args.warmup, flush, stream, peaks, peak_kind, fp32, local, world,
+                       headline=True)
+    ms = r["ms"]
     if world > 1:
         from paper_2012_07145_gb300 import replicas
         dist.barrier()
         ms = replicas.max_over_ranks(ms, device="cuda")   # the slowest replica bounds the job
 
     # end to end through the C ABI with pinned host buffers
+    p, inputs = r["p"], r["inputs"]
+    C, OH, OW, odt = cfg["out"]
     hin = [_host_tensor(a, dt) for a, dt in inputs]
     hout = torch.empty((C, OH, OW), dtype=_torch_dtype(odt)).pin_memory()
     hbi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(hin, inputs)]
@@ -522,60 +659,24 @@ def run_ours(args, cfg_name):
     for _ in range(e2e_steps):
         p.realize_host(hbi, hbo, stream.cuda_stream)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    err = cfg["parity"](_to_numpy(hout, odt), inputs)
+    err_e2e = cfg["parity"](_to_numpy(hout, odt), inputs)
 
+    # the other workloads, compactly, on the same GPU (rank 0's replica only)
+    others = {}
+    if args.configs and rank == 0 and world == 1:
+        for name in [n for n in args.configs.split(",") if n and n != cfg_name]:
+            if name == "serving":
+                others[name] = serving_compact(rate=1000.0, requests=200)
+                continue
+            oc = table[name]
+            torch.cuda.synchronize()
+            others[name] = compact_entry(name, oc, measure_config(name, oc, args.steps, args.warmup, flush, stream,
+                                                                  peaks, peak_kind, fp32, local))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return None
-    npx = OH * OW
-    peaks, peak_kind = measured_peaks()
-    clock_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
-    launches_per_step = launches / args.steps
-    kernel_ms = ms / launches_per_step
-    if "dominant" in cfg:
-        # a multi-kernel step: its dominant kernel timed alone, on the same input,
-        # with the same L2 flush between launches
-        dom = cfg["dominant"]
-        dp = dom["build"]()
-        dc, dh, dw, ddt = dom["out"]
-        dout = hp.padded_empty(dc, dh, dw, _torch_dtype(ddt), "cuda")
-        dbi = bi
-        if "inputs" in dom:
-            dins = dom["inputs"](0)
-            dtens = [hp.padded_copy(_host_tensor(a, dt), "cuda") for a, dt in dins]
-            dbi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(dtens, dins)]
-        dms, dlaunches, _ = time_steps(dp, dbi, hp.buffer_from_tensor(dout, ddt), args.steps, args.warmup, flush, stream)
-        if dom.get("bound", "alu") == "hbm":
-            achieved = dom["bytes_per_launch"] / (dms * 1e-3) / 1e9
-            roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                    "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
-                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
-        else:
-            achieved = dom["flops_per_launch"] / (dms * 1e-3) / 1e12
-            roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                    "frac": round(achieved / fp32_peak, 4),
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops (FMA) x {clock_mhz} MHz max SM clock"}
-        roof.update({"algorithmic": dom["algorithmic"], "timed": "the dominant group alone, one launch per step",
-                     "launches_per_timed_step": dlaunches / args.steps})
-        kernel_ms = dms
-    elif cfg["bound"] == "alu":
-        achieved = cfg["flops_px"] * npx / launches_per_step / (kernel_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops (FMA) x {clock_mhz} MHz max SM clock",
-                "algorithmic": f"{cfg['flops_px']} FP32 flops per output pixel (18 per 5x5 stage: 2 passes x (1 mul + 4 fma))"}
-    else:
-        achieved = cfg["bytes_px"] * npx / (ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": round(achieved / peaks.get("hbm_gbs", 6800.0), 4),
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                "algorithmic": f"{cfg['bytes_px']} bytes per output pixel (input + output once), over the whole step"}
-    roof.update({"traffic": recorded_traffic(cfg["kernel"], cfg["workload"]), "kernel": cfg["kernel"],
-                 "kernel_ms": round(kernel_ms, 5), "launches_per_step": launches_per_step})
-    if roof["bound"] == "hbm":   # also against the nominal HBM3e bandwidth, for context
-        roof["frac_of_nominal_7900_gbs"] = round(roof["achieved"] / 7900.0, 4)
+    npx = r["npx"]
     in_bytes = int(sum(a.nbytes for a, _ in inputs))
     out_bytes = int(C * OH * OW * hp.DTYPE_BYTES[odt])
     line = {
@@ -595,19 +696,23 @@ def run_ours(args, cfg_name):
                    "schedule": schedule_of(cfg_name, cfg),
                    "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas x{world}",
                    "launch": "CUDA graph replay"},
-        "plain": {"value": round(npx / (plain_ms * 1e-3) / 1e6, 2), "unit": "MPix/s", "ms_per_step": round(plain_ms, 5),
-                  "launches_per_step": plain_launches / plain_steps,
+        "plain": {"value": round(npx / (r["plain_ms"] * 1e-3) / 1e6, 2), "unit": "MPix/s",
+                  "ms_per_step": round(r["plain_ms"], 5),
+                  "launches_per_step": r["plain_launches"] / r["plain_steps"],
                   "schedule": "stage-per-kernel (one launch per stage), CUDA graph replay"},
-        "speedup_vs_plain": round(plain_ms / ms, 3),
+        "speedup_vs_plain": round(r["plain_ms"] / ms, 3),
         "e2e": {"value": round(npx / e2e_s / 1e6, 2), "unit": "MPix/s",
-                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes},
-        "gpu_launches": int(launches),
-        "roofline": roof,
-        "clocks": clocks,
-        "parity_spot": err,
-        "step_ms_p50": round(statistics.median(ms_all), 5),
-        "step_ms_p99": round(float(np.percentile(ms_all, 99)), 5),
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes, "parity_spot": err_e2e},
+        "gpu_launches": int(r["launches"]),
+        "roofline": r["roof"],
+        "fp32_peak_probe": fp32,
+        "clocks": r["clocks"],
+        "parity_spot": r["err"],
+        "step_ms_p50": round(statistics.median(r["ms_all"]), 5),
+        "step_ms_p99": round(float(np.percentile(r["ms_all"], 99)), 5),
     }
+    if others:
+        line["configs"] = others
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cfg, seconds=args.cpu_seconds)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(cfg_name, seconds=args.cpu_seconds)
@@ -701,15 +806,13 @@ def run_reference(args, cfg_name):
 SERVING_SIZES = [(256, 256), (480, 640), (1080, 1920), (1536, 2560), (3072, 4096)]
 
 
-def run_serving(args):
-    """Poisson streams of requests drawn uniformly from {unsharp, Harris,
-    histogram equalize} x five image sizes, through the continuous-batching
-    server; p50/p99 latency and MPix/s per arrival rate."""
+def serving_setup():
+    """One pipeline per kind and size, each with the autotuned schedule of
+    that size, with pinned host inputs and a ring of pinned host outputs."""
     import torch
     from paper_2012_07145_gb300 import hp, pipelines, synth
     import __graft_entry__
     __graft_entry__.build()
-    # one pipeline per kind and size, each with the autotuned schedule of that size
     defaults = {"unsharp": dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=16, threads=128),
                 "harris": dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120, tile_h=14, threads=128),
                 "histeq": dict(schedule="fused")}
@@ -725,52 +828,74 @@ def run_serving(args):
             arr = synth.rgb_f32(h, w, seed=7) if idt == hp.HP_F32 else synth.gray_u8_lowcontrast(h, w, seed=7)
             hin = torch.from_numpy(arr).pin_memory()
             outs = [torch.empty((oc, h, w), dtype=tdt).pin_memory() for _ in range(ring)]
-            bufs[(name, h, w)] = (p, hp.buffer_from_tensor(hin, idt), [hp.buffer_from_tensor(o, 0 if idt == hp.HP_U8 else hp.HP_F32) for o in outs], hin, outs)
+            bufs[(name, h, w)] = (p, hp.buffer_from_tensor(hin, idt),
+                                  [hp.buffer_from_tensor(o, hp.HP_U8 if idt == hp.HP_U8 else hp.HP_F32) for o in outs],
+                                  hin, outs)
+    return [k[0] for k in kinds], bufs, ring
+
+
+def serve_rate(kinds, bufs, ring, lam, n, rng):
+    """n Poisson arrivals at lam per second, kind and size drawn uniformly,
+    through a fresh server; returns the per-rate record."""
+    from paper_2012_07145_gb300 import hp
+    picks = [(kinds[rng.integers(len(kinds))],) + SERVING_SIZES[rng.integers(len(SERVING_SIZES))] for _ in range(n)]
+    gaps = rng.exponential(1.0 / lam, n)
+    srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
+    # make the slots' pipeline copies resident for every kind and size
+    # (lowering, scratch, kernel state), then one request per slot and key
+    # (kernel attributes are set on a kernel's first launch)
+    for k in bufs:
+        srv.prepare(bufs[k][0], [bufs[k][1]])
+    warm = [srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][j % ring]) for k in bufs for j in range(8)]
+    for t in warm:
+        srv.wait(t, 120000)
+    base = srv.stats()
+    t0 = time.perf_counter()
+    due = t0
+    tickets = []
+    for i, (name, h, w) in enumerate(picks):
+        due += gaps[i]
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            if due - now > 2e-4:
+                time.sleep((due - now) - 1e-4)
+        p, bi, bos, _, _ = bufs[(name, h, w)]
+        tickets.append(srv.submit(p, [bi], bos[i % ring]))
+    lats = []
+    for t in tickets:
+        st, lat = srv.wait(t, 300000)
+        if st == hp.HP_OK:
+            lats.append(lat)
+    t1 = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    mpix = sum(h * w for _, h, w in picks) / 1e6
+    return {"rate_per_s": lam, "requests": n, "completed": len(lats),
+            "p50_ms": round(float(np.percentile(lats, 50)) / 1e3, 3),
+            "p99_ms": round(float(np.percentile(lats, 99)) / 1e3, 3),
+            "mpix_per_s": round(mpix / (t1 - t0), 1),
+            "batched_launches": int(stats.batched_launches - base.batched_launches),
+            "peak_hbm_bytes": int(stats.peak_bytes)}
+
+
+def serving_compact(rate=1000.0, requests=200):
+    kinds, bufs, ring = serving_setup()
+    rec = serve_rate(kinds, bufs, ring, rate, requests, np.random.default_rng(0))
+    rec.update({"workload": "serving_mix_unsharp_harris_histeq_poisson", "slots": 8, "max_batch": 8,
+                "latency": "host submit to completion observed by the server (includes host copies)"})
+    return rec
+
+
+def run_serving(args):
+    """Poisson streams of requests drawn uniformly from {unsharp, Harris,
+    histogram equalize} x five image sizes, through the continuous-batching
+    server; p50/p99 latency and MPix/s per arrival rate."""
+    kinds, bufs, ring = serving_setup()
     rates = [float(r) for r in args.rates.split(",")]
     rng = np.random.default_rng(0)
-    per_rate = []
-    for lam in rates:
-        n = args.requests
-        picks = [(kinds[rng.integers(3)][0],) + SERVING_SIZES[rng.integers(len(SERVING_SIZES))] for _ in range(n)]
-        gaps = rng.exponential(1.0 / lam, n)
-        srv = hp.Server(hbm_budget_bytes=8 << 30, slots=8, max_batch=8)
-        # make the slots' pipeline copies resident for every kind and size
-        # (lowering, scratch, kernel state), then one request per slot and key
-        # (kernel attributes are set on a kernel's first launch)
-        for k in bufs:
-            srv.prepare(bufs[k][0], [bufs[k][1]])
-        warm = [srv.submit(bufs[k][0], [bufs[k][1]], bufs[k][2][j % ring]) for k in bufs for j in range(8)]
-        for t in warm:
-            srv.wait(t, 120000)
-        base = srv.stats()
-        t0 = time.perf_counter()
-        due = t0
-        tickets = []
-        for i, (name, h, w) in enumerate(picks):
-            due += gaps[i]
-            while True:
-                now = time.perf_counter()
-                if now >= due:
-                    break
-                if due - now > 2e-4:
-                    time.sleep((due - now) - 1e-4)
-            p, bi, bos, _, _ = bufs[(name, h, w)]
-            tickets.append(srv.submit(p, [bi], bos[i % ring]))
-        lats = []
-        for t in tickets:
-            st, lat = srv.wait(t, 300000)
-            if st == hp.HP_OK:
-                lats.append(lat)
-        t1 = time.perf_counter()
-        stats = srv.stats()
-        srv.close()
-        mpix = sum(h * w for _, h, w in picks) / 1e6
-        per_rate.append({"rate_per_s": lam, "requests": n, "completed": len(lats),
-                         "p50_ms": round(float(np.percentile(lats, 50)) / 1e3, 3),
-                         "p99_ms": round(float(np.percentile(lats, 99)) / 1e3, 3),
-                         "mpix_per_s": round(mpix / (t1 - t0), 1),
-                         "batched_launches": int(stats.batched_launches - base.batched_launches),
-                         "peak_hbm_bytes": int(stats.peak_bytes)})
+    per_rate = [serve_rate(kinds, bufs, ring, lam, args.requests, rng) for lam in rates]
     top = per_rate[-1]
     return {"metric": METRIC, "value": top["mpix_per_s"], "unit": "MPix/s", "n_gpus": 1, "steps": args.requests,
             "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -794,6 +919,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--rates", default="200,500,1000,2000", help="serving: Poisson arrival rates per second")
     ap.add_argument("--requests", type=int, default=300, help="serving: requests per arrival rate")
+    ap.add_argument("--configs", default=DEFAULT_CONFIGS,
+                    help="workloads reported compactly in the headline line ('' for none)")
     ap.add_argument("--only-fused", action="store_true",
                     help="time the fused pipeline only (for profiler runs); prints no bench line")
     args = ap.parse_args()

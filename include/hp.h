@@ -362,7 +362,9 @@ hp_status hp_pipeline_destroy(hp_pipeline* p);
  *
  * Computes exactly what the HP_HISTOGRAM -> HP_CDF_LUT -> HP_LUT_APPLY pipeline
  * computes, with the same kernels.  The caller passes the device input and
- * output (1-channel u8, equal sizes, 16-byte aligned data and row strides); the
+ * output (1-channel u8, equal sizes, 16-byte aligned data and row strides;
+ * input == output is allowed, since every thread reads its bytes before it
+ * writes them and the table is built only after the whole image is counted); the
  * 256 histogram counters and the 256-entry table live in a fixed 1280-byte
  * array inside the library's device image, which every GPU that loads the
  * library holds until the process exits.  Images of more than
@@ -379,6 +381,20 @@ hp_status hp_pipeline_destroy(hp_pipeline* p);
  * allocating library routine is called. */
 #define HP_NOALLOC_MAX_PIXELS 4294967295ULL
 hp_status hp_histeq_u8_noalloc(const hp_buffer* input, const hp_buffer* output, void* stream);
+
+/* FP32 throughput of this GPU, measured: the denominator of the ALU roofline
+ * that the benchmark reports (the paper has no counterpart; it measures no
+ * roofline).  Runs `launches` launches of a kernel whose threads each execute
+ * `iters` x 128 independent FP32 fmas (8 chains), on every SM at the kernel's
+ * maximum occupancy, after one untimed launch, on `stream`; times them with
+ * CUDA events and SYNCHRONISES on the last event.  paired = 0 issues scalar
+ * fma instructions, paired = 1 the paired form (fma.rn.f32x2, two fmas per
+ * instruction).  Results: *flops_per_s (2 flops per fma), and when not null
+ * *ms_per_launch and *sm_count (the device's multiprocessor count).
+ * HP_ERR_INVALID_ARG for a null result pointer or counts below 1,
+ * HP_ERR_CUDA if a query or launch fails. */
+hp_status hp_measure_fp32_peak(int paired, int iters, int launches, void* stream, double* flops_per_s,
+                               double* ms_per_launch, int* sm_count);
 
 /* Message of the last failure on this thread ("" if none). */
 const char* hp_last_error(void);

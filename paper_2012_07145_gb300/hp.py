@@ -76,7 +76,7 @@ EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_s
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
            "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy",
-           "hp_prepare", "hp_server_prepare"]
+           "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak"]
 
 _lib = None
 
@@ -111,6 +111,8 @@ def lib():
         L.hp_server_destroy.argtypes = [P]
         L.hp_prepare.argtypes = [P, _IP, _IP, ctypes.c_int, P]
         L.hp_server_prepare.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int]
+        L.hp_measure_fp32_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), _IP]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
         for name in EXPORTS:
@@ -182,6 +184,15 @@ def padded_copy(src, device="cuda"):
 def histeq_u8_noalloc(inp: Buffer, out: Buffer, stream=None):
     """Allocation-free histogram equalization (hp_histeq_u8_noalloc)."""
     check(lib().hp_histeq_u8_noalloc(ctypes.byref(inp), ctypes.byref(out), ctypes.c_void_p(stream or 0)))
+
+
+def measure_fp32_peak(paired: bool, iters: int = 2048, launches: int = 100, stream=None):
+    """FP32 throughput of the current GPU (hp_measure_fp32_peak): returns
+    (flop/s, ms per launch, SM count)."""
+    f, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    check(lib().hp_measure_fp32_peak(int(paired), iters, launches, ctypes.c_void_p(stream or 0), ctypes.byref(f),
+                                     ctypes.byref(ms), ctypes.byref(sms)))
+    return f.value, ms.value, sms.value
 
 
 class Pipeline:

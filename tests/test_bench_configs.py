@@ -117,3 +117,18 @@ def test_every_workload_lowers_at_tiny_and_ragged_sizes(table, size):
                 info = p.group_info([size], g)
                 assert 0 <= info.kernel < len(hp.KERNEL_NAMES), (name, size, g)
                 assert info.grid_x >= 1 and info.grid_y >= 1 and info.threads >= 32, (name, size, g)
+
+
+def test_chain_flop_counts_are_the_methods_work(table):
+    """The ALU roofline counts the method's work: 14 flops per binomial stage
+    and 10 per box stage (a separable pass: ((a+e) + 4(b+d)) + 6c then x 1/16,
+    or (((a+b) + (c+d)) + e) x 1/5; an fma counts 2), not the kernel's own
+    instruction mix, which is reported separately as FP32 instructions."""
+    assert table["chain32"]["flops_px"] == 16 * 14 + 16 * 10 == 384
+    assert table["chain4"]["flops_px"] == 4 * 14 == 56
+    assert table["chain32"]["fp32_instr_px"] == 320
+    names = set(table) | {"serving"}
+    spec = importlib.util.spec_from_file_location("bench_cfg2", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert set(b.DEFAULT_CONFIGS.split(",")) <= names

@@ -340,3 +340,11 @@ def test_binding_constants_equal_the_header():
     kernels = sorted((int(v), n) for n, v in pairs if n.startswith("HP_KERNEL_"))
     assert [v for v, _ in kernels] == list(range(len(hp.KERNEL_NAMES)))
     assert [n[len("HP_KERNEL_"):].lower() for _, n in kernels] == list(hp.KERNEL_NAMES)
+
+
+def test_fp32_probe_refuses_bad_arguments_before_any_cuda_call():
+    L = hp.lib()
+    f, ms, sms = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    assert L.hp_measure_fp32_peak(0, 16, 1, None, None, ctypes.byref(ms), ctypes.byref(sms)) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_measure_fp32_peak(0, 0, 1, None, ctypes.byref(f), None, None) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_measure_fp32_peak(1, 16, 0, None, ctypes.byref(f), None, None) == hp.HP_ERR_INVALID_ARG

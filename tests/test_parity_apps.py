@@ -12,6 +12,7 @@ from oracle import local_laplacian as oll
 from oracle import unsharp as ous
 from paper_2012_07145_gb300 import hp, pipelines, synth
 
+import ll_bound
 from gpu_util import bits, rel_err, run, to_device, to_numpy, u16_close
 
 pytestmark = pytest.mark.gpu
@@ -272,27 +273,53 @@ def test_local_laplacian_identity_parameters_full_size():
 
 
 # With alpha < 1 the remap r(i) = g + sign(d) sigma (|d|/sigma)^alpha has an
-# unbounded slope at d = i - g = 0: an FP32 rounding of d (about 1e-8 here)
-# moves r by up to sigma^(1-alpha) |delta d|^alpha.  Pixels whose gray value
-# lies that close to a level g_k therefore carry an error set by the
-# conditioning of the method, not by the kernels.  Bound used (float output,
-# [0,1] units): max error 1e-4 (6.6 LSB of u16) and 99.9th percentile 2e-6;
-# u16 output: at most 7 LSB and under 1% of values off by any amount.
-@pytest.mark.parametrize("h,w,levels,alpha", [(192, 320, 6, 0.25), (37, 53, 4, 0.25), (192, 320, 6, 0.5)])
-def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha):
+# unbounded slope at d = i - g = 0, so an FP32 evaluation may differ from the
+# exact remap by far more than its own rounding at pixels whose gray value lies
+# near a level g_k.  The gate is per pixel and derived (tests/ll_bound.py):
+#     |gpu - oracle| <= 1e-5 * range + B(p)
+# where B(p) propagates the Hoelder bound sigma^(1-alpha) ((a+delta)^alpha -
+# (a-delta)^alpha) of each remap (a = |d|, delta the FP32 uncertainty of d)
+# through the pyramids, the interpolation, the collapse and the colour step.
+# Where B is negligible (most pixels) this is the plain FP32 tolerance.  The
+# u16 result: |gpu - 65535 oracle| <= 0.75 + 65535 B(p), i.e. exact except
+# within 0.25 LSB of a rounding boundary, widened by the same bound.
+def _ll_gate(yf, ref, bound, label, min_well):
+    err = np.abs(yf.astype(np.float64) - ref)
+    rng = float(ref.max() - ref.min())
+    excess = err - (TOL * rng + bound)
+    well = bound <= 1e-6
+    print(f"{label}: float max err {err.max():.3e}; on the {well.mean():.1%} of values with B <= 1e-6: "
+          f"{err[well].max():.3e}; worst err - allowed {excess.max():.3e}")
+    assert (excess <= 0).all()
+    assert well.mean() >= min_well    # the plain tolerance holds on most of a large image
+
+
+def _ll_gate_u16(got, ref, bound):
+    dev = np.abs(got.astype(np.float64) - np.clip(ref * 65535.0, 0, 65535))
+    assert (dev <= 0.75 + 65535.0 * bound).all()
+
+
+# (min_well: the share of values whose bound is negligible; on the 37x53 image
+# the saturated corner's pixels, all on the level g = 1, reach most pixels
+# through the coarse levels)
+@pytest.mark.parametrize("h,w,levels,alpha,min_well", [(192, 320, 6, 0.25, 0.9), (37, 53, 4, 0.25, 0.0),
+                                                       (192, 320, 6, 0.5, 0.9), (1536, 2560, 8, 0.25, 0.9)])
+def test_local_laplacian_detail_enhance_against_oracle(h, w, levels, alpha, min_well):
     img = synth.rgb_u16_gradient_noise(h, w, seed=1)
     ref = oll.local_laplacian_float(img, levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0)
+    bound = ll_bound.output_bound(img, levels, 8, 0.1, alpha, 1.0)
     pf, ids_f = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0,
                                           out_storage=hp.HP_F32)
     x = to_device(img, hp.HP_U16)
     yf = to_numpy(run(pf, [x], [hp.HP_U16], (3, h, w), hp.HP_F32))
-    err = np.abs(yf.astype(np.float64) - ref)
-    print(f"LL alpha={alpha} {w}x{h}: float max err {err.max():.3e}, p99.9 {np.percentile(err, 99.9):.3e}")
-    assert err.max() <= 1e-4 and np.percentile(err, 99.9) <= 2e-6
+    _ll_gate(yf, ref, bound, f"LL alpha={alpha} {w}x{h} J={levels}", min_well)
     p, ids = pipelines.local_laplacian(levels=levels, k_levels=8, sigma_r=0.1, alpha=alpha, beta=1.0)
     plain = _ll_run(p, img)
-    d = np.abs(plain.astype(np.int64) - oll.quantize_u16(ref).astype(np.int64))
-    assert d.max() <= 7 and (d > 0).mean() < 0.01
+    _ll_gate_u16(plain, ref, bound)
+    pipelines.local_laplacian_fused_schedule(p, ids)                  # the benchmark's schedule
+    assert np.array_equal(_ll_run(p, img), plain)
+    if h * w > 1 << 20:
+        return                                                        # full size: the benched schedules only
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16)
     assert np.array_equal(_ll_run(p, img), plain)
     pipelines.local_laplacian_fused_schedule(p, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
