@@ -145,6 +145,7 @@ struct ChainArgs {
   int depth;
   int tile_w, tile_h, tiles_x, tiles_y;
   int threads, seg;
+  int cols;                // streaming chain kernel: columns per lane (4 or 8)
   int storage[kChainMax];
   float w[kChainMax][10];  // per stage: wx[5] then wy[5]
   int epilogue;            // 0: none; 1: unsharp out = in + amount*(in - chain(in))
@@ -262,10 +263,11 @@ struct LutApplyArgs {
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream);
 // streaming stencil chain (2 or 4 stages in registers): one warp per strip of one plane
 bool chain_rows_depth_ok(int depth);
-int chain_rows_strip_w(int depth, int in_dtype);
-int chain_rows_smem_bytes(int depth, int threads, int in_dtype);
-int chain_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes);
-int launch_chain_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream);
+int chain_rows_strip_w(int depth, int in_dtype, int cols = 4);
+int chain_rows_cols(int depth, int in_dtype, int tile_w);
+int chain_rows_smem_bytes(int depth, int cols, int threads, int in_dtype);
+int chain_rows_grid(const ChainArgs& a, int cols, int units, int threads, int smem_bytes);
+int launch_chain_rows(const ChainArgs& a, int cols, int rows, int grid, int smem_bytes, void* stream);
 int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype);
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream);
 int launch_pointwise(const PointwiseArgs& a, void* stream);

@@ -1,24 +1,34 @@
 // Streaming stencil chain: D successive 5x5 stencils (D = 2 or 4) fused in
-// registers, per channel plane.
+// registers, per channel plane -- the long-range fusion of the stencil chain
+// (Sec. 2, Fig. 1) with every intermediate kept in registers (Sec. 4.7).
 //
-// Each warp owns a strip of output columns, four per lane, and walks down a
-// run of rows.  Input rows arrive as TMA boxes through a ring of shared-memory
-// slots private to the warp.  Every step reads one input row and pushes it
-// through all D stages: a stage's x pass takes its two neighbours on each side
-// from the adjacent lanes, its y pass runs over a 5-row register window of its
-// x-pass results, and its output row feeds the next stage's x pass at once.
-// Stage s therefore lags the input by 2(s+1) rows; the run starts 2D rows
-// above its first output row and ends 2D rows below its last.  Each stage
-// loses two columns of validity on each side, so 2D columns of halo (the outer
-// lanes) surround the strip.  No barrier wider than the warp is taken and no
-// intermediate touches shared or global memory.
+// Each warp owns a strip of columns, C consecutive ones per lane (C = 4 or 8),
+// and walks down a run of rows.  Input rows arrive as TMA boxes (32 C columns
+// x 4 rows) through a ring of shared-memory slots private to the warp.  Every
+// step reads one input row and pushes it through all D stages: a stage's x
+// pass takes its two neighbours on each side from the adjacent lanes (warp
+// shuffles), its y pass runs over a 5-row register window of its x-pass
+// results, and its output row feeds the next stage's x pass at once.  Stage s
+// lags the input by 2(s+1) rows.  Each stage loses two columns of validity on
+// each side, so whole lanes of halo (2D columns at least) surround the strip.
+// No barrier wider than the warp is taken and no intermediate touches shared
+// or global memory; a run's only shared-memory traffic is one load per input
+// row and lane.
+//
+// A run of R output rows starting at row oy reads input rows from
+// y0 = max(oy - 2D, 0) and takes R + 4D steps (R + 2D + oy at the image top).
+// In a run that starts inside the image, the first steps of the later stages
+// run on rows that are not valid yet; their results fall out of the windows
+// before any valid output reads them, so every stage runs at every step and
+// the steady loop has no per-stage test.  Boundary conditions, per stage on
+// its own producer (clamp to edge): at the image top, a stage's first input
+// row (row 0) also fills the two window rows above it; below the image, a
+// stage's window repeats its row H - 1 instead of an x pass; in strips that
+// touch the left or right image edge, each stage's input row takes the edge
+// column's value outside the image (shuffled from the lane that holds it).
 //
 // Stage expressions and per-stage rounding are those of stage_math.cuh, so the
-// result is bit-identical to every other schedule.  Boundary conditions, per
-// stage on its own producer (clamp to edge, Sec. 3): in strips that touch the
-// left or right image edge, each stage's input row takes the edge column's
-// value outside the image (shuffled from the lane that holds it); rows outside
-// the image take the nearest edge row's x-pass result (a copy in the window).
+// result is bit-identical to every other schedule.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -34,24 +44,29 @@ namespace {
 // times slower to arrive than boxes of 2 or 4.
 constexpr int kBoxRows = 4;      // rows per TMA box
 constexpr int kRing = 3;         // boxes per warp ring
-constexpr int kBarBytes = 512;   // mbarriers of up to 16 warps x kRing
+constexpr int kMaxWarps = 8;     // warps per block (256 threads)
+constexpr int kBarBytes = 256;   // mbarriers of up to kMaxWarps x kRing
 constexpr unsigned kFull = 0xffffffffu;
 
 struct StripGeom {
+  int cols;        // columns per lane (4 or 8)
   int halo_lanes;  // lanes on each side that only feed neighbours
-  int strip_w;     // output columns per strip: 4 (32 - 2 halo_lanes)
-  int slot_bytes;  // one ring slot: 128 columns x kBoxRows rows
+  int strip_w;     // output columns per strip: cols (32 - 2 halo_lanes)
+  int box_w;       // columns per TMA box row: 32 cols
+  int slot_bytes;  // one ring slot: box_w columns x kBoxRows rows
 };
 
 // 2D columns of halo on each side, in whole lanes; a TMA box must also start
 // on a 16-byte boundary (8 columns of a 2-byte input).
-__host__ __device__ inline StripGeom strip_geom(int depth, int esize) {
+__host__ __device__ inline StripGeom strip_geom(int depth, int cols, int esize) {
   StripGeom g;
-  int hl = (2 * depth + 3) / 4;
-  if (esize == 2 && hl < 2) hl = 2;
+  g.cols = cols;
+  int hl = (2 * depth + cols - 1) / cols;
+  if (esize == 2 && (cols * hl) % 8) hl += 1;
   g.halo_lanes = hl;
-  g.strip_w = 4 * (32 - 2 * hl);
-  g.slot_bytes = 128 * kBoxRows * esize;
+  g.strip_w = cols * (32 - 2 * hl);
+  g.box_w = 32 * cols;
+  g.slot_bytes = g.box_w * kBoxRows * esize;
   return g;
 }
 
@@ -62,7 +77,7 @@ struct CRowsParams {
 };
 
 struct Unit {
-  int x0, oy, plane, n_in, nbox;  // x0: image column of lane 0's first column; n_in input rows
+  int x0, oy, ye, y0, plane, n_steps, n_in, nbox;  // x0: image column of lane 0's first column
 };
 
 __device__ __forceinline__ Unit unit_geom(const CRowsParams& kp, const StripGeom& g, int u, int depth) {
@@ -71,9 +86,13 @@ __device__ __forceinline__ Unit unit_geom(const CRowsParams& kp, const StripGeom
   U.plane = u / per_plane;
   const int v = u - U.plane * per_plane;
   const int run = v / kp.strips, s = v - run * kp.strips;
-  U.x0 = s * g.strip_w - 4 * g.halo_lanes;
+  const int H = kp.a.in.h;
+  U.x0 = s * g.strip_w - g.cols * g.halo_lanes;
   U.oy = run * kp.rows;
-  U.n_in = min(kp.rows, kp.a.out.h - U.oy) + 4 * depth;
+  U.ye = min(U.oy + kp.rows, kp.a.out.h);
+  U.y0 = max(U.oy - 2 * depth, 0);
+  U.n_steps = U.ye - U.y0 + 2 * depth;
+  U.n_in = min(U.y0 + U.n_steps, H) - U.y0;  // input rows inside the image
   U.nbox = (U.n_in + kBoxRows - 1) / kBoxRows;
   return U;
 }
@@ -94,8 +113,7 @@ __device__ __forceinline__ void issue_one(const CRowsParams& kp, const StripGeom
   if (lane == 0) {
     const int s = R.issued % kRing;
     mbar_arrive_expect_tx(R.bars + s, (unsigned)g.slot_bytes);
-    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.oy - 2 * D + R.ij * kBoxRows, R.IU.plane,
-                R.bars + s);
+    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.y0 + R.ij * kBoxRows, R.IU.plane, R.bars + s);
   }
   ++R.issued;
   if (++R.ij == R.IU.nbox) {
@@ -106,46 +124,52 @@ __device__ __forceinline__ void issue_one(const CRowsParams& kp, const StripGeom
 }
 
 // Every lane's value at a column outside [0, W) becomes the value at the
-// nearest column inside, fetched from the lane that holds it.  (Out of line,
-// by value: only strips at the image's left and right edges call it.)
-__device__ __noinline__ float4 clamp_cols4(float4 q, int c0, int x0, int W) {
-  const float v[4] = {q.x, q.y, q.z, q.w};
-  float o[4];
+// nearest column inside, fetched from the lane that holds it.  (Only strips
+// at the image's left and right edges call it.)
+template <int C>
+__device__ __forceinline__ void clamp_cols(float (&v)[C], int c0, int x0, int W) {
+  float o[C];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < C; ++k) {
     const int c = c0 + k;
     const int s = min(max(c, 0), W - 1);
     const int off = s - x0;
-    const int sl = off >> 2, sk = off & 3;
-    const float t0 = __shfl_sync(kFull, v[0], sl), t1 = __shfl_sync(kFull, v[1], sl);
-    const float t2 = __shfl_sync(kFull, v[2], sl), t3 = __shfl_sync(kFull, v[3], sl);
-    const float t = sk == 0 ? t0 : sk == 1 ? t1 : sk == 2 ? t2 : t3;
+    const int sl = off / C, sk = off - sl * C;
+    float t = 0.0f;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const float tj = __shfl_sync(kFull, v[j], sl);
+      t = sk == j ? tj : t;
+    }
     o[k] = c == s ? v[k] : t;
   }
-  return make_float4(o[0], o[1], o[2], o[3]);
-}
-
-__device__ __forceinline__ void clamp_cols(float (&v)[4], int c0, int x0, int W) {
-  const float4 r = clamp_cols4(make_float4(v[0], v[1], v[2], v[3]), c0, x0, W);
-  v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
-}
-
-__device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (&v)[4]) {
-  if (dtype == HP_F32) {
-    const float4 q = *reinterpret_cast<const float4*>(p);
-    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
-  } else {
-    const uint2 q = *reinterpret_cast<const uint2*>(p);
-    const unsigned u[2] = {q.x, q.y};
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const unsigned short lo = (unsigned short)(u[i] & 0xffffu), hi = (unsigned short)(u[i] >> 16);
-      if (dtype == HP_BF16) {
-        v[2 * i] = __bfloat162float(__ushort_as_bfloat16(lo));
-        v[2 * i + 1] = __bfloat162float(__ushort_as_bfloat16(hi));
-      } else {
-        v[2 * i] = __half2float(__ushort_as_half(lo));
-        v[2 * i + 1] = __half2float(__ushort_as_half(hi));
+  for (int k = 0; k < C; ++k) v[k] = o[k];
+}
+
+template <int C>
+__device__ __forceinline__ void load_row(const unsigned char* p, int dtype, float (&v)[C]) {
+  if (dtype == HP_F32) {
+#pragma unroll
+    for (int q = 0; q < C / 4; ++q) {
+      const float4 f = reinterpret_cast<const float4*>(p)[q];
+      v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < C / 4; ++q) {
+      const uint2 u2 = reinterpret_cast<const uint2*>(p)[q];
+      const unsigned u[2] = {u2.x, u2.y};
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const unsigned short lo = (unsigned short)(u[i] & 0xffffu), hi = (unsigned short)(u[i] >> 16);
+        if (dtype == HP_BF16) {
+          v[4 * q + 2 * i] = __bfloat162float(__ushort_as_bfloat16(lo));
+          v[4 * q + 2 * i + 1] = __bfloat162float(__ushort_as_bfloat16(hi));
+        } else {
+          v[4 * q + 2 * i] = __half2float(__ushort_as_half(lo));
+          v[4 * q + 2 * i + 1] = __half2float(__ushort_as_half(hi));
+        }
       }
     }
   }
@@ -153,23 +177,26 @@ __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (
 
 __host__ __device__ constexpr int mod5(int x) { return ((x % 5) + 5) % 5; }
 
-// One run of rows of one strip of one plane.  Step t reads input row t of the
-// run (image row oy - 2D + t); stage s's input row at that step is t - 2s, its
-// output row t - 2(s+1), valid from t = 4(s+1) on; the last stage's output row
-// t - 2D is image row oy + t - 4D.  Windows are indexed by row mod 5, so a
-// loop unrolled five times keeps them in fixed registers.  F32: every storage
-// type is f32 (no rounding).  ODT: 0 f32, 1 f16, 2 bf16 packed stores, 3 any.
-template <int D, int ODT, bool F32>
+// One run of rows of one strip of one plane.  Step t reads input row y0 + t;
+// stage s's input row at that step is i = y0 + t - 2s and its y pass gives
+// its output row i - 2; the last stage's output row is y0 + t - 2D.  Windows
+// are indexed by step mod 5 (stage s's newest row at step t sits in slot
+// (t - 2s) mod 5), so a loop unrolled five times keeps them in fixed
+// registers.  F32: every storage type is f32 (no rounding).  ODT: 0 f32,
+// 1 f16, 2 bf16 packed stores, 3 any.
+template <int D, int C, int ODT, bool F32>
 struct ChainRun {
   const CRowsParams& kp;
   const StripGeom& g;
   Ring& R;
   const Unit U;
-  const int lane, stride, c0, esize;
+  const int lane, stride, c0, esize, H;
   const bool hb;             // the strip touches the left or right image edge
-  const bool vedge;          // the run reads rows outside the image
-  float hx[D][5][4];         // per stage: x-pass results of its last 5 input rows
-  bool st_full, st_part;     // the lane stores four columns / some of its columns
+  const bool top;            // the run starts at image row 0 (clamped rows above it)
+  const int t_store;         // first step whose output row is the run's
+  const int t_edge;          // first step whose input row lies below the image (edge handling from there on)
+  float hx[D][5][C];         // per stage: x-pass results of its last 5 input rows
+  bool st_full, st_part;     // the lane stores all its columns / some of them
   char* out_row;             // the next output row
   unsigned q;                // box being read
   int rr;                    // row within it
@@ -177,14 +204,22 @@ struct ChainRun {
 
   __device__ __forceinline__ ChainRun(const CRowsParams& kp_, const StripGeom& g_, Ring& R_, const Unit& U_,
                                       int lane_, int stride_)
-      : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + 4 * lane_),
-        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), hb(U_.x0 < 0 || U_.x0 + 128 > kp_.a.in.w),
-        vedge(U_.oy < 2 * D || U_.oy + U_.n_in - 2 * D > kp_.a.in.h), q(R_.released), rr(0), slot(nullptr) {
+      : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + C * lane_),
+        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), H(kp_.a.in.h),
+        hb(U_.x0 < 0 || U_.x0 + 32 * C > kp_.a.in.w), top(U_.y0 == 0),
+        t_store(U_.oy - U_.y0 + 2 * D), t_edge(kp_.a.in.h - U_.y0),
+        q(R_.released), rr(0), slot(nullptr) {
     const int W = kp.a.out.w;
     const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
-    st_full = mine && c0 + 3 < W && ODT != 3;
+    st_full = mine && c0 + C - 1 < W && ODT != 3;
     st_part = mine && c0 < W && !st_full;
     out_row = (char*)kp.a.out.data + (long long)U.plane * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int k = 0; k < C; ++k) hx[s][j][k] = 0.0f;
   }
 
   __device__ __forceinline__ bool wait_box() {
@@ -192,7 +227,7 @@ struct ChainRun {
     if (lane == 0) ok = mbar_wait_poll(R.bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
     __syncwarp();
     ok = __shfl_sync(kFull, ok, 0);
-    slot = R.slots + (q % kRing) * g.slot_bytes + lane * 4 * esize;
+    slot = R.slots + (q % kRing) * g.slot_bytes + lane * C * esize;
     return ok != 0;
   }
 
@@ -203,94 +238,117 @@ struct ChainRun {
     issue_one<D>(kp, g, R, stride, lane);
   }
 
-  // x pass of stage S over a row (columns c0-2 .. c0+5) into window slot J,
-  // then the window copies of the image's top and bottom boundary rows (y is
-  // the row's image row).
+  // x pass of stage S over a row into window slot J (columns c0-2 .. c0+C+1:
+  // two neighbours on each side from the adjacent lanes).
   template <int S, int J>
-  __device__ __forceinline__ void xpass(const float (&v)[4], int y) {
+  __device__ __forceinline__ void xpass(const float (&v)[C]) {
     const float* w = kp.a.w[S];
-    const float l2 = __shfl_up_sync(kFull, v[2], 1), l1 = __shfl_up_sync(kFull, v[3], 1);
+    const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
-    hx[S][J][0] = tap5(w, l2, l1, v[0], v[1], v[2]);
-    hx[S][J][1] = tap5(w, l1, v[0], v[1], v[2], v[3]);
-    hx[S][J][2] = tap5(w, v[0], v[1], v[2], v[3], r1);
-    hx[S][J][3] = tap5(w, v[1], v[2], v[3], r1, r2);
-    if (vedge) {
-      if (y == 0) {  // rows -2 and -1 of this stage's input are row 0
+    float e[C + 4];
+    e[0] = l2; e[1] = l1;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { hx[S][mod5(J - 1)][k] = hx[S][J][k]; hx[S][mod5(J - 2)][k] = hx[S][J][k]; }
-      }
-      if (y >= kp.a.in.h) {  // rows H and H + 1 are row H - 1
+    for (int k = 0; k < C; ++k) e[k + 2] = v[k];
+    e[C + 2] = r1; e[C + 3] = r2;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) hx[S][J][k] = hx[S][mod5(J - 1)][k];
-      }
-    }
+    for (int k = 0; k < C; ++k) hx[S][J][k] = tap5(w, e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
   }
 
-  // y pass of stage S whose newest window row sits in slot J; then either the
-  // next stage's x pass or the store.
-  template <int S, int M>
-  __device__ __forceinline__ void stage(int t) {
+  // Stage S at a step of phase M (= t mod 5); v is its input row (image row
+  // i = y0 + t - 2S for S = 0, stage S-1's output row otherwise).  EDGE: the
+  // step may need the top or bottom boundary handling.
+  template <int S, int M, bool EDGE>
+  __device__ __forceinline__ void stage(int t, float (&v)[C]) {
     constexpr int J = mod5(M - 2 * S);
-    const float* w = kp.a.w[S] + 5;
-    float o[4];
+    if (EDGE) {
+      const int i = U.y0 + t - 2 * S;
+      if (i >= H) {
+        // below the image: this stage's producer row is its row H - 1
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < C; ++k) hx[S][J][k] = hx[S][mod5(J - 1)][k];
+      } else {
+        if (hb) clamp_cols<C>(v, c0, U.x0, kp.a.in.w);
+        xpass<S, J>(v);
+        if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
+#pragma unroll
+          for (int k = 0; k < C; ++k) { hx[S][mod5(J - 1)][k] = hx[S][J][k]; hx[S][mod5(J - 2)][k] = hx[S][J][k]; }
+        }
+      }
+    } else {
+      if (hb) clamp_cols<C>(v, c0, U.x0, kp.a.in.w);
+      xpass<S, J>(v);
+    }
+    const float* w = kp.a.w[S] + 5;
+    float o[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
       float b = tap5(w, hx[S][mod5(J + 1)][k], hx[S][mod5(J + 2)][k], hx[S][mod5(J + 3)][k], hx[S][mod5(J + 4)][k],
                      hx[S][J][k]);
       if (!F32) b = round_storage(kp.a.storage[S], b);
       o[k] = b;
     }
     if constexpr (S + 1 < D) {
-      if (hb) clamp_cols(o, c0, U.x0, kp.a.in.w);
-      xpass<S + 1, mod5(M - 2 * (S + 1))>(o, U.oy - 2 * D + t - 2 * (S + 1));
-      stage<S + 1, M>(t);
+      stage<S + 1, M, EDGE>(t, o);
       return;
     }
-    if (t < 4 * D) return;  // the chain's output is not valid yet
+    if (t < t_store) return;  // the chain's output is not the run's yet
     char* row = out_row;
     out_row += kp.a.out.rs;
     if (st_full) {
       if (ODT == 0) {
-        *reinterpret_cast<float4*>(row + 4LL * c0) = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+        for (int q4 = 0; q4 < C / 4; ++q4)
+          reinterpret_cast<float4*>(row + 4LL * c0)[q4] = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
       } else {
-        uint2 u;
-        if (ODT == 1) {
-          __half2 p0 = __floats2half2_rn(o[0], o[1]), p1 = __floats2half2_rn(o[2], o[3]);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
-        } else {
-          __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
+#pragma unroll
+        for (int q4 = 0; q4 < C / 4; ++q4) {
+          uint2 u;
+          if (ODT == 1) {
+            __half2 p0 = __floats2half2_rn(o[4 * q4], o[4 * q4 + 1]), p1 = __floats2half2_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
+            u.x = *reinterpret_cast<unsigned*>(&p0);
+            u.y = *reinterpret_cast<unsigned*>(&p1);
+          } else {
+            __nv_bfloat162 p0 = __floats2bfloat162_rn(o[4 * q4], o[4 * q4 + 1]);
+            __nv_bfloat162 p1 = __floats2bfloat162_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
+            u.x = *reinterpret_cast<unsigned*>(&p0);
+            u.y = *reinterpret_cast<unsigned*>(&p1);
+          }
+          reinterpret_cast<uint2*>(row + 2LL * c0)[q4] = u;
         }
-        *reinterpret_cast<uint2*>(row + 2LL * c0) = u;
       }
     } else if (st_part) {
-      const int y = U.oy + t - 4 * D;
+      const int y = U.y0 + t - 2 * D;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < C; ++k)
         if (c0 + k < kp.a.out.w) store_px(kp.a.out, U.plane, c0 + k, y, o[k]);
     }
   }
 
+  // One step: the input row (from the ring while it lies inside the image)
+  // through all D stages.
   template <int M>
   __device__ __forceinline__ bool step(int t) {
-    if (rr == 0 && !wait_box()) return false;
-    float v[4];
-    load4(slot + rr * 128 * esize, kp.a.in.dtype, v);
-    if (++rr == kBoxRows) {
-      rr = 0;
-      release_box();
+    float v[C];
+    if (U.y0 + t < H) {
+      if (rr == 0 && !wait_box()) return false;
+      load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
+      if (++rr == kBoxRows) {
+        rr = 0;
+        release_box();
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < C; ++k) v[k] = 0.0f;
     }
-    if (hb) clamp_cols(v, c0, U.x0, kp.a.in.w);
-    xpass<0, M>(v, U.oy - 2 * D + t);
-    stage<0, M>(t);
+    // the top rows of a top run (first 2(D-1) + 1 steps) and the steps at
+    // which some stage's input row lies below the image take the edge path
+    if ((top && t <= 2 * (D - 1)) || t >= t_edge) stage<0, M, true>(t, v);
+    else stage<0, M, false>(t, v);
     return true;
   }
 
   __device__ __forceinline__ bool run() {
-    const int n = U.n_in;
+    const int n = U.n_steps;
     int t = 0;
     while (true) {
       if (!step<0>(t)) return false;
@@ -312,13 +370,13 @@ struct ChainRun {
   }
 };
 
-template <int D, int ODT, bool F32>
-__global__ void __launch_bounds__(256, 2) k_chain_rows(const __grid_constant__ CRowsParams kp) {
+template <int D, int C, int ODT, bool F32>
+__global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const StripGeom g = strip_geom(D, kp.a.in.dtype == HP_F32 ? 4 : 2);
+  const StripGeom g = strip_geom(D, C, kp.a.in.dtype == HP_F32 ? 4 : 2);
   const int gw = blockIdx.x * nw + warp, stride = gridDim.x * nw;
   if (gw >= kp.units) return;
   Ring R;
@@ -336,7 +394,7 @@ __global__ void __launch_bounds__(256, 2) k_chain_rows(const __grid_constant__ C
   R.IU = unit_geom(kp, g, gw, D);
   for (int i = 0; i < kRing; ++i) issue_one<D>(kp, g, R, stride, lane);
   for (int u = gw; u < kp.units; u += stride) {
-    ChainRun<D, ODT, F32> run(kp, g, R, unit_geom(kp, g, u, D), lane, stride);
+    ChainRun<D, C, ODT, F32> run(kp, g, R, unit_geom(kp, g, u, D), lane, stride);
     if (!run.run()) {
       // a box never arrived: report, wait (bounded) for the copies still in
       // flight into this warp's slots, and stop
@@ -353,46 +411,63 @@ __global__ void __launch_bounds__(256, 2) k_chain_rows(const __grid_constant__ C
 
 typedef void (*CRowsKernel)(CRowsParams);
 
-template <int D>
-CRowsKernel pick_d(const ChainArgs& a, int* variant) {
+template <int D, int C>
+CRowsKernel pick_dc(const ChainArgs& a, int* variant) {
   bool f32 = a.in.dtype == HP_F32 && a.out.dtype == HP_F32;
   for (int s = 0; s < D; ++s) f32 &= a.storage[s] == HP_F32;
   const int odt = a.out.dtype == HP_F32 ? 0 : a.out.dtype == HP_F16 ? 1 : a.out.dtype == HP_BF16 ? 2 : 3;
-  if (f32) { *variant = 0; return k_chain_rows<D, 0, true>; }
+  if (f32) { *variant = 0; return k_chain_rows<D, C, 0, true>; }
   *variant = 1 + odt;
   switch (odt) {
-    case 0: return k_chain_rows<D, 0, false>;
-    case 1: return k_chain_rows<D, 1, false>;
-    case 2: return k_chain_rows<D, 2, false>;
-    default: return k_chain_rows<D, 3, false>;
+    case 0: return k_chain_rows<D, C, 0, false>;
+    case 1: return k_chain_rows<D, C, 1, false>;
+    case 2: return k_chain_rows<D, C, 2, false>;
+    default: return k_chain_rows<D, C, 3, false>;
   }
 }
 
-CRowsKernel pick_kernel(const ChainArgs& a, int* variant) {
-  if (a.depth == 2) return pick_d<2>(a, variant);
-  CRowsKernel k = pick_d<4>(a, variant);
-  *variant += 5;
+// Instantiations: 4 columns per lane at depth 2 and 4, 8 columns at depth 2
+// (at depth 4 the windows of 8 columns would not fit in registers).
+CRowsKernel pick_kernel(const ChainArgs& a, int cols, int* variant) {
+  int base = 0;
+  CRowsKernel k;
+  if (a.depth == 2 && cols == 8) k = pick_dc<2, 8>(a, variant), base = 10;
+  else if (a.depth == 2) k = pick_dc<2, 4>(a, variant), base = 0;
+  else k = pick_dc<4, 4>(a, variant), base = 5;
+  *variant += base;
   return k;
 }
+
+int esize_of(int dtype) { return dtype == HP_F32 ? 4 : 2; }
 
 }  // namespace
 
 bool chain_rows_depth_ok(int depth) { return depth == 2 || depth == 4; }
 
-int chain_rows_strip_w(int depth, int in_dtype) { return strip_geom(depth, in_dtype == HP_F32 ? 4 : 2).strip_w; }
+// Strip width with `cols` columns per lane (4, the default, or 8) for this
+// depth and input type.
+int chain_rows_strip_w(int depth, int in_dtype, int cols) { return strip_geom(depth, cols, esize_of(in_dtype)).strip_w; }
 
-int chain_rows_smem_bytes(int depth, int threads, int in_dtype) {
-  const StripGeom g = strip_geom(depth, in_dtype == HP_F32 ? 4 : 2);
+// Columns per lane a schedule's tile width selects (4 or 8), or 0 if the width
+// is not a strip width of this depth and input type.
+int chain_rows_cols(int depth, int in_dtype, int tile_w) {
+  for (int c : {4, 8})
+    if ((c == 4 || depth == 2) && strip_geom(depth, c, esize_of(in_dtype)).strip_w == tile_w) return c;
+  return 0;
+}
+
+int chain_rows_smem_bytes(int depth, int cols, int threads, int in_dtype) {
+  const StripGeom g = strip_geom(depth, cols, esize_of(in_dtype));
   return 128 + kBarBytes + (threads / 32) * kRing * g.slot_bytes;
 }
 
 // Persistent grid: enough CTAs to fill every SM at the kernel's occupancy, or
 // fewer when there are fewer units.
-int chain_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes) {
+int chain_rows_grid(const ChainArgs& a, int cols, int units, int threads, int smem_bytes) {
   const int nw = threads / 32;
   const int need = (units + nw - 1) / nw;
   int dev = 0, sms = 0, per_sm = 0, variant = 0;
-  CRowsKernel kern = pick_kernel(a, &variant);
+  CRowsKernel kern = pick_kernel(a, cols, &variant);
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       allow_max_dynamic_smem((const void*)kern) != 0 ||
@@ -404,28 +479,29 @@ int chain_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes) 
   return need < sms * per_sm ? need : sms * per_sm;
 }
 
-int launch_chain_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream) {
+int launch_chain_rows(const ChainArgs& a, int cols, int rows, int grid, int smem_bytes, void* stream) {
   int variant;
-  CRowsKernel kern = pick_kernel(a, &variant);
-  static bool configured[10] = {};
+  CRowsKernel kern = pick_kernel(a, cols, &variant);
+  static bool configured[15] = {};
   if (!configured[variant]) {
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
     configured[variant] = true;
   }
+  if (a.threads / 32 > kMaxWarps) return (int)cudaErrorInvalidValue;
   CRowsParams kp;
   memset(&kp, 0, sizeof kp);
   kp.a = a;
   const int dt = a.in.dtype;
-  const int esize = dt == HP_F32 ? 4 : 2;
-  const StripGeom g = strip_geom(a.depth, esize);
+  const int esize = esize_of(dt);
+  const StripGeom g = strip_geom(a.depth, cols, esize);
   kp.strips = (a.out.w + g.strip_w - 1) / g.strip_w;
   kp.runs = (a.out.h + rows - 1) / rows;
   kp.rows = rows;
   kp.units = kp.strips * kp.runs * a.out.c;
   CUtensorMapDataType tdt = dt == HP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                             : dt == HP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  if (encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, 128, kBoxRows, 1))
+  if (encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, g.box_w, kBoxRows, 1))
     return (int)cudaErrorInvalidValue;
   { const int le_ = launch_kernel(kern, dim3(grid), dim3(a.threads), smem_bytes, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);

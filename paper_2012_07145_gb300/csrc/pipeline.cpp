@@ -890,25 +890,29 @@ hp_status build_chain_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp
   if (!chain_rows_depth_ok(a.depth))
     return fail(HP_ERR_SCHEDULE, "the streaming chain kernel fuses 2 or 4 stencils (group of %d)", a.depth);
   const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
-  const int sw = chain_rows_strip_w(a.depth, in_dt);
-  if (a.tile_w != sw)
-    return fail(HP_ERR_SCHEDULE, "streaming chain strips of %d stages are %d columns wide for this input type (tile_w %d)",
-                a.depth, sw, a.tile_w);
+  const int cols = chain_rows_cols(a.depth, in_dt, a.tile_w);
+  if (!cols)
+    return fail(HP_ERR_SCHEDULE,
+                "streaming chain strips of %d stages are %d (4 columns per lane) or %d (8) columns wide for this "
+                "input type (tile_w %d)",
+                a.depth, chain_rows_strip_w(a.depth, in_dt, 4), chain_rows_strip_w(a.depth, in_dt, 8), a.tile_w);
+  const int sw = a.tile_w;
+  a.cols = cols;
   if (a.threads % 32 != 0 || a.threads < 32 || a.threads > 256)
     return fail(HP_ERR_SCHEDULE, "streaming chain threads per block must be a multiple of 32 in [32, 256]");
   Dom od = plan.dom[gp.output];
   const int planes = p->stages[gp.output].channels;
   a.tiles_x = (od.w + sw - 1) / sw;
-  gp.smem = chain_rows_smem_bytes(a.depth, a.threads, in_dt);
+  gp.smem = chain_rows_smem_bytes(a.depth, cols, a.threads, in_dt);
   if (gp.smem > kSmemLimit) return fail(HP_ERR_SCHEDULE, "streaming chain needs %d bytes of shared memory", gp.smem);
   a.in.dtype = in_dt;
   a.out.dtype = p->stages[gp.output].storage;
   if (a.tile_h == 0)
     gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x * planes,
-                                            (long long)chain_rows_grid(a, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
+                                            (long long)chain_rows_grid(a, cols, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
   if (a.tile_h < 1 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming chain needs tile_h >= 1 rows per run");
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
-  gp.grid_x = chain_rows_grid(a, a.tiles_x * a.tiles_y * planes, a.threads, gp.smem);
+  gp.grid_x = chain_rows_grid(a, cols, a.tiles_x * a.tiles_y * planes, a.threads, gp.smem);
   gp.grid_y = 1;
   gp.grid_z = 1;
   return HP_OK;
@@ -1183,7 +1187,8 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         const int depth = (int)gp.members.size();
         const int sw = single ? stencil_rows_strip_w(in_dt) : chain_rows_depth_ok(depth) ? chain_rows_strip_w(depth, in_dt) : -1;
         gp.tile_w = pick(p->tile_w, g, single ? sw : 64);
-        const bool streaming = impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && gp.tile_w == sw);
+        const bool strip_w = single ? gp.tile_w == sw : chain_rows_depth_ok(depth) && chain_rows_cols(depth, in_dt, gp.tile_w);
+        const bool streaming = impl == HP_IMPL_WAVE || (impl == HP_IMPL_AUTO && strip_w);
         gp.tile_h = pick(p->tile_h, g, streaming ? 0 : 32);  // 0: the streaming kernels' adaptive run length
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
@@ -1538,7 +1543,7 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.in = ref_view(p, plan, p->stages[first].inputs[0], inputs, output);
         a.out = out;
         a.err = p->d_err;
-        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_chain_rows(a, a.tile_h, gp.grid_x, gp.smem, stream)
+        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_chain_rows(a, a.cols, a.tile_h, gp.grid_x, gp.smem, stream)
                                                 : launch_chain(a, gp.smem, stream);
         break;
       }

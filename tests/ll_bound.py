@@ -12,6 +12,9 @@ kernel's, and this module bounds it per output pixel:
 
 1. Uncertainty of d in FP32, per pixel and level (u = 2^-24):
      |delta d| <= u (7 |i| + |g_k| + |d|)
+   (plus the same with 2^-53 for the FP64 oracle's own rounding of d, which
+   matters where d is within a few ulps of 0: the oracle's gray of a saturated
+   pixel is 1 - 2^-53, not 1)
    gray i = 0.299 R s + 0.587 G s + 0.114 B s with s = 1/65535: every term has
    at most six relative roundings (s, the product with s, the weight, up to
    three accumulations), all terms are positive, so |delta i| <= 6u|i| (7 with
@@ -42,12 +45,15 @@ from oracle.local_laplacian import GRAY_WEIGHTS
 from oracle.pyramid import gaussian_pyramid, upsample
 
 U = 2.0 ** -24
+U64 = 2.0 ** -53
 C_GRAY = 7.0
 
 
 def delta_d(gray, gk):
-    """Bound of the FP32 uncertainty of d = gray - g_k (item 1)."""
-    return U * (C_GRAY * np.abs(gray) + abs(gk) + np.abs(gray - gk))
+    """Bound of |d_fp32 - d_oracle| for d = gray - g_k (item 1): the FP32
+    uncertainty plus the oracle's own FP64 one (the same count of roundings at
+    2^-53), which the comparison with the oracle also sees."""
+    return (U + U64) * (C_GRAY * np.abs(gray) + abs(gk) + np.abs(gray - gk))
 
 
 def remap_error_bound(gray, gk, sigma, alpha, beta):

@@ -112,12 +112,12 @@ def test_cuda_graph_replay_matches_and_counts_launches():
 
 @pytest.mark.parametrize("h,w", [(1, 1), (3, 7), (17, 33), (65, 129), (200, 300), (77, 250)])
 @pytest.mark.parametrize("depth,tw,th,thr", [(2, 120, 64, 256), (2, 120, 5, 64), (4, 112, 32, 256), (4, 112, 7, 96),
-                                             (4, 112, 1, 32)])
+                                             (4, 112, 1, 32), (2, 240, 16, 128), (2, 240, 3, 256), (2, 240, 1, 32)])
 def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th, thr):
-    """The streaming chain kernel (2 or 4 stages in registers per warp strip)
-    against the generic interpreter run stage by stage, over images narrower
-    and shorter than a strip or a run, runs cut at every offset against the
-    4-row boxes, and 1..8 warps per block."""
+    """The streaming chain kernel (2 or 4 stages in registers per warp strip,
+    4 or 8 columns per lane) against the generic interpreter run stage by
+    stage, over images narrower and shorter than a strip or a run, runs cut at
+    every offset against the 4-row boxes, and 1..8 warps per block."""
     img = synth.stencil_input(h, w, seed=h * 7 + w)
     p = pipelines.stencil_chain(16, "alternate")
     p.schedule(list(range(16)), impl=[hp.HP_IMPL_GENERIC] * 16)
@@ -138,17 +138,18 @@ def test_streaming_kernel_16bit_storage(st):
     p = pipelines.stencil_chain(8, "alternate", storage=dt)
     p.schedule(list(range(8)), impl=[hp.HP_IMPL_GENERIC] * 8)
     base = chain_run(p, img, dt)
-    for depth in (2, 4):
-        pipelines.chain_schedule(p, depth=depth, tile_w=112, tile_h=19, impl=hp.HP_IMPL_WAVE)
-        assert torch.equal(bits(chain_run(p, img, dt)), bits(base)), depth
+    for depth, tw in ((2, 112), (4, 112), (2, 240)):
+        pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=19, impl=hp.HP_IMPL_WAVE)
+        assert torch.equal(bits(chain_run(p, img, dt)), bits(base)), (depth, tw)
 
 
-def test_streaming_kernel_full_size_against_oracle():
+@pytest.mark.parametrize("depth,tw,th,thr", [(4, 112, 0, 256), (4, 112, 32, 128), (2, 240, 16, 128)])
+def test_streaming_kernel_full_size_bit_identical(depth, tw, th, thr):
     H, W = 1536, 2560
     img = synth.stencil_input(H, W, seed=0)
     p = pipelines.stencil_chain(32, "alternate")
     plain = chain_run(p, img)
-    pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=0, impl=hp.HP_IMPL_WAVE)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, threads=thr, impl=hp.HP_IMPL_WAVE)
     fused = chain_run(p, img)
     assert torch.equal(bits(fused), bits(plain))
 
