@@ -123,28 +123,44 @@ __device__ __forceinline__ void issue_one(const CRowsParams& kp, const StripGeom
   }
 }
 
-// Every lane's value at a column outside [0, W) becomes the value at the
-// nearest column inside, fetched from the lane that holds it.  (Only strips
-// at the image's left and right edges call it.)
-template <int C>
-__device__ __forceinline__ void clamp_cols(float (&v)[C], int c0, int x0, int W) {
-  float o[C];
-#pragma unroll
+// Per-unit description of the image's left and right edges inside a strip:
+// a stage's input row takes, at columns outside [0, W), the value of the
+// nearest column inside (clamp to edge), fetched from the lane that holds it
+// with one shuffle per edge.
+struct EdgeFix {
+  int lmask, rmask;  // per lane: bit k set if column c0 + k lies left of 0 / right of W - 1
+  int l_lane;        // lane holding column 0 (at its element 0)
+  int r_lane, r_k;   // lane and element holding column W - 1
+};
+
+__device__ __forceinline__ EdgeFix edge_fix_of(int c0, int x0, int W, int C) {
+  EdgeFix f;
+  f.lmask = f.rmask = 0;
   for (int k = 0; k < C; ++k) {
-    const int c = c0 + k;
-    const int s = min(max(c, 0), W - 1);
-    const int off = s - x0;
-    const int sl = off / C, sk = off - sl * C;
-    float t = 0.0f;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const float tj = __shfl_sync(kFull, v[j], sl);
-      t = sk == j ? tj : t;
-    }
-    o[k] = c == s ? v[k] : t;
+    if (c0 + k < 0) f.lmask |= 1 << k;
+    if (c0 + k > W - 1) f.rmask |= 1 << k;
   }
+  f.l_lane = (0 - x0) / C;
+  f.r_lane = (W - 1 - x0) / C;
+  f.r_k = (W - 1 - x0) - f.r_lane * C;
+  return f;
+}
+
+template <int C>
+__device__ __forceinline__ void clamp_cols(float (&v)[C], const EdgeFix& f, bool left, bool right) {
+  if (left) {
+    const float e = __shfl_sync(kFull, v[0], f.l_lane);
 #pragma unroll
-  for (int k = 0; k < C; ++k) v[k] = o[k];
+    for (int k = 0; k < C; ++k) v[k] = (f.lmask >> k) & 1 ? e : v[k];
+  }
+  if (right) {
+    float mine = v[0];
+#pragma unroll
+    for (int k = 1; k < C; ++k) mine = f.r_k == k ? v[k] : mine;
+    const float e = __shfl_sync(kFull, mine, f.r_lane);
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = (f.rmask >> k) & 1 ? e : v[k];
+  }
 }
 
 template <int C>
@@ -175,15 +191,20 @@ __device__ __forceinline__ void load_row(const unsigned char* p, int dtype, floa
   }
 }
 
-__host__ __device__ constexpr int mod5(int x) { return ((x % 5) + 5) % 5; }
-
 // One run of rows of one strip of one plane.  Step t reads input row y0 + t;
-// stage s's input row at that step is i = y0 + t - 2s and its y pass gives
-// its output row i - 2; the last stage's output row is y0 + t - 2D.  Windows
-// are indexed by step mod 5 (stage s's newest row at step t sits in slot
-// (t - 2s) mod 5), so a loop unrolled five times keeps them in fixed
-// registers.  F32: every storage type is f32 (no rounding).  ODT: 0 f32,
-// 1 f16, 2 bf16 packed stores, 3 any.
+// stage s's input row at that step is i = y0 + t - 2s, and its y pass
+// completes its output row i - 2; the last stage's output row is y0 + t - 2D.
+//
+// The y pass keeps, per stage and column, four partial sums instead of a
+// window of x-pass rows: when the x-pass row h of input row i arrives, the
+// partial sum of output row i - 2 takes its last tap and leaves, those of rows
+// i - 1, i and i + 1 take one tap each, and row i + 2's starts.  The taps of
+// every output row are still applied oldest row first, as tap5 applies them,
+// so the sums are bit-identical to the window form, and each update writes the
+// next slot's register: the loop body is a single step, with no rotation of
+// registers and no unrolling (the kernel's code stays small enough for the
+// instruction cache).  F32: every storage type is f32 (no rounding).  ODT:
+// 0 f32, 1 f16, 2 bf16 packed stores, 3 any.
 template <int D, int C, int ODT, bool F32>
 struct ChainRun {
   const CRowsParams& kp;
@@ -191,11 +212,13 @@ struct ChainRun {
   Ring& R;
   const Unit U;
   const int lane, stride, c0, esize, H;
-  const bool hb;             // the strip touches the left or right image edge
+  const bool hl, hr;         // the strip reaches past the left / right image edge
+  const EdgeFix ef;
   const bool top;            // the run starts at image row 0 (clamped rows above it)
   const int t_store;         // first step whose output row is the run's
-  const int t_edge;          // first step whose input row lies below the image (edge handling from there on)
-  float hx[D][5][C];         // per stage: x-pass results of its last 5 input rows
+  const int t_edge;          // first step whose input row is the image's last (edge handling from there on)
+  float acc[D][4][C];        // per stage: partial sums of its output rows i - 1 .. i + 2
+  float h[D][C];             // per stage: its newest x-pass row (kept: below the image it repeats row H - 1)
   bool st_full, st_part;     // the lane stores all its columns / some of them
   char* out_row;             // the next output row
   unsigned q;                // box being read
@@ -206,8 +229,9 @@ struct ChainRun {
                                       int lane_, int stride_)
       : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + C * lane_),
         esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), H(kp_.a.in.h),
-        hb(U_.x0 < 0 || U_.x0 + 32 * C > kp_.a.in.w), top(U_.y0 == 0),
-        t_store(U_.oy - U_.y0 + 2 * D), t_edge(kp_.a.in.h - U_.y0),
+        hl(U_.x0 < 0), hr(U_.x0 + 32 * C > kp_.a.in.w), ef(edge_fix_of(U_.x0 + C * lane_, U_.x0, kp_.a.in.w, C)),
+        top(U_.y0 == 0),
+        t_store(U_.oy - U_.y0 + 2 * D), t_edge(kp_.a.in.h - 1 - U_.y0),
         q(R_.released), rr(0), slot(nullptr) {
     const int W = kp.a.out.w;
     const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
@@ -217,9 +241,11 @@ struct ChainRun {
 #pragma unroll
     for (int s = 0; s < D; ++s)
 #pragma unroll
-      for (int j = 0; j < 5; ++j)
+      for (int k = 0; k < C; ++k) {
+        h[s][k] = 0.0f;
 #pragma unroll
-        for (int k = 0; k < C; ++k) hx[s][j][k] = 0.0f;
+        for (int j = 0; j < 4; ++j) acc[s][j][k] = 0.0f;
+      }
   }
 
   __device__ __forceinline__ bool wait_box() {
@@ -238,9 +264,9 @@ struct ChainRun {
     issue_one<D>(kp, g, R, stride, lane);
   }
 
-  // x pass of stage S over a row into window slot J (columns c0-2 .. c0+C+1:
-  // two neighbours on each side from the adjacent lanes).
-  template <int S, int J>
+  // x pass of stage S over its input row v (columns c0-2 .. c0+C+1: two
+  // neighbours on each side from the adjacent lanes) into h[S].
+  template <int S>
   __device__ __forceinline__ void xpass(const float (&v)[C]) {
     const float* w = kp.a.w[S];
     const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
@@ -251,44 +277,50 @@ struct ChainRun {
     for (int k = 0; k < C; ++k) e[k + 2] = v[k];
     e[C + 2] = r1; e[C + 3] = r2;
 #pragma unroll
-    for (int k = 0; k < C; ++k) hx[S][J][k] = tap5(w, e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
+    for (int k = 0; k < C; ++k) h[S][k] = tap5(w, e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
   }
 
-  // Stage S at a step of phase M (= t mod 5); v is its input row (image row
-  // i = y0 + t - 2S for S = 0, stage S-1's output row otherwise).  EDGE: the
-  // step may need the top or bottom boundary handling.
-  template <int S, int M, bool EDGE>
-  __device__ __forceinline__ void stage(int t, float (&v)[C]) {
-    constexpr int J = mod5(M - 2 * S);
-    if (EDGE) {
-      const int i = U.y0 + t - 2 * S;
-      if (i >= H) {
-        // below the image: this stage's producer row is its row H - 1
-#pragma unroll
-        for (int k = 0; k < C; ++k) hx[S][J][k] = hx[S][mod5(J - 1)][k];
-      } else {
-        if (hb) clamp_cols<C>(v, c0, U.x0, kp.a.in.w);
-        xpass<S, J>(v);
-        if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
-#pragma unroll
-          for (int k = 0; k < C; ++k) { hx[S][mod5(J - 1)][k] = hx[S][J][k]; hx[S][mod5(J - 2)][k] = hx[S][J][k]; }
-        }
-      }
-    } else {
-      if (hb) clamp_cols<C>(v, c0, U.x0, kp.a.in.w);
-      xpass<S, J>(v);
-    }
+  // y pass of stage S with h[S] as its newest row: the partial sums advance
+  // one row and o receives the completed output row (rounded to the stage's
+  // storage type).
+  template <int S>
+  __device__ __forceinline__ void ypass(float (&o)[C]) {
     const float* w = kp.a.w[S] + 5;
-    float o[C];
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-      float b = tap5(w, hx[S][mod5(J + 1)][k], hx[S][mod5(J + 2)][k], hx[S][mod5(J + 3)][k], hx[S][mod5(J + 4)][k],
-                     hx[S][J][k]);
+      const float x = h[S][k];
+      float b = __fmaf_rn(w[4], x, acc[S][0][k]);
+      acc[S][0][k] = __fmaf_rn(w[3], x, acc[S][1][k]);
+      acc[S][1][k] = __fmaf_rn(w[2], x, acc[S][2][k]);
+      acc[S][2][k] = __fmaf_rn(w[1], x, acc[S][3][k]);
+      acc[S][3][k] = __fmul_rn(w[0], x);
       if (!F32) b = round_storage(kp.a.storage[S], b);
       o[k] = b;
     }
+  }
+
+  // Stage S at step t, input row v.  EDGE: the step may need the top or
+  // bottom boundary handling.
+  template <int S, bool EDGE>
+  __device__ __forceinline__ void stage(int t, float (&v)[C]) {
+    float o[C];
+    if (EDGE) {
+      const int i = U.y0 + t - 2 * S;
+      if (i < H) {  // else below the image: h[S] still holds row H - 1, the clamped row
+        if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
+        xpass<S>(v);
+        if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
+          ypass<S>(o);
+          ypass<S>(o);
+        }
+      }
+    } else {
+      if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
+      xpass<S>(v);
+    }
+    ypass<S>(o);
     if constexpr (S + 1 < D) {
-      stage<S + 1, M, EDGE>(t, o);
+      stage<S + 1, EDGE>(t, o);
       return;
     }
     if (t < t_store) return;  // the chain's output is not the run's yet
@@ -324,43 +356,28 @@ struct ChainRun {
     }
   }
 
-  // One step: the input row (from the ring while it lies inside the image)
-  // through all D stages.
-  template <int M>
-  __device__ __forceinline__ bool step(int t) {
-    float v[C];
-    if (U.y0 + t < H) {
-      if (rr == 0 && !wait_box()) return false;
-      load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
-      if (++rr == kBoxRows) {
-        rr = 0;
-        release_box();
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < C; ++k) v[k] = 0.0f;
-    }
-    // the top rows of a top run (first 2(D-1) + 1 steps) and the steps at
-    // which some stage's input row lies below the image take the edge path
-    if ((top && t <= 2 * (D - 1)) || t >= t_edge) stage<0, M, true>(t, v);
-    else stage<0, M, false>(t, v);
-    return true;
-  }
-
   __device__ __forceinline__ bool run() {
     const int n = U.n_steps;
-    int t = 0;
-    while (true) {
-      if (!step<0>(t)) return false;
-      if (++t >= n) break;
-      if (!step<1>(t)) return false;
-      if (++t >= n) break;
-      if (!step<2>(t)) return false;
-      if (++t >= n) break;
-      if (!step<3>(t)) return false;
-      if (++t >= n) break;
-      if (!step<4>(t)) return false;
-      if (++t >= n) break;
+    const int edge_lo = top ? 2 * (D - 1) : -1;  // steps 0 .. edge_lo: some stage's input row is row 0
+#pragma unroll 1
+    for (int t = 0; t < n; ++t) {
+      float v[C];
+      if (U.y0 + t < H) {
+        if (rr == 0 && !wait_box()) return false;
+        load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
+        if (++rr == kBoxRows) {
+          rr = 0;
+          release_box();
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) v[k] = 0.0f;
+      }
+      // the top rows of a top run, and the steps from the one that reads the
+      // image's last row on (some stage's input row is H - 1 or below the
+      // image), take the edge path
+      if (t <= edge_lo || t >= t_edge) stage<0, true>(t, v);
+      else stage<0, false>(t, v);
     }
     if (rr != 0) {  // the unit's last box had rows to spare
       rr = 0;
