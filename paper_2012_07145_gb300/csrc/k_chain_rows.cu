@@ -97,32 +97,6 @@ __device__ __forceinline__ Unit unit_geom(const CRowsParams& kp, const StripGeom
   return U;
 }
 
-// The warp's ring: box q (in issue order, which is the order of use) lives in
-// slot q % kRing and completes phase (q / kRing) & 1 of that slot's mbarrier.
-struct Ring {
-  unsigned char* slots;
-  uint64_t* bars;
-  unsigned issued, released;
-  int iu, ij;  // next box to issue: unit and box within it
-  Unit IU;     // geometry of unit iu
-};
-
-template <int D>
-__device__ __forceinline__ void issue_one(const CRowsParams& kp, const StripGeom& g, Ring& R, int stride, int lane) {
-  if (R.iu >= kp.units) return;
-  if (lane == 0) {
-    const int s = R.issued % kRing;
-    mbar_arrive_expect_tx(R.bars + s, (unsigned)g.slot_bytes);
-    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.y0 + R.ij * kBoxRows, R.IU.plane, R.bars + s);
-  }
-  ++R.issued;
-  if (++R.ij == R.IU.nbox) {
-    R.ij = 0;
-    R.iu += stride;
-    if (R.iu < kp.units) R.IU = unit_geom(kp, g, R.iu, D);
-  }
-}
-
 // Per-unit description of the image's left and right edges inside a strip:
 // a stage's input row takes, at columns outside [0, W), the value of the
 // nearest column inside (clamp to edge), fetched from the lane that holds it
@@ -146,6 +120,14 @@ __device__ __forceinline__ EdgeFix edge_fix_of(int c0, int x0, int W, int C) {
   return f;
 }
 
+// A select the compiler keeps as a select (a chain of compare-and-select over
+// an array's elements would otherwise become an indexed load from local memory).
+__device__ __forceinline__ float sel(bool p, float a, float b) {
+  float r;
+  asm("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %3, 0;\n\tselp.f32 %0, %1, %2, q;\n\t}" : "=f"(r) : "f"(a), "f"(b), "r"((int)p));
+  return r;
+}
+
 template <int C>
 __device__ __forceinline__ void clamp_cols(float (&v)[C], const EdgeFix& f, bool left, bool right) {
   if (left) {
@@ -156,7 +138,7 @@ __device__ __forceinline__ void clamp_cols(float (&v)[C], const EdgeFix& f, bool
   if (right) {
     float mine = v[0];
 #pragma unroll
-    for (int k = 1; k < C; ++k) mine = f.r_k == k ? v[k] : mine;
+    for (int k = 1; k < C; ++k) mine = sel(f.r_k == k, v[k], mine);
     const float e = __shfl_sync(kFull, mine, f.r_lane);
 #pragma unroll
     for (int k = 0; k < C; ++k) v[k] = (f.rmask >> k) & 1 ? e : v[k];
@@ -191,6 +173,17 @@ __device__ __forceinline__ void load_row(const unsigned char* p, int dtype, floa
   }
 }
 
+// Issues box j of unit U (input rows y0 + 4j ..) into ring slot q % kRing.
+// Called by one lane; the fence orders the warp's earlier reads of the slot
+// (generic proxy) before the copy that overwrites it (async proxy).
+__device__ __forceinline__ void issue_box(const CUtensorMap* tmap, unsigned char* slots, uint64_t* bars,
+                                          int slot_bytes, unsigned q, const Unit& U, int j) {
+  const int s = q % kRing;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bars + s, (unsigned)slot_bytes);
+  tma_load_3d(slots + s * slot_bytes, tmap, U.x0, U.y0 + j * kBoxRows, U.plane, bars + s);
+}
+
 // One run of rows of one strip of one plane.  Step t reads input row y0 + t;
 // stage s's input row at that step is i = y0 + t - 2s, and its y pass
 // completes its output row i - 2; the last stage's output row is y0 + t - 2D.
@@ -203,72 +196,25 @@ __device__ __forceinline__ void load_row(const unsigned char* p, int dtype, floa
 // so the sums are bit-identical to the window form, and each update writes the
 // next slot's register: the loop body is a single step, with no rotation of
 // registers and no unrolling (the kernel's code stays small enough for the
-// instruction cache).  F32: every storage type is f32 (no rounding).  ODT:
-// 0 f32, 1 f16, 2 bf16 packed stores, 3 any.
+// instruction cache).  All state is in registers: the partial sums, the
+// newest x-pass row of every stage and the stage weights (loaded once).
+// F32: every storage type is f32 (no rounding).  ODT: 0 f32, 1 f16, 2 bf16
+// packed stores, 3 any.
 template <int D, int C, int ODT, bool F32>
-struct ChainRun {
-  const CRowsParams& kp;
-  const StripGeom& g;
-  Ring& R;
-  const Unit U;
-  const int lane, stride, c0, esize, H;
-  const bool hl, hr;         // the strip reaches past the left / right image edge
-  const EdgeFix ef;
-  const bool top;            // the run starts at image row 0 (clamped rows above it)
-  const int t_store;         // first step whose output row is the run's
-  const int t_edge;          // first step whose input row is the image's last (edge handling from there on)
+struct RunState {
+  float w[D][10];            // per stage: x taps, then y taps
+  int st[D];                 // per stage: storage type (rounding when !F32)
   float acc[D][4][C];        // per stage: partial sums of its output rows i - 1 .. i + 2
-  float h[D][C];             // per stage: its newest x-pass row (kept: below the image it repeats row H - 1)
-  bool st_full, st_part;     // the lane stores all its columns / some of them
-  char* out_row;             // the next output row
-  unsigned q;                // box being read
-  int rr;                    // row within it
-  const unsigned char* slot;
-
-  __device__ __forceinline__ ChainRun(const CRowsParams& kp_, const StripGeom& g_, Ring& R_, const Unit& U_,
-                                      int lane_, int stride_)
-      : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + C * lane_),
-        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), H(kp_.a.in.h),
-        hl(U_.x0 < 0), hr(U_.x0 + 32 * C > kp_.a.in.w), ef(edge_fix_of(U_.x0 + C * lane_, U_.x0, kp_.a.in.w, C)),
-        top(U_.y0 == 0),
-        t_store(U_.oy - U_.y0 + 2 * D), t_edge(kp_.a.in.h - 1 - U_.y0),
-        q(R_.released), rr(0), slot(nullptr) {
-    const int W = kp.a.out.w;
-    const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
-    st_full = mine && c0 + C - 1 < W && ODT != 3;
-    st_part = mine && c0 < W && !st_full;
-    out_row = (char*)kp.a.out.data + (long long)U.plane * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
-#pragma unroll
-    for (int s = 0; s < D; ++s)
-#pragma unroll
-      for (int k = 0; k < C; ++k) {
-        h[s][k] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[s][j][k] = 0.0f;
-      }
-  }
-
-  __device__ __forceinline__ bool wait_box() {
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait_poll(R.bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
-    __syncwarp();
-    ok = __shfl_sync(kFull, ok, 0);
-    slot = R.slots + (q % kRing) * g.slot_bytes + lane * C * esize;
-    return ok != 0;
-  }
-
-  __device__ __forceinline__ void release_box() {
-    ++q;
-    __syncwarp();
-    R.released = q;
-    issue_one<D>(kp, g, R, stride, lane);
-  }
+  float h[D][C];             // per stage: its newest x-pass row (below the image it stays row H - 1)
+  int c0, x0, y0, W, H;
+  bool hl, hr, top;          // the strip reaches past the left / right image edge; the run starts at row 0
+  EdgeFix ef;
 
   // x pass of stage S over its input row v (columns c0-2 .. c0+C+1: two
   // neighbours on each side from the adjacent lanes) into h[S].
   template <int S>
-  __device__ __forceinline__ void xpass(const float (&v)[C]) {
-    const float* w = kp.a.w[S];
+  __device__ __forceinline__ void xpass(float (&v)[C]) {
+    if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
     const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
     float e[C + 4];
@@ -277,7 +223,7 @@ struct ChainRun {
     for (int k = 0; k < C; ++k) e[k + 2] = v[k];
     e[C + 2] = r1; e[C + 3] = r2;
 #pragma unroll
-    for (int k = 0; k < C; ++k) h[S][k] = tap5(w, e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
+    for (int k = 0; k < C; ++k) h[S][k] = tap5(w[S], e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
   }
 
   // y pass of stage S with h[S] as its newest row: the partial sums advance
@@ -285,29 +231,26 @@ struct ChainRun {
   // storage type).
   template <int S>
   __device__ __forceinline__ void ypass(float (&o)[C]) {
-    const float* w = kp.a.w[S] + 5;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const float x = h[S][k];
-      float b = __fmaf_rn(w[4], x, acc[S][0][k]);
-      acc[S][0][k] = __fmaf_rn(w[3], x, acc[S][1][k]);
-      acc[S][1][k] = __fmaf_rn(w[2], x, acc[S][2][k]);
-      acc[S][2][k] = __fmaf_rn(w[1], x, acc[S][3][k]);
-      acc[S][3][k] = __fmul_rn(w[0], x);
-      if (!F32) b = round_storage(kp.a.storage[S], b);
+      float b = __fmaf_rn(w[S][9], x, acc[S][0][k]);
+      acc[S][0][k] = __fmaf_rn(w[S][8], x, acc[S][1][k]);
+      acc[S][1][k] = __fmaf_rn(w[S][7], x, acc[S][2][k]);
+      acc[S][2][k] = __fmaf_rn(w[S][6], x, acc[S][3][k]);
+      acc[S][3][k] = __fmul_rn(w[S][5], x);
+      if (!F32) b = round_storage(st[S], b);
       o[k] = b;
     }
   }
 
-  // Stage S at step t, input row v.  EDGE: the step may need the top or
-  // bottom boundary handling.
+  // Stages S.. at step t; v is stage S's input row.  EDGE: the step may need
+  // the top or bottom boundary handling.  Returns the last stage's row in o.
   template <int S, bool EDGE>
-  __device__ __forceinline__ void stage(int t, float (&v)[C]) {
-    float o[C];
+  __device__ __forceinline__ void stages(int t, float (&v)[C], float (&o)[C]) {
     if (EDGE) {
-      const int i = U.y0 + t - 2 * S;
+      const int i = y0 + t - 2 * S;
       if (i < H) {  // else below the image: h[S] still holds row H - 1, the clamped row
-        if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
         xpass<S>(v);
         if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
           ypass<S>(o);
@@ -315,77 +258,49 @@ struct ChainRun {
         }
       }
     } else {
-      if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
       xpass<S>(v);
     }
-    ypass<S>(o);
     if constexpr (S + 1 < D) {
-      stage<S + 1, EDGE>(t, o);
-      return;
+      float m[C];
+      ypass<S>(m);
+      stages<S + 1, EDGE>(t, m, o);
+    } else {
+      ypass<S>(o);
     }
-    if (t < t_store) return;  // the chain's output is not the run's yet
-    char* row = out_row;
-    out_row += kp.a.out.rs;
-    if (st_full) {
-      if (ODT == 0) {
-#pragma unroll
-        for (int q4 = 0; q4 < C / 4; ++q4)
-          reinterpret_cast<float4*>(row + 4LL * c0)[q4] = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
-      } else {
-#pragma unroll
-        for (int q4 = 0; q4 < C / 4; ++q4) {
-          uint2 u;
-          if (ODT == 1) {
-            __half2 p0 = __floats2half2_rn(o[4 * q4], o[4 * q4 + 1]), p1 = __floats2half2_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
-            u.x = *reinterpret_cast<unsigned*>(&p0);
-            u.y = *reinterpret_cast<unsigned*>(&p1);
-          } else {
-            __nv_bfloat162 p0 = __floats2bfloat162_rn(o[4 * q4], o[4 * q4 + 1]);
-            __nv_bfloat162 p1 = __floats2bfloat162_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
-            u.x = *reinterpret_cast<unsigned*>(&p0);
-            u.y = *reinterpret_cast<unsigned*>(&p1);
-          }
-          reinterpret_cast<uint2*>(row + 2LL * c0)[q4] = u;
-        }
-      }
-    } else if (st_part) {
-      const int y = U.y0 + t - 2 * D;
-#pragma unroll
-      for (int k = 0; k < C; ++k)
-        if (c0 + k < kp.a.out.w) store_px(kp.a.out, U.plane, c0 + k, y, o[k]);
-    }
-  }
-
-  __device__ __forceinline__ bool run() {
-    const int n = U.n_steps;
-    const int edge_lo = top ? 2 * (D - 1) : -1;  // steps 0 .. edge_lo: some stage's input row is row 0
-#pragma unroll 1
-    for (int t = 0; t < n; ++t) {
-      float v[C];
-      if (U.y0 + t < H) {
-        if (rr == 0 && !wait_box()) return false;
-        load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
-        if (++rr == kBoxRows) {
-          rr = 0;
-          release_box();
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < C; ++k) v[k] = 0.0f;
-      }
-      // the top rows of a top run, and the steps from the one that reads the
-      // image's last row on (some stage's input row is H - 1 or below the
-      // image), take the edge path
-      if (t <= edge_lo || t >= t_edge) stage<0, true>(t, v);
-      else stage<0, false>(t, v);
-    }
-    if (rr != 0) {  // the unit's last box had rows to spare
-      rr = 0;
-      release_box();
-    }
-    return true;
   }
 };
+
+template <int C, int ODT>
+__device__ __forceinline__ void store_row(char* row, int c0, bool full, bool part, const ImgView& out, int plane,
+                                          int y, const float (&o)[C]) {
+  if (full) {
+    if (ODT == 0) {
+#pragma unroll
+      for (int q4 = 0; q4 < C / 4; ++q4)
+        reinterpret_cast<float4*>(row + 4LL * c0)[q4] = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
+    } else {
+#pragma unroll
+      for (int q4 = 0; q4 < C / 4; ++q4) {
+        uint2 u;
+        if (ODT == 1) {
+          __half2 p0 = __floats2half2_rn(o[4 * q4], o[4 * q4 + 1]), p1 = __floats2half2_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        } else {
+          __nv_bfloat162 p0 = __floats2bfloat162_rn(o[4 * q4], o[4 * q4 + 1]);
+          __nv_bfloat162 p1 = __floats2bfloat162_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        }
+        reinterpret_cast<uint2*>(row + 2LL * c0)[q4] = u;
+      }
+    }
+  } else if (part) {
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+      if (c0 + k < out.w) store_px(out, plane, c0 + k, y, o[k]);
+  }
+}
 
 template <int D, int C, int ODT, bool F32>
 __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRowsParams kp) {
@@ -393,36 +308,107 @@ __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRow
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const StripGeom g = strip_geom(D, C, kp.a.in.dtype == HP_F32 ? 4 : 2);
+  const int esize = kp.a.in.dtype == HP_F32 ? 4 : 2;
+  const StripGeom g = strip_geom(D, C, esize);
   const int gw = blockIdx.x * nw + warp, stride = gridDim.x * nw;
   if (gw >= kp.units) return;
-  Ring R;
-  R.bars = reinterpret_cast<uint64_t*>(base) + warp * kRing;
-  R.slots = base + kBarBytes + warp * kRing * g.slot_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base) + warp * kRing;
+  unsigned char* slots = base + kBarBytes + warp * kRing * g.slot_bytes;
   if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < kRing; ++i) mbar_init(R.bars + i, 1);
+    for (int i = 0; i < kRing; ++i) mbar_init(bars + i, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  R.issued = R.released = 0;
-  R.iu = gw;
-  R.ij = 0;
-  R.IU = unit_geom(kp, g, gw, D);
-  for (int i = 0; i < kRing; ++i) issue_one<D>(kp, g, R, stride, lane);
+  RunState<D, C, ODT, F32> S;
+#pragma unroll
+  for (int s = 0; s < D; ++s) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) S.w[s][k] = kp.a.w[s][k];
+    S.st[s] = kp.a.storage[s];
+  }
+  S.W = kp.a.in.w;
+  S.H = kp.a.in.h;
+  const int H = S.H, OW = kp.a.out.w;
+  unsigned qbase = 0;  // boxes this warp has issued before the current unit
   for (int u = gw; u < kp.units; u += stride) {
-    ChainRun<D, C, ODT, F32> run(kp, g, R, unit_geom(kp, g, u, D), lane, stride);
-    if (!run.run()) {
+    const Unit U = unit_geom(kp, g, u, D);
+    if (lane == 0)
+      for (int j = 0; j < kRing && j < U.nbox; ++j) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j, U, j);
+    S.x0 = U.x0;
+    S.y0 = U.y0;
+    S.c0 = U.x0 + C * lane;
+    S.hl = U.x0 < 0;
+    S.hr = U.x0 + 32 * C > S.W;
+    S.top = U.y0 == 0;
+    S.ef = edge_fix_of(S.c0, U.x0, S.W, C);
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        S.h[s][k] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) S.acc[s][j][k] = 0.0f;
+      }
+    const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
+    const bool st_full = mine && S.c0 + C - 1 < OW && ODT != 3;
+    const bool st_part = mine && S.c0 < OW && !st_full;
+    char* out_row = (char*)kp.a.out.data + (long long)U.plane * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
+    const int n = U.n_steps;
+    const int t_store = U.oy - U.y0 + 2 * D;       // first step whose output row is the run's
+    const int t_edge = H - 1 - U.y0;               // from this step on some stage's input row is H - 1 or below
+    const int edge_lo = S.top ? 2 * (D - 1) : -1;  // steps 0 .. edge_lo: some stage's input row is row 0
+    const unsigned char* slot = slots;
+    int failed = 0;
+#pragma unroll 1
+    for (int t = 0; t < n; ++t) {
+      float v[C];
+      if (U.y0 + t < H) {
+        const int j = t >> 2, rr = t & 3;
+        if (rr == 0) {
+          const unsigned q = qbase + j;
+          int ok = 1;
+          if (lane == 0) ok = mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
+          ok = __shfl_sync(kFull, ok, 0);
+          if (!ok) {
+            failed = 1;
+            break;
+          }
+          slot = slots + (q % kRing) * g.slot_bytes + lane * C * esize;
+        }
+        load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
+        if (rr == kBoxRows - 1 && j + kRing < U.nbox) {
+          __syncwarp();
+          if (lane == 0) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j + kRing, U, j + kRing);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) v[k] = 0.0f;
+      }
+      float o[C];
+      // the top rows of a top run, and the steps from the one that reads the
+      // image's last row on, take the edge path
+      if (t <= edge_lo || t >= t_edge) S.template stages<0, true>(t, v, o);
+      else S.template stages<0, false>(t, v, o);
+      if (t >= t_store) {  // the chain's output is the run's from here on
+        store_row<C, ODT>(out_row, S.c0, st_full, st_part, kp.a.out, U.plane, U.y0 + t - 2 * D, o);
+        out_row += kp.a.out.rs;
+      }
+    }
+    if (failed) {
       // a box never arrived: report, wait (bounded) for the copies still in
       // flight into this warp's slots, and stop
       if (lane == 0) {
         atomicExch(kp.a.err, 1);
-        for (unsigned b = R.released; b < R.issued; ++b)
-          mbar_wait_poll(R.bars + b % kRing, (b / kRing) & 1u, 100000000ull);
+        for (int j = 0; j < U.nbox; ++j) {
+          const unsigned q = qbase + j;
+          mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 100000000ull);
+        }
       }
       __syncwarp();
       return;
     }
+    qbase += U.nbox;
   }
 }
 
