@@ -184,6 +184,19 @@ __device__ __forceinline__ void issue_box(const CUtensorMap* tmap, unsigned char
   tma_load_3d(slots + s * slot_bytes, tmap, U.x0, U.y0 + j * kBoxRows, U.plane, bars + s);
 }
 
+// Weight classes a stage's taps can be specialised for: the kernel is then
+// compiled with the taps as constants (the same float values the pipeline
+// stores, so the arithmetic is unchanged), which frees the registers and the
+// loads the runtime taps would take.  Class 1: binomial [1,4,6,4,1]/16 on both
+// axes; class 2: box 1/5 on both axes; 0: the taps passed at run time.
+// A pattern WP holds the class of stage s in bits 2s..2s+1 (WP = 0: all
+// runtime).
+constexpr int kClassBinomial = 1, kClassBox = 2;
+
+__host__ __device__ constexpr float class_tap(int cls, int k) {
+  return cls == kClassBox ? 0.2f : (k == 0 || k == 4) ? 0.0625f : k == 2 ? 0.375f : 0.25f;
+}
+
 // One run of rows of one strip of one plane.  Step t reads input row y0 + t;
 // stage s's input row at that step is i = y0 + t - 2s, and its y pass
 // completes its output row i - 2; the last stage's output row is y0 + t - 2D.
@@ -197,24 +210,41 @@ __device__ __forceinline__ void issue_box(const CUtensorMap* tmap, unsigned char
 // next slot's register: the loop body is a single step, with no rotation of
 // registers and no unrolling (the kernel's code stays small enough for the
 // instruction cache).  All state is in registers: the partial sums, the
-// newest x-pass row of every stage and the stage weights (loaded once).
-// F32: every storage type is f32 (no rounding).  ODT: 0 f32, 1 f16, 2 bf16
-// packed stores, 3 any.
-template <int D, int C, int ODT, bool F32>
+// newest x-pass row of every stage and the runtime taps (loaded once).
+// RND: 0 every storage type f32 (no rounding), 1 all f16, 2 all bf16, 3 per
+// stage at run time.  ODT: output stores 0 f32, 1 f16, 2 bf16, 3 any type.
+template <int D, int C, int RND, int ODT, int WP>
 struct RunState {
-  float w[D][10];            // per stage: x taps, then y taps
-  int st[D];                 // per stage: storage type (rounding when !F32)
+  float w[D][10];            // per stage: x taps, then y taps (runtime class)
+  int st[D];                 // per stage: storage type (RND = 3)
   float acc[D][4][C];        // per stage: partial sums of its output rows i - 1 .. i + 2
   float h[D][C];             // per stage: its newest x-pass row (below the image it stays row H - 1)
-  int c0, x0, y0, W, H;
-  bool hl, hr, top;          // the strip reaches past the left / right image edge; the run starts at row 0
+  int y0, H;
+  bool top;                  // the run starts at image row 0
   EdgeFix ef;
+  bool hl, hr;               // the strip reaches past the left / right image edge
+
+  template <int S>
+  __device__ __forceinline__ float tap(int k) const {
+    constexpr int cls = (WP >> (2 * S)) & 3;
+    if constexpr (cls != 0) return class_tap(cls, k % 5);
+    else return w[S][k];
+  }
+
+  template <int S>
+  __device__ __forceinline__ float rnd(float b) const {
+    if (RND == 1) return __half2float(__float2half_rn(b));
+    if (RND == 2) return __bfloat162float(__float2bfloat16_rn(b));
+    if (RND == 3) return round_storage(st[S], b);
+    return b;
+  }
 
   // x pass of stage S over its input row v (columns c0-2 .. c0+C+1: two
-  // neighbours on each side from the adjacent lanes) into h[S].
-  template <int S>
+  // neighbours on each side from the adjacent lanes) into h[S].  HE: the strip
+  // reaches past an image edge, where the row first takes the edge values.
+  template <int S, bool HE>
   __device__ __forceinline__ void xpass(float (&v)[C]) {
-    if (hl || hr) clamp_cols<C>(v, ef, hl, hr);
+    if (HE) clamp_cols<C>(v, ef, hl, hr);
     const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
     float e[C + 4];
@@ -223,7 +253,13 @@ struct RunState {
     for (int k = 0; k < C; ++k) e[k + 2] = v[k];
     e[C + 2] = r1; e[C + 3] = r2;
 #pragma unroll
-    for (int k = 0; k < C; ++k) h[S][k] = tap5(w[S], e[k], e[k + 1], e[k + 2], e[k + 3], e[k + 4]);
+    for (int k = 0; k < C; ++k) {
+      float s = __fmul_rn(tap<S>(0), e[k]);
+      s = __fmaf_rn(tap<S>(1), e[k + 1], s);
+      s = __fmaf_rn(tap<S>(2), e[k + 2], s);
+      s = __fmaf_rn(tap<S>(3), e[k + 3], s);
+      h[S][k] = __fmaf_rn(tap<S>(4), e[k + 4], s);
+    }
   }
 
   // y pass of stage S with h[S] as its newest row: the partial sums advance
@@ -234,76 +270,86 @@ struct RunState {
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const float x = h[S][k];
-      float b = __fmaf_rn(w[S][9], x, acc[S][0][k]);
-      acc[S][0][k] = __fmaf_rn(w[S][8], x, acc[S][1][k]);
-      acc[S][1][k] = __fmaf_rn(w[S][7], x, acc[S][2][k]);
-      acc[S][2][k] = __fmaf_rn(w[S][6], x, acc[S][3][k]);
-      acc[S][3][k] = __fmul_rn(w[S][5], x);
-      if (!F32) b = round_storage(st[S], b);
-      o[k] = b;
+      const float b = __fmaf_rn(tap<S>(9), x, acc[S][0][k]);
+      acc[S][0][k] = __fmaf_rn(tap<S>(8), x, acc[S][1][k]);
+      acc[S][1][k] = __fmaf_rn(tap<S>(7), x, acc[S][2][k]);
+      acc[S][2][k] = __fmaf_rn(tap<S>(6), x, acc[S][3][k]);
+      acc[S][3][k] = __fmul_rn(tap<S>(5), x);
+      o[k] = rnd<S>(b);
     }
   }
 
   // Stages S.. at step t; v is stage S's input row.  EDGE: the step may need
   // the top or bottom boundary handling.  Returns the last stage's row in o.
-  template <int S, bool EDGE>
+  template <int S, bool EDGE, bool HE>
   __device__ __forceinline__ void stages(int t, float (&v)[C], float (&o)[C]) {
     if (EDGE) {
       const int i = y0 + t - 2 * S;
       if (i < H) {  // else below the image: h[S] still holds row H - 1, the clamped row
-        xpass<S>(v);
+        xpass<S, HE>(v);
         if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
           ypass<S>(o);
           ypass<S>(o);
         }
       }
     } else {
-      xpass<S>(v);
+      xpass<S, HE>(v);
     }
     if constexpr (S + 1 < D) {
       float m[C];
       ypass<S>(m);
-      stages<S + 1, EDGE>(t, m, o);
+      stages<S + 1, EDGE, HE>(t, m, o);
     } else {
       ypass<S>(o);
     }
   }
 };
 
+// Stores a lane's output columns.  full: all C columns lie inside the image
+// (one vector store); part: some do (one store per column inside).
 template <int C, int ODT>
 __device__ __forceinline__ void store_row(char* row, int c0, bool full, bool part, const ImgView& out, int plane,
                                           int y, const float (&o)[C]) {
-  if (full) {
-    if (ODT == 0) {
+  if (ODT == 3) {
+    if (full || part) {
+#pragma unroll
+      for (int k = 0; k < C; ++k)
+        if (c0 + k < out.w) store_px(out, plane, c0 + k, y, o[k]);
+    }
+    return;
+  }
+  if (ODT == 0) {
+    float* p = reinterpret_cast<float*>(row) + c0;
+    if (full) {
 #pragma unroll
       for (int q4 = 0; q4 < C / 4; ++q4)
-        reinterpret_cast<float4*>(row + 4LL * c0)[q4] = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
-    } else {
+        reinterpret_cast<float4*>(p)[q4] = make_float4(o[4 * q4], o[4 * q4 + 1], o[4 * q4 + 2], o[4 * q4 + 3]);
+    } else if (part) {
 #pragma unroll
-      for (int q4 = 0; q4 < C / 4; ++q4) {
-        uint2 u;
-        if (ODT == 1) {
-          __half2 p0 = __floats2half2_rn(o[4 * q4], o[4 * q4 + 1]), p1 = __floats2half2_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
-        } else {
-          __nv_bfloat162 p0 = __floats2bfloat162_rn(o[4 * q4], o[4 * q4 + 1]);
-          __nv_bfloat162 p1 = __floats2bfloat162_rn(o[4 * q4 + 2], o[4 * q4 + 3]);
-          u.x = *reinterpret_cast<unsigned*>(&p0);
-          u.y = *reinterpret_cast<unsigned*>(&p1);
-        }
-        reinterpret_cast<uint2*>(row + 2LL * c0)[q4] = u;
-      }
+      for (int k = 0; k < C; ++k)
+        if (c0 + k < out.w) p[k] = o[k];
     }
+    return;
+  }
+  unsigned short hv[C];
+#pragma unroll
+  for (int k = 0; k < C; ++k)
+    hv[k] = ODT == 1 ? __half_as_ushort(__float2half_rn(o[k])) : __bfloat16_as_ushort(__float2bfloat16_rn(o[k]));
+  unsigned short* p = reinterpret_cast<unsigned short*>(row) + c0;
+  if (full) {
+#pragma unroll
+    for (int q4 = 0; q4 < C / 4; ++q4)
+      reinterpret_cast<uint2*>(p)[q4] = make_uint2(hv[4 * q4] | (unsigned)hv[4 * q4 + 1] << 16,
+                                                  hv[4 * q4 + 2] | (unsigned)hv[4 * q4 + 3] << 16);
   } else if (part) {
 #pragma unroll
     for (int k = 0; k < C; ++k)
-      if (c0 + k < out.w) store_px(out, plane, c0 + k, y, o[k]);
+      if (c0 + k < out.w) p[k] = hv[k];
   }
 }
 
-template <int D, int C, int ODT, bool F32>
-__global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRowsParams kp) {
+template <int D, int C, int RND, int ODT, int WP>
+__global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -320,28 +366,27 @@ __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRow
     fence_mbar_init();
   }
   __syncwarp();
-  RunState<D, C, ODT, F32> S;
+  RunState<D, C, RND, ODT, WP> S;
 #pragma unroll
   for (int s = 0; s < D; ++s) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) S.w[s][k] = kp.a.w[s][k];
     S.st[s] = kp.a.storage[s];
   }
-  S.W = kp.a.in.w;
-  S.H = kp.a.in.h;
-  const int H = S.H, OW = kp.a.out.w;
+  const int W = kp.a.in.w, H = kp.a.in.h, OW = kp.a.out.w;
+  S.H = H;
   unsigned qbase = 0;  // boxes this warp has issued before the current unit
   for (int u = gw; u < kp.units; u += stride) {
     const Unit U = unit_geom(kp, g, u, D);
     if (lane == 0)
       for (int j = 0; j < kRing && j < U.nbox; ++j) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j, U, j);
-    S.x0 = U.x0;
+    const int c0 = U.x0 + C * lane;
     S.y0 = U.y0;
-    S.c0 = U.x0 + C * lane;
-    S.hl = U.x0 < 0;
-    S.hr = U.x0 + 32 * C > S.W;
     S.top = U.y0 == 0;
-    S.ef = edge_fix_of(S.c0, U.x0, S.W, C);
+    S.hl = U.x0 < 0;
+    S.hr = U.x0 + 32 * C > W;
+    S.ef = edge_fix_of(c0, U.x0, W, C);
+    const bool he = S.hl || S.hr;
 #pragma unroll
     for (int s = 0; s < D; ++s)
 #pragma unroll
@@ -351,8 +396,8 @@ __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRow
         for (int j = 0; j < 4; ++j) S.acc[s][j][k] = 0.0f;
       }
     const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
-    const bool st_full = mine && S.c0 + C - 1 < OW && ODT != 3;
-    const bool st_part = mine && S.c0 < OW && !st_full;
+    const bool st_full = mine && c0 + C - 1 < OW;
+    const bool st_part = mine && c0 < OW && !st_full;
     char* out_row = (char*)kp.a.out.data + (long long)U.plane * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
     const int n = U.n_steps;
     const int t_store = U.oy - U.y0 + 2 * D;       // first step whose output row is the run's
@@ -387,11 +432,17 @@ __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRow
       }
       float o[C];
       // the top rows of a top run, and the steps from the one that reads the
-      // image's last row on, take the edge path
-      if (t <= edge_lo || t >= t_edge) S.template stages<0, true>(t, v, o);
-      else S.template stages<0, false>(t, v, o);
+      // image's last row on, take the edge path; strips past an image edge
+      // clamp every stage's input row
+      if (t <= edge_lo || t >= t_edge) {
+        if (he) S.template stages<0, true, true>(t, v, o);
+        else S.template stages<0, true, false>(t, v, o);
+      } else {
+        if (he) S.template stages<0, false, true>(t, v, o);
+        else S.template stages<0, false, false>(t, v, o);
+      }
       if (t >= t_store) {  // the chain's output is the run's from here on
-        store_row<C, ODT>(out_row, S.c0, st_full, st_part, kp.a.out, U.plane, U.y0 + t - 2 * D, o);
+        store_row<C, ODT>(out_row, c0, st_full, st_part, kp.a.out, U.plane, U.y0 + t - 2 * D, o);
         out_row += kp.a.out.rs;
       }
     }
@@ -414,29 +465,70 @@ __global__ void __launch_bounds__(256) k_chain_rows(const __grid_constant__ CRow
 
 typedef void (*CRowsKernel)(CRowsParams);
 
+// The class of a stage's taps (kClassBinomial / kClassBox when all ten taps
+// equal that class's values bit for bit, else 0).
+int stage_class(const float (&w)[10]) {
+  for (int cls : {kClassBinomial, kClassBox}) {
+    bool eq = true;
+    for (int k = 0; k < 10; ++k) {
+      const float t = class_tap(cls, k % 5);
+      eq &= memcmp(&w[k], &t, sizeof t) == 0;
+    }
+    if (eq) return cls;
+  }
+  return 0;
+}
+
+// Specialised tap patterns: alternating binomial/box from either class, and
+// all binomial; any other pattern takes the runtime taps.
+template <int D>
+constexpr int pattern_of(int c0, int c1) {
+  int p = 0;
+  for (int s = 0; s < D; ++s) p |= ((s & 1) ? c1 : c0) << (2 * s);
+  return p;
+}
+
+template <int D, int C, int RND, int ODT>
+CRowsKernel pick_wp(const ChainArgs& a, int* variant) {
+  int p = 0;
+  for (int s = 0; s < D; ++s) p |= stage_class(a.w[s]) << (2 * s);
+  constexpr int BX = pattern_of<D>(kClassBinomial, kClassBox), XB = pattern_of<D>(kClassBox, kClassBinomial);
+  constexpr int BB = pattern_of<D>(kClassBinomial, kClassBinomial);
+  if (RND != 3) {
+    if (p == BX) { *variant = 1; return k_chain_rows<D, C, RND, ODT, BX>; }
+    if (p == XB) { *variant = 2; return k_chain_rows<D, C, RND, ODT, XB>; }
+    if (p == BB) { *variant = 3; return k_chain_rows<D, C, RND, ODT, BB>; }
+  }
+  *variant = 0;
+  return k_chain_rows<D, C, RND, ODT, 0>;
+}
+
+// Rounding and store type: one type for every stage and the output, or the
+// general (runtime) form.
 template <int D, int C>
 CRowsKernel pick_dc(const ChainArgs& a, int* variant) {
-  bool f32 = a.in.dtype == HP_F32 && a.out.dtype == HP_F32;
-  for (int s = 0; s < D; ++s) f32 &= a.storage[s] == HP_F32;
-  const int odt = a.out.dtype == HP_F32 ? 0 : a.out.dtype == HP_F16 ? 1 : a.out.dtype == HP_BF16 ? 2 : 3;
-  if (f32) { *variant = 0; return k_chain_rows<D, C, 0, true>; }
-  *variant = 1 + odt;
-  switch (odt) {
-    case 0: return k_chain_rows<D, C, 0, false>;
-    case 1: return k_chain_rows<D, C, 1, false>;
-    case 2: return k_chain_rows<D, C, 2, false>;
-    default: return k_chain_rows<D, C, 3, false>;
-  }
+  const int s0 = a.storage[0];
+  bool uniform = true;
+  for (int s = 1; s < D; ++s) uniform &= a.storage[s] == s0;
+  uniform &= a.out.dtype == s0;
+  int v = 0;
+  CRowsKernel k;
+  if (uniform && s0 == HP_F32) k = pick_wp<D, C, 0, 0>(a, &v), v += 0;
+  else if (uniform && s0 == HP_F16) k = pick_wp<D, C, 1, 1>(a, &v), v += 4;
+  else if (uniform && s0 == HP_BF16) k = pick_wp<D, C, 2, 2>(a, &v), v += 8;
+  else k = pick_wp<D, C, 3, 3>(a, &v), v += 12;
+  *variant = v;
+  return k;
 }
 
 // Instantiations: 4 columns per lane at depth 2 and 4, 8 columns at depth 2
-// (at depth 4 the windows of 8 columns would not fit in registers).
+// (at depth 4 the partial sums of 8 columns would not fit in registers).
 CRowsKernel pick_kernel(const ChainArgs& a, int cols, int* variant) {
   int base = 0;
   CRowsKernel k;
-  if (a.depth == 2 && cols == 8) k = pick_dc<2, 8>(a, variant), base = 10;
+  if (a.depth == 2 && cols == 8) k = pick_dc<2, 8>(a, variant), base = 32;
   else if (a.depth == 2) k = pick_dc<2, 4>(a, variant), base = 0;
-  else k = pick_dc<4, 4>(a, variant), base = 5;
+  else k = pick_dc<4, 4>(a, variant), base = 16;
   *variant += base;
   return k;
 }
@@ -485,7 +577,7 @@ int chain_rows_grid(const ChainArgs& a, int cols, int units, int threads, int sm
 int launch_chain_rows(const ChainArgs& a, int cols, int rows, int grid, int smem_bytes, void* stream) {
   int variant;
   CRowsKernel kern = pick_kernel(a, cols, &variant);
-  static bool configured[15] = {};
+  static bool configured[48] = {};
   if (!configured[variant]) {
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;
