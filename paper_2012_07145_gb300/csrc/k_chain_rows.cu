@@ -222,7 +222,7 @@ struct RunState {
   int y0, H;
   bool top;                  // the run starts at image row 0
   EdgeFix ef;
-  bool hl, hr;               // the strip reaches past the left / right image edge
+  bool hl, hr, he;           // the strip reaches past the left / right / either image edge
 
   template <int S>
   __device__ __forceinline__ float tap(int k) const {
@@ -240,11 +240,11 @@ struct RunState {
   }
 
   // x pass of stage S over its input row v (columns c0-2 .. c0+C+1: two
-  // neighbours on each side from the adjacent lanes) into h[S].  HE: the strip
-  // reaches past an image edge, where the row first takes the edge values.
-  template <int S, bool HE>
+  // neighbours on each side from the adjacent lanes) into h[S].  In a strip
+  // that reaches past an image edge the row first takes the edge values.
+  template <int S>
   __device__ __forceinline__ void xpass(float (&v)[C]) {
-    if (HE) clamp_cols<C>(v, ef, hl, hr);
+    if (he) clamp_cols<C>(v, ef, hl, hr);
     const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
     float e[C + 4];
@@ -254,53 +254,74 @@ struct RunState {
     e[C + 2] = r1; e[C + 3] = r2;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-      float s = __fmul_rn(tap<S>(0), e[k]);
-      s = __fmaf_rn(tap<S>(1), e[k + 1], s);
-      s = __fmaf_rn(tap<S>(2), e[k + 2], s);
-      s = __fmaf_rn(tap<S>(3), e[k + 3], s);
-      h[S][k] = __fmaf_rn(tap<S>(4), e[k + 4], s);
+      float sum = __fmul_rn(tap<S>(0), e[k]);
+      sum = __fmaf_rn(tap<S>(1), e[k + 1], sum);
+      sum = __fmaf_rn(tap<S>(2), e[k + 2], sum);
+      sum = __fmaf_rn(tap<S>(3), e[k + 3], sum);
+      h[S][k] = __fmaf_rn(tap<S>(4), e[k + 4], sum);
     }
   }
 
-  // y pass of stage S with h[S] as its newest row: the partial sums advance
-  // one row and o receives the completed output row (rounded to the stage's
-  // storage type).
-  template <int S>
+  // y pass of stage S with h[S] as its newest row, at phase P (the step
+  // number minus 2S, mod 4): the partial sums advance one row and o receives
+  // the completed output row (rounded to the stage's storage type).  Partial
+  // sum j (output row i - 1 + j after the update) lives in slot (j + P) & 3, so
+  // every update reads and writes one slot: no register moves.
+  template <int S, int P>
   __device__ __forceinline__ void ypass(float (&o)[C]) {
+    constexpr int q0 = (P + 3) & 3, q1 = P & 3, q2 = (P + 1) & 3, q3 = (P + 2) & 3;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
       const float x = h[S][k];
-      const float b = __fmaf_rn(tap<S>(9), x, acc[S][0][k]);
-      acc[S][0][k] = __fmaf_rn(tap<S>(8), x, acc[S][1][k]);
-      acc[S][1][k] = __fmaf_rn(tap<S>(7), x, acc[S][2][k]);
-      acc[S][2][k] = __fmaf_rn(tap<S>(6), x, acc[S][3][k]);
-      acc[S][3][k] = __fmul_rn(tap<S>(5), x);
+      const float b = __fmaf_rn(tap<S>(9), x, acc[S][q0][k]);
+      acc[S][q1][k] = __fmaf_rn(tap<S>(8), x, acc[S][q1][k]);
+      acc[S][q2][k] = __fmaf_rn(tap<S>(7), x, acc[S][q2][k]);
+      acc[S][q3][k] = __fmaf_rn(tap<S>(6), x, acc[S][q3][k]);
+      acc[S][q0][k] = __fmul_rn(tap<S>(5), x);
       o[k] = rnd<S>(b);
     }
   }
 
-  // Stages S.. at step t; v is stage S's input row.  EDGE: the step may need
-  // the top or bottom boundary handling.  Returns the last stage's row in o.
-  template <int S, bool EDGE, bool HE>
+  float o[C];                // the last stage's row of the latest step
+
+  // Step t (t mod 4 = U): the input row (from the box's slot while it lies
+  // inside the image) through all D stages into o.
+  template <int U, bool EDGE>
+  __device__ __forceinline__ void step(int t, const unsigned char* slot, int dtype, int esize, int box_w) {
+    float v[C];
+    if (!EDGE || y0 + t < H) {
+      load_row<C>(slot + U * box_w * esize, dtype, v);
+    } else {
+#pragma unroll
+      for (int k = 0; k < C; ++k) v[k] = 0.0f;
+    }
+    stages<0, U, EDGE>(t, v, o);
+  }
+
+  // Stages S.. at step t, whose number mod 4 is U; v is stage S's input row.
+  // EDGE: the step may need the top or bottom boundary handling.  Returns the
+  // last stage's row in o.
+  template <int S, int U, bool EDGE>
   __device__ __forceinline__ void stages(int t, float (&v)[C], float (&o)[C]) {
+    constexpr int P = ((U - 2 * S) % 4 + 4) % 4;
     if (EDGE) {
       const int i = y0 + t - 2 * S;
       if (i < H) {  // else below the image: h[S] still holds row H - 1, the clamped row
-        xpass<S, HE>(v);
+        xpass<S>(v);
         if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
-          ypass<S>(o);
-          ypass<S>(o);
+          ypass<S, (P + 2) & 3>(o);
+          ypass<S, (P + 3) & 3>(o);
         }
       }
     } else {
-      xpass<S, HE>(v);
+      xpass<S>(v);
     }
     if constexpr (S + 1 < D) {
       float m[C];
-      ypass<S>(m);
-      stages<S + 1, EDGE, HE>(t, m, o);
+      ypass<S, P>(m);
+      stages<S + 1, U, EDGE>(t, m, o);
     } else {
-      ypass<S>(o);
+      ypass<S, P>(o);
     }
   }
 };
@@ -348,6 +369,16 @@ __device__ __forceinline__ void store_row(char* row, int c0, bool full, bool par
   }
 }
 
+// The store of step t's output row, once the chain's output is the run's.
+template <int C, int ODT>
+__device__ __forceinline__ void store_if(int t, int t_store, char*& out_row, int c0, bool full, bool part,
+                                         const ImgView& out, const Unit& U, int D, const float (&o)[C]) {
+  if (t >= t_store) {
+    store_row<C, ODT>(out_row, c0, full, part, out, U.plane, U.y0 + t - 2 * D, o);
+    out_row += out.rs;
+  }
+}
+
 template <int D, int C, int RND, int ODT, int WP>
 __global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParams kp) {
   grid_dep_wait();
@@ -386,7 +417,7 @@ __global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParam
     S.hl = U.x0 < 0;
     S.hr = U.x0 + 32 * C > W;
     S.ef = edge_fix_of(c0, U.x0, W, C);
-    const bool he = S.hl || S.hr;
+    S.he = S.hl || S.hr;
 #pragma unroll
     for (int s = 0; s < D; ++s)
 #pragma unroll
@@ -403,47 +434,55 @@ __global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParam
     const int t_store = U.oy - U.y0 + 2 * D;       // first step whose output row is the run's
     const int t_edge = H - 1 - U.y0;               // from this step on some stage's input row is H - 1 or below
     const int edge_lo = S.top ? 2 * (D - 1) : -1;  // steps 0 .. edge_lo: some stage's input row is row 0
-    const unsigned char* slot = slots;
     int failed = 0;
+    // One box (4 input rows) per iteration, its four steps unrolled so that
+    // each stage's partial sums keep fixed registers.  Boxes whose steps are
+    // all away from the image's top and bottom rows take the plain steps.
 #pragma unroll 1
-    for (int t = 0; t < n; ++t) {
-      float v[C];
-      if (U.y0 + t < H) {
-        const int j = t >> 2, rr = t & 3;
-        if (rr == 0) {
-          const unsigned q = qbase + j;
-          int ok = 1;
-          if (lane == 0) ok = mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
-          ok = __shfl_sync(kFull, ok, 0);
-          if (!ok) {
-            failed = 1;
-            break;
-          }
-          slot = slots + (q % kRing) * g.slot_bytes + lane * C * esize;
+    for (int j = 0; 4 * j < n; ++j) {
+      const int t0 = 4 * j;
+      const unsigned char* slot = nullptr;
+      if (t0 < U.n_in) {
+        const unsigned q = qbase + j;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
+        ok = __shfl_sync(kFull, ok, 0);
+        if (!ok) {
+          failed = 1;
+          break;
         }
-        load_row<C>(slot + rr * g.box_w * esize, kp.a.in.dtype, v);
-        if (rr == kBoxRows - 1 && j + kRing < U.nbox) {
-          __syncwarp();
-          if (lane == 0) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j + kRing, U, j + kRing);
+        slot = slots + (q % kRing) * g.slot_bytes + lane * C * esize;
+      }
+      if (t0 > edge_lo && t0 + 3 < t_edge && t0 + 3 < n) {
+        S.template step<0, false>(t0, slot, kp.a.in.dtype, esize, g.box_w);
+        store_if<C, ODT>(t0, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        S.template step<1, false>(t0 + 1, slot, kp.a.in.dtype, esize, g.box_w);
+        store_if<C, ODT>(t0 + 1, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        S.template step<2, false>(t0 + 2, slot, kp.a.in.dtype, esize, g.box_w);
+        store_if<C, ODT>(t0 + 2, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        S.template step<3, false>(t0 + 3, slot, kp.a.in.dtype, esize, g.box_w);
+        store_if<C, ODT>(t0 + 3, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+      } else {
+        if (t0 < n) {
+          S.template step<0, true>(t0, slot, kp.a.in.dtype, esize, g.box_w);
+          store_if<C, ODT>(t0, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
         }
-      } else {
-#pragma unroll
-        for (int k = 0; k < C; ++k) v[k] = 0.0f;
+        if (t0 + 1 < n) {
+          S.template step<1, true>(t0 + 1, slot, kp.a.in.dtype, esize, g.box_w);
+          store_if<C, ODT>(t0 + 1, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        }
+        if (t0 + 2 < n) {
+          S.template step<2, true>(t0 + 2, slot, kp.a.in.dtype, esize, g.box_w);
+          store_if<C, ODT>(t0 + 2, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        }
+        if (t0 + 3 < n) {
+          S.template step<3, true>(t0 + 3, slot, kp.a.in.dtype, esize, g.box_w);
+          store_if<C, ODT>(t0 + 3, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        }
       }
-      float o[C];
-      // the top rows of a top run, and the steps from the one that reads the
-      // image's last row on, take the edge path; strips past an image edge
-      // clamp every stage's input row
-      if (t <= edge_lo || t >= t_edge) {
-        if (he) S.template stages<0, true, true>(t, v, o);
-        else S.template stages<0, true, false>(t, v, o);
-      } else {
-        if (he) S.template stages<0, false, true>(t, v, o);
-        else S.template stages<0, false, false>(t, v, o);
-      }
-      if (t >= t_store) {  // the chain's output is the run's from here on
-        store_row<C, ODT>(out_row, c0, st_full, st_part, kp.a.out, U.plane, U.y0 + t - 2 * D, o);
-        out_row += kp.a.out.rs;
+      if (j + kRing < U.nbox) {  // this box's slot is read: refill it
+        __syncwarp();
+        if (lane == 0) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j + kRing, U, j + kRing);
       }
     }
     if (failed) {
