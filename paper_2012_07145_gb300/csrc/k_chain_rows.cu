@@ -215,6 +215,7 @@ __host__ __device__ constexpr float class_tap(int cls, int k) {
 // stage at run time.  ODT: output stores 0 f32, 1 f16, 2 bf16, 3 any type.
 template <int D, int C, int RND, int ODT, int WP>
 struct RunState {
+  static constexpr int kD = D, kC = C, kODT = ODT;
   float w[D][10];            // per stage: x taps, then y taps (runtime class)
   int st[D];                 // per stage: storage type (RND = 3)
   float acc[D][4][C];        // per stage: partial sums of its output rows i - 1 .. i + 2
@@ -242,9 +243,9 @@ struct RunState {
   // x pass of stage S over its input row v (columns c0-2 .. c0+C+1: two
   // neighbours on each side from the adjacent lanes) into h[S].  In a strip
   // that reaches past an image edge the row first takes the edge values.
-  template <int S>
+  template <int S, bool HE>
   __device__ __forceinline__ void xpass(float (&v)[C]) {
-    if (he) clamp_cols<C>(v, ef, hl, hr);
+    if (HE) clamp_cols<C>(v, ef, hl, hr);
     const float l2 = __shfl_up_sync(kFull, v[C - 2], 1), l1 = __shfl_up_sync(kFull, v[C - 1], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
     float e[C + 4];
@@ -286,7 +287,7 @@ struct RunState {
 
   // Step t (t mod 4 = U): the input row (from the box's slot while it lies
   // inside the image) through all D stages into o.
-  template <int U, bool EDGE>
+  template <int U, bool EDGE, bool HE>
   __device__ __forceinline__ void step(int t, const unsigned char* slot, int dtype, int esize, int box_w) {
     float v[C];
     if (!EDGE || y0 + t < H) {
@@ -295,31 +296,31 @@ struct RunState {
 #pragma unroll
       for (int k = 0; k < C; ++k) v[k] = 0.0f;
     }
-    stages<0, U, EDGE>(t, v, o);
+    stages<0, U, EDGE, HE>(t, v, o);
   }
 
   // Stages S.. at step t, whose number mod 4 is U; v is stage S's input row.
   // EDGE: the step may need the top or bottom boundary handling.  Returns the
   // last stage's row in o.
-  template <int S, int U, bool EDGE>
+  template <int S, int U, bool EDGE, bool HE>
   __device__ __forceinline__ void stages(int t, float (&v)[C], float (&o)[C]) {
     constexpr int P = ((U - 2 * S) % 4 + 4) % 4;
     if (EDGE) {
       const int i = y0 + t - 2 * S;
       if (i < H) {  // else below the image: h[S] still holds row H - 1, the clamped row
-        xpass<S>(v);
+        xpass<S, HE>(v);
         if (top && i == 0) {  // rows -2 and -1 of this stage's producer are its row 0
           ypass<S, (P + 2) & 3>(o);
           ypass<S, (P + 3) & 3>(o);
         }
       }
     } else {
-      xpass<S>(v);
+      xpass<S, HE>(v);
     }
     if constexpr (S + 1 < D) {
       float m[C];
       ypass<S, P>(m);
-      stages<S + 1, U, EDGE>(t, m, o);
+      stages<S + 1, U, EDGE, HE>(t, m, o);
     } else {
       ypass<S, P>(o);
     }
@@ -370,13 +371,36 @@ __device__ __forceinline__ void store_row(char* row, int c0, bool full, bool par
 }
 
 // The store of step t's output row, once the chain's output is the run's.
-template <int C, int ODT>
+// Lanes with only some columns inside the image exist in strips past the
+// right image edge (HE) alone.
+template <int C, int ODT, bool HE>
 __device__ __forceinline__ void store_if(int t, int t_store, char*& out_row, int c0, bool full, bool part,
                                          const ImgView& out, const Unit& U, int D, const float (&o)[C]) {
   if (t >= t_store) {
-    store_row<C, ODT>(out_row, c0, full, part, out, U.plane, U.y0 + t - 2 * D, o);
+    store_row<C, ODT>(out_row, c0, full, HE && part, out, U.plane, U.y0 + t - 2 * D, o);
     out_row += out.rs;
   }
+}
+
+// The four steps of one box (steps t0 .. t0 + 3, those below n).  EDGE: some
+// step needs the top or bottom boundary handling; HE: the strip reaches past
+// an image edge.
+template <bool EDGE, bool HE, class RS>
+__device__ __forceinline__ void box_steps(RS& S, int t0, int n, const unsigned char* slot, const CRowsParams& kp,
+                                          int esize, int box_w, int t_store, char*& out_row, int c0, bool full,
+                                          bool part, const Unit& U) {
+  constexpr int C = RS::kC, ODT = RS::kODT, D = RS::kD;
+  S.template step<0, EDGE, HE>(t0, slot, kp.a.in.dtype, esize, box_w);
+  store_if<C, ODT, HE>(t0, t_store, out_row, c0, full, part, kp.a.out, U, D, S.o);
+  if (EDGE && t0 + 1 >= n) return;
+  S.template step<1, EDGE, HE>(t0 + 1, slot, kp.a.in.dtype, esize, box_w);
+  store_if<C, ODT, HE>(t0 + 1, t_store, out_row, c0, full, part, kp.a.out, U, D, S.o);
+  if (EDGE && t0 + 2 >= n) return;
+  S.template step<2, EDGE, HE>(t0 + 2, slot, kp.a.in.dtype, esize, box_w);
+  store_if<C, ODT, HE>(t0 + 2, t_store, out_row, c0, full, part, kp.a.out, U, D, S.o);
+  if (EDGE && t0 + 3 >= n) return;
+  S.template step<3, EDGE, HE>(t0 + 3, slot, kp.a.in.dtype, esize, box_w);
+  store_if<C, ODT, HE>(t0 + 3, t_store, out_row, c0, full, part, kp.a.out, U, D, S.o);
 }
 
 template <int D, int C, int RND, int ODT, int WP>
@@ -454,31 +478,11 @@ __global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParam
         slot = slots + (q % kRing) * g.slot_bytes + lane * C * esize;
       }
       if (t0 > edge_lo && t0 + 3 < t_edge && t0 + 3 < n) {
-        S.template step<0, false>(t0, slot, kp.a.in.dtype, esize, g.box_w);
-        store_if<C, ODT>(t0, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        S.template step<1, false>(t0 + 1, slot, kp.a.in.dtype, esize, g.box_w);
-        store_if<C, ODT>(t0 + 1, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        S.template step<2, false>(t0 + 2, slot, kp.a.in.dtype, esize, g.box_w);
-        store_if<C, ODT>(t0 + 2, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        S.template step<3, false>(t0 + 3, slot, kp.a.in.dtype, esize, g.box_w);
-        store_if<C, ODT>(t0 + 3, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
+        if (S.he) box_steps<false, true>(S, t0, n, slot, kp, esize, g.box_w, t_store, out_row, c0, st_full, st_part, U);
+        else box_steps<false, false>(S, t0, n, slot, kp, esize, g.box_w, t_store, out_row, c0, st_full, st_part, U);
       } else {
-        if (t0 < n) {
-          S.template step<0, true>(t0, slot, kp.a.in.dtype, esize, g.box_w);
-          store_if<C, ODT>(t0, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        }
-        if (t0 + 1 < n) {
-          S.template step<1, true>(t0 + 1, slot, kp.a.in.dtype, esize, g.box_w);
-          store_if<C, ODT>(t0 + 1, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        }
-        if (t0 + 2 < n) {
-          S.template step<2, true>(t0 + 2, slot, kp.a.in.dtype, esize, g.box_w);
-          store_if<C, ODT>(t0 + 2, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        }
-        if (t0 + 3 < n) {
-          S.template step<3, true>(t0 + 3, slot, kp.a.in.dtype, esize, g.box_w);
-          store_if<C, ODT>(t0 + 3, t_store, out_row, c0, st_full, st_part, kp.a.out, U, D, S.o);
-        }
+        if (S.he) box_steps<true, true>(S, t0, n, slot, kp, esize, g.box_w, t_store, out_row, c0, st_full, st_part, U);
+        else box_steps<true, false>(S, t0, n, slot, kp, esize, g.box_w, t_store, out_row, c0, st_full, st_part, U);
       }
       if (j + kRing < U.nbox) {  // this box's slot is read: refill it
         __syncwarp();
