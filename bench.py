@@ -57,6 +57,25 @@ def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
         ref = [ost.stencil_chain_point(img, ost.chain_kinds(n, pattern), x, y) for x, y in pts]
         return max(abs(float(out[0][y, x]) - r) for (x, y), r in zip(pts, ref))
 
+    def lowp_error(out, inputs):
+        """The 16-bit storage error against the FP64 oracle on the top band of
+        the image (rows whose whole dependency cone lies in the band): the
+        oracle fed the rounded input, and the original input."""
+        import torch
+        from oracle import stencil as ost
+        band, keep = 4 * n + 64, 64
+        img = inputs[0][0][0][:band].astype(np.float64)
+        rounded = torch.from_numpy(inputs[0][0][0][:band].astype(np.float32)).to(
+            torch.float16 if storage_name == "f16" else torch.bfloat16).double().numpy()
+        kinds = ost.chain_kinds(n, pattern)
+        got = out[0][:keep].astype(np.float64)
+        errs = []
+        for src in (rounded, img):
+            ref = ost.stencil_chain(src, kinds)[:keep]
+            errs.append(float(np.abs(got - ref).max() / (ref.max() - ref.min())))
+        return {"rounded_input": errs[0], "original_input": errs[1],
+                "measure": f"max |gpu - oracle| / range over rows 0..{keep - 1} (oracle on rows 0..{band - 1})"}
+
     # the method's work per output pixel (a separable 5x5 stage, per pass):
     # binomial ((a+e) + 4(b+d)) + 6c, then x 1/16: 7 flops (an fma counts 2);
     # box (((a+b) + (c+d)) + e) x 1/5: 5 flops
@@ -69,7 +88,8 @@ def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
                 build=lambda: pipelines.stencil_chain(n, pattern, storage=st), fused=fused,
                 flops_px=flops_px, algorithmic=algorithmic, fp32_instr_px=10 * n,
                 bytes_px=2 * esize, bound="alu", kernel="k_chain", dtype=storage_name,
-                oracle_sample=oracle_sample, parity=parity, sample_rows=64)
+                oracle_sample=oracle_sample, parity=parity, sample_rows=64,
+                lowp_error=lowp_error if storage_name != "f32" else None)
 
 
 def config_table():
@@ -115,6 +135,19 @@ def config_table():
         ref = ohr.harris(rgb)[:62, :62]
         return float(np.abs(out[0][:62, :62] - ref).max() / (ref.max() - ref.min()))
 
+    def harris_bf16_error(out, inputs):
+        import torch
+        from oracle import harris as ohr
+        band = inputs[0][0][:, :96, :]
+        rounded = torch.from_numpy(band).to(torch.bfloat16).double().numpy()
+        got = out[0][:92].astype(np.float64)
+        errs = []
+        for src in (rounded, band.astype(np.float64)):
+            ref = ohr.harris(src)[:92]
+            errs.append(float(np.abs(got - ref).max() / (ref.max() - ref.min())))
+        return {"rounded_input": errs[0], "original_input": errs[1],
+                "measure": "max |gpu - oracle| / range over rows 0..91 (oracle on rows 0..95)"}
+
     cfgs["harris_bf16"] = dict(workload=f"harris_rgb_{W}x{H}_bf16", h=H, w=W,
                                inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_BF16)],
                                out=(1, H, W, hp.HP_BF16),
@@ -122,7 +155,8 @@ def config_table():
                                fused=app_schedule("harris_bf16", W, H, dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
                                                                            tile_w=112, tile_h=14, threads=128))[0],
                                flops_px=68, bytes_px=8, bound="hbm", kernel="k_harris_rows", dtype="bf16",
-                               oracle_sample=harris_sample, parity=harris_bf16_parity, sample_rows=128)
+                               oracle_sample=harris_sample, parity=harris_bf16_parity, sample_rows=128,
+                               lowp_error=harris_bf16_error)
     UH, UW = 3072, 4096
 
     def unsharp_sample(rows):
@@ -527,7 +561,9 @@ def measure_config(cfg_name, cfg, steps, warmup, flush, stream, peaks, peak_kind
     clocks = sampler.stop()
     torch.cuda.synchronize()
     assert p.device_error() == 0, "a kernel reported a device-side error"
-    err = cfg["parity"](_to_numpy(yout, odt), inputs)
+    out_np = _to_numpy(yout, odt)
+    err = cfg["parity"](out_np, inputs)
+    lowp = cfg["lowp_error"](out_np, inputs) if cfg.get("lowp_error") else None
 
     npx = OH * OW
     fp32_peak = fp32["peak_tflops"]
@@ -586,7 +622,7 @@ def measure_config(cfg_name, cfg, steps, warmup, flush, stream, peaks, peak_kind
     if roof["bound"] == "hbm":   # also against the nominal HBM3e bandwidth, for context
         roof["frac_of_nominal_7900_gbs"] = round(roof["achieved"] / 7900.0, 4)
     res = dict(npx=npx, ms=ms, ms_all=ms_all, launches=launches, plain_ms=plain_ms, plain_launches=plain_launches,
-               plain_steps=plain_steps, roof=roof, clocks=clocks, err=err, p=p, inputs=inputs)
+               plain_steps=plain_steps, roof=roof, clocks=clocks, err=err, p=p, inputs=inputs, lowp=lowp)
     return res
 
 
@@ -598,7 +634,8 @@ def compact_entry(cfg_name, cfg, r):
             "launches_per_step": r["launches"] / max(1, len(r["ms_all"])),
             "clocks": {k: r["clocks"].get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "parity": r["err"], "parity_kind": cfg.get("parity_kind", "max |gpu - oracle| at sampled points"),
-            "schedule": schedule_of(cfg_name, cfg)}
+            "schedule": schedule_of(cfg_name, cfg),
+            **({"error_vs_fp64": r["lowp"]} if r.get("lowp") else {})}
 
 
 def run_ours(args, cfg_name):

@@ -105,30 +105,39 @@ def histeq() -> hp.Pipeline:
 
 
 def local_laplacian(levels: int = 8, k_levels: int = 8, sigma_r: float = 0.1, alpha: float = 1.0,
-                    beta: float = 1.0, out_storage: int = hp.HP_U16):
+                    beta: float = 1.0, out_storage: int = hp.HP_U16, fine_storage: int = hp.HP_F32,
+                    fine_levels: int = 0):
     """Local Laplacian filter (Paris et al.; K discrete intensity levels) of a
     u16 RGB image.  The output is u16 (rounded from out * 65535), or with
     out_storage = HP_F32 the float result in [0, 1] units before quantisation.
+    fine_storage / fine_levels: the stages of pyramid levels l < fine_levels
+    (remapped and gray pyramid level, upsample, Laplacian, interpolated level,
+    collapse step) are stored in fine_storage (HP_F16 / HP_BF16; the
+    arithmetic stays f32); the coarser levels and the gray image stay f32.
     Returns (pipeline, stage-id map)."""
     J, K = levels, k_levels
     p = hp.Pipeline([hp.HP_U16], [3])
     ids = {}
     F = hp.HP_F32
+
+    def st(l):
+        return fine_storage if l < fine_levels else F
+
     gray = p.add_stage(hp.HP_POINTWISE, [p.input(0)], 1, F, op=hp.HP_OP_GRAY, params=[1.0 / 65535.0])
-    G = [p.add_stage(hp.HP_POINTWISE, [gray], K + 1, F, op=hp.HP_OP_LL_REMAP, params=[sigma_r, alpha, beta, K])]
-    for _ in range(1, J):
-        G.append(p.add_stage(hp.HP_DOWNSAMPLE2, [G[-1]], K + 1, F))
+    G = [p.add_stage(hp.HP_POINTWISE, [gray], K + 1, st(0), op=hp.HP_OP_LL_REMAP, params=[sigma_r, alpha, beta, K])]
+    for l in range(1, J):
+        G.append(p.add_stage(hp.HP_DOWNSAMPLE2, [G[-1]], K + 1, st(l)))
     U, L, Lout = [], [], []
     for l in range(J - 1):
-        U.append(p.add_stage(hp.HP_UPSAMPLE2, [G[l + 1], G[l]], K + 1, F))
-        L.append(p.add_stage(hp.HP_POINTWISE, [G[l], U[l]], K + 1, F, op=hp.HP_OP_SUB))
-        Lout.append(p.add_stage(hp.HP_POINTWISE, [G[l], L[l]], 1, F, op=hp.HP_OP_LL_INTERP, params=[K]))
+        U.append(p.add_stage(hp.HP_UPSAMPLE2, [G[l + 1], G[l]], K + 1, st(l)))
+        L.append(p.add_stage(hp.HP_POINTWISE, [G[l], U[l]], K + 1, st(l), op=hp.HP_OP_SUB))
+        Lout.append(p.add_stage(hp.HP_POINTWISE, [G[l], L[l]], 1, st(l), op=hp.HP_OP_LL_INTERP, params=[K]))
     R = [None] * J
     UR = [None] * (J - 1)
-    R[J - 1] = p.add_stage(hp.HP_POINTWISE, [G[J - 1]], 1, F, op=hp.HP_OP_SELECT, params=[K])
+    R[J - 1] = p.add_stage(hp.HP_POINTWISE, [G[J - 1]], 1, st(J - 1), op=hp.HP_OP_SELECT, params=[K])
     for l in range(J - 2, -1, -1):
-        UR[l] = p.add_stage(hp.HP_UPSAMPLE2, [R[l + 1], Lout[l]], 1, F)
-        R[l] = p.add_stage(hp.HP_POINTWISE, [Lout[l], UR[l]], 1, F, op=hp.HP_OP_ADD)
+        UR[l] = p.add_stage(hp.HP_UPSAMPLE2, [R[l + 1], Lout[l]], 1, st(l))
+        R[l] = p.add_stage(hp.HP_POINTWISE, [Lout[l], UR[l]], 1, st(l), op=hp.HP_OP_ADD)
     out_scale = 65535.0 if out_storage == hp.HP_U16 else 1.0
     out = p.add_stage(hp.HP_POINTWISE, [p.input(0), gray, R[0]], 3, out_storage, op=hp.HP_OP_LL_COLOUR,
                       params=[1.0 / 65535.0, out_scale])
