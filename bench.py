@@ -40,10 +40,10 @@ def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
     from paper_2012_07145_gb300 import hp, pipelines, synth
     st = {"f32": hp.HP_F32, "f16": hp.HP_F16, "bf16": hp.HP_BF16}[storage_name]
     esize = 4 if storage_name == "f32" else 2
-    tuned_name = name if storage_name == "f32" else None
+    tkey = (f"stencil_chain_{n}_{pattern}", W, H, storage_name)
 
     def fused(p):
-        pipelines.chain_schedule(p, **(tuned(tuned_name) if tuned_name else tuned("chain32")))
+        apply_tuned(p, None, tkey, lambda q: pipelines.chain_schedule(q, depth=8, tile_w=64, tile_h=32))
 
     def oracle_sample(rows):
         from oracle import stencil as ost
@@ -86,7 +86,7 @@ def _chain_cfg(name, n, pattern, H, W, storage_name="f32"):
     return dict(workload=f"stencil_chain_{n}_{pattern}_{W}x{H}_{storage_name}", h=H, w=W,
                 inputs=lambda seed: [(synth.stencil_input(H, W, seed=seed), st)], out=(1, H, W, st),
                 build=lambda: pipelines.stencil_chain(n, pattern, storage=st), fused=fused,
-                flops_px=flops_px, algorithmic=algorithmic, fp32_instr_px=10 * n,
+                tuned_key=tkey, flops_px=flops_px, algorithmic=algorithmic, fp32_instr_px=10 * n,
                 bytes_px=2 * esize, bound="alu", kernel="k_chain", dtype=storage_name,
                 oracle_sample=oracle_sample, parity=parity, sample_rows=64,
                 lowp_error=lowp_error if storage_name != "f32" else None)
@@ -105,7 +105,9 @@ def config_table():
     wave = _chain_cfg("chain32", 32, "alternate", 1536, 2560)
     wave["workload"] += "_streaming"
     wave["kernel"] = "k_chain_rows"
-    wave["fused"] = lambda p: pipelines.chain_schedule(p, depth=4, tile_w=112, tile_h=0, impl=hp.HP_IMPL_WAVE)
+    wave["fused"] = lambda p: pipelines.chain_schedule(p, depth=2, tile_w=120, tile_h=0, threads=256,
+                                                       impl=hp.HP_IMPL_WAVE)
+    wave["tuned_key"] = None
     cfgs["chain32_wave"] = wave
     H, W = 1536, 2560
 
@@ -123,8 +125,9 @@ def config_table():
     cfgs["harris"] = dict(workload=f"harris_rgb_{W}x{H}_f32", h=H, w=W,
                           inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_F32)], out=(1, H, W, hp.HP_F32),
                           build=lambda: pipelines.harris(),
-                          fused=app_schedule("harris", W, H, dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=120,
-                                                                  tile_h=14, threads=256))[0],
+                          fused=app_schedule("harris", W, H, "f32", dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
+                                                                         tile_w=120, tile_h=14, threads=256)),
+                          tuned_key=("harris", W, H, "f32"),
                           flops_px=68, bytes_px=16, bound="hbm", kernel="k_harris_rows", dtype="f32",
                           oracle_sample=harris_sample, parity=harris_parity, sample_rows=128)
     def harris_bf16_parity(out, inputs):
@@ -152,8 +155,9 @@ def config_table():
                                inputs=lambda seed: [(synth.rgb_f32(H, W, seed=seed), hp.HP_BF16)],
                                out=(1, H, W, hp.HP_BF16),
                                build=lambda: pipelines.harris(io_storage=hp.HP_BF16, inner_storage=hp.HP_BF16),
-                               fused=app_schedule("harris_bf16", W, H, dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
-                                                                           tile_w=112, tile_h=14, threads=128))[0],
+                               fused=app_schedule("harris", W, H, "bf16", dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
+                                                                               tile_w=112, tile_h=14, threads=128)),
+                               tuned_key=("harris", W, H, "bf16"),
                                flops_px=68, bytes_px=8, bound="hbm", kernel="k_harris_rows", dtype="bf16",
                                oracle_sample=harris_sample, parity=harris_bf16_parity, sample_rows=128,
                                lowp_error=harris_bf16_error)
@@ -173,8 +177,9 @@ def config_table():
     cfgs["unsharp"] = dict(workload=f"unsharp_rgb_{UW}x{UH}_f32", h=UH, w=UW,
                            inputs=lambda seed: [(synth.rgb_f32(UH, UW, seed=seed), hp.HP_F32)],
                            out=(3, UH, UW, hp.HP_F32), build=lambda: pipelines.unsharp(),
-                           fused=app_schedule("unsharp", UW, UH, dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
-                                                                      tile_w=120, tile_h=16, threads=128))[0],
+                           fused=app_schedule("unsharp", UW, UH, "f32", dict(schedule="fused", impl=hp.HP_IMPL_WAVE,
+                                                                             tile_w=120, tile_h=16, threads=128)),
+                           tuned_key=("unsharp", UW, UH, "f32"),
                            flops_px=63, bytes_px=24, bound="hbm", kernel="k_stencil_rows", dtype="f32",
                            oracle_sample=unsharp_sample, parity=unsharp_parity, sample_rows=96)
 
@@ -191,7 +196,8 @@ def config_table():
     cfgs["histeq"] = dict(workload=f"histeq_u8_{UW}x{UH}", h=UH, w=UW,
                           inputs=lambda seed: [(synth.gray_u8_lowcontrast(UH, UW, seed=seed), hp.HP_U8)],
                           out=(1, UH, UW, hp.HP_U8), build=lambda: pipelines.histeq(),
-                          fused=app_schedule("histeq", UW, UH, dict(schedule="fused"))[0],
+                          fused=app_schedule("histeq", UW, UH, "u8", dict(schedule="fused")),
+                          tuned_key=("histeq", UW, UH, "u8"),
                           flops_px=0, bytes_px=2, bound="hbm", kernel="k_histeq", dtype="u8",
                           oracle_sample=histeq_sample, parity=histeq_parity, sample_rows=256)
 
@@ -199,8 +205,9 @@ def config_table():
         return pipelines.local_laplacian(levels=8, k_levels=8)[0]
 
     def ll_fused(p):
-        pl, ids = pipelines.local_laplacian(levels=8, k_levels=8)
-        pipelines.local_laplacian_fused_schedule(p, ids)
+        pl, ids = pipelines.local_laplacian(levels=8, k_levels=8)      # the stage ids of p's identical build
+        apply_tuned(p, ids, ("local_laplacian_J8_K8", W, H, "u16"),
+                    lambda q: pipelines.local_laplacian_fused_schedule(q, ids))
 
     def ll_sample(rows):
         from oracle import local_laplacian as oll
@@ -223,6 +230,7 @@ def config_table():
     cfgs["ll"] = dict(workload=f"local_laplacian_rgb_u16_{W}x{H}_J8_K8", h=H, w=W,
                       inputs=lambda seed: [(synth.rgb_u16_gradient_noise(H, W, seed=seed), hp.HP_U16)],
                       out=(3, H, W, hp.HP_U16), build=ll_build, fused=ll_fused,
+                      tuned_key=("local_laplacian_J8_K8", W, H, "u16"),
                       flops_px=0, bytes_px=12, bound="alu", kernel="k_ll_remap_rows", dtype="u16",
                       dominant=ll_dominant, oracle_sample=ll_sample, parity=ll_parity, sample_rows=128)
     def maxfilter_sample(rows):
@@ -314,35 +322,32 @@ def config_table():
     return cfgs
 
 
-def tuned(name, default=None):
-    """Schedule parameters chosen by the autotuner (schedules.json), else the default."""
-    path = os.path.join(ROOT, "paper_2012_07145_gb300", "schedules.json")
-    if name and os.path.exists(path):
-        db = json.load(open(path))
-        if name in db:
-            return db[name]["params"]
-    return default if default is not None else dict(depth=8, tile_w=64, tile_h=32, threads=256, serial_y=8)
-
-
-def app_schedule(app, w, h, default):
-    """A function applying the tuned schedule of an application at w x h
-    (schedules.json, written by tuner.py), else the given default entry."""
+def apply_tuned(p, ids, tkey, default):
+    """Applies the autotuner's stored schedule of a workload (schedules.json,
+    keyed by pipeline, size and storage type), else the default schedule."""
     from paper_2012_07145_gb300 import tuner
-    entry = tuned(f"{app}_{w}x{h}", default)
-    return (lambda p: tuner.apply_schedule(p, entry)), entry
+    entry = tuner.lookup(*tkey)
+    if entry is None:
+        default(p)
+    else:
+        tuner.apply_entry(p, ids, tkey[0], entry)
+
+
+def app_schedule(app, w, h, dtype, default):
+    """A function applying the tuned schedule of an application at w x h and
+    this storage type, else the given default schedule."""
+    from paper_2012_07145_gb300 import tuner
+    return lambda p: apply_tuned(p, None, (app, w, h, dtype), lambda q: tuner.apply_schedule(q, default))
 
 
 def schedule_of(cfg_name, cfg):
     """The schedule a bench line ran, for its config record."""
-    if cfg_name in ("chain32", "chain32_f16", "chain32_bf16"):
-        return dict(tuned("chain32"), source="schedules.json chain32 (tuner.py)")
-    app = cfg["workload"].split("_")[0]
-    if cfg["workload"].endswith("_bf16") and app == "harris":
-        app = "harris_bf16"
-    key = f"{app}_{cfg['w']}x{cfg['h']}"
-    if app in ("harris", "harris_bf16", "unsharp", "histeq"):
-        return dict(tuned(key, {}), source=f"schedules.json {key} (tuner.py)")
-    return "fused (see pipelines.py)"
+    from paper_2012_07145_gb300 import tuner
+    tkey = cfg.get("tuned_key")
+    entry = tuner.lookup(*tkey) if tkey else None
+    if entry is None:
+        return "default (see pipelines.py)"
+    return dict(entry["params"], source=f"schedules.json {tuner.key(*tkey)} (tuner.py)")
 
 
 # ------------------------------------------------------------------ helpers --
@@ -861,7 +866,7 @@ def serving_setup():
     for name, build, ic, idt, oc, tdt in kinds:
         for (h, w) in SERVING_SIZES:
             p = build()
-            app_schedule(name, w, h, defaults[name])[0](p)
+            app_schedule(name, w, h, "u8" if name == "histeq" else "f32", defaults[name])(p)
             arr = synth.rgb_f32(h, w, seed=7) if idt == hp.HP_F32 else synth.gray_u8_lowcontrast(h, w, seed=7)
             hin = torch.from_numpy(arr).pin_memory()
             outs = [torch.empty((oc, h, w), dtype=tdt).pin_memory() for _ in range(ring)]

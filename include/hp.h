@@ -295,9 +295,20 @@ hp_status hp_infer_bounds(hp_pipeline* p, const int* in_widths, const int* in_he
  *   programmatic dependent launch, so that a kernel's blocks may be scheduled
  *   while its predecessor's last blocks drain.  Every kernel waits for its
  *   predecessor to complete before it touches memory, so results are the same
- *   either way. */
-enum { HP_OPT_CUDA_GRAPH = 1, HP_OPT_OVERLAP = 2 };
+ *   either way.
+ * HP_OPT_PROBE_ATTRS (0/1, default 0): while on, every realize that launches
+ *   kernels (not a graph replay) records the register count and local-memory
+ *   (spill) bytes per thread of each kernel it launches; hp_kernel_attrs_get
+ *   returns them.  For the benchmark-driven search, which prunes schedules
+ *   whose kernels spill (Sec. 4.6 prunes on hardware limits). */
+enum { HP_OPT_CUDA_GRAPH = 1, HP_OPT_OVERLAP = 2, HP_OPT_PROBE_ATTRS = 3 };
 hp_status hp_set_option(hp_pipeline* p, int option, long long value);
+
+/* Kernels launched by the last realize that ran with HP_OPT_PROBE_ATTRS on,
+ * the largest register count per thread among them, and the largest
+ * local-memory size per thread (non-zero: the kernel spills or keeps a stack
+ * array).  HP_ERR_INVALID_ARG for null arguments. */
+hp_status hp_kernel_attrs_get(hp_pipeline* p, int* n_kernels, int* max_registers, long long* max_local_bytes);
 
 /* ---- Serving loop ---------------------------------------------------------
  * Continuous batching of pipeline requests on one GPU.  Requests (a pipeline,

@@ -335,8 +335,20 @@ extern unsigned long long g_launches;
 // memory access, so the order of reads and writes is that of plain launches.
 extern thread_local int t_overlap;
 
+// Register and local-memory (spill) figures of the kernels a realize
+// launches, gathered when the pipeline's HP_OPT_PROBE_ATTRS is on (for the
+// tuner's pruning): t_probe points at the realizing pipeline's record.
+struct KernelProbe {
+  int kernels;
+  int max_regs;
+  long long max_local;
+};
+extern thread_local KernelProbe* t_probe;
+void probe_kernel(const void* func);
+
 template <typename... KArgs, typename... Args>
 inline int launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, void* stream, Args... args) {
+  if (t_probe) probe_kernel((const void*)kern);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;

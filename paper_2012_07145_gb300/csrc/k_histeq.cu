@@ -271,6 +271,7 @@ int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (t_probe) probe_kernel((const void*)k_histeq);
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_histeq, p);
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)e;

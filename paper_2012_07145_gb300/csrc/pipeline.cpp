@@ -24,6 +24,18 @@ namespace hp {
 
 unsigned long long g_launches = 0;
 thread_local int t_overlap = 0;
+thread_local KernelProbe* t_probe = nullptr;
+
+void probe_kernel(const void* func) {
+  cudaFuncAttributes at;
+  if (cudaFuncGetAttributes(&at, func) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  ++t_probe->kernels;
+  if (at.numRegs > t_probe->max_regs) t_probe->max_regs = at.numRegs;
+  if ((long long)at.localSizeBytes > t_probe->max_local) t_probe->max_local = (long long)at.localSizeBytes;
+}
 
 namespace {
 
@@ -145,6 +157,8 @@ struct hp_pipeline {
   int* d_err = nullptr;
   bool use_graph = false;
   bool overlap = true;   // programmatic dependent launch between the realize's kernels
+  bool probe = false;    // gather the launched kernels' register / local-memory figures
+  hp::KernelProbe probed{0, 0, 0};
   cudaStream_t capture_stream = nullptr;
   unsigned long long uses = 0;
 };
@@ -1524,9 +1538,17 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
 hp_status run_groups(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, const hp_buffer* output, void* stream) {
   struct Overlap {
     int saved;
-    explicit Overlap(int on) : saved(t_overlap) { t_overlap = on; }
-    ~Overlap() { t_overlap = saved; }
-  } guard(p->overlap ? 1 : 0);
+    KernelProbe* saved_probe;
+    Overlap(int on, KernelProbe* probe) : saved(t_overlap), saved_probe(t_probe) {
+      t_overlap = on;
+      t_probe = probe;
+    }
+    ~Overlap() {
+      t_overlap = saved;
+      t_probe = saved_probe;
+    }
+  } guard(p->overlap ? 1 : 0, p->probe ? &p->probed : nullptr);
+  if (p->probe) p->probed = KernelProbe{0, 0, 0};
   return run_groups_impl(p, plan, inputs, output, stream);
 }
 
@@ -2135,6 +2157,10 @@ hp_status hp_set_option(hp_pipeline* p, int option, long long value) {
       }
       p->overlap = value != 0;
       return HP_OK;
+    case HP_OPT_PROBE_ATTRS:
+      p->probe = value != 0;
+      p->probed = hp::KernelProbe{0, 0, 0};
+      return HP_OK;
     default:
       return fail(HP_ERR_INVALID_ARG, "unknown option %d", option);
   }
@@ -2154,3 +2180,12 @@ const char* hp_last_error(void) { return t_err.c_str(); }
 unsigned long long hp_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 }  // extern "C"
+
+hp_status hp_kernel_attrs_get(hp_pipeline* p, int* n_kernels, int* max_registers, long long* max_local_bytes) {
+  using namespace hp;
+  if (!p || !n_kernels || !max_registers || !max_local_bytes) return fail(HP_ERR_INVALID_ARG, "null argument");
+  *n_kernels = p->probed.kernels;
+  *max_registers = p->probed.max_regs;
+  *max_local_bytes = p->probed.max_local;
+  return HP_OK;
+}

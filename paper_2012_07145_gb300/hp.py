@@ -23,6 +23,7 @@ HP_U8, HP_U16, HP_F16, HP_BF16, HP_F32, HP_U32 = range(6)
 HP_INLINE = -1
 HP_OPT_CUDA_GRAPH = 1
 HP_OPT_OVERLAP = 2
+HP_OPT_PROBE_ATTRS = 3
 HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE = 0, 1, 2
 (HP_KERNEL_STENCIL_CHAIN, HP_KERNEL_UNSHARP, HP_KERNEL_HARRIS, HP_KERNEL_GENERIC, HP_KERNEL_POINTWISE,
  HP_KERNEL_DOWNSAMPLE, HP_KERNEL_UPSAMPLE, HP_KERNEL_HISTOGRAM, HP_KERNEL_CDF_LUT, HP_KERNEL_LUT_APPLY,
@@ -76,7 +77,7 @@ EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_s
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
            "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy",
-           "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak"]
+           "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak", "hp_kernel_attrs_get"]
 
 _lib = None
 
@@ -113,6 +114,7 @@ def lib():
         L.hp_server_prepare.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int]
         L.hp_measure_fp32_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), _IP]
+        L.hp_kernel_attrs_get.argtypes = [P, _IP, _IP, ctypes.POINTER(ctypes.c_longlong)]
         L.hp_last_error.restype = ctypes.c_char_p
         L.hp_launch_count.restype = ctypes.c_ulonglong
         for name in EXPORTS:
@@ -260,6 +262,16 @@ class Pipeline:
     def overlap_launches(self, on: bool = True):
         """Programmatic dependent launch between the realize's kernels (the default)."""
         self.set_option(HP_OPT_OVERLAP, 1 if on else 0)
+
+    def probe_kernel_attrs(self, on: bool = True):
+        """Record the launched kernels' registers and local-memory bytes (HP_OPT_PROBE_ATTRS)."""
+        self.set_option(HP_OPT_PROBE_ATTRS, 1 if on else 0)
+
+    def kernel_attrs(self):
+        """(kernels, max registers, max local bytes per thread) of the last probed realize."""
+        n, r, loc = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        check(lib().hp_kernel_attrs_get(self.h, ctypes.byref(n), ctypes.byref(r), ctypes.byref(loc)))
+        return n.value, r.value, loc.value
 
     def device_error(self) -> int:
         """Reads and clears the device error word (0 = none); synchronises."""

@@ -27,9 +27,11 @@ from gpu_util import bits, rel_err, run, to_device, to_numpy
 pytestmark = pytest.mark.gpu
 TOL = 1e-5   # max |gpu - oracle| / (max - min of the oracle output), FP32 stages
 
-DB = json.load(open(os.path.join(os.path.dirname(tuner.__file__), "schedules.json")))
-CHAIN_KEYS = sorted(k for k in DB if k.startswith("chain"))
-APP_KEYS = sorted(k for k in DB if not k.startswith("chain"))
+DB = json.load(open(tuner.DB_PATH))
+CHAIN_KEYS = sorted(k for k in DB if k.startswith("stencil_chain_"))
+APP_KEYS = sorted(k for k in DB if k.split("/")[0] in ("harris", "unsharp", "histeq"))
+LL_KEYS = sorted(k for k in DB if k.startswith("local_laplacian_"))
+STORAGE = {"f32": hp.HP_F32, "f16": hp.HP_F16, "bf16": hp.HP_BF16}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -37,68 +39,66 @@ def built():
     __graft_entry__.build()
 
 
-def _chain_workload(key):
-    """(stages, pattern, H, W, storage) of a stored chain entry."""
-    e = DB[key]
-    wl = e.get("workload", {})
-    return (wl.get("stages", 32 if key.startswith("chain32") else 4),
-            wl.get("pattern", "alternate" if key.startswith("chain32") else "binomial"),
-            wl.get("h", 1536 if key.startswith("chain32") else 512),
-            wl.get("w", 2560 if key.startswith("chain32") else 512),
-            {"f32": hp.HP_F32, "f16": hp.HP_F16, "bf16": hp.HP_BF16}[wl.get("dtype", "f32")])
-
-
 @pytest.mark.parametrize("key", CHAIN_KEYS)
 def test_stored_chain_schedule_whole_image_against_oracle(key):
-    n, pattern, H, W, st = _chain_workload(key)
+    pipeline, W, H, dtype = tuner.parse_key(key)
+    _, _, n, pattern = pipeline.split("_")
+    n, st = int(n), STORAGE[dtype]
     img = synth.stencil_input(H, W, seed=0)
     p = pipelines.stencil_chain(n, pattern, storage=st)
     plain = run(p, [to_device(img, st)], [st], (1, H, W), st)
-    pipelines.chain_schedule(p, **DB[key]["params"])
+    tuner.apply_entry(p, None, pipeline, DB[key])
     fused = run(p, [to_device(img, st)], [st], (1, H, W), st)
     assert torch.equal(bits(fused), bits(plain))
     if st != hp.HP_F32:
-        return          # 16-bit storage: the error is stated (test_parity_chain), not gated
+        return          # 16-bit storage: the error is stated (test_parity_lowp), not gated
     ref = ost.stencil_chain(img[0].astype(np.float64), ost.chain_kinds(n, pattern))
     err = rel_err(to_numpy(fused)[0], ref)
-    print(f"{key}: {W}x{H}, {DB[key]['params']}: max rel err over the whole image {err:.3e}")
+    print(f"{key}: {DB[key]['params']}: max rel err over the whole image {err:.3e}")
     assert err <= TOL
-
-
-def _app_key(key):
-    app, size = key.rsplit("_", 1)
-    w, h = (int(v) for v in size.split("x"))
-    return app, w, h
 
 
 @pytest.mark.parametrize("key", APP_KEYS)
 def test_stored_app_schedule_whole_image_against_oracle(key):
-    app, W, H = _app_key(key)
-    p, bi, ref_t, y, odt = tuner.app_io(app, H, W)
-    stream = torch.cuda.current_stream().cuda_stream
-    p.realize(bi, hp.buffer_from_tensor(ref_t, odt), stream)        # stage-per-kernel (default)
-    tuner.apply_schedule(p, DB[key]["params"])
-    p.realize(bi, hp.buffer_from_tensor(y, odt), stream)
-    torch.cuda.synchronize()
-    assert p.device_error() == 0
+    app, W, H, dtype = tuner.parse_key(key)
+    wl = tuner.workload(app, W, H, dtype)
+    p, _ = wl["build"]()
+    (img, idt), = wl["inputs"]()
+    x = to_device(img, idt)
+    oc, _, _, odt = wl["out"]
+    ref_t = run(p, [x], [idt], (oc, H, W), odt)                        # stage-per-kernel (default)
+    tuner.apply_entry(p, None, app, DB[key])
+    y = run(p, [x], [idt], (oc, H, W), odt)
     assert torch.equal(bits(y), bits(ref_t))
     got = to_numpy(y)
     if app == "histeq":
-        img = synth.gray_u8_lowcontrast(H, W, seed=0)[0]
-        assert np.array_equal(got[0], ohe.equalize(img)[2])           # integer path: bit-exact
+        assert np.array_equal(got[0], ohe.equalize(img[0])[2])        # integer path: bit-exact
         return
-    rgb = synth.rgb_f32(H, W, seed=0)
-    if app == "harris_bf16":
-        rgb16 = torch.from_numpy(rgb).to(torch.bfloat16).double().numpy()
-        e1 = rel_err(got[0], ohr.harris(rgb16))
-        e2 = rel_err(got[0], ohr.harris(rgb.astype(np.float64)))
-        print(f"{key}: bf16 storage, rel err vs oracle on the rounded input {e1:.3e}, on the original {e2:.3e}")
+    if dtype != "f32":
+        rounded = to_numpy(x).astype(np.float64)
+        e1 = rel_err(got[0], ohr.harris(rounded))
+        e2 = rel_err(got[0], ohr.harris(img.astype(np.float64)))
+        print(f"{key}: 16-bit storage, rel err vs oracle on the rounded input {e1:.3e}, on the original {e2:.3e}")
         assert np.isfinite(e1) and e1 < 0.05                           # stated, not gated (sanity bound)
         return
-    if app == "harris":
-        ref = ohr.harris(rgb.astype(np.float64))[None]
-    else:
-        ref = ous.unsharp(rgb.astype(np.float64))
+    ref = ohr.harris(img.astype(np.float64))[None] if app == "harris" else ous.unsharp(img.astype(np.float64))
     err = max(rel_err(got[c], ref[c]) for c in range(ref.shape[0]))
     print(f"{key}: {DB[key]['params']}: max rel err over the whole image {err:.3e}")
     assert err <= TOL
+
+
+@pytest.mark.parametrize("key", LL_KEYS)
+def test_stored_local_laplacian_schedule_bit_identical_and_identity(key):
+    """The tuned per-level schedule equals the stage-per-kernel one bit for
+    bit at full size, and with alpha = beta = 1 returns the input (the
+    oracle's exact result) within one LSB."""
+    pipeline, W, H, dtype = tuner.parse_key(key)
+    img = synth.rgb_u16_gradient_noise(H, W, seed=0)
+    wl = tuner.workload(pipeline, W, H, dtype)
+    p, ids = wl["build"]()
+    x = to_device(img, hp.HP_U16)
+    plain = to_numpy(run(p, [x], [hp.HP_U16], (3, H, W), hp.HP_U16))
+    tuner.apply_entry(p, ids, pipeline, DB[key])
+    fused = to_numpy(run(p, [x], [hp.HP_U16], (3, H, W), hp.HP_U16))
+    assert np.array_equal(fused, plain)
+    assert np.abs(fused.astype(np.int64) - img.astype(np.int64)).max() <= 1

@@ -18,7 +18,7 @@ def built():
 
 def test_chain_candidates_lower_with_the_mirrored_shared_memory():
     W, H = 2560, 1536
-    cands = tuner.chain_candidates(32, W, H)
+    cands = [c for c in tuner.chain_candidates(32, W, H) if c.get("impl") != hp.HP_IMPL_WAVE]   # the tiled ones
     assert len(cands) > 100
     p = pipelines.stencil_chain(32)
     for c in cands:
@@ -60,25 +60,16 @@ def _expected_app_kernel(app, c):
     if c.get("impl") == hp.HP_IMPL_GENERIC:
         return hp.HP_KERNEL_GENERIC
     if c.get("impl") == hp.HP_IMPL_WAVE:
-        return hp.HP_KERNEL_HARRIS_ROWS if app.startswith("harris") else hp.HP_KERNEL_STENCIL_ROWS
-    return hp.HP_KERNEL_HARRIS if app.startswith("harris") else hp.HP_KERNEL_UNSHARP
+        return hp.HP_KERNEL_HARRIS_ROWS if app == "harris" else hp.HP_KERNEL_STENCIL_ROWS
+    return hp.HP_KERNEL_HARRIS if app == "harris" else hp.HP_KERNEL_UNSHARP
 
 
-def _app_pipeline(app):
-    if app == "harris":
-        return pipelines.harris()
-    if app == "harris_bf16":
-        return pipelines.harris(io_storage=hp.HP_BF16, inner_storage=hp.HP_BF16)
-    if app == "unsharp":
-        return pipelines.unsharp()
-    return pipelines.histeq()
-
-
-@pytest.mark.parametrize("app", ["harris", "harris_bf16", "unsharp", "histeq"])
-def test_app_candidates_lower_to_the_kernel_they_time(app):
-    p = _app_pipeline(app)
+@pytest.mark.parametrize("app,dtype", [("harris", "f32"), ("harris", "bf16"), ("unsharp", "f32"), ("histeq", "u8")])
+def test_app_candidates_lower_to_the_kernel_they_time(app, dtype):
+    wl = tuner.workload(app, 2560, 1536, dtype)
+    p, _ = wl["build"]()
     n = len(p.stages)
-    for c in tuner.app_candidates(app):
+    for c in tuner.app_candidates(app, dtype):
         tuner.apply_schedule(p, c)
         want = _expected_app_kernel(app, c)
         if want is None:
@@ -89,23 +80,49 @@ def test_app_candidates_lower_to_the_kernel_they_time(app):
         assert info.kernel == want, (app, c)
 
 
-def test_every_stored_schedule_lowers_to_its_kernel():
+@pytest.mark.parametrize("n,dtype", [(32, "f32"), (32, "bf16"), (4, "f32")])
+def test_streaming_chain_candidates_lower_to_the_streaming_kernel(n, dtype):
+    """The tuner's mirror of the streaming kernel's strip widths (4 or 8
+    columns per lane, 2-byte inputs aligned to 8 columns) is the library's."""
+    pattern = "alternate" if n == 32 else "binomial"
+    W, H = (2560, 1536) if n == 32 else (512, 512)
+    wl = tuner.workload(f"stencil_chain_{n}_{pattern}", W, H, dtype)
+    p, _ = wl["build"]()
+    stream = [c for c in wl["candidates"](False) if c.get("impl") == hp.HP_IMPL_WAVE]
+    assert len(stream) >= 18
+    for c in stream:
+        wl["apply"](p, None, c)
+        assert p.group_count() == n // c["depth"]
+        assert p.group_info([(W, H)], 0).kernel == hp.HP_KERNEL_STENCIL_WAVE, c
+
+
+def test_local_laplacian_candidates_lower():
+    wl = tuner.workload("local_laplacian_J8_K8", 2560, 1536, "u16")
+    p, ids = wl["build"]()
+    for c in wl["candidates"](False):
+        wl["apply"](p, ids, c)
+        assert p.group_count() == 14
+        kinds = [p.group_info([(2560, 1536)], g).kernel for g in range(p.group_count())]
+        assert all(0 <= k < len(hp.KERNEL_NAMES) for k in kinds)
+
+
+def test_keys_round_trip():
+    for wl in tuner.BENCH_WORKLOADS:
+        assert tuner.parse_key(tuner.key(*wl)) == wl
+
+
+def test_every_stored_schedule_lowers():
+    """Every entry of schedules.json is keyed by its workload, lowers through
+    the C ABI at its size, and was faster than the stage-per-kernel schedule."""
     db = json.load(open(tuner.DB_PATH))
-    assert "chain32" in db
-    for name, entry in db.items():
-        c = entry["params"]
-        if name == "chain32":
-            p = pipelines.stencil_chain(32)
-            pipelines.chain_schedule(p, **c)
-            assert p.group_info([(2560, 1536)], 0).kernel == hp.HP_KERNEL_STENCIL_CHAIN
-            assert entry["ms"] < entry["plain_ms"]
-            continue
-        app, size = name.rsplit("_", 1)
-        W, H = (int(v) for v in size.split("x"))
-        p = _app_pipeline(app)
-        tuner.apply_schedule(p, c)
-        want = _expected_app_kernel(app, c)
-        got = [p.group_info([(W, H)], g).kernel for g in range(p.group_count())]
-        assert got == ([want] if want is not None else got), (name, got)
+    assert tuner.key("stencil_chain_32_alternate", 2560, 1536, "f32") in db
+    for k, entry in db.items():
+        pipeline, w, h, dtype = tuner.parse_key(k)
+        assert entry["workload"] == dict(pipeline=pipeline, w=w, h=h, dtype=dtype)
+        wl = tuner.workload(pipeline, w, h, dtype)
+        p, ids = wl["build"]()
+        tuner.apply_entry(p, ids, pipeline, entry)
+        kinds = [p.group_info([(w, h)], g).kernel for g in range(p.group_count())]
+        assert all(0 <= x < len(hp.KERNEL_NAMES) for x in kinds), k
         if entry.get("plain_ms") is not None:
-            assert entry["ms"] <= entry["plain_ms"], name
+            assert entry["ms"] <= entry["plain_ms"], k
