@@ -404,7 +404,7 @@ __device__ __forceinline__ void box_steps(RS& S, int t0, int n, const unsigned c
 }
 
 template <int D, int C, int RND, int ODT, int WP>
-__global__ void __maxnreg__(168) k_chain_rows(const __grid_constant__ CRowsParams kp) {
+__global__ void __maxnreg__(200) k_chain_rows(const __grid_constant__ CRowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);

@@ -151,9 +151,15 @@ struct MaxRun {
   }
 };
 
-// RND: a storage rounding or a non-f32 output (else plain maxima, float4 stores)
+// RND: a storage rounding or a non-f32 output (else plain maxima, float4 stores).
+// Three CTAs per SM, except the vertical-only windows of radius 3 and 4, whose
+// ring of 2r+1 row maxima needs more registers than that leaves (they run at
+// two CTAs per SM rather than spill).
+template <int RX, int RY>
+constexpr int max_rows_min_blocks() { return RX == 0 && RY >= 3 ? 2 : 3; }
+
 template <int IDT, int RX, int RY, bool RND>
-__global__ void __launch_bounds__(256, 3) k_max_rows(const MaxParams P) {
+__global__ void __launch_bounds__(256, max_rows_min_blocks<RX, RY>()) k_max_rows(const MaxParams P) {
   grid_dep_wait();
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int u = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < P.units; u += nw) {

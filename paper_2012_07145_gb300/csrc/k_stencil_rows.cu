@@ -279,7 +279,7 @@ struct StripRun {
 };
 
 template <bool F32, bool EPI>
-__global__ void __launch_bounds__(256, 3) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
+__global__ void __launch_bounds__(256, 2) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
