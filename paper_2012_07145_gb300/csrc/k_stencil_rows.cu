@@ -144,7 +144,20 @@ __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (
 // run.  Windows are indexed by row mod 5, so a loop unrolled five times keeps
 // them in fixed registers.  F32 = every storage type is f32 (no rounding, one
 // 128-bit store per lane and row).
-template <bool F32, bool EPI>
+// The binomial [1,4,6,4,1]/16 taps (the unsharp blur, the same float values
+// the pipeline stores) as compile-time constants.
+__device__ __forceinline__ float tap5_binomial_const(float a, float b, float c, float d, float e) {
+  float s = __fmul_rn(0.0625f, a);
+  s = __fmaf_rn(0.25f, b, s);
+  s = __fmaf_rn(0.375f, c, s);
+  s = __fmaf_rn(0.25f, d, s);
+  return __fmaf_rn(0.0625f, e, s);
+}
+
+// BIN: both passes take the binomial taps (checked bit for bit on the host),
+// compiled as constants: no registers for the taps, which lets the unsharp
+// kernel keep five CTAs of 128 threads per SM without spilling.
+template <bool F32, bool EPI, bool BIN>
 struct StripRun {
   const SRowsParams& kp;
   const StripGeom& g;
@@ -213,10 +226,10 @@ struct StripRun {
     // x pass: columns c0-2 .. c0+5
     const float l2 = __shfl_up_sync(kFull, v[2], 1), l1 = __shfl_up_sync(kFull, v[3], 1);
     const float r1 = __shfl_down_sync(kFull, v[0], 1), r2 = __shfl_down_sync(kFull, v[1], 1);
-    hx[M][0] = tap5(wx, l2, l1, v[0], v[1], v[2]);
-    hx[M][1] = tap5(wx, l1, v[0], v[1], v[2], v[3]);
-    hx[M][2] = tap5(wx, v[0], v[1], v[2], v[3], r1);
-    hx[M][3] = tap5(wx, v[1], v[2], v[3], r1, r2);
+    hx[M][0] = BIN ? tap5_binomial_const(l2, l1, v[0], v[1], v[2]) : tap5(wx, l2, l1, v[0], v[1], v[2]);
+    hx[M][1] = BIN ? tap5_binomial_const(l1, v[0], v[1], v[2], v[3]) : tap5(wx, l1, v[0], v[1], v[2], v[3]);
+    hx[M][2] = BIN ? tap5_binomial_const(v[0], v[1], v[2], v[3], r1) : tap5(wx, v[0], v[1], v[2], v[3], r1);
+    hx[M][3] = BIN ? tap5_binomial_const(v[1], v[2], v[3], r1, r2) : tap5(wx, v[1], v[2], v[3], r1, r2);
     if (vedge && (r < 1 || r >= a.in.h)) {
       if (r == 0) {  // rows -2 and -1 are row 0
 #pragma unroll
@@ -233,7 +246,8 @@ struct StripRun {
       float o[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        float b = tap5(wy, hx[J0][k], hx[J1][k], hx[J2][k], hx[J3][k], hx[M][k]);
+        float b = BIN ? tap5_binomial_const(hx[J0][k], hx[J1][k], hx[J2][k], hx[J3][k], hx[M][k])
+                      : tap5(wy, hx[J0][k], hx[J1][k], hx[J2][k], hx[J3][k], hx[M][k]);
         if (!F32) b = round_storage(a.storage[0], b);
         if (EPI) {
           b = op_unsharp(raw[J2][k], b, a.amount);
@@ -278,8 +292,8 @@ struct StripRun {
   }
 };
 
-template <bool F32, bool EPI>
-__global__ void __launch_bounds__(256, 2) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
+template <bool F32, bool EPI, bool BIN>
+__global__ void __maxnreg__(BIN ? 96 : 128) k_stencil_rows(const __grid_constant__ SRowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
@@ -302,7 +316,7 @@ __global__ void __launch_bounds__(256, 2) k_stencil_rows(const __grid_constant__
   R.IU = unit_geom(kp, g, gw);
   for (int i = 0; i < kRing; ++i) issue_one(kp, g, R, stride, lane);
   for (int u = gw; u < kp.units; u += stride) {
-    StripRun<F32, EPI> run(kp, g, R, unit_geom(kp, g, u), lane, stride);
+    StripRun<F32, EPI, BIN> run(kp, g, R, unit_geom(kp, g, u), lane, stride);
     if (!run.run()) {
       // a box never arrived: report, wait (bounded) for the copies still in
       // flight into this warp's slots, and stop
@@ -319,12 +333,24 @@ __global__ void __launch_bounds__(256, 2) k_stencil_rows(const __grid_constant__
 
 typedef void (*SRowsKernel)(SRowsParams);
 
+// Whether both passes' taps are the binomial ones, bit for bit.
+bool binomial_taps(const ChainArgs& a) {
+  static const float b[5] = {0.0625f, 0.25f, 0.375f, 0.25f, 0.0625f};
+  return memcmp(a.w[0], b, sizeof b) == 0 && memcmp(a.w[0] + 5, b, sizeof b) == 0;
+}
+
+template <bool BIN>
+SRowsKernel pick_fe(bool f32, bool epi) {
+  if (epi) return f32 ? k_stencil_rows<true, true, BIN> : k_stencil_rows<false, true, BIN>;
+  return f32 ? k_stencil_rows<true, false, BIN> : k_stencil_rows<false, false, BIN>;
+}
+
 SRowsKernel pick_kernel(const ChainArgs& a, int* variant) {
   const bool f32 = a.in.dtype == HP_F32 && a.storage[0] == HP_F32 && a.out.dtype == HP_F32;
   const bool epi = a.epilogue == 1;
-  *variant = (f32 ? 0 : 1) + (epi ? 2 : 0);
-  if (epi) return f32 ? k_stencil_rows<true, true> : k_stencil_rows<false, true>;
-  return f32 ? k_stencil_rows<true, false> : k_stencil_rows<false, false>;
+  const bool bin = binomial_taps(a);
+  *variant = (f32 ? 0 : 1) + (epi ? 2 : 0) + (bin ? 4 : 0);
+  return bin ? pick_fe<true>(f32, epi) : pick_fe<false>(f32, epi);
 }
 
 }  // namespace
@@ -357,7 +383,7 @@ int stencil_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes
 int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream) {
   int variant;
   SRowsKernel kern = pick_kernel(a, &variant);
-  static bool configured[4] = {false, false, false, false};
+  static bool configured[8] = {};
   if (!configured[variant]) {
     int e = allow_max_dynamic_smem((const void*)kern);
     if (e) return e;

@@ -150,7 +150,7 @@ def app_candidates(app, dtype="f32"):
         out.append(dict(schedule="fused", impl=hp.HP_IMPL_AUTO, tile_w=tw, tile_h=th, threads=t, serial_y=sy))
     runs = (8, 11, 14, 17, 20, 26, 32) if app == "harris" else (12, 16, 20, 24, 32, 48, 64, 96)
     strip = 112 if dtype in ("f16", "bf16") else 120      # 2-byte inputs take 112-column strips
-    for th, t in itertools.product(runs, (128, 256)):
+    for th, t in itertools.product(runs, (64, 128, 192, 256)):
         out.append(dict(schedule="fused", impl=hp.HP_IMPL_WAVE, tile_w=strip, tile_h=th, threads=t))
     return out
 
