@@ -311,17 +311,23 @@ hp_status hp_set_option(hp_pipeline* p, int option, long long value);
 hp_status hp_kernel_attrs_get(hp_pipeline* p, int* n_kernels, int* max_registers, long long* max_local_bytes);
 
 /* ---- Serving loop ---------------------------------------------------------
- * Continuous batching of pipeline requests on one GPU.  Requests (a pipeline,
- * HOST input buffers, a HOST output buffer) are admitted in arrival order as
- * soon as one of `slots` CUDA streams and enough of an HBM arena reserved at
- * creation (`hbm_budget_bytes`) are free; admitted requests run concurrently
- * (copy in, realize, copy out).  Up to `max_batch` queued requests for the same
- * pipeline and image size are served by one realize when every stage acts on
- * each channel separately (stencils, resampling, per-channel point-wise ops):
- * their planes are stacked, so each kernel launches once for the batch and
- * every result equals the request's solo result.  Host buffers must stay
- * valid until the request completes; pinned memory gives asynchronous copies.
- * The pipeline must outlive the server.  Latency = submit to the completion the
+ * Continuous batching of pipeline requests on one GPU (north of the paper's
+ * benchmark loop, Sec. 6).  Requests (a pipeline, input buffers, an output
+ * buffer) are admitted in arrival order as soon as one of `slots` CUDA streams
+ * and enough of an HBM arena reserved at creation (`hbm_budget_bytes`) are
+ * free; admitted requests run concurrently (copy in, realize, copy out).  Up to
+ * `max_batch` queued requests for the same pipeline, image size and buffer
+ * kind are served by one realize: their images are stacked as planes, so each
+ * kernel launches once, as one persistent grid, for the batch, and every
+ * result equals the request's solo result.  Batching covers pipelines whose
+ * stages act on each channel separately (stencils, resampling, per-channel
+ * point-wise ops) and the fused Harris and histogram-equalization kernels.
+ * Each slot keeps the staging region of a request shape resident in the
+ * arena after the request (least recently used regions of idle slots are
+ * given back when the arena is full), so its realize of that shape replays as
+ * a CUDA graph from the second request on.  Buffers must stay valid until the
+ * request completes; pinned host memory gives asynchronous copies.  The
+ * pipeline must outlive the server.  Latency = submit to the completion the
  * server's worker thread observes. */
 typedef struct hp_server hp_server;
 typedef struct {
@@ -331,6 +337,10 @@ typedef struct {
   double p50_us, p99_us, mean_us, max_us;
   double mpix;                          /* output megapixels completed */
   double busy_s;                        /* first submit to last completion */
+  unsigned long long graph_replays;     /* slot realizes served by an instantiated CUDA graph */
+  unsigned long long resident_bytes;    /* arena bytes held by resident staging regions now */
+  unsigned long long device_requests;   /* requests submitted with device buffers */
+  unsigned long long evictions;         /* staging regions given back to admit other shapes */
 } hp_server_stats;
 
 /* Reserves the arena (cudaMalloc of hbm_budget_bytes, at least 1 MiB), creates
@@ -338,9 +348,15 @@ typedef struct {
  * HP_ERR_INVALID_ARG for arguments out of range, HP_ERR_OOM if the arena
  * cannot be reserved. */
 hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slots, int max_batch);
-/* Enqueues a request; *ticket identifies it.  Never blocks on the GPU. */
+/* Enqueues a request with HOST buffers; *ticket identifies it.  Never blocks
+ * on the GPU. */
 hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
                            const hp_buffer* output, unsigned long long* ticket);
+/* The same with DEVICE buffers (no host copies): served alone, the realize
+ * runs on the buffers themselves; in a batch they are gathered into and
+ * scattered from the slot's staging region by device-to-device copies. */
+hp_status hp_server_submit_device(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                                  const hp_buffer* output, unsigned long long* ticket);
 /* Waits up to timeout_ms for a request; HP_ERR_TIMEOUT if it is not complete
  * by then (it stays queued or running), else the request's status. */
 hp_status hp_server_wait(hp_server* s, unsigned long long ticket, int timeout_ms, double* latency_us);

@@ -214,6 +214,7 @@ struct HarrisArgs {
   // 3 x-taps then 3 y-taps of: Ix, Iy, Sxx, Syy, Sxy
   float w[5][6];
   int tile_w, tile_h, tiles_x, tiles_y, threads, seg;
+  int batch;                // images stacked in the buffers (in: 3 planes each, out: 1)
   int* err;
 };
 
@@ -287,8 +288,8 @@ int stencil_rows_grid(const ChainArgs& a, int units, int threads, int smem_bytes
 int launch_stencil_rows(const ChainArgs& a, int rows, int grid, int smem_bytes, void* stream);
 // histogram equalization in one cooperative kernel; `state` is histeq_state_bytes() of zeroed device memory
 size_t histeq_state_bytes();
-int histeq_grid(int w, int h);
-int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, int grid, void* stream);
+int histeq_grid(int w, int h, int batch);
+int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, int grid, int batch, void* stream);
 int launch_ll_down(const LLDownArgs& a, int smem_bytes, void* stream);
 int ll_down_smem_bytes(int tile_w, int tile_h, int channels, int remap);
 int launch_ll_level(const LLLevelArgs& a, void* stream);

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(512) k_harris(const __grid_constant__ HarrisKP
     mbar_init(bar, 1);
     fence_mbar_init();
     mbar_arrive_expect_tx(bar, (unsigned)(g.bw * g.GH * 3 * esize));
-    tma_load_3d(region, &kp.tmap, ox - g.A, oy - 2, 0, bar);
+    tma_load_3d(region, &kp.tmap, ox - g.A, oy - 2, 3 * blockIdx.z, bar);  // image blockIdx.z of a batch
     if (!mbar_wait_bounded(bar, 0, 2000000000ull)) *status = 1;
   }
   __syncthreads();
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(512) k_harris(const __grid_constant__ HarrisKP
     const int nb = a.tile_w >> 2;
     const int nseg = (a.tile_h + a.seg - 1) / a.seg;
     const int hlim = min(a.tile_h, a.out.h - oy), wlim = min(a.tile_w, a.out.w - ox);
-    char* out_row0 = (char*)a.out.data + (long long)oy * a.out.rs;
+    char* out_row0 = (char*)a.out.data + (long long)blockIdx.z * a.out.ps + (long long)oy * a.out.rs;
     for (int it = threadIdx.x; it < nb * nseg; it += blockDim.x) {
       const int sg = it / nb, b = it - sg * nb;
       const int r0 = sg * a.seg, r1 = min(a.tile_h, r0 + a.seg);
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(512) k_harris(const __grid_constant__ HarrisKP
           return;
         }
         const float vv[4] = {r.x, r.y, r.z, r.w};
-        for (int i = 0; i < 4 && x + i < wlim; ++i) store_px(a.out, 0, gx + i, oy + y, vv[i]);
+        for (int i = 0; i < 4 && x + i < wlim; ++i) store_px(a.out, blockIdx.z, gx + i, oy + y, vv[i]);
       };
       int y = r0;
       while (true) {
@@ -330,7 +330,7 @@ int launch_harris(const HarrisArgs& a, int smem_bytes, void* stream) {
   if (g.bw > 256 || g.GH > 256 ||
       encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, g.bw, g.GH, 3))
     return (int)cudaErrorInvalidValue;
-  dim3 grid(a.tiles_x, a.tiles_y, 1);
+  dim3 grid(a.tiles_x, a.tiles_y, a.batch > 1 ? a.batch : 1);
   { const int le_ = launch_kernel(kern, dim3(grid), dim3(a.threads), smem_bytes, stream, kp); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();

@@ -58,10 +58,14 @@ struct RowsParams {
 
 struct Unit {
   int x0, oy, n_in, nbox;  // x0: image column of lane 0's first column; n_in input rows from oy - 2
+  int img;                 // image of a batch (input planes 3 img .. 3 img + 2, output plane img)
 };
 
 __device__ __forceinline__ Unit unit_geom(const RowsParams& kp, const StripGeom& g, int u) {
   Unit U;
+  const int per_img = kp.units / (kp.a.batch > 1 ? kp.a.batch : 1);
+  U.img = u / per_img;
+  u -= U.img * per_img;
   const int s = u % kp.strips, r = u / kp.strips;
   U.x0 = s * g.strip_w - 4 * g.halo_lanes;
   U.oy = r * kp.rows;
@@ -86,7 +90,8 @@ __device__ __forceinline__ void issue_one(const RowsParams& kp, const StripGeom&
   if (lane == 0) {
     const int s = R.issued % kRing;
     mbar_arrive_expect_tx(R.bars + s, (unsigned)g.slot_bytes);
-    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.oy - 2 + R.ij * kBoxRows, 0, R.bars + s);
+    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.oy - 2 + R.ij * kBoxRows, 3 * R.IU.img,
+                R.bars + s);
   }
   ++R.issued;
   if (++R.ij == R.IU.nbox) {
@@ -243,7 +248,7 @@ struct StripRun {
     const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
     st_full = mine && c0 + 3 < W && ODT != 3;
     st_part = mine && c0 < W && !st_full;
-    out_row = (char*)kp.a.out.data + (long long)U.oy * kp.a.out.rs;
+    out_row = (char*)kp.a.out.data + (long long)U.img * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
   }
 
   // Waits for box q (one lane polls, bounded), then the warp reads it.
@@ -383,10 +388,10 @@ struct StripRun {
         *reinterpret_cast<uint2*>(row + 2LL * c0) = u;
       }
     } else if (st_part) {
-      const int y = (int)((row - (char*)a.out.data) / a.out.rs);
+      const int y = (int)((row - (char*)a.out.data - (long long)U.img * a.out.ps) / a.out.rs);
 #pragma unroll
       for (int k = 0; k < 4; ++k)
-        if (c0 + k < a.out.w) store_px(a.out, 0, c0 + k, y, o[k]);
+        if (c0 + k < a.out.w) store_px(a.out, U.img, c0 + k, y, o[k]);
     }
   }
 
@@ -537,7 +542,7 @@ int launch_harris_rows(const HarrisArgs& a, int rows, int grid, int smem_bytes, 
   const StripGeom g = strip_geom(esize);
   kp.strips = (a.out.w + g.strip_w - 1) / g.strip_w;
   kp.rows = rows;
-  kp.units = kp.strips * ((a.out.h + rows - 1) / rows);
+  kp.units = kp.strips * ((a.out.h + rows - 1) / rows) * (a.batch > 1 ? a.batch : 1);
   CUtensorMapDataType tdt = dt == HP_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                             : dt == HP_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   if (encode_tmap_3d(&kp.tmap, tdt, esize, a.in.data, a.in.w, a.in.h, a.in.c, a.in.rs, a.in.ps, 128, kBoxRows, 3))

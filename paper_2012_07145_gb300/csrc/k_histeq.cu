@@ -47,11 +47,12 @@ struct EqState {
 
 struct EqParams {
   ImgView in, out;
-  EqState* st;
+  EqState* st;                  // one state per image of the batch
   int* err;
-  long long n_chunks, per_cta;  // chunks in the image; chunks per CTA
+  long long n_chunks, per_cta;  // chunks in an image; chunks per CTA
   int cpr;                      // chunks per row
   int staged;                   // per_cta chunks fit in shared memory: no second read
+  int ctas;                     // CTAs per image (a batch's images take consecutive groups of CTAs)
 };
 
 __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* a) {
@@ -60,12 +61,12 @@ __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* a) {
   return v;
 }
 
-__device__ __forceinline__ int chunk_bytes(const EqParams& p, long long ch, const unsigned char** src,
+__device__ __forceinline__ int chunk_bytes(const EqParams& p, int img, long long ch, const unsigned char** src,
                                            unsigned char** dst) {
   const int y = (int)(ch / p.cpr);
   const int x0 = (int)(ch - (long long)y * p.cpr) << 4;
-  *src = (const unsigned char*)p.in.data + (long long)y * p.in.rs + x0;
-  *dst = (unsigned char*)p.out.data + (long long)y * p.out.rs + x0;
+  *src = (const unsigned char*)p.in.data + (long long)img * p.in.ps + (long long)y * p.in.rs + x0;
+  *dst = (unsigned char*)p.out.data + (long long)img * p.out.ps + (long long)y * p.out.rs + x0;
   return min(16, p.in.w - x0);
 }
 
@@ -117,12 +118,15 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   __shared__ unsigned char table[256];
   __shared__ unsigned int s_gen;
   __shared__ int s_last, s_ok;
+  // image of the batch and this CTA's place among the image's CTAs
+  const int img = blockIdx.x / p.ctas, cta = blockIdx.x - img * p.ctas;
+  EqState* const st = p.st + img;
   for (int i = threadIdx.x; i < 256 * 32; i += blockDim.x) sh[i] = 0;
-  if (threadIdx.x == 0) s_gen = ld_relaxed(&p.st->gen);
+  if (threadIdx.x == 0) s_gen = ld_relaxed(&st->gen);
   __syncthreads();
   const unsigned int gen = s_gen, buf = gen & 1u;
   unsigned int* hl = sh + (threadIdx.x & 31);
-  const long long c0 = (long long)blockIdx.x * p.per_cta;
+  const long long c0 = (long long)cta * p.per_cta;
   const long long c1 = min(p.n_chunks, c0 + p.per_cta);
   const bool staged = p.staged != 0;  // the slice is kept in shared memory for the lookup
 
@@ -139,7 +143,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
       if (ch < c1) {
         const unsigned char* src;
         unsigned char* dst;
-        nb[u] = chunk_bytes(p, ch, &src, &dst);
+        nb[u] = chunk_bytes(p, img, ch, &src, &dst);
         q[u] = load_chunk(src, nb[u]);
       }
     }
@@ -163,30 +167,30 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
     for (int j = 0; j < 8; ++j) s += row[(j + v) & 7];
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (part == 0 && s) atomicAdd(&p.st->hist[buf][blockIdx.x % kEqCopies][v], s);
+    if (part == 0 && s) atomicAdd(&st->hist[buf][cta % kEqCopies][v], s);
   }
 
   // ---- grid-wide barrier (bounded) ----
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(&p.st->count, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&st->count, 1u) == (unsigned)p.ctas - 1;
     s_ok = 1;
   }
   __syncthreads();
   if (s_last) {
     // every CTA's counts are in: clear the other histogram and the counter for
     // the next launch, then release the others
-    for (int v = threadIdx.x; v < kEqCopies * 256; v += blockDim.x) (&p.st->hist[buf ^ 1u][0][0])[v] = 0;
+    for (int v = threadIdx.x; v < kEqCopies * 256; v += blockDim.x) (&st->hist[buf ^ 1u][0][0])[v] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
-      p.st->count = 0;
+      st->count = 0;
       __threadfence();
-      atomicExch(&p.st->gen, gen + 1u);
+      atomicExch(&st->gen, gen + 1u);
     }
   } else if (threadIdx.x == 0) {
     const unsigned long long t0 = global_ns();
-    while (ld_relaxed(&p.st->gen) == gen) {
+    while (ld_relaxed(&st->gen) == gen) {
       if (global_ns() - t0 > 1000000000ull) {
         s_ok = 0;
         atomicExch(p.err, 3);
@@ -202,14 +206,14 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   unsigned int h = 0;
   if (threadIdx.x < 256)
 #pragma unroll
-    for (int c = 0; c < kEqCopies; ++c) h += __ldcg(&p.st->hist[buf][c][threadIdx.x]);
+    for (int c = 0; c < kEqCopies; ++c) h += __ldcg(&st->hist[buf][c][threadIdx.x]);
   cdf_lut_cta(h, table);
   __syncthreads();
 #pragma unroll 1
   for (long long ch = c0 + threadIdx.x; ch < c1; ch += blockDim.x) {
     const unsigned char* src;
     unsigned char* dst;
-    const int n = chunk_bytes(p, ch, &src, &dst);
+    const int n = chunk_bytes(p, img, ch, &src, &dst);
     store_chunk(table, staged ? stage[ch - c0] : load_chunk(src, n), n, dst);
   }
 }
@@ -233,19 +237,21 @@ int max_coop_ctas() {
 
 }  // namespace
 
-size_t histeq_state_bytes() { return sizeof(EqState); }
+size_t histeq_state_bytes() { return sizeof(EqState); }  // per image of a batch
 
-// CTAs of the launch: one per 2048 chunks (32 KB of image), at most all
-// co-resident ones.
-int histeq_grid(int w, int h) {
+// CTAs per image: one per 2048 chunks (32 KB of image), at most the
+// co-resident ones shared by the batch's images.
+int histeq_grid(int w, int h, int batch) {
   const long long chunks = (long long)((w + 15) / 16) * h;
   long long g = (chunks + 2047) / 2048;
-  const int cap = max_coop_ctas();
+  const int cap = max_coop_ctas() / (batch > 1 ? batch : 1);
   if (g > cap) g = cap;
   return g < 1 ? 1 : (int)g;
 }
 
-int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, int grid, void* stream) {
+// grid: CTAs per image (histeq_grid); the launch has grid x batch CTAs, all
+// co-resident (cooperative).
+int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, int grid, int batch, void* stream) {
   static bool configured = false;
   if (!configured) {
     int e = allow_max_dynamic_smem((const void*)k_histeq);
@@ -261,8 +267,10 @@ int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, 
   p.n_chunks = (long long)p.cpr * in.h;
   p.per_cta = (p.n_chunks + grid - 1) / grid;
   p.staged = p.per_cta * 16 <= kEqStageMax;
+  p.ctas = grid;
+  if (batch < 1) batch = 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.gridDim = dim3(grid * batch, 1, 1);
   cfg.blockDim = dim3(kEqThreads, 1, 1);
   cfg.dynamicSmemBytes = kEqHistBytes + (p.staged ? (int)p.per_cta * 16 : 0);
   cfg.stream = (cudaStream_t)stream;

@@ -157,6 +157,8 @@ struct hp_pipeline {
   int* d_err = nullptr;
   bool use_graph = false;
   bool overlap = true;   // programmatic dependent launch between the realize's kernels
+  int batch = 1;         // images per realize (a server's batched copy; see clone_pipeline)
+  unsigned long long graph_replays = 0;  // realizes served by an instantiated graph
   bool probe = false;    // gather the launched kernels' register / local-memory figures
   hp::KernelProbe probed{0, 0, 0};
   cudaStream_t capture_stream = nullptr;
@@ -949,6 +951,7 @@ void harris_common_args(const hp_pipeline* p, GroupPlan& gp, int roles[10]) {
   a.tile_h = gp.tile_h;
   a.threads = gp.threads;
   a.seg = gp.seg;
+  a.batch = p->batch;
 }
 
 hp_status build_harris(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
@@ -989,11 +992,11 @@ hp_status build_harris_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& g
   a.in.dtype = in_dt;
   a.out.dtype = p->stages[gp.output].storage;
   if (a.tile_h == 0)
-    gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x,
+    gp.tile_h = a.tile_h = default_run_rows(od.h, a.tiles_x * p->batch,
                                             (long long)harris_rows_grid(a, 1 << 30, a.threads, gp.smem) * (a.threads / 32));
   if (a.tile_h < 4 || a.tile_h > 65536) return fail(HP_ERR_SCHEDULE, "streaming Harris needs tile_h >= 4 rows per run");
   a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
-  gp.grid_x = harris_rows_grid(a, a.tiles_x * a.tiles_y, a.threads, gp.smem);
+  gp.grid_x = harris_rows_grid(a, a.tiles_x * a.tiles_y * p->batch, a.threads, gp.smem);
   gp.grid_y = 1;
   gp.ext_refs.assign(1, p->stages[roles[0]].inputs[0]);
   return HP_OK;
@@ -1410,8 +1413,8 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
       case HP_KERNEL_HISTEQ: {
         Dom od = plan.dom[gp.output];
         gp.threads = 1024;
-        gp.grid_x = histeq_grid(od.w, od.h);
-        gp.aux_bytes = histeq_state_bytes();
+        gp.grid_x = histeq_grid(od.w, od.h, p->batch);
+        gp.aux_bytes = histeq_state_bytes() * p->batch;
         gp.ext_refs.assign(1, p->stages[gp.members[0]].inputs[0]);
         break;
       }
@@ -1429,6 +1432,10 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
       }
     }
     if (s) return s;
+    if (p->batch > 1 && gp.kernel != HP_KERNEL_HARRIS && gp.kernel != HP_KERNEL_HARRIS_ROWS &&
+        gp.kernel != HP_KERNEL_HISTEQ)
+      return fail(HP_ERR_UNSUPPORTED, "a batch of %d images needs every group on a batch-aware kernel "
+                                      "(fused Harris or histogram equalization)", p->batch);
   }
   return HP_OK;
 }
@@ -1670,7 +1677,8 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         break;
       }
       case HP_KERNEL_HISTEQ:
-        e = launch_histeq(ref_view(p, plan, gp.ext_refs[0], inputs, output), out, gp.aux, p->d_err, gp.grid_x, stream);
+        e = launch_histeq(ref_view(p, plan, gp.ext_refs[0], inputs, output), out, gp.aux, p->d_err, gp.grid_x,
+                          p->batch, stream);
         break;
       case HP_KERNEL_HISTOGRAM: {
         HistArgs a{};
@@ -1728,6 +1736,7 @@ hp_status run_graph(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, int n_i
     int e = cudaGraphLaunch(g.exec, (cudaStream_t)stream);
     if (e) return cuda_fail(e, "cudaGraphLaunch");
     __atomic_add_fetch(&g_launches, g.kernels, __ATOMIC_RELAXED);
+    ++p->graph_replays;
     return HP_OK;
   }
   if (std::find(plan.seen.begin(), plan.seen.end(), key) == plan.seen.end()) {
@@ -1884,7 +1893,7 @@ static hp_status collect_in_dom(hp_pipeline* p, const hp_buffer* inputs, int n_i
     return fail(HP_ERR_INVALID_ARG, "expected %d input buffers", p ? (int)p->in_dtypes.size() : 0);
   in_dom.clear();
   for (int i = 0; i < n_inputs; ++i) {
-    hp_status s = check_buffer(inputs[i], p->in_dtypes[i], p->in_channels[i], Dom{0, 0}, "input", i);
+    hp_status s = check_buffer(inputs[i], p->in_dtypes[i], p->in_channels[i] * p->batch, Dom{0, 0}, "input", i);
     if (s) return s;
     in_dom.push_back(Dom{inputs[i].width, inputs[i].height});
   }
@@ -1934,7 +1943,7 @@ hp_status hp_realize(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, cons
   Plan* plan = nullptr;
   if ((s = get_plan(p, in_dom, &plan))) return s;
   const Stage& os = p->stages[p->output];
-  if ((s = check_buffer(*output, os.storage, os.channels, plan->dom[p->output], "output", 0))) return s;
+  if ((s = check_buffer(*output, os.storage, os.channels * p->batch, plan->dom[p->output], "output", 0))) return s;
   if (!p->d_err && (s = alloc_error_word(p, stream))) return s;
   if ((s = ensure_scratch(p, *plan, (cudaStream_t)stream))) return s;
   if (!p->use_graph) return run_groups(p, *plan, inputs, output, stream);
@@ -2097,16 +2106,40 @@ bool pipeline_stackable(const hp_pipeline* p) {
   return true;
 }
 
-// A copy of the pipeline's algorithm and schedule (no plans, no scratch); with
-// batch > 1 every channel count is multiplied by batch (stackable pipelines).
+unsigned long long pipeline_graph_replays(const hp_pipeline* p) { return p->graph_replays; }
+
+hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch);
+
+// Whether `batch` images of these input sizes can be realized by one call of a
+// batched copy of p: a stackable pipeline always; otherwise its lowering for
+// the sizes must put every group on a batch-aware kernel.
+bool pipeline_batch_ok(const hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int batch) {
+  if (batch <= 1 || pipeline_stackable(p)) return true;
+  hp_pipeline* c = clone_pipeline(p, batch);
+  std::vector<Dom> in_dom;
+  for (int i = 0; i < n_inputs; ++i) in_dom.push_back(Dom{widths[i], heights[i]});
+  Plan* plan = nullptr;
+  const bool ok = get_plan(c, in_dom, &plan) == HP_OK;
+  hp_pipeline_destroy(c);
+  return ok;
+}
+
+// A copy of the pipeline's algorithm and schedule (no plans, no scratch) for
+// `batch` images stacked as planes: a stackable pipeline (every stage acts on
+// each channel separately) gets every channel count multiplied by batch; any
+// other pipeline keeps its channels and realizes `batch` images per call,
+// which its kernels must support (lowering refuses the batch otherwise).
 hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch) {
-  if (batch > 1 && !pipeline_stackable(p)) return nullptr;
   auto* c = new hp_pipeline();
   c->in_dtypes = p->in_dtypes;
   c->in_channels = p->in_channels;
-  for (int& ch : c->in_channels) ch *= batch;
   c->stages = p->stages;
-  for (Stage& s : c->stages) s.channels *= batch;
+  if (batch > 1 && pipeline_stackable(p)) {
+    for (int& ch : c->in_channels) ch *= batch;
+    for (Stage& s : c->stages) s.channels *= batch;
+  } else {
+    c->batch = batch;
+  }
   c->output = p->output;
   c->has_schedule = p->has_schedule;
   c->group_of = p->group_of;

@@ -1,20 +1,34 @@
 // Serving loop: continuous batching of pipeline requests on one GPU.
 //
-// Requests (a pipeline, host input buffers, a host output buffer) arrive at
-// any time through hp_server_submit.  A worker thread admits them in arrival
-// order as soon as a slot (a CUDA stream) and device memory are free: request
-// buffers come from one arena reserved at creation, so admission is by HBM
-// footprint (a slot's pipeline copies allocate their own small scratch the
-// first time they run an image size).  Admitted work runs
-// concurrently on the slots' streams (copies in, realize, copies out), so a
-// request that arrives while others are on the GPU overlaps with them.
-// Requests for the same pipeline and image size whose stages all act on each
-// channel separately (stencils, point-wise per-channel ops, resampling) are
-// batched: their planes are stacked into one image and served by one realize,
-// which launches each kernel once for the whole batch.  Each slot keeps its
-// own copies of the pipelines it runs, so concurrent requests never share a
-// pipeline's scratch.  Latency is measured from submit to the completion the
-// worker observes.
+// Requests (a pipeline, input buffers, an output buffer) arrive at any time
+// through hp_server_submit (host buffers) or hp_server_submit_device (device
+// buffers).  A worker thread admits them in arrival order as soon as a slot (a
+// CUDA stream) and device memory are free.  Admitted work runs concurrently on
+// the slots' streams, so a request that arrives while others are on the GPU
+// overlaps with them.
+//
+// Batching: up to max_batch queued requests for the same pipeline, image size
+// and buffer kind are served by one realize of a batched copy of the pipeline,
+// which launches each kernel once for the whole batch: their images are
+// stacked as planes of one buffer.  Pipelines whose stages all act on each
+// channel separately (stencils, per-channel point-wise ops, resampling) simply
+// see more channels; the fused Harris and histogram-equalization kernels take
+// the batch as an image index (each image keeps its own planes, and for the
+// histogram its own counters and table).  The kernels of a batch are
+// persistent: one grid sized to the GPU walks every image's work units.
+//
+// Residency: each slot keeps, per (pipeline, batch size, image size), a
+// staging region in the HBM arena reserved at creation, and keeps it after
+// the request completes, so later requests of that shape reuse the same device
+// addresses.  That makes every slot's realize of a shape a CUDA graph after its
+// second use (the slots' pipeline copies replay their launch sequence as a
+// graph per set of buffer addresses).  Admission is by HBM footprint: a region
+// is taken from the arena first-fit; when the arena is full, the least
+// recently used regions of idle slots are given back first.  A device request
+// served alone needs no staging at all: the realize runs on the caller's
+// buffers.  Each slot keeps its own copies of the pipelines it runs, so
+// concurrent requests never share a pipeline's scratch.  Latency is measured
+// from submit to the completion the worker observes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +48,8 @@
 namespace hp {
 // Provided by pipeline.cpp.
 hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch);
-bool pipeline_stackable(const hp_pipeline* p);
+bool pipeline_batch_ok(const hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int batch);
+unsigned long long pipeline_graph_replays(const hp_pipeline* p);
 }  // namespace hp
 
 namespace {
@@ -50,16 +65,25 @@ struct Request {
   hp_pipeline* p = nullptr;
   std::vector<hp_buffer> in;
   hp_buffer out{};
+  bool device = false;  // buffers in device memory (no host copies)
   Clock::time_point t_submit;
 };
+
+// A slot's staging region for one request shape and batch size.
+struct Resident {
+  long long off = 0, bytes = 0;
+  unsigned long long last = 0;  // admission counter at its last use
+};
+
+typedef std::vector<long long> ShapeKey;  // pipeline, batch, buffer kind, every buffer's size / type / channels
 
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
   std::vector<Request*> batch;
-  long long off = 0, bytes = 0;
-  hp_status status = HP_OK;
+  Resident* cur = nullptr;  // staging of the batch in flight (null: a device request served in place)
+  std::map<ShapeKey, Resident> resident;
   std::map<std::pair<hp_pipeline*, int>, hp_pipeline*> clones;
 };
 
@@ -77,11 +101,14 @@ struct hp_server {
   std::deque<Request*> queue;
   std::map<unsigned long long, Result> results;
   std::vector<double> latencies;
+  std::map<std::vector<long long>, bool> batch_ok;  // (pipeline, input sizes) -> batchable
   std::mutex mu;
+  std::mutex clone_mu;  // the slots' pipeline copies (the worker and hp_server_prepare)
   std::condition_variable cv_done, cv_work;
   std::thread worker;
   bool stop = false;
-  unsigned long long next_ticket = 1, submitted = 0, completed = 0, failed = 0, batched = 0;
+  unsigned long long next_ticket = 1, submitted = 0, completed = 0, failed = 0, batched = 0, admissions = 0;
+  unsigned long long device_requests = 0, evictions = 0;
   double mpix = 0;
   Clock::time_point t_first, t_last;
   bool any = false;
@@ -90,38 +117,102 @@ struct hp_server {
 
 namespace {
 
-// Footprint of one request: every input and the output, packed.
-long long request_bytes(const Request& r) {
+long long buffer_bytes(const hp_buffer& x) { return r256((long long)x.width * dtype_size(x.dtype)) * x.height * x.channels; }
+
+// Staging footprint of `batch` requests of r's shape: every input and the
+// output, packed.
+long long staging_bytes(const Request& r, int batch) {
   long long b = 0;
-  for (const hp_buffer& x : r.in) b += r256((long long)x.width * dtype_size(x.dtype)) * x.height * x.channels;
-  b += r256((long long)r.out.width * dtype_size(r.out.dtype)) * r.out.height * r.out.channels;
-  return b + 256 * (long long)(r.in.size() + 1);
+  for (const hp_buffer& x : r.in) b += r256(buffer_bytes(x) * batch);
+  return b + r256(buffer_bytes(r.out) * batch);
 }
 
 bool same_shape(const Request& a, const Request& b) {
-  if (a.p != b.p || a.in.size() != b.in.size()) return false;
+  if (a.p != b.p || a.device != b.device || a.in.size() != b.in.size()) return false;
   for (size_t i = 0; i < a.in.size(); ++i)
-    if (a.in[i].width != b.in[i].width || a.in[i].height != b.in[i].height || a.in[i].dtype != b.in[i].dtype)
+    if (a.in[i].width != b.in[i].width || a.in[i].height != b.in[i].height || a.in[i].dtype != b.in[i].dtype ||
+        a.in[i].channels != b.in[i].channels)
       return false;
-  return a.out.width == b.out.width && a.out.height == b.out.height;
+  return a.out.width == b.out.width && a.out.height == b.out.height && a.out.channels == b.out.channels &&
+         a.out.dtype == b.out.dtype;
 }
 
+ShapeKey shape_key(const Request& r, int batch) {
+  ShapeKey k{(long long)(uintptr_t)r.p, batch, r.device ? 1 : 0};
+  for (const hp_buffer& b : r.in) k.insert(k.end(), {b.width, b.height, b.channels, b.dtype});
+  k.insert(k.end(), {r.out.width, r.out.height, r.out.channels, r.out.dtype});
+  return k;
+}
+
+// The slot's copy of p for batches of `batch` (made on first use); the caller
+// holds clone_mu.
 hp_pipeline* slot_clone(Slot& sl, hp_pipeline* p, int batch) {
   auto key = std::make_pair(p, batch);
   auto it = sl.clones.find(key);
   if (it != sl.clones.end()) return it->second;
   hp_pipeline* c = hp::clone_pipeline(p, batch);
+  if (c) hp_set_option(c, HP_OPT_CUDA_GRAPH, 1);  // a slot's realize of a shape replays as a graph
   sl.clones[key] = c;
   return c;
 }
 
-// Device layout of a batch: for each input i, B stacked images of C_i planes;
-// then the output, B stacked images.  Row stride is the packed width rounded
-// to 16 bytes.
+// Whether requests of r's pipeline and input sizes may share a realize
+// (computed once per pipeline and sizes; called with the server lock held).
+bool batchable(hp_server* s, const Request& r) {
+  std::vector<long long> k{(long long)(uintptr_t)r.p};
+  std::vector<int> ws, hs;
+  for (const hp_buffer& b : r.in) {
+    k.push_back(b.width);
+    k.push_back(b.height);
+    ws.push_back(b.width);
+    hs.push_back(b.height);
+  }
+  auto it = s->batch_ok.find(k);
+  if (it != s->batch_ok.end()) return it->second;
+  const bool ok = hp::pipeline_batch_ok(r.p, ws.data(), hs.data(), (int)ws.size(), 2);
+  s->batch_ok[k] = ok;
+  return ok;
+}
+
+// Gives back the least recently used staging region of an idle slot; false
+// when there is none.
+bool evict_one(hp_server* s) {
+  Slot* best_slot = nullptr;
+  std::map<ShapeKey, Resident>::iterator best;
+  for (Slot& sl : s->slots) {
+    if (sl.busy) continue;
+    for (auto it = sl.resident.begin(); it != sl.resident.end(); ++it)
+      if (!best_slot || it->second.last < best->second.last) {
+        best_slot = &sl;
+        best = it;
+      }
+  }
+  if (!best_slot) return false;
+  s->arena.release(best->second.off, best->second.bytes);
+  best_slot->resident.erase(best);
+  ++s->evictions;
+  return true;
+}
+
+// Device layout of a batch (staged): for each input i, B stacked images of C_i
+// planes; then the output, B stacked images.  Row stride is the packed width
+// rounded to 16 bytes.  A device request served alone runs in place.
 hp_status launch_batch(hp_server* s, Slot& sl) {
   const int B = (int)sl.batch.size();
   const Request& r0 = *sl.batch[0];
-  char* dev = s->arena.base + sl.off;
+  cudaStream_t st = sl.stream;
+  std::lock_guard<std::mutex> ck(s->clone_mu);  // hp_server_prepare may touch this slot's copies
+  hp_pipeline* p = slot_clone(sl, r0.p, B);
+  if (!p) return hp::report_error(HP_ERR_INVALID_ARG, "server: pipeline cannot be copied");
+  if (!sl.cur) {  // a device request alone: its own buffers
+    hp_status rs = hp_realize(p, r0.in.data(), (int)r0.in.size(), &r0.out, st);
+    if (rs) return rs;
+    if (cudaEventRecord(sl.done, st)) return hp::report_error(HP_ERR_CUDA, "server: event record failed");
+    return HP_OK;
+  }
+  const cudaMemcpyKind to_dev = r0.device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const cudaMemcpyKind from_dev = r0.device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  char* dev = s->arena.base + sl.cur->off;
   std::vector<hp_buffer> din(r0.in.size());
   long long pos = 0;
   for (size_t i = 0; i < r0.in.size(); ++i) {
@@ -139,7 +230,6 @@ hp_status launch_batch(hp_server* s, Slot& sl) {
   dout.row_stride_bytes = (((long long)r0.out.width * dtype_size(r0.out.dtype)) + 15) / 16 * 16;
   dout.plane_stride_bytes = dout.row_stride_bytes * r0.out.height;
   dout.channels = r0.out.channels * B;
-  cudaStream_t st = sl.stream;
   for (int j = 0; j < B; ++j) {
     const Request& r = *sl.batch[j];
     for (size_t i = 0; i < r.in.size(); ++i) {
@@ -148,13 +238,11 @@ hp_status launch_batch(hp_server* s, Slot& sl) {
         char* dst = (char*)din[i].data + (long long)(j * h.channels + c) * din[i].plane_stride_bytes;
         const char* src = (const char*)h.data + (long long)c * h.plane_stride_bytes;
         if (cudaMemcpy2DAsync(dst, din[i].row_stride_bytes, src, h.row_stride_bytes,
-                              (size_t)h.width * dtype_size(h.dtype), h.height, cudaMemcpyHostToDevice, st))
-          return hp::report_error(HP_ERR_CUDA, "server: host-to-device copy failed");
+                              (size_t)h.width * dtype_size(h.dtype), h.height, to_dev, st))
+          return hp::report_error(HP_ERR_CUDA, "server: copy of an input into staging failed");
       }
     }
   }
-  hp_pipeline* p = slot_clone(sl, r0.p, B);
-  if (!p) return hp::report_error(HP_ERR_INVALID_ARG, "server: pipeline cannot be batched");
   hp_status rs = hp_realize(p, din.data(), (int)din.size(), &dout, st);
   if (rs) return rs;
   for (int j = 0; j < B; ++j) {
@@ -163,8 +251,8 @@ hp_status launch_batch(hp_server* s, Slot& sl) {
       const char* src = (const char*)dout.data + (long long)(j * h.channels + c) * dout.plane_stride_bytes;
       char* dst = (char*)h.data + (long long)c * h.plane_stride_bytes;
       if (cudaMemcpy2DAsync(dst, h.row_stride_bytes, src, dout.row_stride_bytes, (size_t)h.width * dtype_size(h.dtype),
-                            h.height, cudaMemcpyDeviceToHost, st))
-        return hp::report_error(HP_ERR_CUDA, "server: device-to-host copy failed");
+                            h.height, from_dev, st))
+        return hp::report_error(HP_ERR_CUDA, "server: copy of an output from staging failed");
     }
   }
   if (cudaEventRecord(sl.done, st)) return hp::report_error(HP_ERR_CUDA, "server: event record failed");
@@ -187,9 +275,67 @@ void finish_slot(hp_server* s, Slot& sl, hp_status st) {
   }
   if (sl.batch.size() > 1) ++s->batched;
   sl.batch.clear();
-  s->arena.release(sl.off, sl.bytes);
+  sl.cur = nullptr;  // the staging region stays resident for the next request of its shape
   sl.busy = false;
   s->t_last = now;
+}
+
+// Admits the request at the head of the queue (with the same-shape requests
+// that may join it) onto a free slot; returns the slot, or null when no slot
+// or memory is free (the request stays queued).  Called with the lock held.
+Slot* admit(hp_server* s) {
+  Request* head = s->queue.front();
+  std::vector<size_t> pick{0};
+  if (s->max_batch > 1 && batchable(s, *head)) {
+    for (size_t i = 1; i < s->queue.size() && (int)pick.size() < s->max_batch && i < 64; ++i)
+      if (same_shape(*head, *s->queue[i])) pick.push_back(i);
+  }
+  while (true) {
+    const int B = (int)pick.size();
+    const ShapeKey key = shape_key(*head, B);
+    const bool staged = !(head->device && B == 1);
+    // a free slot, preferably one that keeps this shape resident
+    Slot* slot = nullptr;
+    for (Slot& sl : s->slots) {
+      if (sl.busy) continue;
+      if (!slot) slot = &sl;
+      if (staged && sl.resident.count(key)) {
+        slot = &sl;
+        break;
+      }
+    }
+    if (!slot) return nullptr;
+    Resident* region = nullptr;
+    if (staged) {
+      auto it = slot->resident.find(key);
+      if (it != slot->resident.end()) {
+        region = &it->second;
+      } else {
+        const long long bytes = staging_bytes(*head, B);
+        long long off = 0;
+        bool ok = s->arena.alloc(bytes, &off);
+        while (!ok && evict_one(s)) ok = s->arena.alloc(bytes, &off);
+        if (!ok) {
+          if (B > 1) {  // the head alone may still fit
+            pick.resize(1);
+            continue;
+          }
+          return nullptr;
+        }
+        Resident& r = slot->resident[key];
+        r.off = off;
+        r.bytes = bytes;
+        region = &r;
+      }
+      region->last = ++s->admissions;
+    }
+    slot->batch.clear();
+    for (size_t i : pick) slot->batch.push_back(s->queue[i]);
+    for (size_t k = pick.size(); k-- > 0;) s->queue.erase(s->queue.begin() + pick[k]);
+    slot->cur = region;
+    slot->busy = true;
+    return slot;
+  }
 }
 
 void worker_loop(hp_server* s) {
@@ -199,52 +345,27 @@ void worker_loop(hp_server* s) {
     bool progress = false;
     // completions
     for (Slot& sl : s->slots) {
-      if (!sl.busy) continue;
+      if (!sl.busy || sl.batch.empty()) continue;
       cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       finish_slot(s, sl, q == cudaSuccess ? HP_OK : HP_ERR_CUDA);
       progress = true;
     }
     if (progress) s->cv_done.notify_all();
-    // admissions, in arrival order
+    // admissions, in arrival order; the copies and launches are enqueued
+    // without the lock, so submitters and waiters are not held up
     while (!s->queue.empty()) {
-      Slot* free_slot = nullptr;
-      for (Slot& sl : s->slots)
-        if (!sl.busy) {
-          free_slot = &sl;
-          break;
-        }
-      if (!free_slot) break;
-      Request* head = s->queue.front();
-      std::vector<size_t> pick{0};
-      if (s->max_batch > 1 && hp::pipeline_stackable(head->p)) {
-        for (size_t i = 1; i < s->queue.size() && (int)pick.size() < s->max_batch && i < 64; ++i)
-          if (same_shape(*head, *s->queue[i])) pick.push_back(i);
-      }
-      long long bytes = 0;
-      for (size_t i : pick) bytes += request_bytes(*s->queue[i]);
-      long long off = 0;
-      if (!s->arena.alloc(bytes, &off)) {
-        if (pick.size() > 1) {  // try the head alone before waiting for memory
-          pick.resize(1);
-          bytes = request_bytes(*head);
-          if (!s->arena.alloc(bytes, &off)) break;
-        } else {
-          break;
-        }
-      }
-      Slot& sl = *free_slot;
-      sl.batch.clear();
-      for (size_t i : pick) sl.batch.push_back(s->queue[i]);
-      for (size_t k = pick.size(); k-- > 0;) s->queue.erase(s->queue.begin() + pick[k]);
-      sl.off = off;
-      sl.bytes = bytes;
-      sl.busy = true;
-      hp_status st = launch_batch(s, sl);
+      Slot* sl = admit(s);
+      if (!sl) break;
+      lk.unlock();
+      hp_status st = launch_batch(s, *sl);
       if (st) {
-        cudaStreamSynchronize(sl.stream);
+        cudaStreamSynchronize(sl->stream);
         cudaGetLastError();
-        finish_slot(s, sl, st);
+      }
+      lk.lock();
+      if (st) {
+        finish_slot(s, *sl, st);
         s->cv_done.notify_all();
       }
       progress = true;
@@ -257,6 +378,43 @@ void worker_loop(hp_server* s) {
       s->cv_work.wait_for(lk, std::chrono::microseconds(idle ? 2000 : 20));
     }
   }
+}
+
+hp_status submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output,
+                 unsigned long long* ticket, bool device) {
+  if (!s || !p || !inputs || n_inputs < 1 || n_inputs > 16 || !output || !ticket)
+    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: bad arguments");
+  auto* r = new Request();
+  r->p = p;
+  r->device = device;
+  r->in.assign(inputs, inputs + n_inputs);
+  r->out = *output;
+  for (const hp_buffer& b : r->in)
+    if (!b.data || b.width < 1 || b.height < 1 || b.channels < 1) {
+      delete r;
+      return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty input buffer");
+    }
+  if (!r->out.data || r->out.width < 1 || r->out.height < 1 || r->out.channels < 1) {
+    delete r;
+    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty output buffer");
+  }
+  if (staging_bytes(*r, 1) > s->arena.size) {
+    delete r;
+    return hp::report_error(HP_ERR_OOM, "hp_server_submit: request larger than the whole HBM budget");
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->t_submit = Clock::now();
+  if (!s->any) {
+    s->t_first = r->t_submit;
+    s->any = true;
+  }
+  r->ticket = s->next_ticket++;
+  *ticket = r->ticket;
+  ++s->submitted;
+  if (device) ++s->device_requests;
+  s->queue.push_back(r);
+  s->cv_work.notify_one();
+  return HP_OK;
 }
 
 }  // namespace
@@ -300,37 +458,12 @@ hp_status hp_server_create(hp_server** out, long long hbm_budget_bytes, int slot
 
 hp_status hp_server_submit(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
                            const hp_buffer* output, unsigned long long* ticket) {
-  if (!s || !p || !inputs || n_inputs < 1 || n_inputs > 16 || !output || !ticket)
-    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: bad arguments");
-  auto* r = new Request();
-  r->p = p;
-  r->in.assign(inputs, inputs + n_inputs);
-  r->out = *output;
-  for (const hp_buffer& b : r->in)
-    if (!b.data || b.width < 1 || b.height < 1) {
-      delete r;
-      return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty input buffer");
-    }
-  if (!r->out.data || r->out.width < 1 || r->out.height < 1 || r->out.channels < 1) {
-    delete r;
-    return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_submit: empty output buffer");
-  }
-  if (request_bytes(*r) > s->arena.size) {
-    delete r;
-    return hp::report_error(HP_ERR_OOM, "hp_server_submit: request larger than the whole HBM budget");
-  }
-  std::lock_guard<std::mutex> lk(s->mu);
-  r->t_submit = Clock::now();
-  if (!s->any) {
-    s->t_first = r->t_submit;
-    s->any = true;
-  }
-  r->ticket = s->next_ticket++;
-  *ticket = r->ticket;
-  ++s->submitted;
-  s->queue.push_back(r);
-  s->cv_work.notify_one();
-  return HP_OK;
+  return submit(s, p, inputs, n_inputs, output, ticket, false);
+}
+
+hp_status hp_server_submit_device(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                                  const hp_buffer* output, unsigned long long* ticket) {
+  return submit(s, p, inputs, n_inputs, output, ticket, true);
 }
 
 hp_status hp_server_wait(hp_server* s, unsigned long long ticket, int timeout_ms, double* latency_us) {
@@ -358,6 +491,15 @@ hp_status hp_server_stats_get(hp_server* s, hp_server_stats* st) {
   st->batched_launches = s->batched;
   st->peak_bytes = (unsigned long long)s->arena.peak;
   st->mpix = s->mpix;
+  st->device_requests = s->device_requests;
+  st->evictions = s->evictions;
+  {
+    std::lock_guard<std::mutex> ck(s->clone_mu);
+    for (Slot& sl : s->slots) {
+      for (auto& kv : sl.clones) st->graph_replays += hp::pipeline_graph_replays(kv.second);
+      for (auto& kv : sl.resident) st->resident_bytes += (unsigned long long)kv.second.bytes;
+    }
+  }
   if (s->any) st->busy_s = std::chrono::duration<double>(s->t_last - s->t_first).count();
   if (!s->latencies.empty()) {
     std::vector<double> v = s->latencies;
@@ -381,7 +523,7 @@ hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* input
     ws[i] = inputs[i].width;
     hs[i] = inputs[i].height;
   }
-  std::lock_guard<std::mutex> lk(s->mu);  // the worker touches slot copies only under the lock
+  std::lock_guard<std::mutex> ck(s->clone_mu);  // the worker realizes the slots' copies under this lock
   for (Slot& sl : s->slots) {
     hp_pipeline* c = slot_clone(sl, p, 1);
     if (!c) return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: pipeline cannot be copied");
@@ -400,6 +542,7 @@ hp_status hp_server_destroy(hp_server* s) {
   }
   s->worker.join();
   for (Slot& sl : s->slots) {
+    cudaStreamSynchronize(sl.stream);
     for (auto& kv : sl.clones) hp_pipeline_destroy(kv.second);
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);

@@ -70,14 +70,17 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong),
                 ("batched_launches", ctypes.c_ulonglong), ("peak_bytes", ctypes.c_ulonglong),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double),
-                ("max_us", ctypes.c_double), ("mpix", ctypes.c_double), ("busy_s", ctypes.c_double)]
+                ("max_us", ctypes.c_double), ("mpix", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("graph_replays", ctypes.c_ulonglong), ("resident_bytes", ctypes.c_ulonglong),
+                ("device_requests", ctypes.c_ulonglong), ("evictions", ctypes.c_ulonglong)]
 
 
 EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_set", "hp_realize",
            "hp_realize_host", "hp_group_info_get", "hp_group_count", "hp_infer_bounds", "hp_set_option", "hp_check_device_error",
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
            "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy",
-           "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak", "hp_kernel_attrs_get"]
+           "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak", "hp_kernel_attrs_get",
+           "hp_server_submit_device"]
 
 _lib = None
 
@@ -107,6 +110,8 @@ def lib():
         L.hp_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_longlong, ctypes.c_int, ctypes.c_int]
         L.hp_server_submit.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer),
                                        ctypes.POINTER(ctypes.c_ulonglong)]
+        L.hp_server_submit_device.argtypes = [P, P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer),
+                                              ctypes.POINTER(ctypes.c_ulonglong)]
         L.hp_server_wait.argtypes = [P, ctypes.c_ulonglong, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         L.hp_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
         L.hp_server_destroy.argtypes = [P]
@@ -301,8 +306,9 @@ class Pipeline:
 
 
 class Server:
-    """Continuous-batching serving loop (hp_server_*): submit host-buffer
-    requests for any pipeline; they run as slots and HBM budget allow."""
+    """Continuous-batching serving loop (hp_server_*): submit host-buffer (or
+    device-buffer) requests for any pipeline; they run as slots and HBM budget
+    allow."""
 
     def __init__(self, hbm_budget_bytes: int, slots: int = 4, max_batch: int = 8):
         self.h = ctypes.c_void_p()
@@ -313,6 +319,14 @@ class Server:
         arr = (Buffer * len(inputs))(*inputs)
         t = ctypes.c_ulonglong()
         check(lib().hp_server_submit(self.h, pipeline.h, arr, len(inputs), ctypes.byref(output), ctypes.byref(t)))
+        return t.value
+
+    def submit_device(self, pipeline: "Pipeline", inputs, output) -> int:
+        """A request whose buffers are in device memory (no host copies)."""
+        arr = (Buffer * len(inputs))(*inputs)
+        t = ctypes.c_ulonglong()
+        check(lib().hp_server_submit_device(self.h, pipeline.h, arr, len(inputs), ctypes.byref(output),
+                                            ctypes.byref(t)))
         return t.value
 
     def prepare(self, pipeline: "Pipeline", inputs):
