@@ -2113,6 +2113,22 @@ hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch);
 // Whether `batch` images of these input sizes can be realized by one call of a
 // batched copy of p: a stackable pipeline always; otherwise its lowering for
 // the sizes must put every group on a batch-aware kernel.
+// Size, channels and storage type of p's output for these input sizes (one image).
+hp_status pipeline_output_shape(hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int* w, int* h,
+                                int* channels, int* dtype) {
+  std::vector<Dom> in_dom;
+  for (int i = 0; i < n_inputs; ++i) in_dom.push_back(Dom{widths[i], heights[i]});
+  Plan* plan = nullptr;
+  hp_status st = get_plan(p, in_dom, &plan);
+  if (st) return st;
+  const Stage& os = p->stages[p->output];
+  *w = plan->dom[p->output].w;
+  *h = plan->dom[p->output].h;
+  *channels = os.channels;
+  *dtype = os.storage;
+  return HP_OK;
+}
+
 bool pipeline_batch_ok(const hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int batch) {
   if (batch <= 1 || pipeline_stackable(p)) return true;
   hp_pipeline* c = clone_pipeline(p, batch);

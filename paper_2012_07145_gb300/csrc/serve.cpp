@@ -50,6 +50,8 @@ namespace hp {
 hp_pipeline* clone_pipeline(const hp_pipeline* p, int batch);
 bool pipeline_batch_ok(const hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int batch);
 unsigned long long pipeline_graph_replays(const hp_pipeline* p);
+hp_status pipeline_output_shape(hp_pipeline* p, const int* widths, const int* heights, int n_inputs, int* w, int* h,
+                                int* channels, int* dtype);
 }  // namespace hp
 
 namespace {
@@ -194,9 +196,31 @@ bool evict_one(hp_server* s) {
   return true;
 }
 
-// Device layout of a batch (staged): for each input i, B stacked images of C_i
-// planes; then the output, B stacked images.  Row stride is the packed width
-// rounded to 16 bytes.  A device request served alone runs in place.
+// Device layout of a batch in its staging region: for each input i, B stacked
+// images of C_i planes; then the output, B stacked images.  Row stride is the
+// packed width rounded to 16 bytes.
+void staging_layout(char* dev, const Request& r0, int B, std::vector<hp_buffer>& din, hp_buffer& dout) {
+  din.resize(r0.in.size());
+  long long pos = 0;
+  for (size_t i = 0; i < r0.in.size(); ++i) {
+    const hp_buffer& h = r0.in[i];
+    hp_buffer d = h;
+    d.data = dev + pos;
+    d.row_stride_bytes = (((long long)h.width * dtype_size(h.dtype)) + 15) / 16 * 16;
+    d.plane_stride_bytes = d.row_stride_bytes * h.height;
+    d.channels = h.channels * B;
+    din[i] = d;
+    pos += r256(d.plane_stride_bytes * d.channels);
+  }
+  dout = r0.out;
+  dout.data = dev + pos;
+  dout.row_stride_bytes = (((long long)r0.out.width * dtype_size(r0.out.dtype)) + 15) / 16 * 16;
+  dout.plane_stride_bytes = dout.row_stride_bytes * r0.out.height;
+  dout.channels = r0.out.channels * B;
+}
+
+// Runs a staged batch: copies in, the realize, copies out.  A device request
+// served alone runs in place.
 hp_status launch_batch(hp_server* s, Slot& sl) {
   const int B = (int)sl.batch.size();
   const Request& r0 = *sl.batch[0];
@@ -212,24 +236,9 @@ hp_status launch_batch(hp_server* s, Slot& sl) {
   }
   const cudaMemcpyKind to_dev = r0.device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const cudaMemcpyKind from_dev = r0.device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  char* dev = s->arena.base + sl.cur->off;
-  std::vector<hp_buffer> din(r0.in.size());
-  long long pos = 0;
-  for (size_t i = 0; i < r0.in.size(); ++i) {
-    const hp_buffer& h = r0.in[i];
-    hp_buffer d = h;
-    d.data = dev + pos;
-    d.row_stride_bytes = (((long long)h.width * dtype_size(h.dtype)) + 15) / 16 * 16;
-    d.plane_stride_bytes = d.row_stride_bytes * h.height;
-    d.channels = h.channels * B;
-    din[i] = d;
-    pos += r256(d.plane_stride_bytes * d.channels);
-  }
-  hp_buffer dout = r0.out;
-  dout.data = dev + pos;
-  dout.row_stride_bytes = (((long long)r0.out.width * dtype_size(r0.out.dtype)) + 15) / 16 * 16;
-  dout.plane_stride_bytes = dout.row_stride_bytes * r0.out.height;
-  dout.channels = r0.out.channels * B;
+  std::vector<hp_buffer> din;
+  hp_buffer dout;
+  staging_layout(s->arena.base + sl.cur->off, r0, B, din, dout);
   for (int j = 0; j < B; ++j) {
     const Request& r = *sl.batch[j];
     for (size_t i = 0; i < r.in.size(); ++i) {
@@ -523,11 +532,54 @@ hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* input
     ws[i] = inputs[i].width;
     hs[i] = inputs[i].height;
   }
+  // the shape of a single host request with these inputs
+  Request r;
+  r.p = p;
+  r.in.assign(inputs, inputs + n_inputs);
+  int ow = 0, oh = 0, oc = 0, odt = 0;
+  hp_status st = hp::pipeline_output_shape(p, ws.data(), hs.data(), n_inputs, &ow, &oh, &oc, &odt);
+  if (st) return st;
+  r.out = hp_buffer{nullptr, (hp_dtype)odt, oc, ow, oh, 0, 0};
+  const ShapeKey key = shape_key(r, 1);
   std::lock_guard<std::mutex> ck(s->clone_mu);  // the worker realizes the slots' copies under this lock
   for (Slot& sl : s->slots) {
     hp_pipeline* c = slot_clone(sl, p, 1);
     if (!c) return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: pipeline cannot be copied");
-    hp_status st = hp_prepare(c, ws.data(), hs.data(), n_inputs, sl.stream);
+    if ((st = hp_prepare(c, ws.data(), hs.data(), n_inputs, sl.stream))) return st;
+    // the slot's staging region for this shape, resident from now on, and the
+    // graph of its realize on it (two realizes: the first runs, the second
+    // captures), so the first request of the shape already replays a graph;
+    // an idle slot only (a busy one may be using its regions)
+    Resident* region = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (sl.busy) continue;
+      auto it = sl.resident.find(key);
+      if (it == sl.resident.end()) {
+        long long off = 0;
+        const long long bytes = staging_bytes(r, 1);
+        if (!s->arena.alloc(bytes, &off)) continue;  // no room: the shape becomes resident on first use
+        Resident& nr = sl.resident[key];
+        nr.off = off;
+        nr.bytes = bytes;
+        it = sl.resident.find(key);
+      }
+      it->second.last = ++s->admissions;
+      region = &it->second;
+      sl.busy = true;  // the worker leaves the slot alone meanwhile
+    }
+    std::vector<hp_buffer> din;
+    hp_buffer dout;
+    staging_layout(s->arena.base + region->off, r, 1, din, dout);
+    for (int k = 0; k < 2 && !st; ++k) st = hp_realize(c, din.data(), n_inputs, &dout, sl.stream);
+    if (!st && cudaStreamSynchronize(sl.stream) != cudaSuccess) {
+      cudaGetLastError();
+      st = hp::report_error(HP_ERR_CUDA, "hp_server_prepare: realize on the staging region failed");
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      sl.busy = false;
+    }
     if (st) return st;
   }
   return HP_OK;
