@@ -916,11 +916,12 @@ def serve_rate(kinds, bufs, ring, lam, n, rng, device=False):
                 time.sleep((due - now) - 1e-4)
         key = (name, h, w)
         tickets.append(submit(bufs[key][0], [bi_of(key)], bo_of(key, i)))
-    lats = []
-    for t in tickets:
+    lats, per = [], []
+    for t, (name, h, w) in zip(tickets, picks):
         st, lat = srv.wait(t, 300000)
         if st == hp.HP_OK:
             lats.append(lat)
+            per.append((lat, name, h, w))
     t1 = time.perf_counter()
     stats = srv.stats()
     srv.close()
@@ -931,7 +932,8 @@ def serve_rate(kinds, bufs, ring, lam, n, rng, device=False):
             "mpix_per_s": round(mpix / (t1 - t0), 1),
             "batched_launches": int(stats.batched_launches - base.batched_launches),
             "graph_replays": int(stats.graph_replays - base.graph_replays),
-            "peak_hbm_bytes": int(stats.peak_bytes)}
+            "peak_hbm_bytes": int(stats.peak_bytes),
+            "slowest": [f"{n} {w}x{h} {l / 1e3:.2f} ms" for l, n, h, w in sorted(per, reverse=True)[:4]]}
 
 
 def serving_compact(rate=1000.0, requests=300):

@@ -58,6 +58,8 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+constexpr long long kBatchBytesMax = 32LL << 20;  // largest single request (inputs + output) that is batched
+
 int dtype_size(int d) { return d == HP_U8 ? 1 : (d == HP_U16 || d == HP_F16 || d == HP_BF16) ? 2 : 4; }
 using hp::Arena;
 long long r256(long long v) { return hp::round256(v); }
@@ -295,7 +297,10 @@ void finish_slot(hp_server* s, Slot& sl, hp_status st) {
 Slot* admit(hp_server* s) {
   Request* head = s->queue.front();
   std::vector<size_t> pick{0};
-  if (s->max_batch > 1 && batchable(s, *head)) {
+  // only requests of modest size are batched: a large request already fills
+  // the GPU on its own, and a batch would make each request wait for every
+  // other one's copies
+  if (s->max_batch > 1 && staging_bytes(*head, 1) <= kBatchBytesMax && batchable(s, *head)) {
     for (size_t i = 1; i < s->queue.size() && (int)pick.size() < s->max_batch && i < 64; ++i)
       if (same_shape(*head, *s->queue[i])) pick.push_back(i);
   }
