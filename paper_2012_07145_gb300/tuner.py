@@ -15,7 +15,9 @@ sequence, not a compile.  The candidate spaces follow Sec. 4.1-4.3:
     rows per run and threads,
 
 pruned by the rules of Sec. 4.6: hardware limits (shared memory per block,
-threads), too few blocks to keep every SM busy (fewer than 2 x SMs, Sec. 4.3),
+threads), too few blocks to keep the SMs busy (fewer than half the SMs, Sec.
+4.3; small images that live in L2 still gain from larger tiles than 2 x SMs
+blocks would allow),
 thread counts that leave most threads idle, and kernels that spill registers
 to local memory (measured: the library reports the register and local-memory
 figures of the kernels a realize launched).  Every timed candidate's output is
@@ -103,8 +105,8 @@ def chain_candidates(n_stages, W, H, quick=False, esize=4):
         if chain_smem_bytes(d, tw, th) > SMEM_LIMIT:
             continue                                   # hardware limit
         blocks = -(-W // tw) * -(-H // th)
-        if blocks < 2 * SMS and (tw > 32 or th > 16):
-            continue                                   # leaves SMs idle
+        if blocks < SMS // 2 and (tw > 32 or th > 16):
+            continue                                   # leaves most SMs idle
         items = (tw // 4) * -(-th // s)
         if items < t // 2:
             continue                                   # most threads idle in the last stage
