@@ -53,12 +53,15 @@ __host__ __device__ inline StripGeom strip_geom(int esize) {
 struct RowsParams {
   CUtensorMap tmap;
   HarrisArgs a;
-  int strips, units, rows;  // strips across the image; units = strips x row runs; rows per run
+  int strips, units, rows;  // strips across the image; units = strips x row runs x images; rows per run
 };
 
+// A run of output rows oy .. ye-1 of one strip of one image.  Input rows are
+// read from y0 = max(oy - 2, 0): n_steps steps in all, of which the first n_in
+// read a row inside the image.
 struct Unit {
-  int x0, oy, n_in, nbox;  // x0: image column of lane 0's first column; n_in input rows from oy - 2
-  int img;                 // image of a batch (input planes 3 img .. 3 img + 2, output plane img)
+  int x0, oy, ye, y0, n_steps, n_in, nbox;  // x0: image column of lane 0's first column
+  int img;                                  // image of a batch (input planes 3 img .. 3 img + 2, output plane img)
 };
 
 __device__ __forceinline__ Unit unit_geom(const RowsParams& kp, const StripGeom& g, int u) {
@@ -67,61 +70,49 @@ __device__ __forceinline__ Unit unit_geom(const RowsParams& kp, const StripGeom&
   U.img = u / per_img;
   u -= U.img * per_img;
   const int s = u % kp.strips, r = u / kp.strips;
+  const int H = kp.a.in.h;
   U.x0 = s * g.strip_w - 4 * g.halo_lanes;
   U.oy = r * kp.rows;
-  U.n_in = min(kp.rows, kp.a.out.h - U.oy) + 4;
+  U.ye = min(U.oy + kp.rows, kp.a.out.h);
+  U.y0 = max(U.oy - 2, 0);
+  U.n_steps = U.ye - U.y0 + 2;
+  U.n_in = min(U.y0 + U.n_steps, H) - U.y0;
   U.nbox = (U.n_in + kBoxRows - 1) / kBoxRows;
   return U;
 }
 
-// The warp's ring: boxes are numbered in issue order (which is also the order
-// of use); box q lives in slot q % kRing and completes phase (q / kRing) & 1
-// of that slot's mbarrier.
-struct Ring {
-  unsigned char* slots;
-  uint64_t* bars;
-  unsigned issued, released;
-  int iu, ij;   // next box to issue: unit and box within the unit
-  Unit IU;      // geometry of unit iu
-};
-
-__device__ __forceinline__ void issue_one(const RowsParams& kp, const StripGeom& g, Ring& R, int stride, int lane) {
-  if (R.iu >= kp.units) return;
-  if (lane == 0) {
-    const int s = R.issued % kRing;
-    mbar_arrive_expect_tx(R.bars + s, (unsigned)g.slot_bytes);
-    tma_load_3d(R.slots + s * g.slot_bytes, &kp.tmap, R.IU.x0, R.IU.oy - 2 + R.ij * kBoxRows, 3 * R.IU.img,
-                R.bars + s);
-  }
-  ++R.issued;
-  if (++R.ij == R.IU.nbox) {
-    R.ij = 0;
-    R.iu += stride;
-    if (R.iu < kp.units) R.IU = unit_geom(kp, g, R.iu);
-  }
+// Issues box j of unit U (input rows y0 + 2j, y0 + 2j + 1 of its image's three
+// planes) into ring slot q % kRing.  Called by one lane; the fence orders the
+// warp's earlier reads of the slot before the copy that overwrites it.
+__device__ __forceinline__ void issue_box(const CUtensorMap* tmap, unsigned char* slots, uint64_t* bars,
+                                          int slot_bytes, unsigned q, const Unit& U, int j) {
+  const int s = q % kRing;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bars + s, (unsigned)slot_bytes);
+  tma_load_3d(slots + s * slot_bytes, tmap, U.x0, U.y0 + j * kBoxRows, 3 * U.img, bars + s);
 }
 
-// Left and right neighbours of the lane's four columns for a 3-tap x pass,
-// with the boundary condition of the stage they belong to: the neighbour
-// outside the image is the edge column itself.  Column 0 always sits first in
-// a lane (strips start on multiples of 4); column W - 1 may sit anywhere.
+// Left and right neighbours of the lane's four columns for a 3-tap x pass.  In
+// a strip past an image edge (HE), the neighbour outside the image is the edge
+// column itself (column 0 always sits first in a lane: strips start on
+// multiples of 4; column W - 1 may sit anywhere).
 struct Edges {
   bool left;      // the lane's first column is column 0
   bool right[4];  // column k of the lane is column W - 1
 };
 
+template <bool HE>
 __device__ __forceinline__ void neighbours(const float (&v)[4], const Edges& e, float (&l)[4], float (&r)[4]) {
   const float up = __shfl_up_sync(kFull, v[3], 1), dn = __shfl_down_sync(kFull, v[0], 1);
-  l[0] = e.left ? v[0] : up;
+  l[0] = HE && e.left ? v[0] : up;
   l[1] = v[0];
   l[2] = v[1];
   l[3] = v[2];
-  r[0] = e.right[0] ? v[0] : v[1];
-  r[1] = e.right[1] ? v[1] : v[2];
-  r[2] = e.right[2] ? v[2] : v[3];
-  r[3] = e.right[3] ? v[3] : dn;
+  r[0] = HE && e.right[0] ? v[0] : v[1];
+  r[1] = HE && e.right[1] ? v[1] : v[2];
+  r[2] = HE && e.right[2] ? v[2] : v[3];
+  r[3] = HE && e.right[3] ? v[3] : dn;
 }
-
 
 // The stencil weights of the five 3x3 stages (x taps then y taps, in the
 // order Ix, Iy, Sxx, Syy, Sxy).  With SPEC the weights are the Sobel and box
@@ -214,76 +205,54 @@ __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (
   }
 }
 
-// One run of rows of one strip.  Rows are numbered from the first input row
-// (image row oy - 2): step t reads input row t, forms gradient/product row t - 1
-// (from t >= 2) and emits output row t - 2 (from t >= 4).  Windows are indexed
-// by row mod 3, so a loop unrolled three times keeps them in fixed registers.
+// One run of rows of one strip.  Step t reads input row r = y0 + t: gray row
+// r and its two x passes; the Sobel y passes complete gradient row r - 1, whose
+// products and box-sum x passes follow; the box y passes complete output row
+// r - 2.  Every 3-tap y pass keeps two partial sums per column instead of a
+// window of rows: when row i's x pass x arrives, output row i - 1 takes its
+// last tap, row i its middle one, and row i + 1 starts -- the taps of each row
+// still applied oldest first, as tap3v applies them, so every value is the
+// same.  Partial sum j (j = 0: row i, 1: row i + 1, after the update) sits in
+// slot (j + t) & 1, so an update reads and writes one slot and a box of two
+// steps keeps fixed registers.  The stage values that a clamp may repeat below
+// the image (the newest x passes) are kept.
 template <int RND, int ODT, bool SPEC>
-struct StripRun {
-  const RowsParams& kp;
-  const StripGeom& g;
-  Ring& R;
-  const Unit U;
-  const int lane, stride, c0, esize;
+struct HarrisRun {
+  static constexpr int kODT = ODT;
+  const HarrisArgs& a;
   const Weights<SPEC> w;
+  float pA[2][4], pB[2][4];     // Sobel y partial sums (Ix, Iy)
+  float pS[3][2][4];            // box-sum y partial sums (xx, yy, xy)
+  float hA[4], hB[4];           // newest x passes of gray (Ix and Iy x-weights)
+  float hS[3][4];               // newest x passes of the products
   Edges e;
-  const bool vedge;          // the run reads rows outside the image
-  bool st_full, st_part;     // the lane stores four columns / some of its columns
-  char* out_row;             // the next output row
-  float hA[3][4], hB[3][4];  // x passes of gray with the Ix and Iy x-weights
-  float sm[3][3][4];         // x passes of the three products
-  unsigned q;                // box being read
-  int rr;                    // row within it
-  const unsigned char* slot;
+  int y0, H;
+  bool top;
+  float o[4];                   // the response row of the latest step
 
-  __device__ __forceinline__ StripRun(const RowsParams& kp_, const StripGeom& g_, Ring& R_, const Unit& U_, int lane_,
-                                      int stride_)
-      : kp(kp_), g(g_), R(R_), U(U_), lane(lane_), stride(stride_), c0(U_.x0 + 4 * lane_),
-        esize(kp_.a.in.dtype == HP_F32 ? 4 : 2), w(kp_.a.w), vedge(U_.oy < 2 || U_.oy + U_.n_in - 2 > kp_.a.in.h),
-        q(R_.released), rr(0), slot(nullptr) {
-    const int W = kp.a.in.w;
-    e.left = c0 == 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) e.right[k] = c0 + k == W - 1;
-    const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
-    st_full = mine && c0 + 3 < W && ODT != 3;
-    st_part = mine && c0 < W && !st_full;
-    out_row = (char*)kp.a.out.data + (long long)U.img * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
-  }
+  __device__ __forceinline__ HarrisRun(const HarrisArgs& a_) : a(a_), w(a_.w) {}
 
-  // Waits for box q (one lane polls, bounded), then the warp reads it.
-  __device__ __forceinline__ bool wait_box() {
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait_poll(R.bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
-    __syncwarp();
-    ok = __shfl_sync(kFull, ok, 0);
-    slot = R.slots + (q % kRing) * g.slot_bytes + lane * 4 * esize;
-    return ok != 0;
-  }
-
-  // Frees box q's slot for the box kRing later in issue order.
-  __device__ __forceinline__ void release_box() {
-    ++q;
-    __syncwarp();
-    R.released = q;
-    issue_one(kp, g, R, stride, lane);
-  }
-
-  // gray of input row r into window slot M, then both x passes.
-  template <int M>
-  __device__ __forceinline__ bool row_in(int r, bool edge) {
-    const HarrisArgs& a = kp.a;
-    if (rr == 0 && !wait_box()) return false;
-    const unsigned char* p = slot + rr * 128 * esize;
-    const int plane = 128 * kBoxRows * esize;
-    float cr[4], cg[4], cb[4], gv[4];
-    load4(p, a.in.dtype, cr);
-    load4(p + plane, a.in.dtype, cg);
-    load4(p + 2 * plane, a.in.dtype, cb);
-    if (++rr == kBoxRows) {
-      rr = 0;
-      release_box();
+  // A 3-tap y pass step of weight set q over slot pair P (two partial sums):
+  // returns the completed row, advances the sums.
+  template <int PH>
+  __device__ __forceinline__ float ystep(int q, float x, float (&p)[2][4], int k) {
+    constexpr int s0 = PH & 1, s1 = (PH + 1) & 1;
+    const float out = __fmaf_rn(w(q, 5), x, p[s0][k]);
+    const float w3 = w(q, 3);
+    if (SPEC && (w3 == 1.0f || w3 == -1.0f)) {
+      p[s0][k] = __fmaf_rn(w(q, 4), x, p[s1][k]);
+      p[s1][k] = w3 == 1.0f ? x : -x;   // w3 * x is exact for w3 = +-1: the product tap3v's first step rounds to
+    } else {
+      p[s0][k] = __fmaf_rn(w(q, 4), x, p[s1][k]);
+      p[s1][k] = __fmul_rn(w3, x);
     }
+    return out;
+  }
+
+  // Gray row r (input row v of the three planes) and its two x passes.
+  template <bool HE>
+  __device__ __forceinline__ void gray_x(const float (&cr)[4], const float (&cg)[4], const float (&cb)[4]) {
+    float gv[4];
     if (SPEC || a.gray_scale == 1.0f) {  // x * 1 is exact: the same value as op_gray with scale 1
 #pragma unroll
       for (int k = 0; k < 4; ++k) gv[k] = __fmaf_rn(0.114f, cb[k], __fmaf_rn(0.587f, cg[k], __fmul_rn(0.299f, cr[k])));
@@ -293,37 +262,26 @@ struct StripRun {
     }
     rs4<RND>(gv, a.st[0]);
     float l[4], rt[4];
-    neighbours(gv, e, l, rt);
-    xpass3(w, 0, l, gv, rt, hA[M]);
-    xpass3(w, 1, l, gv, rt, hB[M]);
-    constexpr int P = (M + 2) % 3;  // the previous row's slot
-    if (!edge) return true;
-    if (r == 0) {                   // row -1 of gray is row 0
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { hA[P][k] = hA[M][k]; hB[P][k] = hB[M][k]; }
-    }
-    if (r == a.in.h) {              // row H of gray is row H - 1
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { hA[M][k] = hA[P][k]; hB[M][k] = hB[P][k]; }
-    }
-    return true;
+    neighbours<HE>(gv, e, l, rt);
+    xpass3(w, 0, l, gv, rt, hA);
+    xpass3(w, 1, l, gv, rt, hB);
   }
 
-  // Gradients and products of row r - 1 (window rows r-2, r-1, r), then the x
-  // passes of the box sums, into product slot (M + 2) % 3.
-  template <int M>
-  __device__ __forceinline__ void row_grad(int r, bool edge) {
-    const HarrisArgs& a = kp.a;
-    constexpr int I0 = (M + 1) % 3, I1 = (M + 2) % 3, I2 = M;
-    constexpr int S = (M + 2) % 3, SP = (M + 1) % 3;  // this product row's slot; the previous one's
-    float pr[3][4], ix[4], iy[4];
+  // The Sobel y passes with the newest gray x passes (gradient row i - 1),
+  // then that row's products and their box-sum x passes into hS.  DUP: the
+  // gray row also stands for the row above it (image row 0).
+  template <int PH, bool HE>
+  __device__ __forceinline__ void grad_prod(bool valid) {
+    float ix[4], iy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      ix[k] = tapw(w, 0, 3, hA[I0][k], hA[I1][k], hA[I2][k]);
-      iy[k] = tapw(w, 1, 3, hB[I0][k], hB[I1][k], hB[I2][k]);
+      ix[k] = ystep<PH>(0, hA[k], pA, k);
+      iy[k] = ystep<PH>(1, hB[k], pB, k);
     }
+    if (!valid) return;   // the gradient row is above the run's first: its products are not needed
     rs4<RND>(ix, a.st[1]);
     rs4<RND>(iy, a.st[2]);
+    float pr[3][4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       pr[0][k] = __fmul_rn(ix[k], ix[k]);
@@ -336,36 +294,21 @@ struct StripRun {
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       float l[4], rt[4];
-      neighbours(pr[b], e, l, rt);
-      xpass3(w, 2 + b, l, pr[b], rt, sm[S][b]);
-    }
-    if (!edge) return;
-    if (r == 1) {           // product row 0 was just formed: row -1 is row 0
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sm[SP][b][k] = sm[S][b][k];
-    }
-    if (r == a.in.h + 1) {  // product row H is row H - 1
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sm[S][b][k] = sm[SP][b][k];
+      neighbours<HE>(pr[b], e, l, rt);
+      xpass3(w, 2 + b, l, pr[b], rt, hS[b]);
     }
   }
 
-  // Box sums (y pass over product rows r-3, r-2, r-1) and the response of
-  // output row r - 2 = image row y.
-  template <int M>
-  __device__ __forceinline__ void row_out() {
-    const HarrisArgs& a = kp.a;
-    constexpr int J0 = M, J1 = (M + 1) % 3, J2 = (M + 2) % 3;
-    float o[4], sxx[4], syy[4], sxy[4];
+  // The box-sum y passes with the newest product x passes, then the response
+  // of the completed row into o.
+  template <int PH>
+  __device__ __forceinline__ void box_resp() {
+    float sxx[4], syy[4], sxy[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      sxx[k] = tapw(w, 2, 3, sm[J0][0][k], sm[J1][0][k], sm[J2][0][k]);
-      syy[k] = tapw(w, 3, 3, sm[J0][1][k], sm[J1][1][k], sm[J2][1][k]);
-      sxy[k] = tapw(w, 4, 3, sm[J0][2][k], sm[J1][2][k], sm[J2][2][k]);
+      sxx[k] = ystep<PH>(2, hS[0][k], pS[0], k);
+      syy[k] = ystep<PH>(3, hS[1][k], pS[1], k);
+      sxy[k] = ystep<PH>(4, hS[2][k], pS[2], k);
     }
     rs4<RND>(sxx, a.st[6]);
     rs4<RND>(syy, a.st[7]);
@@ -375,91 +318,164 @@ struct StripRun {
       const float v = op_harris(sxx[k], syy[k], sxy[k], a.k);
       o[k] = ODT == 3 ? round_storage(a.out.dtype, v) : v;
     }
-    char* row = out_row;
-    out_row += a.out.rs;
-    if (st_full) {
-      if (ODT == 0) {
-        *reinterpret_cast<float4*>(row + 4LL * c0) = make_float4(o[0], o[1], o[2], o[3]);
-      } else {
-        __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
-        uint2 u;
-        u.x = *reinterpret_cast<unsigned*>(&p0);
-        u.y = *reinterpret_cast<unsigned*>(&p1);
-        *reinterpret_cast<uint2*>(row + 2LL * c0) = u;
-      }
-    } else if (st_part) {
-      const int y = (int)((row - (char*)a.out.data - (long long)U.img * a.out.ps) / a.out.rs);
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (c0 + k < a.out.w) store_px(a.out, U.img, c0 + k, y, o[k]);
-    }
   }
 
-  template <int M>
-  __device__ __forceinline__ bool step(int t) {
-    const int r = U.oy - 2 + t;
-    const bool edge = vedge && (r < 2 || r >= kp.a.in.h);  // a window row outside the image may need a copy
-    if (!row_in<M>(r, edge)) return false;
-    if (t >= 2) row_grad<M>(r, edge);
-    if (t >= 4) row_out<M>();
-    return true;
-  }
-
-  __device__ __forceinline__ bool run() {
-    const int n = U.n_in;
-    int t = 0;
-    while (true) {
-      if (!step<0>(t)) return false;
-      if (++t >= n) break;
-      if (!step<1>(t)) return false;
-      if (++t >= n) break;
-      if (!step<2>(t)) return false;
-      if (++t >= n) break;
+  // Step t (t & 1 = PH) on input row (cr, cg, cb); EDGE: the image's top
+  // or bottom rows are near (clamped rows), HE: the strip reaches past an
+  // image edge.
+  template <int PH, bool EDGE, bool HE>
+  __device__ __forceinline__ void step(int t, const float (&cr)[4], const float (&cg)[4], const float (&cb)[4]) {
+    if (!EDGE) {
+      gray_x<HE>(cr, cg, cb);
+      grad_prod<PH, HE>(true);
+      box_resp<PH>();
+      return;
     }
-    if (rr != 0) {  // the unit's last box had rows to spare
-      rr = 0;
-      release_box();
-    }
-    return true;
+    const int r = y0 + t;                     // gray row
+    if (r < H) gray_x<HE>(cr, cg, cb);        // else row H - 1's x passes stand for row r (clamped)
+    if (top && r == 0) grad_prod<(PH + 1) & 1, HE>(false);   // gray row -1 is row 0
+    // gradient row r - 1: its products when it lies in the image; below it
+    // the product row is row H - 1's, whose x passes hS still hold
+    grad_prod<PH, HE>(r - 1 >= 0 && r - 1 < H);
+    if (top && r == 1) box_resp<(PH + 1) & 1>();             // product row -1 is row 0
+    box_resp<PH>();
   }
 };
 
+template <int ODT>
+__device__ __forceinline__ void store_out(char* row, int c0, bool full, bool part, const ImgView& out, int img, int y,
+                                          const float (&o)[4]) {
+  if (full) {
+    if (ODT == 0) {
+      *reinterpret_cast<float4*>(row + 4LL * c0) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]), p1 = __floats2bfloat162_rn(o[2], o[3]);
+      uint2 u;
+      u.x = *reinterpret_cast<unsigned*>(&p0);
+      u.y = *reinterpret_cast<unsigned*>(&p1);
+      *reinterpret_cast<uint2*>(row + 2LL * c0) = u;
+    }
+  } else if (part) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (c0 + k < out.w) store_px(out, img, c0 + k, y, o[k]);
+  }
+}
+
+// The two steps of one box; EDGE: check each step against the run's end.
+template <bool EDGE, bool HE, class Run>
+__device__ __forceinline__ void box_steps(Run& R, int t0, int n, const unsigned char* slot, int dtype, int esize,
+                                          int t_store, char*& out_row, int c0, bool full, bool part, const Unit& U,
+                                          const ImgView& out) {
+  constexpr int ODT = Run::kODT;
+  const int plane = 128 * kBoxRows * esize;
+#pragma unroll
+  for (int u = 0; u < kBoxRows; ++u) {
+    const int t = t0 + u;
+    if (EDGE && t >= n) return;
+    float cr[4], cg[4], cb[4];
+    if (!EDGE || U.y0 + t < R.H) {
+      const unsigned char* p = slot + u * 128 * esize;
+      load4(p, dtype, cr);
+      load4(p + plane, dtype, cg);
+      load4(p + 2 * plane, dtype, cb);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cr[k] = cg[k] = cb[k] = 0.0f;
+    }
+    if (u == 0) R.template step<0, EDGE, HE>(t, cr, cg, cb);
+    else R.template step<1, EDGE, HE>(t, cr, cg, cb);
+    if (t >= t_store) {
+      store_out<ODT>(out_row, c0, full, HE && part, out, U.img, U.y0 + t - 2, R.o);
+      out_row += out.rs;
+    }
+  }
+}
+
 template <int RND, int ODT, bool SPEC>
-__global__ void __launch_bounds__(256, 2) k_harris_rows(const __grid_constant__ RowsParams kp) {
+__global__ void __launch_bounds__(256) k_harris_rows(const __grid_constant__ RowsParams kp) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const StripGeom g = strip_geom(kp.a.in.dtype == HP_F32 ? 4 : 2);
+  const int esize = kp.a.in.dtype == HP_F32 ? 4 : 2;
+  const StripGeom g = strip_geom(esize);
   const int gw = blockIdx.x * nw + warp, stride = gridDim.x * nw;
   if (gw >= kp.units) return;
-  Ring R;
-  R.bars = reinterpret_cast<uint64_t*>(base) + warp * kRing;
-  R.slots = base + kBarBytes + warp * kRing * g.slot_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base) + warp * kRing;
+  unsigned char* slots = base + kBarBytes + warp * kRing * g.slot_bytes;
   if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < kRing; ++i) mbar_init(R.bars + i, 1);
+    for (int i = 0; i < kRing; ++i) mbar_init(bars + i, 1);
     fence_mbar_init();
   }
   __syncwarp();
-  R.issued = R.released = 0;
-  R.iu = gw;
-  R.ij = 0;
-  R.IU = unit_geom(kp, g, gw);
-  for (int i = 0; i < kRing; ++i) issue_one(kp, g, R, stride, lane);
+  HarrisRun<RND, ODT, SPEC> R(kp.a);
+  const int W = kp.a.in.w, H = kp.a.in.h;
+  R.H = H;
+  unsigned qbase = 0;  // boxes this warp has issued before the current unit
   for (int u = gw; u < kp.units; u += stride) {
-    StripRun<RND, ODT, SPEC> run(kp, g, R, unit_geom(kp, g, u), lane, stride);
-    if (!run.run()) {
+    const Unit U = unit_geom(kp, g, u);
+    if (lane == 0)
+      for (int j = 0; j < kRing && j < U.nbox; ++j) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j, U, j);
+    const int c0 = U.x0 + 4 * lane;
+    R.y0 = U.y0;
+    R.top = U.y0 == 0;
+    R.e.left = c0 == 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) R.e.right[k] = c0 + k == W - 1;
+    const bool he = U.x0 < 0 || U.x0 + 128 > W;
+    const bool mine = lane >= g.halo_lanes && lane < 32 - g.halo_lanes;
+    const bool st_full = mine && c0 + 3 < kp.a.out.w && ODT != 3;
+    const bool st_part = mine && c0 < kp.a.out.w && !st_full;
+    char* out_row = (char*)kp.a.out.data + (long long)U.img * kp.a.out.ps + (long long)U.oy * kp.a.out.rs;
+    const int n = U.n_steps;
+    const int t_store = U.oy - U.y0 + 2;          // first step whose output row is the run's
+    const int t_edge = H - U.y0;                   // from this step on the gray row lies below the image
+    const int t_top = R.top ? 1 : -1;              // steps 0 .. t_top: gray row 0 or 1 of a top run
+    int failed = 0;
+#pragma unroll 1
+    for (int j = 0; kBoxRows * j < n; ++j) {
+      const int t0 = kBoxRows * j;
+      const unsigned char* slot = nullptr;
+      if (t0 < U.n_in) {
+        const unsigned q = qbase + j;
+        int ok = 1;
+        if (lane == 0) ok = mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 2000000000ull);
+        ok = __shfl_sync(kFull, ok, 0);
+        if (!ok) {
+          failed = 1;
+          break;
+        }
+        slot = slots + (q % kRing) * g.slot_bytes + lane * 4 * esize;
+      }
+      const bool edge = t0 <= t_top || t0 + kBoxRows - 1 >= t_edge || t0 + kBoxRows > n;
+      if (edge) {
+        if (he) box_steps<true, true>(R, t0, n, slot, kp.a.in.dtype, esize, t_store, out_row, c0, st_full, st_part, U, kp.a.out);
+        else box_steps<true, false>(R, t0, n, slot, kp.a.in.dtype, esize, t_store, out_row, c0, st_full, st_part, U, kp.a.out);
+      } else {
+        if (he) box_steps<false, true>(R, t0, n, slot, kp.a.in.dtype, esize, t_store, out_row, c0, st_full, st_part, U, kp.a.out);
+        else box_steps<false, false>(R, t0, n, slot, kp.a.in.dtype, esize, t_store, out_row, c0, st_full, st_part, U, kp.a.out);
+      }
+      if (j + kRing < U.nbox) {  // this box's slot is read: refill it
+        __syncwarp();
+        if (lane == 0) issue_box(&kp.tmap, slots, bars, g.slot_bytes, qbase + j + kRing, U, j + kRing);
+      }
+    }
+    if (failed) {
       // a box never arrived: report, wait (bounded) for the copies still in
       // flight into this warp's slots, and stop
       if (lane == 0) {
         atomicExch(kp.a.err, 1);
-        for (unsigned b = R.released; b < R.issued; ++b)
-          mbar_wait_poll(R.bars + b % kRing, (b / kRing) & 1u, 100000000ull);
+        for (int j = 0; j < U.nbox; ++j) {
+          const unsigned q = qbase + j;
+          mbar_wait_poll(bars + q % kRing, (q / kRing) & 1u, 100000000ull);
+        }
       }
       __syncwarp();
       return;
     }
+    qbase += U.nbox;
   }
 }
 
