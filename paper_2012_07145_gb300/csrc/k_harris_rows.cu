@@ -212,9 +212,8 @@ __device__ __forceinline__ void load4(const unsigned char* p, int dtype, float (
 // window of rows: when row i's x pass x arrives, output row i - 1 takes its
 // last tap, row i its middle one, and row i + 1 starts -- the taps of each row
 // still applied oldest first, as tap3v applies them, so every value is the
-// same.  Partial sum j (j = 0: row i, 1: row i + 1, after the update) sits in
-// slot (j + t) & 1, so an update reads and writes one slot and a box of two
-// steps keeps fixed registers.  The stage values that a clamp may repeat below
+// same.  The two partial sums swap slots every step (see ystep), so a box of
+// two steps keeps fixed registers.  The stage values that a clamp may repeat below
 // the image (the newest x passes) are kept.
 template <int RND, int ODT, bool SPEC>
 struct HarrisRun {
@@ -234,18 +233,19 @@ struct HarrisRun {
 
   // A 3-tap y pass step of weight set q over slot pair P (two partial sums):
   // returns the completed row, advances the sums.
+  // Slot PH & 1 holds the partial sum of the row that completes now (two
+  // taps in), slot (PH + 1) & 1 that of the next row (one tap in); after the
+  // update the roles of the slots swap, which the next step's phase follows.
   template <int PH>
   __device__ __forceinline__ float ystep(int q, float x, float (&p)[2][4], int k) {
     constexpr int s0 = PH & 1, s1 = (PH + 1) & 1;
     const float out = __fmaf_rn(w(q, 5), x, p[s0][k]);
     const float w3 = w(q, 3);
-    if (SPEC && (w3 == 1.0f || w3 == -1.0f)) {
-      p[s0][k] = __fmaf_rn(w(q, 4), x, p[s1][k]);
-      p[s1][k] = w3 == 1.0f ? x : -x;   // w3 * x is exact for w3 = +-1: the product tap3v's first step rounds to
-    } else {
-      p[s0][k] = __fmaf_rn(w(q, 4), x, p[s1][k]);
-      p[s1][k] = __fmul_rn(w3, x);
-    }
+    p[s1][k] = __fmaf_rn(w(q, 4), x, p[s1][k]);
+    if (SPEC && (w3 == 1.0f || w3 == -1.0f))
+      p[s0][k] = w3 == 1.0f ? x : -x;   // w3 * x is exact for w3 = +-1: the product tap3v's first step rounds to
+    else
+      p[s0][k] = __fmul_rn(w3, x);
     return out;
   }
 
