@@ -386,7 +386,9 @@ __device__ __forceinline__ void box_steps(Run& R, int t0, int n, const unsigned 
     if (u == 0) R.template step<0, EDGE, HE>(t, cr, cg, cb);
     else R.template step<1, EDGE, HE>(t, cr, cg, cb);
     if (t >= t_store) {
-      store_out<ODT>(out_row, c0, full, HE && part, out, U.img, U.y0 + t - 2, R.o);
+      // lanes with only some columns inside the image exist past the right
+      // edge alone; the general output type stores column by column everywhere
+      store_out<ODT>(out_row, c0, full, (HE || ODT == 3) && part, out, U.img, U.y0 + t - 2, R.o);
       out_row += out.rs;
     }
   }
