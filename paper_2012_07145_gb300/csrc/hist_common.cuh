@@ -8,6 +8,35 @@
 
 namespace hp {
 
+// Division of a 32-bit chunk index by the chunks per row, a divisor fixed for
+// the launch: one multiply-high, a subtract, an add and two shifts instead of
+// an integer division (a long instruction sequence on the GPU, and the
+// kernels' largest per-chunk cost when it was done in 64 bits).  The method is
+// that of Granlund and Montgomery, "Division by invariant integers using
+// multiplication" (1994), for every n < 2^32 and 1 <= d < 2^32: with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1 (which fits in 32
+// bits), t = mulhi(m, n) and n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+  unsigned int d, m;
+  int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned int d) {
+  int l = 0;
+  while (l < 32 && (1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (unsigned int)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__device__ __forceinline__ unsigned int fastdiv(unsigned int n, const FastDiv& f) {
+  const unsigned int t = __umulhi(f.m, n);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // Adds byte value v to the warp's sub-histogram wh.  When every active lane
 // holds the same value (flat regions, constant images: the worst case for
 // contention) one lane adds the whole count.

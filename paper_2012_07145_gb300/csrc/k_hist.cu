@@ -26,30 +26,31 @@ constexpr int kHistWarps = kHistThreads / 32;
 
 constexpr int kChunksPerIter = 4;
 
-__global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, unsigned int* __restrict__ hist) {
+// cpr: the chunks per row (16-byte chunks); chunk indices are 32-bit (the
+// host checks that the image's chunks fit).
+__global__ void __launch_bounds__(kHistThreads) k_hist(const ImgView in, const FastDiv cpr, unsigned int* __restrict__ hist) {
   grid_dep_sync();
   __shared__ unsigned int sh[kHistWarps][256];
   for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
   __syncthreads();
   unsigned int* wh = sh[threadIdx.x >> 5];
-  const int chunks_per_row = (in.w + 15) >> 4;
-  const long long n_chunks = (long long)chunks_per_row * in.h;
+  const unsigned int n_chunks = cpr.d * (unsigned int)in.h;
   // a warp takes 32 x kChunksPerIter consecutive chunks per iteration; the
   // loop bound is warp-uniform, so the warp-wide votes below are legal
-  const long long per_iter = (long long)gridDim.x * blockDim.x * kChunksPerIter;
-  const long long warp_base = ((long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kChunksPerIter;
+  const unsigned int per_iter = gridDim.x * blockDim.x * kChunksPerIter;
+  const unsigned int warp_base = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kChunksPerIter;
   const int lane = threadIdx.x & 31;
-  for (long long base = warp_base; base < n_chunks; base += per_iter) {
+  for (unsigned int base = warp_base; base < n_chunks; base += per_iter) {
     unsigned int words[kChunksPerIter][4];
     int nbytes[kChunksPerIter];
 #pragma unroll
     for (int u = 0; u < kChunksPerIter; ++u) {
-      const long long ch = base + u * 32 + lane;
+      const unsigned int ch = base + u * 32 + lane;
       words[u][0] = words[u][1] = words[u][2] = words[u][3] = 0;
       nbytes[u] = 0;
       if (ch < n_chunks) {
-        const int y = (int)(ch / chunks_per_row);
-        const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+        const unsigned int y = fastdiv(ch, cpr);
+        const int x0 = (int)(ch - y * cpr.d) << 4;
         const unsigned char* row = (const unsigned char*)in.data + (long long)y * in.rs;
         nbytes[u] = min(16, in.w - x0);
         if (nbytes[u] == 16) {
@@ -85,27 +86,26 @@ __global__ void __launch_bounds__(256) k_cdf_lut(const unsigned int* __restrict_
   cdf_lut_cta(hist[threadIdx.x], lut);
 }
 
-__global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out,
+__global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgView out, const FastDiv cpr,
                                                    const unsigned char* __restrict__ lut) {
   grid_dep_sync();
   __shared__ unsigned char t[256];
   if (threadIdx.x < 256) t[threadIdx.x] = lut[threadIdx.x];
   __syncthreads();
-  const int chunks_per_row = (in.w + 15) >> 4;
-  const long long n_chunks = (long long)chunks_per_row * in.h;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < n_chunks; c0 += stride * kChunksPerIter) {
+  const unsigned int n_chunks = cpr.d * (unsigned int)in.h;
+  const unsigned int stride = gridDim.x * blockDim.x;
+  for (unsigned int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < n_chunks; c0 += stride * kChunksPerIter) {
     uint4 q[kChunksPerIter];
     int nb[kChunksPerIter];
-    long long chs[kChunksPerIter];
+    unsigned int chs[kChunksPerIter];
 #pragma unroll
     for (int u = 0; u < kChunksPerIter; ++u) {
-      const long long ch = c0 + u * stride;
+      const unsigned int ch = c0 + u * stride;
       chs[u] = ch;
       nb[u] = 0;
       if (ch < n_chunks) {
-        const int y = (int)(ch / chunks_per_row);
-        const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+        const unsigned int y = fastdiv(ch, cpr);
+        const int x0 = (int)(ch - y * cpr.d) << 4;
         nb[u] = min(16, in.w - x0);
         if (nb[u] == 16) q[u] = __ldcs(reinterpret_cast<const uint4*>((const unsigned char*)in.data + (long long)y * in.rs + x0));
       }
@@ -113,9 +113,9 @@ __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgVi
 #pragma unroll
     for (int u = 0; u < kChunksPerIter; ++u) {
       if (nb[u] == 0) continue;
-      const long long ch = chs[u];
-      const int y = (int)(ch / chunks_per_row);
-      const int x0 = (int)(ch - (long long)y * chunks_per_row) << 4;
+      const unsigned int ch = chs[u];
+      const unsigned int y = fastdiv(ch, cpr);
+      const int x0 = (int)(ch - y * cpr.d) << 4;
       unsigned char* dst = (unsigned char*)out.data + (long long)y * out.rs + x0;
       if (nb[u] == 16) {
         __stcs(reinterpret_cast<uint4*>(dst), make_uint4(lut4(t, q[u].x), lut4(t, q[u].y), lut4(t, q[u].z), lut4(t, q[u].w)));
@@ -126,6 +126,11 @@ __global__ void __launch_bounds__(256) k_lut_apply(const ImgView in, const ImgVi
     }
   }
 }
+
+// Chunk indices are 32-bit, with room for a thread's last stride past the end
+// (at most 8 x 152 x 256 x 4 chunks); a histogram counts at most 2^32 - 1
+// pixels anyway.
+bool chunks_fit(long long chunks) { return chunks >= 0 && chunks <= 0xffffffffLL - (1LL << 24); }
 
 int sm_count() {
   static int n = 0;
@@ -145,10 +150,12 @@ int launch_hist(const HistArgs& a, void* stream) {
   int e = (int)cudaMemsetAsync(a.hist, 0, 256 * sizeof(unsigned int), s);
   if (e) return e;
   long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
+  if (!chunks_fit(chunks)) return (int)cudaErrorInvalidValue;
   long long want = (chunks + kHistThreads * kChunksPerIter - 1) / (kHistThreads * kChunksPerIter);
   int blocks = (int)(want < 4LL * sm_count() ? want : 4LL * sm_count());
   if (blocks < 1) blocks = 1;
-  { const int le_ = launch_kernel(k_hist, dim3(blocks), dim3(kHistThreads), 0, (void*)s, a.in, a.hist); if (le_) return le_; }
+  const FastDiv cpr = make_fastdiv((unsigned int)((a.in.w + 15) / 16));
+  { const int le_ = launch_kernel(k_hist, dim3(blocks), dim3(kHistThreads), 0, (void*)s, a.in, cpr, a.hist); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }
@@ -161,10 +168,12 @@ int launch_cdf_lut(const LutArgs& a, void* stream) {
 
 int launch_lut_apply(const LutApplyArgs& a, void* stream) {
   long long chunks = (long long)((a.in.w + 15) / 16) * a.in.h;
+  if (!chunks_fit(chunks)) return (int)cudaErrorInvalidValue;
   long long want = (chunks + 256 * kChunksPerIter - 1) / (256 * kChunksPerIter);
   int blocks = (int)(want < 8LL * sm_count() ? want : 8LL * sm_count());
   if (blocks < 1) blocks = 1;
-  { const int le_ = launch_kernel(k_lut_apply, dim3(blocks), dim3(256), 0, stream, a.in, a.out, a.lut); if (le_) return le_; }
+  const FastDiv cpr = make_fastdiv((unsigned int)((a.in.w + 15) / 16));
+  { const int le_ = launch_kernel(k_lut_apply, dim3(blocks), dim3(256), 0, stream, a.in, a.out, cpr, a.lut); if (le_) return le_; }
   __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED);
   return (int)cudaGetLastError();
 }

@@ -17,11 +17,12 @@
 //
 // The device-wide state (two histograms of kEqCopies copies each -- CTA b adds
 // into copy b % kEqCopies, so no counter takes more than a few atomics -- an
-// arrival counter and a generation number) lives in a zero-initialised
-// scratch that resets itself: launch g counts into histogram g & 1, and the
-// last CTA to arrive clears the other histogram and the counter before it
-// releases the others by bumping the generation, so the next launch (a
-// CUDA-graph replay included) starts clean.
+// arrival counter per launch parity and the launch number g) lives in a
+// zero-initialised scratch that resets itself: launch g counts into histogram
+// g & 1 and arrives at counter g & 1, and every CTA waits for that counter to
+// reach the CTA count.  The last CTA to arrive advances g and clears the other
+// parity's counter and histogram, which nothing reads in this launch, so the
+// next launch (a CUDA-graph replay included) starts clean.
 #include <cuda_runtime.h>
 
 #include "hist_common.cuh"
@@ -33,7 +34,7 @@ namespace hp {
 namespace {
 
 constexpr int kEqThreads = 1024;
-constexpr int kEqU = 4;  // chunk loads in flight per thread
+constexpr int kEqU = 6;  // chunk loads in flight per thread
 constexpr int kEqHistBytes = 256 * 32 * 4;               // 256 bins x 32 lanes
 constexpr int kEqSmemMax = 227 * 1024 - 8 * 1024;        // dynamic shared memory limit used here
 constexpr int kEqStageMax = kEqSmemMax - kEqHistBytes;    // bytes of image a CTA can keep
@@ -41,7 +42,7 @@ constexpr int kEqStageMax = kEqSmemMax - kEqHistBytes;    // bytes of image a CT
 constexpr int kEqCopies = 8;  // device histogram copies (CTA b adds into copy b % 8)
 
 struct EqState {
-  unsigned int gen, count, pad[2];
+  unsigned int gen, count[2], pad;  // launch number; arrivals of the launches of each parity
   unsigned int hist[2][kEqCopies][256];
 };
 
@@ -49,8 +50,8 @@ struct EqParams {
   ImgView in, out;
   EqState* st;                  // one state per image of the batch
   int* err;
-  long long n_chunks, per_cta;  // chunks in an image; chunks per CTA
-  int cpr;                      // chunks per row
+  unsigned int n_chunks, per_cta;  // chunks in an image (< 2^32: at most its pixels); chunks per CTA
+  FastDiv cpr;                     // chunks per row (the divisor of a chunk index)
   int staged;                   // per_cta chunks fit in shared memory: no second read
   int ctas;                     // CTAs per image (a batch's images take consecutive groups of CTAs)
 };
@@ -61,10 +62,10 @@ __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* a) {
   return v;
 }
 
-__device__ __forceinline__ int chunk_bytes(const EqParams& p, int img, long long ch, const unsigned char** src,
+__device__ __forceinline__ int chunk_bytes(const EqParams& p, int img, unsigned int ch, const unsigned char** src,
                                            unsigned char** dst) {
-  const int y = (int)(ch / p.cpr);
-  const int x0 = (int)(ch - (long long)y * p.cpr) << 4;
+  const unsigned int y = fastdiv(ch, p.cpr);
+  const int x0 = (int)(ch - y * p.cpr.d) << 4;
   *src = (const unsigned char*)p.in.data + (long long)img * p.in.ps + (long long)y * p.in.rs + x0;
   *dst = (unsigned char*)p.out.data + (long long)img * p.out.ps + (long long)y * p.out.rs + x0;
   return min(16, p.in.w - x0);
@@ -126,19 +127,19 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   __syncthreads();
   const unsigned int gen = s_gen, buf = gen & 1u;
   unsigned int* hl = sh + (threadIdx.x & 31);
-  const long long c0 = (long long)cta * p.per_cta;
-  const long long c1 = min(p.n_chunks, c0 + p.per_cta);
+  const unsigned int c0 = (unsigned int)cta * p.per_cta;
+  const unsigned int c1 = (unsigned int)min((unsigned long long)p.n_chunks, (unsigned long long)c0 + p.per_cta);
   const bool staged = p.staged != 0;  // the slice is kept in shared memory for the lookup
 
   // ---- count (kEqU loads in flight per thread) ----
-  const long long step = (long long)kEqU * blockDim.x;
+  const unsigned int step = kEqU * blockDim.x;
 #pragma unroll 1
-  for (long long base = c0 + threadIdx.x; base < c1; base += step) {
+  for (unsigned int base = c0 + threadIdx.x; base < c1; base += step) {
     uint4 q[kEqU];
     int nb[kEqU];
 #pragma unroll
     for (int u = 0; u < kEqU; ++u) {
-      const long long ch = base + (long long)u * blockDim.x;
+      const unsigned int ch = base + u * blockDim.x;
       nb[u] = 0;
       if (ch < c1) {
         const unsigned char* src;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
 #pragma unroll
     for (int u = 0; u < kEqU; ++u) {
       if (nb[u] == 0) continue;
-      if (staged) stage[base + (long long)u * blockDim.x - c0] = q[u];
+      if (staged) stage[base + u * blockDim.x - c0] = q[u];
       count_chunk(hl, q[u], nb[u]);
     }
   }
@@ -173,34 +174,34 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
   // ---- grid-wide barrier (bounded) ----
   __syncthreads();
   if (threadIdx.x == 0) {
+    // arrive, then wait until every CTA of this launch has: the barrier is
+    // the arrival counter itself (no CTA has to release the others)
     __threadfence();
-    s_last = atomicAdd(&st->count, 1u) == (unsigned)p.ctas - 1;
+    const unsigned int need = (unsigned)p.ctas;
+    const bool last = atomicAdd(&st->count[buf], 1u) == need - 1;
+    s_last = last;
     s_ok = 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    // every CTA's counts are in: clear the other histogram and the counter for
-    // the next launch, then release the others
-    for (int v = threadIdx.x; v < kEqCopies * 256; v += blockDim.x) (&st->hist[buf ^ 1u][0][0])[v] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st->count = 0;
-      __threadfence();
-      atomicExch(&st->gen, gen + 1u);
-    }
-  } else if (threadIdx.x == 0) {
-    const unsigned long long t0 = global_ns();
-    while (ld_relaxed(&st->gen) == gen) {
-      if (global_ns() - t0 > 1000000000ull) {
-        s_ok = 0;
-        atomicExch(p.err, 3);
-        break;
+    if (!last) {
+      const unsigned long long t0 = global_ns();
+      while (ld_relaxed(&st->count[buf]) < need) {
+        if (global_ns() - t0 > 1000000000ull) {
+          s_ok = 0;
+          atomicExch(p.err, 3);
+          break;
+        }
       }
+    } else {
+      // the next launch (parity buf ^ 1) finds its counter and histogram
+      // zero and the launch number advanced; nothing in this launch reads them
+      st->count[buf ^ 1u] = 0;
+      st->gen = gen + 1u;
     }
     __threadfence();
   }
   __syncthreads();
   if (!s_ok) return;
+  if (s_last)  // the other histogram, for the next launch
+    for (int v = threadIdx.x; v < kEqCopies * 256; v += blockDim.x) (&st->hist[buf ^ 1u][0][0])[v] = 0;
 
   // ---- table, then the lookup ----
   unsigned int h = 0;
@@ -209,12 +210,20 @@ __global__ void __launch_bounds__(kEqThreads, 1) k_histeq(const __grid_constant_
     for (int c = 0; c < kEqCopies; ++c) h += __ldcg(&st->hist[buf][c][threadIdx.x]);
   cdf_lut_cta(h, table);
   __syncthreads();
+  // two chunks per iteration, so that each thread has two independent
+  // lookups in flight
 #pragma unroll 1
-  for (long long ch = c0 + threadIdx.x; ch < c1; ch += blockDim.x) {
-    const unsigned char* src;
-    unsigned char* dst;
-    const int n = chunk_bytes(p, img, ch, &src, &dst);
-    store_chunk(table, staged ? stage[ch - c0] : load_chunk(src, n), n, dst);
+  for (unsigned int base = c0 + threadIdx.x; base < c1; base += 2 * blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const unsigned int ch = base + u * blockDim.x;
+      if (ch < c1) {
+        const unsigned char* src;
+        unsigned char* dst;
+        const int n = chunk_bytes(p, img, ch, &src, &dst);
+        store_chunk(table, staged ? stage[ch - c0] : load_chunk(src, n), n, dst);
+      }
+    }
   }
 }
 
@@ -263,10 +272,14 @@ int launch_histeq(const ImgView& in, const ImgView& out, void* state, int* err, 
   p.out = out;
   p.st = reinterpret_cast<EqState*>(state);
   p.err = err;
-  p.cpr = (in.w + 15) / 16;
-  p.n_chunks = (long long)p.cpr * in.h;
-  p.per_cta = (p.n_chunks + grid - 1) / grid;
-  p.staged = p.per_cta * 16 <= kEqStageMax;
+  const unsigned long long n_chunks = (unsigned long long)((in.w + 15) / 16) * in.h;
+  // 32-bit chunk indices, with room for a thread's last stride past the end
+  // (the counters hold at most 2^32 - 1 pixels anyway)
+  if (n_chunks > 0xffffffffull - 65536 || in.w < 1) return (int)cudaErrorInvalidValue;
+  p.cpr = make_fastdiv((unsigned int)((in.w + 15) / 16));
+  p.n_chunks = (unsigned int)n_chunks;
+  p.per_cta = (unsigned int)((n_chunks + grid - 1) / grid);
+  p.staged = (unsigned long long)p.per_cta * 16 <= (unsigned long long)kEqStageMax;
   p.ctas = grid;
   if (batch < 1) batch = 1;
   cudaLaunchConfig_t cfg = {};
