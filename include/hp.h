@@ -141,7 +141,7 @@ typedef struct {
 enum {
   HP_IMPL_AUTO = 0,    /* the kernel the group's shape selects */
   HP_IMPL_GENERIC = 1, /* the generic interpreter */
-  HP_IMPL_WAVE = 2     /* streaming kernels: a warp walks down a strip of columns, rows arrive
+  HP_IMPL_WAVE = 2,    /* streaming kernels: a warp walks down a strip of columns, rows arrive
                           through a per-warp TMA ring.  Stencil chains of 2 or 4 stages: every stage
                           in registers; strips of 120 columns (2 stages, 4-byte input) or 112 (4
                           stages, or a 2-byte input), tile_h rows per run, threads <= 256.
@@ -159,6 +159,14 @@ enum {
                           A local-Laplacian level (K = 8, f32 stages; level 0 from u16 RGB): the same
                           30-column strips (of the coarser level), tile_h coarse rows per run.  Other
                           groups ignore HP_IMPL_WAVE's request when they have no streaming kernel. */
+  HP_IMPL_LINES = 3     /* line-buffer stencil chain: a chain of an even number of 5x5 stencils (2..8)
+                          whose input, stages and output share one type (f32, f16 or bf16; 16-bit
+                          chains of 4 or 8 stages) runs as one thread block per tile_w x tile_h output
+                          tile (tile_w a multiple of 8, tile_w + 4 depth <= 256 columns, tile_h >=
+                          2 depth + 2 rows); every stage computes 8-column blocks on threads of its
+                          own and passes its rows to the next stage through a shared-memory ring
+                          (threads and serial_y do not apply).  Other groups, and chains outside these
+                          limits, ignore the request and take their default kernel. */
 };
 
 typedef struct {
@@ -228,8 +236,10 @@ enum {
   HP_KERNEL_GRID_SPLAT = 21,    /* bilateral grid splat: one thread per cell (four, two pixel rows
                                   each, for 8 x 8 cells), accumulators in shared memory */
   HP_KERNEL_GRID_SLICE = 22,    /* bilateral grid slice: four pixels of a row per thread, trilinear */
-  HP_KERNEL_GRID_BLUR = 23      /* bilateral grid blur (range levels, x, y; binomial/16), streaming:
+  HP_KERNEL_GRID_BLUR = 23,     /* bilateral grid blur (range levels, x, y; binomial/16), streaming:
                                   one warp per 28 grid columns x 4 range levels, y taps in order */
+  HP_KERNEL_STENCIL_LINES = 24  /* fused chain of 5x5 stencils, line-buffered: every stage on threads of
+                                  its own, rows passed through shared-memory rings (HP_IMPL_LINES) */
 };
 
 /* Create an empty pipeline with n_inputs inputs of the given dtypes and channel

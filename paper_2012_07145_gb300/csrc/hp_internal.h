@@ -138,6 +138,7 @@ HPHD void infer_rects(const GPlan& g, int tx0, int ty0, Rect* rects) {
 // ---------------------------------------------------------------------------
 // Parameters of the specialised kernels.
 // ---------------------------------------------------------------------------
+constexpr int kSmemLimit = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 constexpr int kChainMax = 32;
 
 struct ChainArgs {
@@ -270,6 +271,14 @@ int chain_rows_smem_bytes(int depth, int cols, int threads, int in_dtype);
 int chain_rows_grid(const ChainArgs& a, int cols, int units, int threads, int smem_bytes);
 int launch_chain_rows(const ChainArgs& a, int cols, int rows, int grid, int smem_bytes, void* stream);
 int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype);
+// line-buffer stencil chain (an even number of stages <= kLinesMaxDepth, one
+// thread block per tile, every stage on its own threads, rows through rings)
+constexpr int kLinesMaxDepth = 8;
+constexpr int kLinesMaxThreads = 256;
+bool chain_lines_ok(int depth, int tile_w, int tile_h, int dtype);
+int chain_lines_threads(int depth, int tile_w, int tile_h, int dtype);
+int chain_lines_smem_bytes(int depth, int tile_w, int tile_h, int dtype);
+int launch_chain_lines(const ChainArgs& a, void* stream);
 int launch_generic(const GPlan& g, int threads, int smem_bytes, void* stream);
 int launch_pointwise(const PointwiseArgs& a, void* stream);
 int launch_downsample(const ResampleArgs& a, void* stream);

@@ -67,7 +67,6 @@ bool valid_dtype(int d) { return d >= HP_U8 && d <= HP_U32; }
 
 long long round16(long long v) { return (v + 15) / 16 * 16; }
 
-constexpr int kSmemLimit = 227 * 1024 - 1024;  // opt-in maximum less static shared memory
 
 struct Stage {
   int kind = 0, op = 0, channels = 1, storage = HP_F32;
@@ -898,6 +897,37 @@ hp_status build_chain(const hp_pipeline* p, const Plan& plan, GroupPlan& gp, boo
   return HP_OK;
 }
 
+// Whether a chain group can take the line-buffer kernel: an even number of
+// stages up to kLinesMaxDepth, the input, every stage and the output stored in
+// one type (f32, f16 or bf16), and the group's tile within the kernel's limits.
+bool chain_lines_group_ok(const hp_pipeline* p, const GroupPlan& gp) {
+  const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
+  for (int m : gp.members)
+    if (p->stages[m].storage != in_dt) return false;
+  return chain_lines_ok((int)gp.members.size(), gp.tile_w, gp.tile_h, in_dt);
+}
+
+// A chain on the line-buffer kernel: one thread block per tile_w x tile_h
+// output tile, every stage on its own threads (their count follows from the
+// tile width and the depth; the schedule's threads and serial_y do not apply).
+hp_status build_chain_lines(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
+  chain_common_args(p, gp, false);
+  ChainArgs& a = gp.chain;
+  const int in_dt = stage_dtype_of_ref(p, p->stages[gp.members[0]].inputs[0]);
+  Dom od = plan.dom[gp.output];
+  a.tiles_x = (od.w + a.tile_w - 1) / a.tile_w;
+  a.tiles_y = (od.h + a.tile_h - 1) / a.tile_h;
+  a.threads = chain_lines_threads(a.depth, a.tile_w, a.tile_h, in_dt);
+  a.in.dtype = in_dt;
+  a.out.dtype = p->stages[gp.output].storage;
+  gp.threads = a.threads;
+  gp.smem = chain_lines_smem_bytes(a.depth, a.tile_w, a.tile_h, in_dt);
+  gp.grid_x = a.tiles_x;
+  gp.grid_y = a.tiles_y;
+  gp.grid_z = p->stages[gp.members[0]].channels;
+  return HP_OK;
+}
+
 // A chain of 2 or 4 stencils on the streaming kernel: strips of
 // chain_rows_strip_w columns, tile_h rows per run, every stage in registers.
 hp_status build_chain_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
@@ -1209,7 +1239,10 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         gp.tile_h = pick(p->tile_h, g, streaming ? 0 : 32);  // 0: the streaming kernels' adaptive run length
         gp.threads = pick(p->threads, g, 256);
         gp.seg = pick(p->serial_y, g, 8);
-        if (single && streaming) {
+        if (!single && impl == HP_IMPL_LINES && chain_lines_group_ok(p, gp)) {
+          gp.kernel = HP_KERNEL_STENCIL_LINES;
+          s = build_chain_lines(p, plan, gp);
+        } else if (single && streaming) {
           gp.kernel = HP_KERNEL_STENCIL_ROWS;
           s = build_stencil_rows(p, plan, gp, unsharp);
         } else if (streaming) {
@@ -1566,14 +1599,16 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
     switch (gp.kernel) {
       case HP_KERNEL_STENCIL_CHAIN:
       case HP_KERNEL_UNSHARP:
-      case HP_KERNEL_STENCIL_WAVE: {
+      case HP_KERNEL_STENCIL_WAVE:
+      case HP_KERNEL_STENCIL_LINES: {
         ChainArgs a = gp.chain;
         int first = gp.members[0];
         a.in = ref_view(p, plan, p->stages[first].inputs[0], inputs, output);
         a.out = out;
         a.err = p->d_err;
-        e = gp.kernel == HP_KERNEL_STENCIL_WAVE ? launch_chain_rows(a, a.cols, a.tile_h, gp.grid_x, gp.smem, stream)
-                                                : launch_chain(a, gp.smem, stream);
+        e = gp.kernel == HP_KERNEL_STENCIL_WAVE    ? launch_chain_rows(a, a.cols, a.tile_h, gp.grid_x, gp.smem, stream)
+            : gp.kernel == HP_KERNEL_STENCIL_LINES ? launch_chain_lines(a, stream)
+                                                   : launch_chain(a, gp.smem, stream);
         break;
       }
       case HP_KERNEL_STENCIL_ROWS: {
@@ -1875,7 +1910,7 @@ hp_status hp_schedule_set(hp_pipeline* p, const hp_schedule* s) {
   if ((st = per_group(s->tile_w, tmp.tile_w, 1, 4096, "tile_w")) || (st = per_group(s->tile_h, tmp.tile_h, 1, 4096, "tile_h")) ||
       (st = per_group(s->threads, tmp.threads, 32, 1024, "threads")) ||
       (st = per_group(s->serial_y, tmp.serial_y, 1, 256, "serial_y")) ||
-      (st = per_group(s->impl, tmp.impl, 0, 2, "impl")))
+      (st = per_group(s->impl, tmp.impl, 0, 3, "impl")))
     return st;
   std::vector<GroupShape> shapes;
   if ((st = group_shapes(&tmp, shapes))) return st;

@@ -24,17 +24,17 @@ HP_INLINE = -1
 HP_OPT_CUDA_GRAPH = 1
 HP_OPT_OVERLAP = 2
 HP_OPT_PROBE_ATTRS = 3
-HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE = 0, 1, 2
+HP_IMPL_AUTO, HP_IMPL_GENERIC, HP_IMPL_WAVE, HP_IMPL_LINES = 0, 1, 2, 3
 (HP_KERNEL_STENCIL_CHAIN, HP_KERNEL_UNSHARP, HP_KERNEL_HARRIS, HP_KERNEL_GENERIC, HP_KERNEL_POINTWISE,
  HP_KERNEL_DOWNSAMPLE, HP_KERNEL_UPSAMPLE, HP_KERNEL_HISTOGRAM, HP_KERNEL_CDF_LUT, HP_KERNEL_LUT_APPLY,
  HP_KERNEL_LL_LEVEL, HP_KERNEL_STENCIL_WAVE, HP_KERNEL_HARRIS_ROWS, HP_KERNEL_STENCIL_ROWS,
  HP_KERNEL_HISTEQ, HP_KERNEL_LL_REMAP_ROWS, HP_KERNEL_LL_DOWN_ROWS, HP_KERNEL_LL_LEVEL_ROWS,
  HP_KERNEL_MAX_ROWS, HP_KERNEL_INTERP_ROWS, HP_KERNEL_PW_ROWS, HP_KERNEL_GRID_SPLAT,
- HP_KERNEL_GRID_SLICE, HP_KERNEL_GRID_BLUR) = range(24)
+ HP_KERNEL_GRID_SLICE, HP_KERNEL_GRID_BLUR, HP_KERNEL_STENCIL_LINES) = range(25)
 KERNEL_NAMES = ["stencil_chain", "unsharp", "harris", "generic", "pointwise", "downsample", "upsample",
                 "histogram", "cdf_lut", "lut_apply", "ll_level", "stencil_wave", "harris_rows", "stencil_rows", "histeq",
                 "ll_remap_rows", "ll_down_rows", "ll_level_rows", "max_rows", "interp_rows", "pw_rows", "grid_splat",
-                "grid_slice", "grid_blur"]
+                "grid_slice", "grid_blur", "stencil_lines"]
 DTYPE_BYTES = {HP_U8: 1, HP_U16: 2, HP_F16: 2, HP_BF16: 2, HP_F32: 4, HP_U32: 4}
 
 _IP = ctypes.POINTER(ctypes.c_int)

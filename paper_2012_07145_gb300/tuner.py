@@ -111,6 +111,17 @@ def chain_candidates(n_stages, W, H, quick=False, esize=4):
         if items < t // 2:
             continue                                   # most threads idle in the last stage
         out.append(dict(depth=d, tile_w=tw, tile_h=th, threads=t, serial_y=s))
+    # the line-buffer kernel: an even depth, tile widths with tile_w + 4 depth
+    # at most 256 columns (one TMA box), tile heights of at least 2 depth + 2
+    for d, tw, th in itertools.product((2, 4, 6, 8), (32, 64, 96, 112, 128, 144, 160, 176, 192, 224, 240),
+                                       (16, 32, 48, 64, 96, 128, 192, 256) if not quick else (32, 64, 128)):
+        if d > n_stages or tw + 4 * d > 256 or th < 2 * d + 2 or (esize == 2 and d % 4):
+            continue
+        if any(min(d, n_stages - k) % 2 for k in range(0, n_stages, d)):
+            continue                                   # every group an even number of stages
+        if -(-W // tw) * -(-H // th) < SMS // 2:
+            continue                                   # leaves most SMs idle
+        out.append(dict(depth=d, tile_w=tw, tile_h=th, threads=256, serial_y=8, impl=hp.HP_IMPL_LINES))
     # the streaming kernel: depth 2 (4 or 8 columns per lane) or 4 (4 columns),
     # rows per run (0: one run per resident warp), threads per block
     for d, cols in ((2, 4), (2, 8), (4, 4)):

@@ -116,6 +116,29 @@ def test_lowering_picks_kernels():
     assert hb.group_info([(64, 48)], 0).kernel == hp.HP_KERNEL_HARRIS_ROWS
 
 
+def test_lowering_line_buffer_chain():
+    """HP_IMPL_LINES puts an even-depth chain on the line-buffer kernel, with
+    one block per tile and threads for every stage's 8-column blocks; chains
+    outside its limits keep the tiled kernel."""
+    p = pipelines.stencil_chain(32, "alternate")
+    pipelines.chain_schedule(p, depth=8, tile_w=128, tile_h=64, impl=hp.HP_IMPL_LINES)
+    info = p.group_info([(2560, 1536)], 0)
+    assert info.kernel == hp.HP_KERNEL_STENCIL_LINES and info.n_members == 8
+    assert (info.grid_x, info.grid_y, info.grid_z) == (20, 24, 1)
+    # stages 1..8 are 156, 152, ..., 128 columns wide; pairs take the wider one's
+    # 8-column blocks twice: 2 * (20 + 19 + 18 + 17) = 148 threads, rounded to 160
+    assert info.threads == 160
+    for depth, tw, th in ((3, 64, 32), (8, 128, 17), (8, 232, 64), (2, 64, 5)):
+        q = pipelines.stencil_chain(24, "alternate")
+        pipelines.chain_schedule(q, depth=depth, tile_w=tw, tile_h=th, impl=hp.HP_IMPL_LINES)
+        assert q.group_info([(640, 480)], 0).kernel == hp.HP_KERNEL_STENCIL_CHAIN, (depth, tw, th)
+    # 16-bit chains: 4 or 8 stages (the box start stays 16-byte aligned)
+    for depth, kern in ((2, hp.HP_KERNEL_STENCIL_CHAIN), (4, hp.HP_KERNEL_STENCIL_LINES)):
+        q = pipelines.stencil_chain(8, "alternate", storage=hp.HP_F16)
+        pipelines.chain_schedule(q, depth=depth, tile_w=64, tile_h=32, impl=hp.HP_IMPL_LINES)
+        assert q.group_info([(640, 480)], 0).kernel == kern
+
+
 def test_bounds_inference_stencil_chain():
     # Fusing d 5x5 stages: stage k of the group needs the tile grown by 2(d-1-k) per side, clamped.
     p = pipelines.stencil_chain(4, "binomial")

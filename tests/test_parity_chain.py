@@ -130,6 +130,69 @@ def test_streaming_kernel_is_bit_identical(h, w, depth, tw, th, thr):
     assert torch.equal(bits(y), bits(base))
 
 
+LINES_SHAPES = [(2, 8, 6), (2, 64, 40), (4, 64, 10), (4, 240, 100), (6, 40, 14), (8, 128, 18), (8, 128, 64),
+                (8, 224, 40), (8, 96, 200)]
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (3, 7), (17, 33), (65, 129), (200, 300), (77, 250), (130, 515)])
+@pytest.mark.parametrize("depth,tw,th", LINES_SHAPES)
+def test_line_buffer_kernel_is_bit_identical(h, w, depth, tw, th):
+    """The line-buffer chain kernel (every stage on its own threads, rows through
+    shared-memory rings) against the generic interpreter run stage by stage:
+    images smaller than a tile, tiles cut at the right and bottom edges, tiles
+    touching the top (first row entering three taps) and the bottom (last row
+    fed twice more), and depths 2..8 (16 stages: 6 + 6 + 4 for depth 6)."""
+    img = synth.stencil_input(h, w, seed=h * 11 + w)
+    p = pipelines.stencil_chain(16, "alternate")
+    p.schedule(list(range(16)), impl=[hp.HP_IMPL_GENERIC] * 16)
+    base = chain_run(p, img)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, impl=hp.HP_IMPL_LINES)
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_LINES
+    n0 = hp.launch_count()
+    y = chain_run(p, img)
+    assert hp.launch_count() - n0 == -(-16 // depth)
+    assert torch.equal(bits(y), bits(base))
+
+
+@pytest.mark.parametrize("st", ["f16", "bf16"])
+@pytest.mark.parametrize("depth,tw,th", [(4, 64, 10), (8, 128, 64), (8, 96, 18)])
+def test_line_buffer_kernel_16bit(st, depth, tw, th):
+    dt = {"f16": hp.HP_F16, "bf16": hp.HP_BF16}[st]
+    h, w = 150, 333
+    img = synth.stencil_input(h, w, seed=5)
+    p = pipelines.stencil_chain(8, "alternate", storage=dt)
+    p.schedule(list(range(8)), impl=[hp.HP_IMPL_GENERIC] * 8)
+    base = chain_run(p, img, dt)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, impl=hp.HP_IMPL_LINES)
+    assert p.group_info([(w, h)], 0).kernel == hp.HP_KERNEL_STENCIL_LINES
+    y = chain_run(p, img, dt)
+    assert torch.equal(bits(y), bits(base))
+
+
+def test_line_buffer_kernel_full_size_against_oracle():
+    """32 stages on 2560x1536 as 4 line-buffer launches of 8 stages: bit-identical
+    to the stage-per-kernel schedule over the whole image, and the oracle at
+    sampled points (the whole-image oracle comparison of the stored schedule is
+    in test_parity_schedules)."""
+    H, W = 1536, 2560
+    img = synth.stencil_input(H, W, seed=0)
+    p = pipelines.stencil_chain(32, "alternate")
+    plain = chain_run(p, img)
+    pipelines.chain_schedule(p, depth=8, tile_w=128, tile_h=64, impl=hp.HP_IMPL_LINES)
+    n0 = hp.launch_count()
+    y = chain_run(p, img)
+    assert hp.launch_count() - n0 == 4
+    assert torch.equal(bits(y), bits(plain))
+    kinds = ost.chain_kinds(32, "alternate")
+    got = to_numpy(y)[0]
+    rng = np.random.default_rng(7)
+    pts = [(0, 0), (W - 1, H - 1), (0, H - 1), (W - 1, 0), (127, 63), (128, 64), (1300, 700), (1280, 1535)]
+    pts += [(int(x), int(yy)) for x, yy in zip(rng.integers(0, W, 16), rng.integers(0, H, 16))]
+    ref = np.array([ost.stencil_chain_point(img[0].astype(np.float64), kinds, x, yy) for x, yy in pts])
+    g = np.array([got[yy, x] for x, yy in pts], dtype=np.float64)
+    assert np.abs(g - ref).max() / (ref.max() - ref.min()) <= TOL
+
+
 @pytest.mark.parametrize("st", ["f16", "bf16"])
 def test_streaming_kernel_16bit_storage(st):
     dt = {"f16": hp.HP_F16, "bf16": hp.HP_BF16}[st]

@@ -18,7 +18,8 @@ def built():
 
 def test_chain_candidates_lower_with_the_mirrored_shared_memory():
     W, H = 2560, 1536
-    cands = [c for c in tuner.chain_candidates(32, W, H) if c.get("impl") != hp.HP_IMPL_WAVE]   # the tiled ones
+    cands = [c for c in tuner.chain_candidates(32, W, H)
+             if c.get("impl") not in (hp.HP_IMPL_WAVE, hp.HP_IMPL_LINES)]   # the tiled ones
     assert len(cands) > 100
     p = pipelines.stencil_chain(32)
     for c in cands:
@@ -33,6 +34,21 @@ def test_chain_candidates_lower_with_the_mirrored_shared_memory():
         assert (info.tile_w, info.tile_h, info.threads) == (c["tile_w"], c["tile_h"], c["threads"])
         assert info.smem_bytes == tuner.chain_smem_bytes(c["depth"], c["tile_w"], c["tile_h"]), c
         assert info.grid_x * info.grid_y == -(-W // c["tile_w"]) * -(-H // c["tile_h"])
+
+
+def test_line_buffer_candidates_lower_to_the_line_buffer_kernel():
+    for n, W, H in ((32, 2560, 1536), (4, 512, 512)):
+        cands = [c for c in tuner.chain_candidates(n, W, H) if c.get("impl") == hp.HP_IMPL_LINES]
+        assert len(cands) > 20
+        p = pipelines.stencil_chain(n)
+        for c in cands:
+            pipelines.chain_schedule(p, **c)
+            assert p.group_count() == -(-n // c["depth"])
+            for g in range(p.group_count()):
+                info = p.group_info([(W, H)], g)
+                assert info.kernel == hp.HP_KERNEL_STENCIL_LINES, c
+                assert (info.grid_x, info.grid_y) == (-(-W // c["tile_w"]), -(-H // c["tile_h"]))
+                assert info.threads <= 256 and info.smem_bytes <= tuner.SMEM_LIMIT
 
 
 def test_chain_candidates_prune_what_the_library_refuses():
