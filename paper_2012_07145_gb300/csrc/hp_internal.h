@@ -160,6 +160,7 @@ struct MaxArgs {
   ImgView in, out;
   int radius, shape, rows, threads;
   int st_mid, st_out;  // storages of the two stages (the same for a one-stage group)
+  int* err;            // device error word (bounded waits)
 };
 
 // Interpolate level group (k_interp_rows.cu): I = D over U(coarse), optionally
@@ -316,6 +317,8 @@ int ll_level_rows_grid(const LLLevelArgs& a, int units, int threads);
 int launch_ll_level_rows(const LLLevelArgs& a, int rows, int threads, int grid, void* stream);
 int max_rows_strip_w();
 int max_rows_grid(const MaxArgs& a, int units, int threads);
+// dynamic shared memory of the max filter kernel (the per-warp TMA rings; 0 when it loads from global memory)
+int max_rows_smem_bytes(const MaxArgs& a, int threads);
 int launch_max_rows(const MaxArgs& a, int grid, void* stream);
 int interp_rows_strip_w();
 int interp_rows_grid(const InterpArgs& a, int units, int threads);

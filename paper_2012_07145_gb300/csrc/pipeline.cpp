@@ -1364,7 +1364,7 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         a.in.dtype = stage_dtype_of_ref(p, first.inputs[0]);
         gp.grid_x = max_rows_grid(a, strips * planes * ((od.h + a.rows - 1) / a.rows), gp.threads);
         gp.grid_y = 1;
-        gp.smem = 0;
+        gp.smem = max_rows_smem_bytes(a, gp.threads);
         break;
       }
       case HP_KERNEL_GRID_BLUR: {
@@ -1667,6 +1667,7 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         MaxArgs a = gp.maxa;
         a.in = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.out = out;
+        a.err = p->d_err;
         e = launch_max_rows(a, gp.grid_x, stream);
         break;
       }

@@ -65,14 +65,18 @@ def test_max_filter_full_size_against_oracle_everywhere():
     assert np.array_equal(got, om.max_filter_planes(img, 4, 4))
 
 
-def test_max_filter_bf16_io():
-    h, w = 61, 77
-    img = torch.from_numpy(synth.rgb_f32(h, w, seed=10)).to(torch.bfloat16).float().numpy()
-    p = pipelines.max_filter(3, io_storage=hp.HP_BF16)
+@pytest.mark.parametrize("h,w,radius,rows", [(61, 77, 3, 16), (130, 250, 4, 5), (257, 365, 2, 0)])
+def test_max_filter_bf16_io(h, w, radius, rows):
+    """bf16 input rows reach the streaming kernel as TMA boxes that start four
+    columns left of the strip's halo lane (16-byte alignment): several strips,
+    runs cut at every offset against the 4-row boxes, and the clamped edges."""
+    img = torch.from_numpy(synth.rgb_f32(h, w, seed=10 + h)).to(torch.bfloat16).float().numpy()
+    p = pipelines.max_filter(radius, io_storage=hp.HP_BF16)
+    ref = om.max_filter_planes(img, radius, radius)   # maxima of bf16 values are bf16 values
     for impl in (None, [hp.HP_IMPL_GENERIC]):
-        p.schedule([0, 0], tile_w=[32], tile_h=[16], threads=[128], impl=impl)
+        p.schedule([0, 0], tile_w=[32], tile_h=[rows if impl is None else 16], threads=[128], impl=impl)
         got = to_numpy(run(p, [to_device(img, hp.HP_BF16)], [hp.HP_BF16], (3, h, w), hp.HP_BF16))
-        assert np.array_equal(got, om.max_filter_planes(img, 3, 3))   # maxima of bf16 values are bf16 values
+        assert np.array_equal(got, ref)
 
 
 # ------------------------------------------------------------ interpolate --
