@@ -168,6 +168,7 @@ struct MaxArgs {
 struct InterpArgs {
   ImgView fine, coarse, out;  // D_l (4 ch), I_{l+1} (4 ch), the group's output
   int rows, threads, final_div, vec;
+  int* err;  // device error word (bounded waits)
 };
 
 // Bilateral grid splat / slice (k_grid.cu).
@@ -322,6 +323,8 @@ int max_rows_smem_bytes(const MaxArgs& a, int threads);
 int launch_max_rows(const MaxArgs& a, int grid, void* stream);
 int interp_rows_strip_w();
 int interp_rows_grid(const InterpArgs& a, int units, int threads);
+// dynamic shared memory of the interpolate level kernel (the per-warp TMA rings of the fine level)
+int interp_rows_smem_bytes(int threads);
 int launch_interp_rows(const InterpArgs& a, int grid, void* stream);
 int pw_rows_op_ok(int op);
 int launch_pw_rows(const PwArgs& p, void* stream);

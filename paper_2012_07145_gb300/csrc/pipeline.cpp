@@ -1440,7 +1440,7 @@ hp_status lower(hp_pipeline* p, const std::vector<Dom>& in_dom, Plan& plan) {
         a.rows = gp.tile_h;
         gp.grid_x = interp_rows_grid(a, strips * ((cd.h + a.rows - 1) / a.rows), gp.threads);
         gp.grid_y = 1;
-        gp.smem = 0;
+        gp.smem = interp_rows_smem_bytes(gp.threads);
         break;
       }
       case HP_KERNEL_HISTEQ: {
@@ -1660,6 +1660,7 @@ hp_status run_groups_impl(hp_pipeline* p, Plan& plan, const hp_buffer* inputs, c
         a.fine = ref_view(p, plan, gp.ext_refs[0], inputs, output);
         a.coarse = ref_view(p, plan, gp.ext_refs[1], inputs, output);
         a.out = out;
+        a.err = p->d_err;
         e = launch_interp_rows(a, gp.grid_x, stream);
         break;
       }
