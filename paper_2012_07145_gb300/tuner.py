@@ -234,8 +234,9 @@ def apply_entry(p, ids, pipeline, entry):
 
 # ------------------------------------------------------------------ timing --
 def time_candidate(p, bi, bo, stream, flush, reps=15, probe=False):
-    """Median ms of `reps` graph replays (L2 flushed before each); with probe,
-    also the (kernels, max registers, max local bytes) of the launched kernels."""
+    """Median ms of `reps` graph replays (L2 flushed before each: written and
+    read back); with probe, also the (kernels, max registers, max local bytes)
+    of the launched kernels."""
     import torch
     s = stream.cuda_stream
     if probe:
@@ -248,7 +249,8 @@ def time_candidate(p, bi, bo, stream, flush, reps=15, probe=False):
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
-        flush.zero_()
+        flush.zero_()   # evict the candidate's data from L2, then leave clean lines there
+        torch.sum(flush)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
