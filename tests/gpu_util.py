@@ -25,14 +25,48 @@ def empty(c, h, w, dtype: int) -> torch.Tensor:
     return hp.padded_empty(c, h, w, TORCH_OF[dtype])
 
 
+# Guard bands around an output: every row is followed by at least 16 bytes of
+# padding, every plane by a whole padding row, and the image by GUARD bytes on
+# each side; all of it holds CANARY before a realize and must hold it after.
+GUARD = 256
+CANARY = 0xA5
+
+
+def guarded_empty(c: int, h: int, w: int, dtype: int, device="cuda") -> torch.Tensor:
+    """A [C][H][W] output with the C ABI's 16-byte strides inside a canary-filled
+    allocation (row padding, a guard row per plane, guard bytes before and after)."""
+    tdt = TORCH_OF[dtype]
+    es = torch.empty((), dtype=tdt).element_size()
+    per = 16 // es
+    wp = (w + per - 1) // per * per + per
+    plane = wp * (h + 1)
+    raw = torch.full((2 * GUARD + c * plane * es,), CANARY, dtype=torch.uint8, device=device)
+    out = raw.view(tdt)[GUARD // es:].as_strided((c, h, w), (plane, wp, 1))
+    out.guard = (raw, c, h, w * es, wp * es, plane * es)
+    return out
+
+
+def outside_writes(out: torch.Tensor) -> int:
+    """Bytes outside the image of a guarded_empty output that no longer hold CANARY."""
+    raw, c, h, wb, rs, ps = out.guard
+    mask = torch.ones_like(raw, dtype=torch.bool)
+    mask[GUARD:].as_strided((c, h, wb), (ps, rs, 1)).fill_(False)
+    return int(((raw != CANARY) & mask).sum())
+
+
 def run(p: hp.Pipeline, inputs, in_dtypes, out_shape, out_dtype, out=None) -> torch.Tensor:
-    """Realize pipeline p on device tensors; returns the output tensor."""
+    """Realize pipeline p on device tensors; returns the output tensor.  A new
+    output is guarded: the realize must write nothing outside the image."""
     bufs = [hp.buffer_from_tensor(t, d) for t, d in zip(inputs, in_dtypes)]
-    if out is None:
-        out = empty(*out_shape, out_dtype)
+    guarded = out is None
+    if guarded:
+        out = guarded_empty(*out_shape, out_dtype)
     p.realize(bufs, hp.buffer_from_tensor(out, out_dtype), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert p.device_error() == 0, "kernel reported a device-side error"
+    if guarded:
+        n = outside_writes(out)
+        assert n == 0, f"the realize wrote {n} bytes outside its {tuple(out.shape)} output"
     return out
 
 
