@@ -61,12 +61,16 @@ def run(p: hp.Pipeline, inputs, in_dtypes, out_shape, out_dtype, out=None) -> to
     guarded = out is None
     if guarded:
         out = guarded_empty(*out_shape, out_dtype)
+    # the inputs must come back unchanged (those that are not the output itself)
+    kept = [(t, t.clone()) for t in inputs if t.data_ptr() != out.data_ptr()]
     p.realize(bufs, hp.buffer_from_tensor(out, out_dtype), torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert p.device_error() == 0, "kernel reported a device-side error"
     if guarded:
         n = outside_writes(out)
         assert n == 0, f"the realize wrote {n} bytes outside its {tuple(out.shape)} output"
+    for t, before in kept:
+        assert torch.equal(bits(t), bits(before)), "the realize changed one of its inputs"
     return out
 
 
