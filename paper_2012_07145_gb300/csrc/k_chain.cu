@@ -17,9 +17,10 @@
 //  3. Tiles that touch the image border replicate the edge of every stage into
 //     the out-of-image part of its rectangle, so each stage reads its producer
 //     with the clamp-to-edge boundary on the producer's own domain.
-//  4. The last stage is written to global memory with 128-bit (f32) or 64-bit
-//     (f16/bf16) coalesced stores; an optional unsharp epilogue combines it
-//     with the chain's input.
+//  4. The last stage goes straight from the y pass to global memory, one
+//     128-bit (f32) or 64-bit (f16/bf16) store per 4-column row; with the
+//     optional unsharp epilogue it is staged in shared memory and combined
+//     with the chain's input on the way out.
 // Every value uses the separable x-then-y fma chain of stage_math.cuh and is
 // rounded to the stage's storage type, so the result is bit-identical to the
 // stage-per-kernel schedule (which is this kernel with d = 1).
@@ -109,6 +110,44 @@ struct SmemSink {
   int P;
   __device__ __forceinline__ void put(int b, int y, const float4& v) const {
     *reinterpret_cast<float4*>(dst + y * P + 4 * b) = v;
+  }
+};
+
+// Output sink of the last stage (no epilogue): the output image, rows and
+// columns past the tile or the image dropped.
+template <int ODT>
+struct GlobalSink {
+  char* plane;
+  long long rs;
+  int ox, oy, th, tw, W, H;
+  const ImgView* out;
+  int ch;
+  __device__ __forceinline__ void put(int b, int y, const float4& v) const {
+    if (y >= th || oy + y >= H) return;
+    const int x = 4 * b, gx = ox + x;
+    char* row = plane + (long long)(oy + y) * rs;
+    if (ODT != 3 && x + 3 < tw && gx + 3 < W) {
+      if (ODT == 0) {
+        *reinterpret_cast<float4*>(row + 4LL * gx) = v;
+      } else {
+        uint2 u;
+        if (ODT == 1) {
+          __half2 p0 = __floats2half2_rn(v.x, v.y), p1 = __floats2half2_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        } else {
+          __nv_bfloat162 p0 = __floats2bfloat162_rn(v.x, v.y), p1 = __floats2bfloat162_rn(v.z, v.w);
+          u.x = *reinterpret_cast<unsigned*>(&p0);
+          u.y = *reinterpret_cast<unsigned*>(&p1);
+        }
+        *reinterpret_cast<uint2*>(row + 2LL * gx) = u;
+      }
+    } else {
+      const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (x + k < tw && gx + k < W) store_px(*out, ch, gx + k, oy + y, vv[k]);
+    }
   }
 };
 
@@ -245,6 +284,13 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       wy[k] = a.w[s - 1][5 + k];
     }
     const int dt = a.storage[s - 1];
+    if (s == d && a.epilogue == 0) {
+      // the last stage straight to the output; nothing reads shared memory after it
+      GlobalSink<ODT> gs{(char*)a.out.data + (long long)ch * a.out.ps, a.out.rs, ox, oy, a.tile_h, a.tile_w,
+                         a.out.w, a.out.h, &a.out, ch};
+      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, gs);
+      return;
+    }
     sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, SmemSink{dst, g.P});
     if (s < d && border) {
       __syncthreads();
@@ -253,7 +299,8 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
     __syncthreads();
   }
 
-  // ---- copy the last stage out with coalesced 128-bit (f32) / 64-bit stores ----
+  // ---- with the unsharp epilogue: combine and copy the last stage out with
+  // coalesced 128-bit (f32) / 64-bit stores ----
   const float* last = (d & 1) ? bufB : bufA;
   const int hlim = min(a.tile_h, a.out.h - oy), wlim = min(a.tile_w, a.out.w - ox);
   const int nb4 = a.tile_w >> 2;
