@@ -210,7 +210,9 @@ __device__ __forceinline__ float staged_value(const unsigned char* st, int idx, 
   return reinterpret_cast<const float*>(st)[idx];
 }
 
-template <int RND, int ODT, int SEG>
+// PC: the buffers' row pitch as a compile-time constant (0: the tile's own, at
+// run time); with it every shared-memory row of a sweep is an immediate offset.
+template <int RND, int ODT, int SEG, int PC>
 __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKParams kp) {
   grid_dep_sync();
   const ChainArgs& a = kp.a;
@@ -222,6 +224,7 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
   volatile int* status = reinterpret_cast<volatile int*>(base + 64);
   const int d = a.depth;
   const ChainGeom g = chain_geom(d, a.tile_w, a.tile_h);
+  const int P = PC ? PC : g.P;
   float* bufA = reinterpret_cast<float*>(base + kSmemHeader);
   float* bufB = bufA + g.buf;
   const int ch = blockIdx.z;
@@ -288,10 +291,10 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
       // the last stage straight to the output; nothing reads shared memory after it
       GlobalSink<ODT> gs{(char*)a.out.data + (long long)ch * a.out.ps, a.out.rs, ox, oy, a.tile_h, a.tile_w,
                          a.out.w, a.out.h, &a.out, ch};
-      sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, gs);
+      sweep<SEG, RND>(src, P, Ws, Hs, wx, wy, dt, gs);
       return;
     }
-    sweep<SEG, RND>(src, g.P, Ws, Hs, wx, wy, dt, SmemSink{dst, g.P});
+    sweep<SEG, RND>(src, P, Ws, Hs, wx, wy, dt, SmemSink{dst, P});
     if (s < d && border) {
       __syncthreads();
       fixup(dst, g.P, ox - 2 * (d - s), oy - 2 * (d - s), Ws, Hs, W, H);
@@ -353,9 +356,16 @@ __global__ void __launch_bounds__(512) k_chain(const __grid_constant__ ChainKPar
 
 typedef void (*ChainKernel)(ChainKParams);
 
+// The pitch of a 64-column tile of depth 4 (64 + 16 columns) is compiled in
+// for the uniform-type kernels.
+constexpr int kPitch64d4 = 80;
+
 template <int RND, int ODT>
-ChainKernel by_seg(int seg) {
-  return seg == 4 ? k_chain<RND, ODT, 4> : seg == 16 ? k_chain<RND, ODT, 16> : k_chain<RND, ODT, 8>;
+ChainKernel by_seg(int seg, int pitch) {
+  if (RND != 3 && pitch == kPitch64d4)
+    return seg == 4 ? k_chain<RND, ODT, 4, kPitch64d4> : seg == 16 ? k_chain<RND, ODT, 16, kPitch64d4>
+                                                                  : k_chain<RND, ODT, 8, kPitch64d4>;
+  return seg == 4 ? k_chain<RND, ODT, 4, 0> : seg == 16 ? k_chain<RND, ODT, 16, 0> : k_chain<RND, ODT, 8, 0>;
 }
 
 // Picks the instantiation: one rounding kind for every stage and a vector
@@ -367,11 +377,13 @@ ChainKernel pick_kernel(const ChainArgs& a, int* variant) {
   for (int i = 1; i < a.depth; ++i) uniform &= a.storage[i] == s0;
   const int si = a.seg == 4 ? 0 : a.seg == 16 ? 2 : 1;
   const bool same = uniform && a.out.dtype == s0;
-  if (same && s0 == HP_F32) { *variant = 0 * 3 + si; return by_seg<0, 0>(a.seg); }
-  if (same && s0 == HP_F16) { *variant = 1 * 3 + si; return by_seg<1, 1>(a.seg); }
-  if (same && s0 == HP_BF16) { *variant = 2 * 3 + si; return by_seg<2, 2>(a.seg); }
+  const int pitch = chain_geom(a.depth, a.tile_w, a.tile_h).P;
+  const int pc = pitch == kPitch64d4 ? 12 : 0;  // the compiled-pitch kernels' variant numbers follow
+  if (same && s0 == HP_F32) { *variant = pc + 0 * 3 + si; return by_seg<0, 0>(a.seg, pitch); }
+  if (same && s0 == HP_F16) { *variant = pc + 1 * 3 + si; return by_seg<1, 1>(a.seg, pitch); }
+  if (same && s0 == HP_BF16) { *variant = pc + 2 * 3 + si; return by_seg<2, 2>(a.seg, pitch); }
   *variant = 3 * 3 + si;
-  return by_seg<3, 3>(a.seg);
+  return by_seg<3, 3>(a.seg, pitch);
 }
 
 }  // namespace
@@ -383,7 +395,7 @@ int chain_smem_bytes(int depth, int tile_w, int tile_h, int in_dtype) {
 }
 
 int launch_chain(const ChainArgs& a, int smem_bytes, void* stream) {
-  static bool configured[12] = {};
+  static bool configured[24] = {};
   int variant = 0;
   ChainKernel kern = pick_kernel(a, &variant);
   if (!configured[variant]) {  // opt in once: static shared memory also counts against the default 48 KB
