@@ -164,8 +164,13 @@ __device__ __forceinline__ void sweep(const float* __restrict__ src, int P, int 
   const int nb = Ws >> 2;
   const int nseg = (Hs + SEG - 1) / SEG;
   const int items = nb * nseg;
+  // it / nb as a float product: (it + 0.5) / nb lies at least 0.5 / nb from an
+  // integer, and the product (a correctly rounded reciprocal, one rounding)
+  // is off by less than (it / nb) 2^-22, which is smaller for every it below
+  // 2^21 (a tile has fewer than 2^12 items); the truncation is the exact quotient
+  const float rnb = __frcp_rn((float)nb);
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int sg = it / nb;
+    const int sg = (int)(((float)it + 0.5f) * rnb);
     const int b = it - sg * nb;
     const int r0 = sg * SEG;
     const float* p = src + r0 * P + 4 * b;
