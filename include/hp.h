@@ -327,7 +327,8 @@ hp_status hp_kernel_attrs_get(hp_pipeline* p, int* n_kernels, int* max_registers
  * and enough of an HBM arena reserved at creation (`hbm_budget_bytes`) are
  * free; admitted requests run concurrently (copy in, realize, copy out).  Up to
  * `max_batch` queued requests for the same pipeline, image size and buffer
- * kind are served by one realize: their images are stacked as planes, so each
+ * kind, with at most 32 MB of inputs and outputs in all, are served by one
+ * realize: their images are stacked as planes, so each
  * kernel launches once, as one persistent grid, for the batch, and every
  * result equals the request's solo result.  Batching covers pipelines whose
  * stages act on each channel separately (stencils, resampling, per-channel
@@ -373,8 +374,13 @@ hp_status hp_server_wait(hp_server* s, unsigned long long ticket, int timeout_ms
 hp_status hp_server_stats_get(hp_server* s, hp_server_stats* stats);
 /* Makes every slot's copy of pipeline p ready for requests whose inputs have
  * the sizes of `inputs` (only width, height, dtype and channels are read):
- * lowering, scratch and kernel state, so the first such request does no
- * allocation or lowering on the worker thread.  Call before traffic. */
+ * lowering, scratch and kernel state, a resident staging region and the
+ * captured graph of the realize, so the first such request does no
+ * allocation, lowering or capture on the worker thread.  When the server
+ * batches requests of this shape (max_batch > 1, a batchable pipeline) the
+ * same is done for every batch it may form: 2 .. max_batch requests of at most
+ * 32 MB of inputs and outputs in all, with host and with device buffers.
+ * Call before traffic. */
 hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* inputs, int n_inputs);
 /* Finishes queued and running requests, then frees the server. */
 hp_status hp_server_destroy(hp_server* s);

@@ -58,7 +58,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-constexpr long long kBatchBytesMax = 32LL << 20;  // largest single request (inputs + output) that is batched
+constexpr long long kBatchBytesMax = 32LL << 20;  // largest batch (inputs + outputs of all its requests)
 
 int dtype_size(int d) { return d == HP_U8 ? 1 : (d == HP_U16 || d == HP_F16 || d == HP_BF16) ? 2 : 4; }
 using hp::Arena;
@@ -297,11 +297,13 @@ void finish_slot(hp_server* s, Slot& sl, hp_status st) {
 Slot* admit(hp_server* s) {
   Request* head = s->queue.front();
   std::vector<size_t> pick{0};
-  // only requests of modest size are batched: a large request already fills
-  // the GPU on its own, and a batch would make each request wait for every
-  // other one's copies
-  if (s->max_batch > 1 && staging_bytes(*head, 1) <= kBatchBytesMax && batchable(s, *head)) {
-    for (size_t i = 1; i < s->queue.size() && (int)pick.size() < s->max_batch && i < 64; ++i)
+  // only requests of modest size are batched, and a batch holds at most
+  // kBatchBytesMax: a large request already fills the GPU on its own, and a
+  // batch makes each request wait for every other one's copies
+  if (s->max_batch > 1 && staging_bytes(*head, 2) <= kBatchBytesMax && batchable(s, *head)) {
+    for (size_t i = 1; i < s->queue.size() && (int)pick.size() < s->max_batch && i < 64 &&
+                       staging_bytes(*head, (int)pick.size() + 1) <= kBatchBytesMax;
+         ++i)
       if (same_shape(*head, *s->queue[i])) pick.push_back(i);
   }
   while (true) {
@@ -545,48 +547,64 @@ hp_status hp_server_prepare(hp_server* s, hp_pipeline* p, const hp_buffer* input
   hp_status st = hp::pipeline_output_shape(p, ws.data(), hs.data(), n_inputs, &ow, &oh, &oc, &odt);
   if (st) return st;
   r.out = hp_buffer{nullptr, (hp_dtype)odt, oc, ow, oh, 0, 0};
-  const ShapeKey key = shape_key(r, 1);
-  std::lock_guard<std::mutex> ck(s->clone_mu);  // the worker realizes the slots' copies under this lock
-  for (Slot& sl : s->slots) {
-    hp_pipeline* c = slot_clone(sl, p, 1);
-    if (!c) return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: pipeline cannot be copied");
-    if ((st = hp_prepare(c, ws.data(), hs.data(), n_inputs, sl.stream))) return st;
-    // the slot's staging region for this shape, resident from now on, and the
-    // graph of its realize on it (two realizes: the first runs, the second
-    // captures), so the first request of the shape already replays a graph;
-    // an idle slot only (a busy one may be using its regions)
-    Resident* region = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      if (sl.busy) continue;
-      auto it = sl.resident.find(key);
-      if (it == sl.resident.end()) {
-        long long off = 0;
-        const long long bytes = staging_bytes(r, 1);
-        if (!s->arena.alloc(bytes, &off)) continue;  // no room: the shape becomes resident on first use
-        Resident& nr = sl.resident[key];
-        nr.off = off;
-        nr.bytes = bytes;
-        it = sl.resident.find(key);
-      }
-      it->second.last = ++s->admissions;
-      region = &it->second;
-      sl.busy = true;  // the worker leaves the slot alone meanwhile
-    }
-    std::vector<hp_buffer> din;
-    hp_buffer dout;
-    staging_layout(s->arena.base + region->off, r, 1, din, dout);
-    for (int k = 0; k < 2 && !st; ++k) st = hp_realize(c, din.data(), n_inputs, &dout, sl.stream);
-    if (!st && cudaStreamSynchronize(sl.stream) != cudaSuccess) {
-      cudaGetLastError();
-      st = hp::report_error(HP_ERR_CUDA, "hp_server_prepare: realize on the staging region failed");
-    }
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      sl.busy = false;
-    }
-    if (st) return st;
+  // the batches of this shape the server may form (2 .. max_batch requests of
+  // at most kBatchBytesMax in all, host or device buffers) are made ready too,
+  // so that no batch size is lowered, allocated or captured while requests
+  // are in flight
+  bool batches;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    batches = s->max_batch > 1 && staging_bytes(r, 2) <= kBatchBytesMax && batchable(s, r);
   }
+  int bmax = 1;
+  if (batches)
+    while (bmax < s->max_batch && staging_bytes(r, bmax + 1) <= kBatchBytesMax) ++bmax;
+  std::lock_guard<std::mutex> ck(s->clone_mu);  // the worker realizes the slots' copies under this lock
+  for (int B = 1; B <= bmax; ++B)
+    for (int dev = 0; dev < (B > 1 ? 2 : 1); ++dev) {
+      r.device = dev != 0;
+      const ShapeKey key = shape_key(r, B);
+      for (Slot& sl : s->slots) {
+        hp_pipeline* c = slot_clone(sl, p, B);
+        if (!c) return hp::report_error(HP_ERR_INVALID_ARG, "hp_server_prepare: pipeline cannot be copied");
+        if ((st = hp_prepare(c, ws.data(), hs.data(), n_inputs, sl.stream))) return st;
+        // the slot's staging region for this shape, resident from now on, and
+        // the graph of its realize on it (two realizes: the first runs, the
+        // second captures), so the first request of the shape already replays
+        // a graph; an idle slot only (a busy one may be using its regions)
+        Resident* region = nullptr;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          if (sl.busy) continue;
+          auto it = sl.resident.find(key);
+          if (it == sl.resident.end()) {
+            long long off = 0;
+            const long long bytes = staging_bytes(r, B);
+            if (!s->arena.alloc(bytes, &off)) continue;  // no room: the shape becomes resident on first use
+            Resident& nr = sl.resident[key];
+            nr.off = off;
+            nr.bytes = bytes;
+            it = sl.resident.find(key);
+          }
+          it->second.last = ++s->admissions;
+          region = &it->second;
+          sl.busy = true;  // the worker leaves the slot alone meanwhile
+        }
+        std::vector<hp_buffer> din;
+        hp_buffer dout;
+        staging_layout(s->arena.base + region->off, r, B, din, dout);
+        for (int k = 0; k < 2 && !st; ++k) st = hp_realize(c, din.data(), n_inputs, &dout, sl.stream);
+        if (!st && cudaStreamSynchronize(sl.stream) != cudaSuccess) {
+          cudaGetLastError();
+          st = hp::report_error(HP_ERR_CUDA, "hp_server_prepare: realize on the staging region failed");
+        }
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          sl.busy = false;
+        }
+        if (st) return st;
+      }
+    }
   return HP_OK;
 }
 
