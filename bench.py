@@ -697,21 +697,33 @@ def run_ours(args, cfg_name):
         dist.barrier()
         ms = replicas.max_over_ranks(ms, device="cuda")   # the slowest replica bounds the job
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: every step copies
+    # its image in and its result out.  A stream of images through
+    # hp_realize_host_async (the copies of one image overlap the realize of
+    # the next; one wait at the end), and one image per synchronous
+    # hp_realize_host call
     p, inputs = r["p"], r["inputs"]
     C, OH, OW, odt = cfg["out"]
     hin = [_host_tensor(a, dt) for a, dt in inputs]
     hout = torch.empty((C, OH, OW), dtype=_torch_dtype(odt)).pin_memory()
     hbi = [hp.buffer_from_tensor(t, dt) for t, (_, dt) in zip(hin, inputs)]
     hbo = hp.buffer_from_tensor(hout, odt)
+    e2e_steps = max(10, min(args.steps, 200))
+    for _ in range(3):
+        p.realize_host_async(hbi, hbo, stream.cuda_stream)
+    p.realize_host_wait()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        p.realize_host_async(hbi, hbo, stream.cuda_stream)
+    p.realize_host_wait()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    err_e2e = cfg["parity"](_to_numpy(hout, odt), inputs)
     for _ in range(3):
         p.realize_host(hbi, hbo, stream.cuda_stream)
-    e2e_steps = max(10, min(args.steps, 200))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         p.realize_host(hbi, hbo, stream.cuda_stream)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    err_e2e = cfg["parity"](_to_numpy(hout, odt), inputs)
+    e2e_sync_s = (time.perf_counter() - t0) / e2e_steps
 
     # the other workloads, compactly, on the same GPU (rank 0's replica only)
     others = {}
@@ -754,7 +766,11 @@ def run_ours(args, cfg_name):
                   "schedule": "stage-per-kernel (one launch per stage), CUDA graph replay"},
         "speedup_vs_plain": round(r["plain_ms"] / ms, 3),
         "e2e": {"value": round(npx / e2e_s / 1e6, 2), "unit": "MPix/s",
-                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes, "parity_spot": err_e2e},
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes, "parity_spot": err_e2e,
+                "api": "hp_realize_host_async per image (copy in, realize, copy out; consecutive images "
+                       "overlap), hp_realize_host_wait after the last",
+                "one_image_per_call": {"value": round(npx / e2e_sync_s / 1e6, 2), "unit": "MPix/s",
+                                       "api": "hp_realize_host (synchronises every call)"}},
         "gpu_launches": int(r["launches"]),
         "roofline": r["roof"],
         "fp32_peak_probe": fp32,

@@ -277,6 +277,24 @@ hp_status hp_prepare(hp_pipeline* p, const int* widths, const int* heights, int 
 hp_status hp_realize_host(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
                           const hp_buffer* output, void* stream);
 
+/* hp_realize_host without waiting, for a stream of images from host memory:
+ * enqueues the copies of the inputs to device staging (on a copy stream the
+ * pipeline owns), the realize on `stream`, and the copy of the output back
+ * (on a second copy stream the pipeline owns), and returns.  The pipeline
+ * alternates between two staging sets, so consecutive calls overlap: the
+ * copy in of one image with the realize of the previous one and the copy out
+ * of the one before.  Every call's input and output host buffers (pinned
+ * memory: pageable copies are synchronous) must stay valid and unchanged
+ * until hp_realize_host_wait returns; consecutive calls on one pipeline must
+ * pass the same `stream` (the realizes share the pipeline's intermediate
+ * buffers and are ordered by it).  Errors of the enqueueing calls are
+ * returned at once; the device error word is read by hp_check_device_error. */
+hp_status hp_realize_host_async(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
+                                const hp_buffer* output, void* stream);
+/* Waits until every hp_realize_host_async call on p so far has written its
+ * output to host memory (a no-op when there was none). */
+hp_status hp_realize_host_wait(hp_pipeline* p);
+
 /* Lowering facts of group g for inputs of the given sizes (width/height per
  * input).  Host only: needs no GPU. */
 hp_status hp_group_info_get(hp_pipeline* p, const int* in_widths, const int* in_heights,

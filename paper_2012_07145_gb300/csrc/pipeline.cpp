@@ -130,6 +130,7 @@ struct Plan {
   std::vector<GroupPlan> groups; // in execution order
   std::map<int, Scratch> bufs;   // exported stage -> device buffer
   std::vector<Scratch> staging;  // hp_realize_host device copies (inputs..., output)
+  std::vector<Scratch> staging_async[2];  // hp_realize_host_async's two alternating sets
   std::vector<GraphEntry> graphs;
   std::vector<std::vector<long long>> seen;  // keys realized once without a graph
   bool allocated = false;
@@ -162,6 +163,11 @@ struct hp_pipeline {
   hp::KernelProbe probed{0, 0, 0};
   cudaStream_t capture_stream = nullptr;
   unsigned long long uses = 0;
+  // hp_realize_host_async: its copy-in and copy-out streams, and per staging
+  // set the events "inputs copied", "realized" and "output copied back"
+  cudaStream_t host_in = nullptr, host_out = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_free[2] = {};
+  unsigned long long async_calls = 0;
 };
 
 namespace hp {
@@ -1553,11 +1559,15 @@ void free_plan(Plan& plan) {
       gp.aux = nullptr;
     }
   for (auto& sc : plan.staging) cudaFree(sc.ptr);
+  for (auto& set : plan.staging_async)
+    for (auto& sc : set) cudaFree(sc.ptr);
   plan.bufs.clear();
   plan.staging.clear();
+  for (auto& set : plan.staging_async) set.clear();
 }
 
 void drop_plans(hp_pipeline* p) {
+  if (p->host_out) cudaStreamSynchronize(p->host_out);  // no hp_realize_host_async work in flight
   for (auto& kv : p->plans) free_plan(*kv.second);
   p->plans.clear();
 }
@@ -2045,6 +2055,99 @@ hp_status hp_realize_host(hp_pipeline* p, const hp_buffer* inputs, int n_inputs,
   return HP_OK;
 }
 
+hp_status hp_realize_host_async(hp_pipeline* p, const hp_buffer* inputs, int n_inputs, const hp_buffer* output,
+                                void* stream) {
+  std::vector<Dom> in_dom;
+  if (!p || !inputs || n_inputs != (int)p->in_dtypes.size() || !output)
+    return fail(HP_ERR_INVALID_ARG, "hp_realize_host_async: bad arguments");
+  for (int i = 0; i <= n_inputs; ++i)
+    if (!(i < n_inputs ? inputs[i] : *output).data) return fail(HP_ERR_INVALID_ARG, "null host buffer");
+  for (int i = 0; i < n_inputs; ++i) in_dom.push_back(Dom{inputs[i].width, inputs[i].height});
+  Plan* plan = nullptr;
+  hp_status s = get_plan(p, in_dom, &plan);
+  if (s) return s;
+  if (!p->host_in) {
+    cudaStream_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) || cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking)) {
+      cudaGetLastError();
+      if (a) cudaStreamDestroy(a);
+      return fail(HP_ERR_CUDA, "hp_realize_host_async: stream creation failed");
+    }
+    for (int j = 0; j < 2; ++j)
+      if (cudaEventCreateWithFlags(&p->ev_in[j], cudaEventDisableTiming) ||
+          cudaEventCreateWithFlags(&p->ev_done[j], cudaEventDisableTiming) ||
+          cudaEventCreateWithFlags(&p->ev_free[j], cudaEventDisableTiming)) {
+        cudaGetLastError();
+        cudaStreamDestroy(a);
+        cudaStreamDestroy(b);
+        return fail(HP_ERR_CUDA, "hp_realize_host_async: event creation failed");
+      }
+    p->host_in = a;
+    p->host_out = b;
+  }
+  const int j = (int)(p->async_calls & 1);
+  std::vector<Scratch>& set = plan->staging_async[j];
+  if (set.empty()) {
+    set.resize(n_inputs + 1);
+    for (int i = 0; i <= n_inputs; ++i) {
+      const hp_buffer& b = i < n_inputs ? inputs[i] : *output;
+      const size_t bytes = (size_t)round16((long long)b.width * dtype_bytes(b.dtype)) * b.height * b.channels;
+      if (cudaMalloc(&set[i].ptr, bytes)) {
+        cudaGetLastError();
+        for (int k = 0; k < i; ++k) cudaFree(set[k].ptr);
+        set.clear();
+        return fail(HP_ERR_OOM, "cudaMalloc of %zu staging bytes failed", bytes);
+      }
+      set[i].bytes = bytes;
+    }
+  }
+  std::vector<hp_buffer> dev_in(n_inputs);
+  hp_buffer dev_out = *output;
+  for (int i = 0; i <= n_inputs; ++i) {
+    const hp_buffer& b = i < n_inputs ? inputs[i] : *output;
+    hp_buffer d = b;
+    d.data = set[i].ptr;
+    d.row_stride_bytes = round16((long long)b.width * dtype_bytes(b.dtype));
+    d.plane_stride_bytes = d.row_stride_bytes * b.height;
+    if (i < n_inputs) dev_in[i] = d;
+    else dev_out = d;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // the set's previous copy out (two calls back) is done before its staging is reused
+  if (cudaStreamWaitEvent(p->host_in, p->ev_free[j], 0)) return cuda_fail(cudaGetLastError(), "stream wait");
+  for (int i = 0; i < n_inputs; ++i)
+    for (int c = 0; c < inputs[i].channels; ++c) {
+      int e = cudaMemcpy2DAsync((char*)dev_in[i].data + c * dev_in[i].plane_stride_bytes, dev_in[i].row_stride_bytes,
+                                (const char*)inputs[i].data + c * inputs[i].plane_stride_bytes, inputs[i].row_stride_bytes,
+                                (size_t)inputs[i].width * dtype_bytes(inputs[i].dtype), inputs[i].height,
+                                cudaMemcpyHostToDevice, p->host_in);
+      if (e) return cuda_fail(e, "host-to-device copy");
+    }
+  if (cudaEventRecord(p->ev_in[j], p->host_in) || cudaStreamWaitEvent(st, p->ev_in[j], 0))
+    return cuda_fail(cudaGetLastError(), "event record / wait");
+  if ((s = hp_realize(p, dev_in.data(), n_inputs, &dev_out, stream))) return s;
+  if (cudaEventRecord(p->ev_done[j], st) || cudaStreamWaitEvent(p->host_out, p->ev_done[j], 0))
+    return cuda_fail(cudaGetLastError(), "event record / wait");
+  for (int c = 0; c < output->channels; ++c) {
+    int e = cudaMemcpy2DAsync((char*)output->data + c * output->plane_stride_bytes, output->row_stride_bytes,
+                              (const char*)dev_out.data + c * dev_out.plane_stride_bytes, dev_out.row_stride_bytes,
+                              (size_t)output->width * dtype_bytes(output->dtype), output->height,
+                              cudaMemcpyDeviceToHost, p->host_out);
+    if (e) return cuda_fail(e, "device-to-host copy");
+  }
+  if (cudaEventRecord(p->ev_free[j], p->host_out)) return cuda_fail(cudaGetLastError(), "event record");
+  ++p->async_calls;
+  return HP_OK;
+}
+
+hp_status hp_realize_host_wait(hp_pipeline* p) {
+  if (!p) return fail(HP_ERR_INVALID_ARG, "null pipeline");
+  if (!p->host_out) return HP_OK;
+  int e = cudaStreamSynchronize(p->host_out);
+  if (e) return cuda_fail(e, "stream synchronize");
+  return HP_OK;
+}
+
 hp_status hp_group_count(hp_pipeline* p, int* n) {
   if (!p || !n) return fail(HP_ERR_INVALID_ARG, "null argument");
   if (p->output < 0) return fail(HP_ERR_STATE, "no output stage set");
@@ -2256,6 +2359,13 @@ hp_status hp_pipeline_destroy(hp_pipeline* p) {
   if (!p) return fail(HP_ERR_INVALID_ARG, "null pipeline");
   drop_plans(p);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  if (p->host_in) cudaStreamDestroy(p->host_in);
+  if (p->host_out) cudaStreamDestroy(p->host_out);
+  for (int j = 0; j < 2; ++j) {
+    if (p->ev_in[j]) cudaEventDestroy(p->ev_in[j]);
+    if (p->ev_done[j]) cudaEventDestroy(p->ev_done[j]);
+    if (p->ev_free[j]) cudaEventDestroy(p->ev_free[j]);
+  }
   if (p->d_err) cudaFree(p->d_err);
   delete p;
   return HP_OK;

@@ -80,7 +80,7 @@ EXPORTS = ["hp_pipeline_create", "hp_add_stage", "hp_set_output", "hp_schedule_s
            "hp_pipeline_destroy", "hp_last_error", "hp_launch_count", "hp_histeq_u8_noalloc",
            "hp_server_create", "hp_server_submit", "hp_server_wait", "hp_server_stats_get", "hp_server_destroy",
            "hp_prepare", "hp_server_prepare", "hp_measure_fp32_peak", "hp_kernel_attrs_get",
-           "hp_server_submit_device"]
+           "hp_server_submit_device", "hp_realize_host_async", "hp_realize_host_wait"]
 
 _lib = None
 
@@ -99,6 +99,8 @@ def lib():
         L.hp_schedule_set.argtypes = [P, ctypes.POINTER(Schedule)]
         L.hp_realize.argtypes = [P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer), P]
         L.hp_realize_host.argtypes = [P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer), P]
+        L.hp_realize_host_async.argtypes = [P, ctypes.POINTER(Buffer), ctypes.c_int, ctypes.POINTER(Buffer), P]
+        L.hp_realize_host_wait.argtypes = [P]
         L.hp_group_info_get.argtypes = [P, _IP, _IP, ctypes.c_int, ctypes.POINTER(GroupInfo)]
         L.hp_group_count.argtypes = [P, _IP]
         L.hp_infer_bounds.argtypes = [P, _IP, _IP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -257,6 +259,15 @@ class Pipeline:
     def realize_host(self, inputs, output, stream=None):
         arr = (Buffer * len(inputs))(*inputs)
         check(lib().hp_realize_host(self.h, arr, len(inputs), ctypes.byref(output), ctypes.c_void_p(stream or 0)))
+
+    def realize_host_async(self, inputs, output, stream=None):
+        """Enqueues copy in, realize and copy out of host buffers (hp_realize_host_async);
+        the buffers must stay alive and unchanged until realize_host_wait()."""
+        arr = (Buffer * len(inputs))(*inputs)
+        check(lib().hp_realize_host_async(self.h, arr, len(inputs), ctypes.byref(output), ctypes.c_void_p(stream or 0)))
+
+    def realize_host_wait(self):
+        check(lib().hp_realize_host_wait(self.h))
 
     def set_option(self, option: int, value: int):
         check(lib().hp_set_option(self.h, option, value))

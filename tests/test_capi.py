@@ -139,6 +139,21 @@ def test_lowering_line_buffer_chain():
         assert q.group_info([(640, 480)], 0).kernel == kern
 
 
+def test_async_host_realize_refuses_bad_arguments_before_any_cuda_call():
+    """hp_realize_host_async checks its arguments (and every host pointer) before
+    lowering or touching the device; waiting with nothing enqueued returns at once."""
+    L = hp.lib()
+    assert L.hp_realize_host_async(None, None, 0, None, None) == hp.HP_ERR_INVALID_ARG
+    assert L.hp_realize_host_wait(None) == hp.HP_ERR_INVALID_ARG
+    p = pipelines.stencil_chain(4, "binomial")
+    inp = hp.Buffer(None, hp.HP_F32, 1, 64, 32, 256, 256 * 32)
+    out = hp.Buffer(None, hp.HP_F32, 1, 64, 32, 256, 256 * 32)
+    with pytest.raises(hp.HPError) as e:
+        p.realize_host_async([inp], out)
+    assert e.value.status == hp.HP_ERR_INVALID_ARG
+    p.realize_host_wait()
+
+
 def test_bounds_inference_stencil_chain():
     # Fusing d 5x5 stages: stage k of the group needs the tile grown by 2(d-1-k) per side, clamped.
     p = pipelines.stencil_chain(4, "binomial")
