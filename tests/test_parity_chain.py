@@ -53,6 +53,27 @@ def test_small_and_ragged_against_oracle(h, w, depth):
     assert torch.equal(bits(y), bits(base))
 
 
+# Tiled-kernel shapes at the edges of its geometry: 16 and 32 stages in one
+# launch (halo wider than the image), a tile taller than one TMA box (two
+# stacked boxes), rows wider than a TMA box (clamped per-thread loads), and an
+# odd depth whose halo origin is not 16-byte aligned (boxes staged and shifted).
+@pytest.mark.parametrize("depth,tw,th,thr,seg,h,w", [
+    (16, 8, 8, 64, 4, 45, 70), (32, 8, 8, 128, 8, 70, 45), (2, 8, 300, 64, 16, 610, 20),
+    (2, 264, 16, 256, 8, 40, 600), (3, 248, 20, 256, 4, 33, 520), (5, 200, 12, 128, 16, 50, 410)])
+def test_tiled_chain_geometry_edges(depth, tw, th, thr, seg, h, w):
+    img = synth.stencil_input(h, w, seed=depth * 100 + tw)
+    kinds = ost.chain_kinds(32, "alternate")
+    ref = ost.stencil_chain(img[0].astype(np.float64), kinds)
+    p = pipelines.stencil_chain(32, "alternate")
+    base = chain_run(p, img)
+    pipelines.chain_schedule(p, depth=depth, tile_w=tw, tile_h=th, threads=thr, serial_y=seg)
+    n0 = hp.launch_count()
+    y = chain_run(p, img)
+    assert hp.launch_count() - n0 == -(-32 // depth)
+    assert torch.equal(bits(y), bits(base))
+    assert rel_err(to_numpy(y)[0], ref) <= TOL
+
+
 def test_config2_fused_32_stage_full_size():
     H, W = 1536, 2560
     img = synth.stencil_input(H, W, seed=0)

@@ -85,13 +85,15 @@ def chain_boxes(d, tw, th, dt, tiles_x):
 def test_tiled_chain_boxes(dt):
     esize = ESIZE[dt]
     checked = 0
-    for d, tw, th in itertools.product(range(1, 9), range(8, 257, 8), (1, 6, 16, 31, 64, 100, 200, 252, 300)):
+    for d, tw, th in itertools.product(list(range(1, 9)) + [16, 32], range(8, 257, 8),
+                                       (1, 6, 16, 31, 64, 100, 200, 252, 300)):
         res, g = chain_boxes(d, tw, th, dt, tiles_x=6)
         if 128 + 128 + 2 * g["buf"] * 4 > SMEM_LIMIT or res is None:
             continue
         boxes, tx = res
         total = sum(check_box(dims, esize, x, dst) for dims, x, dst, _ in boxes) // 6
         assert total == tx          # one mbarrier expects every box of the tile
+        assert tx < 1 << 20         # within an mbarrier's transaction count
         checked += 1
     assert checked > 100
 
