@@ -153,7 +153,7 @@ enum {
                           (120 / 112 columns), tile_h rows per run, threads <= 256; again the default
                           under HP_IMPL_AUTO when tile_w is the strip width.
                           A pyramid downsample of f32 planes, and the first local-Laplacian
-                          downsample with gray and the remap inlined (K = 8, u16 or f32 input, 2 sigma
+                          downsample with gray and the remap inlined (K = 8, u16 or f32 input, sigma
                           below the level spacing 1/7): strips of 30 coarse columns, tile_h coarse rows
                           per run, threads <= 256; the default under HP_IMPL_AUTO when tile_w is 30.
                           A local-Laplacian level (K = 8, f32 stages; level 0 from u16 RGB): the same

@@ -20,7 +20,7 @@
 // Remap cost: outside the band |g - g_k| <= sigma the remap is one
 // multiply-add (op_ll_remap_outside, bit-identical to op_ll_remap there).  The
 // host selects the remap kernel only when no gray value can lie in the band of
-// three levels (2 sigma below the level spacing 1/(K-1), with a margin for the
+// three levels (sigma below the level spacing 1/(K-1), with a margin for the
 // rounding of g - g_k and of g_k), so the full remap (divide and power) runs
 // for the first two levels of the band at most, whatever the image.
 #include <cuda_runtime.h>
@@ -352,8 +352,8 @@ bool all_f32(const LLDownArgs& a) {
 int ll_remap_rows_strip_w() { return kStripW; }
 
 // The streaming kernel covers K = 8 levels with gray as channel K, u16 or f32
-// input, and a band narrower than the level spacing: |g - g_k| <= sigma can
-// then hold for two levels at most.  (Computed |g - g_k| is within 2^-24 sigma
+// input, and sigma below the level spacing: |g - g_k| <= sigma can then hold
+// for two levels at most.  (Computed |g - g_k| is within 2^-24 sigma
 // of the exact value when it is <= sigma, and g_k within 2^-24 of k/(K-1); the
 // 1e-6 margin covers both.)  sigma must be positive: at sigma <= 0 the full
 // remap's d = 0 case is not inside the band.

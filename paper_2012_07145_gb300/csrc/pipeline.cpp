@@ -1095,7 +1095,7 @@ hp_status build_ll_rows(const hp_pipeline* p, const Plan& plan, GroupPlan& gp) {
   const bool remap = gp.kernel == HP_KERNEL_LL_REMAP_ROWS;
   const int src_dt = stage_dtype_of_ref(p, gp.ext_refs[0]);
   if (remap ? !ll_remap_rows_ok(a, src_dt) : !ll_down_rows_ok(a, src_dt))
-    return fail(HP_ERR_SCHEDULE, remap ? "the streaming remap downsample needs K = 8, u16 or f32 input and 0 < 2 sigma < 1/7"
+    return fail(HP_ERR_SCHEDULE, remap ? "the streaming remap downsample needs K = 8, u16 or f32 input and 0 < sigma < 1/7"
                                        : "the streaming downsample needs f32 planes");
   if (gp.tile_w != ll_remap_rows_strip_w())
     return fail(HP_ERR_SCHEDULE, "streaming downsample strips are %d coarse columns wide (tile_w %d)",

@@ -213,6 +213,12 @@ def test_local_laplacian_lowering():
     pipelines.local_laplacian_fused_schedule(wide, wide_ids, tile=16)
     assert wide.group_info([(160, 96)], 0).kernel == hp.HP_KERNEL_DOWNSAMPLE
     assert wide.group_info([(160, 96)], 1).kernel == hp.HP_KERNEL_LL_DOWN_ROWS
+    # the boundary: sigma just below the spacing 1/7 takes the streaming remap
+    # kernel (its two-level band logic holds), sigma = 1/7 does not
+    for sigma, streaming in ((0.142, True), (1.0 / 7.0, False)):
+        q, q_ids = pipelines.local_laplacian(levels=J, k_levels=8, sigma_r=sigma)
+        pipelines.local_laplacian_fused_schedule(q, q_ids, tile=16)
+        assert (q.group_info([(160, 96)], 0).kernel == hp.HP_KERNEL_LL_REMAP_ROWS) == streaming, sigma
     pipelines.local_laplacian_fused_schedule(pl, ids, tile=16)
     assert pl.group_info([(160, 96)], n - 1).n_members == 8      # level 0: + colour, gray, remap
     pipelines.local_laplacian_fused_schedule(pl, ids, tile=16, impl=hp.HP_IMPL_GENERIC)
